@@ -1,0 +1,192 @@
+"""Oracle for the FMM constant-pH electrostatics path -- TEST INFRASTRUCTURE ONLY.
+
+A plain FP64 CPU restatement of what the GPU fast multipole method
+approximates.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+``cpu_baseline`` leg may import it.  It shares no code with the CUDA path
+(``paper_2410_01626_b300``): it neither imports that package nor is imported
+by it.
+
+What it computes (citations are to arXiv 2410.01626):
+
+* ``charges``: q_i = qA_i + lambda_{s(i)} (qB_i - qA_i), dq_i = qB_i - qA_i
+  (Sec. 2.1, Eq. 1: the Hamiltonian is interpolated linearly in lambda, and
+  the protonated and deprotonated forms differ only in their charges).  Atoms
+  outside every site keep q_i = qA_i.
+* ``direct``: open-boundary Coulomb potential phi_i = sum_{j != i} q_j / r_ij
+  and its gradient (the quantity the FMM solver of Sec. 2.6 approximates).
+* ``ewald``: the same for a periodic cube with tinfoil boundary and uniform
+  neutralising background, phi_i = dE_Ewald / dq_i.
+* ``evaluate``: E = 1/2 k_e sum q_i phi_i, F_i = -k_e q_i grad phi_i and
+  dV/dlambda_k = k_e sum_{i in site k} dq_i phi_i (E is quadratic in the
+  charges, so dE/dq_i = k_e phi_i; the chain rule through q_i(lambda) gives
+  the site derivative that drives the lambda particle, Sec. 2.1).
+* ``binning``: the Morton-key leaf binning specification (keys, stable
+  permutation, leaf ranges).
+
+Pins (tests/test_oracle.py): two-charge closed form, NaCl Madelung constant,
+Wigner constant of a single charge with background, alpha independence, the
+de Leeuw-Perram-Smith tinfoil/vacuum relation, finite differences in x and
+lambda, brute-force binning on tiny inputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import time
+
+import numpy as np
+
+KE_DEFAULT = 138.935458  # kJ mol^-1 nm e^-2 (GROMACS unit system)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (FP64, OpenMP, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        _lib.orc_charges.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, P, P, P]
+        _lib.orc_direct.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P]
+        _lib.orc_ewald.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P]
+        _lib.orc_bin.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                 P, P, P, P, P]
+        _lib.orc_nthreads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def nthreads() -> int:
+    return int(_load().orc_nthreads())
+
+
+def charges(qA, qB, site, lam):
+    """q_i and dq_i in FP64 from FP32 inputs (Sec. 2.1, Eq. 1)."""
+    qA = np.ascontiguousarray(qA, np.float32)
+    qB = np.ascontiguousarray(qB, np.float32)
+    site = np.ascontiguousarray(site, np.int32)
+    lam = np.ascontiguousarray(lam, np.float32)
+    n = len(qA)
+    q = np.empty(n)
+    dq = np.empty(n)
+    _load().orc_charges(n, _p(qA), _p(qB), _p(site), len(lam), _p(lam), _p(q), _p(dq))
+    return q, dq
+
+
+def _targets(targets, n):
+    if targets is None:
+        return None, n
+    t = np.ascontiguousarray(targets, np.int32)
+    return t, len(t)
+
+
+def direct(x, q, targets=None):
+    """Open-boundary potential and its gradient at the target atoms."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    q = np.ascontiguousarray(q, np.float64)
+    t, nt = _targets(targets, len(q))
+    phi = np.empty(nt)
+    grad = np.empty((nt, 3))
+    _load().orc_direct(len(q), _p(x), _p(q), nt, None if t is None else _p(t), _p(phi), _p(grad))
+    return phi, grad
+
+
+def ewald_params(L, tol=1e-11, rc=None):
+    """Splitting parameter, real cutoff and reciprocal index cutoff for a
+    target relative truncation error ``tol`` (erfc(alpha rc) ~ tol and
+    exp(-k^2/4alpha^2) ~ tol)."""
+    s = math.sqrt(-math.log(tol))
+    if rc is None:
+        rc = 0.5 * L
+    alpha = s / rc
+    kmax = 2.0 * alpha * s
+    mmax = int(math.ceil(kmax * L / (2.0 * math.pi)))
+    return alpha, rc, mmax
+
+
+def ewald(x, q, L, targets=None, tol=1e-11, alpha=None, rc=None, mmax=None):
+    """Periodic potential (tinfoil, neutralising background) and its gradient."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    q = np.ascontiguousarray(q, np.float64)
+    a0, rc0, m0 = ewald_params(L, tol, rc)
+    alpha = a0 if alpha is None else alpha
+    rc = rc0 if rc is None else rc
+    if mmax is None:
+        mmax = int(math.ceil(2.0 * alpha * math.sqrt(-math.log(tol)) * L / (2.0 * math.pi)))
+    t, nt = _targets(targets, len(q))
+    phi = np.empty(nt)
+    grad = np.empty((nt, 3))
+    _load().orc_ewald(len(q), _p(x), _p(q), float(L), float(alpha), float(rc), int(mmax), nt,
+                      None if t is None else _p(t), _p(phi), _p(grad))
+    return phi, grad
+
+
+def evaluate(sys_, targets=None, ke=KE_DEFAULT, tol=1e-11, site_atoms=True):
+    """E, F, dV/dlambda for a synthetic system dict (keys of ``synth``).
+
+    With ``targets`` given, phi/F are returned for those atoms only; E is then
+    not computed (it needs every phi) and dV/dlambda is computed from the
+    site atoms, which are added to the evaluated set when ``site_atoms``.
+    """
+    x = np.asarray(sys_["x"], np.float32).astype(np.float64)
+    q, dq = charges(sys_["qA"], sys_["qB"], sys_["site"], sys_["lam"])
+    n = len(q)
+    K = len(sys_["lam"])
+    site = np.asarray(sys_["site"], np.int64)
+    if targets is None:
+        idx = np.arange(n)
+    else:
+        idx = np.asarray(targets, np.int64)
+        if site_atoms:
+            idx = np.union1d(idx, np.nonzero(site >= 0)[0])
+    t0 = time.perf_counter()
+    if sys_["periodic"]:
+        phi, grad = ewald(x, q, sys_["L"], None if targets is None else idx, tol=tol)
+    else:
+        phi, grad = direct(x, q, None if targets is None else idx)
+    dt = time.perf_counter() - t0
+    out = {"idx": idx, "phi": ke * phi, "F": -ke * q[idx, None] * grad, "seconds": dt}
+    if targets is None:
+        out["E"] = 0.5 * ke * float(np.dot(q, phi))
+    dvdl = np.zeros(K)
+    sel = site[idx] >= 0
+    np.add.at(dvdl, site[idx][sel], dq[idx][sel] * phi[sel])
+    out["dVdl"] = ke * dvdl
+    return out
+
+
+def binning(x, origin, L, depth, periodic):
+    """Binning specification: (key, perm, start, count, status)."""
+    x = np.ascontiguousarray(x, np.float32).reshape(-1, 3)
+    n = len(x)
+    o = np.ascontiguousarray(origin, np.float64)
+    nleaf = 1 << (3 * depth)
+    key = np.empty(n, np.uint32)
+    perm = np.empty(n, np.uint32)
+    start = np.empty(nleaf, np.uint32)
+    count = np.empty(nleaf, np.uint32)
+    st = np.zeros(1, np.int32)
+    _load().orc_bin(n, _p(x), _p(o), float(L), int(depth), int(bool(periodic)), _p(key), _p(perm),
+                    _p(start), _p(count), _p(st))
+    return key, perm, start, count, int(st[0])
