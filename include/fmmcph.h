@@ -1,0 +1,191 @@
+/*
+ * fmmcph -- fast multipole Coulomb solver for lambda-dynamics constant pH,
+ * B300 (sm_103a) native.  C ABI.
+ *
+ * What one evaluation computes (arXiv 2410.01626):
+ *   Sites k = 0..K-1 each carry a titration coordinate lambda_k.  Atom i of
+ *   site s(i) carries the charge
+ *       q_i = qA_i + lambda_{s(i)} (qB_i - qA_i)
+ *   (Sec. 2.1, Eq. 1: the Hamiltonian is interpolated linearly between the
+ *   forms A and B, and the forms differ only in their charges; atoms outside
+ *   every site have s(i) = -1 and q_i = qA_i).  The Coulomb solver of
+ *   Sec. 2.6 (a fast multipole method) then returns
+ *       E             = 1/2 k_e sum_i q_i phi_i
+ *       F_i           = -dE/dx_i = -k_e q_i grad phi_i
+ *       dV/dlambda_k  = dE/dlambda_k = k_e sum_{i: s(i)=k} (qB_i - qA_i) phi_i
+ *   with phi_i = sum_{j != i} q_j / |x_i - x_j| in an open cube, or the
+ *   tinfoil Ewald potential (uniform neutralising background) in a periodic
+ *   cube.  dV/dlambda_k is the force on the lambda particle that drives the
+ *   titration (Sec. 2.1, F_lambda = -dH/dlambda).
+ *   The user-facing knobs are the multipole order p and the tree depth
+ *   (Sec. 2.9, minimal mdp figure: p = 8, depth 2 for an 8 nm box).
+ *
+ * Units: x in nm, q in e, k_e defaults to 138.935458 kJ mol^-1 nm e^-2, so E
+ * and dV/dlambda are in kJ/mol and F in kJ mol^-1 nm^-1.
+ *
+ * Conventions for every call:
+ *   - Array arguments are DEVICE pointers unless the name ends in _host.
+ *     They are owned by the caller; the library never frees them.
+ *   - Calls are asynchronous on the CUDA stream passed as `stream` (a
+ *     cudaStream_t; NULL = the legacy default stream).  A handle must not be
+ *     used from two host threads at once.
+ *   - Argument errors are detected on the host, synchronously, and returned
+ *     as a status code; nothing is launched in that case.  Conditions only
+ *     the device can see (an atom outside an open box, a site index >= K)
+ *     set bits in a device status word, read with fmm_status_word().
+ *     The library never traps the GPU.
+ */
+#ifndef FMMCPH_H
+#define FMMCPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = 1,     /* invalid argument (null pointer, size, range)       */
+    FMM_ERR_DOMAIN = 2,  /* device status: an atom outside an open box         */
+    FMM_ERR_CUDA = 3,    /* a CUDA runtime call failed                          */
+    FMM_ERR_OOM = 4,     /* device allocation failed                            */
+    FMM_ERR_TIMEOUT = 5, /* a bounded device wait gave up                       */
+    FMM_ERR_STATE = 6    /* call order violated (e.g. eval before charges)      */
+} fmm_status;
+
+/* device status word bits (fmm_status_word) */
+#define FMM_DEV_DOMAIN 1   /* atom outside [origin, origin + edge] of an open box */
+#define FMM_DEV_SITE 2     /* site index >= K (atom treated as not in a site)    */
+#define FMM_DEV_TIMEOUT 4  /* bounded wait expired                               */
+
+typedef enum {
+    FMM_FP32 = 0,        /* every stage in FP32 on CUDA cores (root/lattice FP64) */
+    FMM_MIXED_TF32 = 1,  /* M2L on tcgen05 tensor cores in TF32, FP32 accumulate  */
+    FMM_MIXED_3XTF32 = 2 /* M2L as three TF32 products (split operands)           */
+} fmm_precision;
+
+typedef struct {
+    double origin[3]; /* lower corner, nm          */
+    double edge;      /* cube edge length L, nm > 0 */
+} fmm_box;
+
+typedef struct {
+    int precision;     /* fmm_precision                           */
+    double coulomb_k;  /* k_e; <= 0 selects 138.935458             */
+    int reserved[8];   /* must be zero                             */
+} fmm_options;
+
+typedef struct fmm_handle fmm_handle;
+
+/* Create a solver for one cubic box.
+ *   periodic: 0 = open boundary, 1 = periodic (tinfoil, neutralising background)
+ *   p:        maximum expansion degree, 1 <= p <= FMM_MAX_P
+ *   depth:    octree depth, 8^depth leaves; 0 <= depth <= 7
+ *   opt:      may be NULL (FP32, default k_e)
+ * Builds the translation operators on the host in FP64 (the periodic lattice
+ * operator by projecting the Ewald remainder onto solid harmonics) and
+ * uploads them.  Synchronous.  Returns FMM_ERR_ARG, FMM_ERR_OOM or
+ * FMM_ERR_CUDA on failure, with *out set to NULL. */
+#define FMM_MAX_P 14
+fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const fmm_options* opt,
+                      fmm_handle** out);
+
+/* Set the atoms' charge forms and the site map, and lambda.
+ *   qA, qB:  [n_atoms] float, charges of forms A and B (e)
+ *   site:    [n_atoms] int32, site index in [0, n_sites) or -1
+ *   lambda:  [n_sites] float (may be NULL when n_sites == 0)
+ * The arrays are copied (stream-ordered), so the caller may reuse them after
+ * the copy has executed.  Grows the handle's device buffers when n_atoms
+ * exceeds the previous capacity (synchronous allocation).  n_atoms >= 0,
+ * n_sites >= 0.  Site indices >= n_sites set FMM_DEV_SITE on the next eval. */
+fmm_status fmm_set_charges(fmm_handle* h, int n_atoms, int n_sites, const float* qA,
+                           const float* qB, const int32_t* site, const float* lambda,
+                           void* stream);
+
+/* Replace lambda ([n_sites] float, device), stream-ordered copy. */
+fmm_status fmm_set_lambda(fmm_handle* h, const float* lambda, void* stream);
+
+/* Use the caller's device buffer for lambda from now on (no copy): each
+ * fmm_eval reads lambda at launch time from `lambda` ([n_sites] float).
+ * Lets a device-side lambda integrator feed the solver with no host call
+ * between steps.  Pass NULL to go back to the handle's own copy. */
+fmm_status fmm_bind_lambda(fmm_handle* h, const float* lambda);
+
+/* One evaluation.
+ *   x:          [n_atoms][3] float positions (nm), input order
+ *   E:          [1] double, energy (kJ/mol)
+ *   F:          [n_atoms][3] float forces, input order (may be NULL)
+ *   dVdlambda:  [n_sites] float (may be NULL)
+ *   phi:        [n_atoms] float, k_e * potential at each atom (kJ/mol/e),
+ *               input order (may be NULL)
+ * Stream-ordered; all outputs are complete when the stream reaches the end
+ * of the call.  Returns FMM_ERR_STATE before fmm_set_charges. */
+fmm_status fmm_eval(fmm_handle* h, const float* x, double* E, float* F, float* dVdlambda,
+                    float* phi, void* stream);
+
+/* The same evaluation with HOST buffers: copies x_host to the device, runs
+ * fmm_eval and copies E, F and dV/dlambda back, then synchronises `stream`.
+ * For page-locked host buffers the copies are asynchronous DMA.  Any output
+ * pointer may be NULL. */
+fmm_status fmm_eval_host(fmm_handle* h, const float* x_host, double* E_host, float* F_host,
+                         float* dVdlambda_host, void* stream);
+
+/* Adjoint of E(x, qA, qB, lambda) for reverse-mode differentiation.
+ *   gbar:       [1] double, dL/dE (device)
+ *   F, phi:     outputs of the preceding fmm_eval (input order)
+ *   grad_x:     [n_atoms][3] float, dL/dx = -F * gbar            (may be NULL)
+ *   grad_qA:    [n_atoms] float, dL/dqA_i = phi_i (1 - lambda_s) * gbar
+ *               (phi_i * gbar for atoms outside sites)           (may be NULL)
+ *   grad_qB:    [n_atoms] float, dL/dqB_i = phi_i lambda_s * gbar (may be NULL)
+ *   dVdlambda:  [n_sites] float from the same fmm_eval
+ *   grad_lambda:[n_sites] float, dL/dlambda = dV/dlambda * gbar   (may be NULL)
+ * E is quadratic in the charges, so dE/dq_i = k_e phi_i (the phi returned by
+ * fmm_eval already includes k_e). */
+fmm_status fmm_adjoint(fmm_handle* h, const double* gbar, const float* F, const float* phi,
+                       const float* dVdlambda, float* grad_x, float* grad_qA, float* grad_qB,
+                       float* grad_lambda, void* stream);
+
+/* Copy the binning of the last fmm_eval into caller device buffers (any may
+ * be NULL): key [n_atoms] uint32 Morton key of each atom's leaf (input
+ * order), perm [n_atoms] uint32 (perm[s] = input index of the s-th atom in
+ * leaf order; stable on (key, index)), start/count [8^depth] uint32. */
+fmm_status fmm_get_binning(fmm_handle* h, uint32_t* key, uint32_t* perm, uint32_t* start,
+                           uint32_t* count, void* stream);
+
+/* Read and clear the device status word (FMM_DEV_* bits).  Synchronises
+ * `stream` first. */
+fmm_status fmm_status_word(fmm_handle* h, int* device_status, void* stream);
+
+/* Per-stage device times of the last fmm_eval when profiling is enabled
+ * (CUDA events between the stages, on the eval's stream): ms[0..n) =
+ * binning, P2M, M2M, lattice, M2L, L2L, near field + L2P + outputs, final
+ * reduction.  Synchronises.  Returns the number of stages written. */
+int fmm_stage_times(fmm_handle* h, float* ms, int n);
+fmm_status fmm_set_profiling(fmm_handle* h, int enable);
+
+/* Number of kernel launches one fmm_eval issues with the current settings. */
+int fmm_launches_per_eval(const fmm_handle* h);
+
+/* Host-side operator construction, exposed for CPU tests of the host logic
+ * (no GPU needed).  Writes the FP64 real-form operator of the given kind in
+ * the library's normalised coefficient basis, nc x nc row-major, nc =
+ * (p+1)^2:
+ *   kind 0: M2L for source offset (o[0], o[1], o[2]) boxes, |o|_inf in 2..3
+ *   kind 1: M2M child octant o[0] (0..7) -> parent
+ *   kind 2: L2L parent -> child octant o[0]
+ *   kind 3: periodic lattice operator (root multipole -> root local)
+ * Returns FMM_OK or FMM_ERR_ARG. */
+fmm_status fmm_host_operator(int kind, int p, const int* o, double* out);
+
+/* Evaluate the normalised regular solid harmonics at u (real form, length
+ * (p+1)^2) on the host -- the basis P2M and L2P use.  Test helper. */
+fmm_status fmm_host_regular(int p, const double* u, double* out);
+
+void fmm_destroy(fmm_handle* h);
+const char* fmm_error_string(fmm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMMCPH_H */

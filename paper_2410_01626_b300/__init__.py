@@ -1,0 +1,15 @@
+"""B300-native fast multipole Coulomb solver for lambda-dynamics constant pH.
+
+Energy E, forces F and per-site derivatives dV/dlambda of the Coulomb energy
+of lambda-interpolated charges (arXiv 2410.01626, Sec. 2.1 Eq. 1 and Sec. 2.6)
+in an open or periodic cube, computed by hand-written sm_103a CUDA kernels
+behind a C ABI (``include/fmmcph.h``).  PyTorch supplies device memory and
+streams only.
+"""
+from .binding import FMM, FmmError, KE_DEFAULT, STAGES, host_operator, host_regular, library_path, load
+from .autograd import FMMEnergy, fmm_energy
+
+load()  # fail loudly at import when the native library is missing
+
+__all__ = ["FMM", "FmmError", "FMMEnergy", "fmm_energy", "KE_DEFAULT", "STAGES", "host_operator",
+           "host_regular", "library_path", "load"]

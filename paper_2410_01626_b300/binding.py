@@ -1,0 +1,246 @@
+"""Thin ctypes binding of the fmmcph C ABI (argument marshalling only).
+
+Every step of the evaluation runs in the library's CUDA kernels; this module
+only passes device pointers, sizes and the current CUDA stream.  There is no
+CPU fallback: if the shared library cannot be loaded, importing the package
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+
+FMM_FP32, FMM_MIXED_TF32, FMM_MIXED_3XTF32 = 0, 1, 2
+PRECISIONS = {"fp32": FMM_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF32}
+DEV_DOMAIN, DEV_SITE, DEV_TIMEOUT = 1, 2, 4
+KE_DEFAULT = 138.935458
+STAGES = ("binning", "p2m", "m2m", "root", "m2l", "l2l", "near", "final")
+
+
+class FmmBox(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("edge", ctypes.c_double)]
+
+
+class FmmOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("coulomb_k", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+
+
+EXPORTS = {
+    "fmm_create": (I, [ctypes.POINTER(FmmBox), I, I, I, ctypes.POINTER(FmmOptions), ctypes.POINTER(P)]),
+    "fmm_set_charges": (I, [P, I, I, P, P, P, P, P]),
+    "fmm_set_lambda": (I, [P, P, P]),
+    "fmm_bind_lambda": (I, [P, P]),
+    "fmm_eval": (I, [P, P, P, P, P, P, P]),
+    "fmm_eval_host": (I, [P, P, P, P, P, P]),
+    "fmm_adjoint": (I, [P, P, P, P, P, P, P, P, P, P]),
+    "fmm_get_binning": (I, [P, P, P, P, P, P]),
+    "fmm_status_word": (I, [P, ctypes.POINTER(I), P]),
+    "fmm_stage_times": (I, [P, P, I]),
+    "fmm_set_profiling": (I, [P, I]),
+    "fmm_launches_per_eval": (I, [P]),
+    "fmm_host_operator": (I, [I, I, P, P]),
+    "fmm_host_regular": (I, [I, P, P]),
+    "fmm_destroy": (None, [P]),
+    "fmm_error_string": (ctypes.c_char_p, [I]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the shared library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not os.path.exists(path):
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code, what=""):
+        msg = load().fmm_error_string(code).decode()
+        super().__init__(f"{what}: {msg} (status {code})")
+        self.code = code
+
+
+def _check(code, what):
+    if code != 0:
+        raise FmmError(code, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class FMM:
+    """One solver handle: a cubic box, boundary, multipole order p and tree depth."""
+
+    def __init__(self, edge, periodic, p, depth, origin=(0.0, 0.0, 0.0), precision="fp32", ke=None):
+        lib = load()
+        box = FmmBox((ctypes.c_double * 3)(*[float(o) for o in origin]), float(edge))
+        opt = FmmOptions(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                         float(ke) if ke else 0.0, (ctypes.c_int * 8)())
+        h = ctypes.c_void_p()
+        _check(lib.fmm_create(ctypes.byref(box), int(bool(periodic)), int(p), int(depth), ctypes.byref(opt),
+                              ctypes.byref(h)), "fmm_create")
+        self._h = h
+        self._lib = lib
+        self.edge, self.periodic, self.p, self.depth = float(edge), bool(periodic), int(p), int(depth)
+        self.origin = tuple(float(o) for o in origin)
+        self.precision = precision
+        self.ke = float(ke) if ke else KE_DEFAULT
+        self.n = 0
+        self.K = 0
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fmm_destroy(self._h)
+        self._h = None
+
+    __del__ = close
+
+    def set_charges(self, qA, qB, site, lam):
+        n = qA.numel()
+        K = lam.numel()
+        _dev(qA, torch.float32, "qA"), _dev(qB, torch.float32, "qB"), _dev(site, torch.int32, "site")
+        if K:
+            _dev(lam, torch.float32, "lambda")
+        _check(self._lib.fmm_set_charges(self._h, n, K, _ptr(qA), _ptr(qB), _ptr(site), _ptr(lam) if K else None,
+                                         _stream()), "fmm_set_charges")
+        self.n, self.K = n, K
+        self._site = site
+
+    def set_lambda(self, lam):
+        _dev(lam, torch.float32, "lambda")
+        _check(self._lib.fmm_set_lambda(self._h, _ptr(lam), _stream()), "fmm_set_lambda")
+
+    def bind_lambda(self, lam):
+        if lam is not None:
+            _dev(lam, torch.float32, "lambda")
+        self._bound = lam
+        _check(self._lib.fmm_bind_lambda(self._h, _ptr(lam)), "fmm_bind_lambda")
+
+    def outputs(self, device=None, phi=False):
+        dev = device or torch.device("cuda")
+        E = torch.empty(1, dtype=torch.float64, device=dev)
+        F = torch.empty(self.n, 3, dtype=torch.float32, device=dev)
+        dV = torch.empty(self.K, dtype=torch.float32, device=dev)
+        ph = torch.empty(self.n, dtype=torch.float32, device=dev) if phi else None
+        return E, F, dV, ph
+
+    def eval_into(self, x, E, F=None, dVdl=None, phi=None):
+        _dev(x, torch.float32, "x")
+        if x.numel() != 3 * self.n:
+            raise ValueError("x must have shape [n_atoms, 3]")
+        _check(self._lib.fmm_eval(self._h, _ptr(x), _ptr(E), _ptr(F), _ptr(dVdl) if self.K else None, _ptr(phi),
+                                  _stream()), "fmm_eval")
+
+    def eval(self, x, phi=False):
+        E, F, dV, ph = self.outputs(x.device, phi)
+        self.eval_into(x, E, F, dV, ph)
+        return E, F, dV, ph
+
+    def eval_host(self, x_host, E_host, F_host, dV_host):
+        """Host buffers (numpy or pinned CPU tensors); copies inside the call."""
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                return ctypes.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(ctypes.c_void_p)
+        _check(self._lib.fmm_eval_host(self._h, hp(x_host), hp(E_host), hp(F_host), hp(dV_host), _stream()),
+               "fmm_eval_host")
+
+    def adjoint(self, gbar, F, phi, dVdl, grad_x=True, grad_qA=True, grad_qB=True, grad_lam=True):
+        dev = F.device
+        gx = torch.empty(self.n, 3, dtype=torch.float32, device=dev) if grad_x else None
+        ga = torch.empty(self.n, dtype=torch.float32, device=dev) if grad_qA else None
+        gb = torch.empty(self.n, dtype=torch.float32, device=dev) if grad_qB else None
+        gl = torch.empty(self.K, dtype=torch.float32, device=dev) if grad_lam else None
+        _check(self._lib.fmm_adjoint(self._h, _ptr(gbar), _ptr(F), _ptr(phi), _ptr(dVdl) if self.K else None,
+                                     _ptr(gx), _ptr(ga), _ptr(gb), _ptr(gl) if self.K else None, _stream()),
+               "fmm_adjoint")
+        return gx, ga, gb, gl
+
+    def binning(self):
+        dev = torch.device("cuda")
+        nleaf = 1 << (3 * self.depth)
+        key = torch.empty(self.n, dtype=torch.int32, device=dev)
+        perm = torch.empty(self.n, dtype=torch.int32, device=dev)
+        start = torch.empty(nleaf, dtype=torch.int32, device=dev)
+        count = torch.empty(nleaf, dtype=torch.int32, device=dev)
+        _check(self._lib.fmm_get_binning(self._h, _ptr(key), _ptr(perm), _ptr(start), _ptr(count), _stream()),
+               "fmm_get_binning")
+        return key, perm, start, count
+
+    def status_word(self):
+        s = ctypes.c_int(0)
+        _check(self._lib.fmm_status_word(self._h, ctypes.byref(s), _stream()), "fmm_status_word")
+        return s.value
+
+    def set_profiling(self, on=True):
+        _check(self._lib.fmm_set_profiling(self._h, int(bool(on))), "fmm_set_profiling")
+
+    def stage_times(self):
+        ms = (ctypes.c_float * len(STAGES))()
+        k = self._lib.fmm_stage_times(self._h, ctypes.cast(ms, ctypes.c_void_p), len(STAGES))
+        return dict(zip(STAGES[:k], list(ms)[:k]))
+
+    def launches_per_eval(self):
+        return int(self._lib.fmm_launches_per_eval(self._h))
+
+
+def host_operator(kind, p, o=(0, 0, 0)):
+    """FP64 real-form operator from the library's host code (no GPU needed)."""
+    lib = load()
+    nc = (p + 1) ** 2
+    out = np.empty((nc, nc))
+    oo = np.ascontiguousarray(o, np.int32)
+    _check(lib.fmm_host_operator(int(kind), int(p), oo.ctypes.data_as(ctypes.c_void_p),
+                                 out.ctypes.data_as(ctypes.c_void_p)), "fmm_host_operator")
+    return out
+
+
+def host_regular(p, u):
+    lib = load()
+    out = np.empty((p + 1) ** 2)
+    uu = np.ascontiguousarray(u, np.float64)
+    _check(lib.fmm_host_regular(int(p), uu.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p)),
+           "fmm_host_regular")
+    return out

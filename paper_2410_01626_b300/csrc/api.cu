@@ -1,0 +1,471 @@
+// C ABI of the fmmcph library: handle lifecycle, argument validation, buffers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fmm_internal.h"
+#include "operators.h"
+
+using namespace fmmcph;
+
+struct fmm_handle {
+    Handle h;
+};
+
+namespace {
+
+template <class T>
+fmm_status dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return FMM_ERR_OOM;
+    }
+    return FMM_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void free_atoms(Handle& h) {
+    dfree(h.qA);
+    dfree(h.qB);
+    dfree(h.site);
+    dfree(h.key);
+    dfree(h.kA);
+    dfree(h.kB);
+    dfree(h.vA);
+    dfree(h.vB);
+    dfree(h.inv);
+    dfree(h.pos);
+    dfree(h.dq);
+    dfree(h.phis);
+    dfree(h.sort_table);
+    h.perm = nullptr;
+    h.sorted_key = nullptr;
+    h.cap = 0;
+}
+
+void free_all(Handle& h) {
+    free_atoms(h);
+    dfree(h.T);
+    dfree(h.A);
+    dfree(h.B);
+    dfree(h.Ad);
+    dfree(h.Lam);
+    dfree(h.tiles);
+    dfree(h.M);
+    dfree(h.L);
+    dfree(h.lam);
+    dfree(h.site_ptr);
+    dfree(h.site_atoms);
+    dfree(h.start);
+    dfree(h.count);
+    dfree(h.epart);
+    dfree(h.leafqdt);
+    dfree(h.root);
+    dfree(h.status);
+    dfree(h.hx_dev);
+    dfree(h.hF_dev);
+    dfree(h.hdV_dev);
+    dfree(h.hE_dev);
+    if (h.ev_valid)
+        for (auto& e : h.ev) cudaEventDestroy(e);
+    h.ev_valid = false;
+}
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+fmm_status cuda_ok(cudaError_t e) {
+    if (e == cudaSuccess) return FMM_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fmm_error_string(fmm_status s) {
+    switch (s) {
+        case FMM_OK: return "ok";
+        case FMM_ERR_ARG: return "invalid argument";
+        case FMM_ERR_DOMAIN: return "atom outside the open box";
+        case FMM_ERR_CUDA: return "CUDA runtime error";
+        case FMM_ERR_OOM: return "device allocation failed";
+        case FMM_ERR_TIMEOUT: return "bounded device wait expired";
+        case FMM_ERR_STATE: return "call order violated";
+    }
+    return "unknown status";
+}
+
+fmm_status fmm_host_operator(int kind, int p, const int* o, double* out) {
+    if (p < 1 || p > FMM_MAX_P || !out) return FMM_ERR_ARG;
+    switch (kind) {
+        case 0: {
+            if (!o) return FMM_ERR_ARG;
+            int mx = std::max(std::abs(o[0]), std::max(std::abs(o[1]), std::abs(o[2])));
+            if (mx < 2 || mx > 3) return FMM_ERR_ARG;
+            op_m2l(p, o, out);
+            return FMM_OK;
+        }
+        case 1:
+        case 2:
+            if (!o || o[0] < 0 || o[0] > 7) return FMM_ERR_ARG;
+            if (kind == 1) op_m2m(p, o[0], out);
+            else op_l2l(p, o[0], out);
+            return FMM_OK;
+        case 3:
+            op_lattice(p, out);
+            return FMM_OK;
+    }
+    return FMM_ERR_ARG;
+}
+
+fmm_status fmm_host_regular(int p, const double* u, double* out) {
+    if (p < 0 || p > 2 * FMM_MAX_P || !u || !out) return FMM_ERR_ARG;
+    regular_real_hat(p, u, out);
+    return FMM_OK;
+}
+
+fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const fmm_options* opt,
+                      fmm_handle** out) {
+    if (!out) return FMM_ERR_ARG;
+    *out = nullptr;
+    if (!box || !(box->edge > 0.0) || !std::isfinite(box->edge)) return FMM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(box->origin[a])) return FMM_ERR_ARG;
+    if (periodic != 0 && periodic != 1) return FMM_ERR_ARG;
+    if (p < 1 || p > FMM_MAX_P || depth < 0 || depth > kMaxDepth) return FMM_ERR_ARG;
+    int precision = FMM_FP32;
+    double ke = 138.935458;
+    if (opt) {
+        for (int r : opt->reserved)
+            if (r != 0) return FMM_ERR_ARG;
+        if (opt->precision < FMM_FP32 || opt->precision > FMM_MIXED_3XTF32) return FMM_ERR_ARG;
+        precision = opt->precision;
+        if (opt->coulomb_k > 0.0) ke = opt->coulomb_k;
+    }
+    fmm_handle* H = new (std::nothrow) fmm_handle();
+    if (!H) return FMM_ERR_OOM;
+    Handle& h = H->h;
+    cudaGetDevice(&h.device);
+    h.box = *box;
+    h.periodic = periodic;
+    h.p = p;
+    h.depth = depth;
+    h.nc = ncoef(p);
+    h.ncp = ncoef_padded(p);
+    h.precision = precision;
+    h.ke = ke;
+    h.s_bin = std::ldexp(1.0, depth) / box->edge;
+    h.lmin = periodic ? 1 : 2;
+    upload_constants(p);
+    configure_kernels(ncoef_padded(p));
+
+    const int nc = h.nc, ncp = h.ncp;
+    fmm_status st = FMM_OK;
+    // ---- operators ----
+    {
+        std::vector<double> op((size_t)nc * nc);
+        std::vector<float> T((size_t)kNumOps * ncp * ncp, 0.f);
+        for (int ox = -3; ox <= 3; ++ox)
+            for (int oy = -3; oy <= 3; ++oy)
+                for (int oz = -3; oz <= 3; ++oz) {
+                    if (std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz))) < 2) continue;
+                    const int o[3] = {ox, oy, oz};
+                    op_m2l(p, o, op.data());
+                    float* dst = T.data() + (size_t)op_index(ox, oy, oz) * ncp * ncp;
+                    for (int j = 0; j < nc; ++j)
+                        for (int k = 0; k < nc; ++k) dst[(size_t)k * ncp + j] = (float)op[(size_t)j * nc + k];
+                }
+        std::vector<float> A((size_t)8 * ncp * ncp, 0.f), B((size_t)8 * ncp * ncp, 0.f);
+        std::vector<double> Ad((size_t)8 * nc * nc);
+        for (int c = 0; c < 8; ++c) {
+            op_m2m(p, c, op.data());
+            std::memcpy(Ad.data() + (size_t)c * nc * nc, op.data(), sizeof(double) * nc * nc);
+            for (int j = 0; j < nc; ++j)
+                for (int k = 0; k < nc; ++k) A[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
+            op_l2l(p, c, op.data());
+            for (int j = 0; j < nc; ++j)
+                for (int k = 0; k < nc; ++k) B[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
+        }
+        if ((st = dalloc(&h.T, T.size())) || (st = dalloc(&h.A, A.size())) || (st = dalloc(&h.B, B.size())) ||
+            (st = dalloc(&h.Ad, Ad.size()))) {
+            free_all(h);
+            delete H;
+            return st;
+        }
+        cudaMemcpy(h.T, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.A, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.Ad, Ad.data(), sizeof(double) * Ad.size(), cudaMemcpyHostToDevice);
+        if (periodic) {
+            op_lattice(p, op.data());
+            if ((st = dalloc(&h.Lam, op.size()))) {
+                free_all(h);
+                delete H;
+                return st;
+            }
+            cudaMemcpy(h.Lam, op.data(), sizeof(double) * op.size(), cudaMemcpyHostToDevice);
+        }
+    }
+    // ---- tree storage and work lists ----
+    h.lvl_off.assign(depth + 2, 0);
+    long acc = 0;
+    for (int l = 0; l <= depth; ++l) {
+        h.lvl_off[l] = acc;
+        acc += 1L << (3 * l);
+    }
+    h.lvl_off[depth + 1] = acc;
+    h.nbox_total = acc;
+    std::vector<M2LTile> tiles;
+    for (int l = h.lmin; l <= depth; ++l) {
+        const int np = 1 << (3 * (l - 1));
+        for (int c = 0; c < 8; ++c)
+            for (int p0 = 0; p0 < np; p0 += 16) tiles.push_back({l, c, p0, std::min(16, np - p0)});
+    }
+    h.ntiles = (int)tiles.size();
+    const long nleaf = 1L << (3 * depth);
+    if ((st = dalloc(&h.M, (size_t)acc * ncp)) || (st = dalloc(&h.L, (size_t)acc * ncp)) ||
+        (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.start, nleaf)) ||
+        (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.epart, (nleaf + 3) / 4)) ||
+        (st = dalloc(&h.leafqdt, 5 * nleaf)) || (st = dalloc(&h.root, nc + 8)) || (st = dalloc(&h.status, 1)) ||
+        (st = dalloc(&h.site_ptr, 1))) {
+        free_all(h);
+        delete H;
+        return st;
+    }
+    h.epart_cap = (int)((nleaf + 3) / 4);
+    if (!tiles.empty())
+        cudaMemcpy(h.tiles, tiles.data(), sizeof(M2LTile) * tiles.size(), cudaMemcpyHostToDevice);
+    cudaMemset(h.M, 0, sizeof(float) * acc * ncp);
+    cudaMemset(h.L, 0, sizeof(float) * acc * ncp);
+    cudaMemset(h.status, 0, sizeof(int));
+    cudaMemset(h.root, 0, sizeof(double) * (nc + 8));
+    cudaMemset(h.site_ptr, 0, sizeof(int));
+    for (auto& e : h.ev) cudaEventCreate(&e);
+    h.ev_valid = true;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        free_all(h);
+        delete H;
+        return FMM_ERR_CUDA;
+    }
+    *out = H;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const float* qB, const int32_t* site,
+                           const float* lambda, void* stream) {
+    if (!H || n < 0 || K < 0) return FMM_ERR_ARG;
+    if (n > 0 && (!qA || !qB || !site)) return FMM_ERR_ARG;
+    if (K > 0 && !lambda) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    cudaStream_t st = S(stream);
+    const int nblk = (n + 4095) / 4096;
+    if (n > h.cap) {
+        free_atoms(h);
+        fmm_status e;
+        if ((e = dalloc(&h.qA, n)) || (e = dalloc(&h.qB, n)) || (e = dalloc(&h.site, n)) || (e = dalloc(&h.key, n)) ||
+            (e = dalloc(&h.kA, n)) || (e = dalloc(&h.kB, n)) || (e = dalloc(&h.vA, n)) || (e = dalloc(&h.vB, n)) ||
+            (e = dalloc(&h.inv, n)) || (e = dalloc(&h.pos, n)) || (e = dalloc(&h.dq, n)) ||
+            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.sort_table, 256L * (nblk > 0 ? nblk : 1)))) {
+            free_atoms(h);
+            h.charges_set = false;
+            return e;
+        }
+        h.cap = n;
+    }
+    if (K > h.lam_cap) {
+        dfree(h.lam);
+        if (dalloc(&h.lam, K)) return FMM_ERR_OOM;
+        h.lam_cap = K;
+    }
+    // site map: validated and grouped on the host (ascending input index within a site)
+    std::vector<int32_t> hs(n);
+    if (n > 0 && cudaMemcpyAsync(hs.data(), site, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
+    std::vector<int> ptr(K + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        if (hs[i] < -1 || hs[i] >= K) return FMM_ERR_ARG;
+        if (hs[i] >= 0) ptr[hs[i] + 1]++;
+    }
+    for (int k = 0; k < K; ++k) ptr[k + 1] += ptr[k];
+    std::vector<int> atoms(ptr[K] > 0 ? ptr[K] : 1);
+    {
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            if (hs[i] >= 0) atoms[fill[hs[i]]++] = i;
+    }
+    if (ptr[K] > h.site_cap || !h.site_atoms) {
+        dfree(h.site_atoms);
+        if (dalloc(&h.site_atoms, atoms.size())) return FMM_ERR_OOM;
+        h.site_cap = (int)atoms.size();
+    }
+    dfree(h.site_ptr);
+    if (dalloc(&h.site_ptr, ptr.size())) return FMM_ERR_OOM;
+    fmm_status e = FMM_OK;
+    if ((e = cuda_ok(cudaMemcpy(h.site_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice))) ||
+        (e = cuda_ok(cudaMemcpy(h.site_atoms, atoms.data(), sizeof(int) * atoms.size(), cudaMemcpyHostToDevice))))
+        return e;
+    if (n > 0) {
+        if ((e = cuda_ok(cudaMemcpyAsync(h.qA, qA, sizeof(float) * n, cudaMemcpyDeviceToDevice, st))) ||
+            (e = cuda_ok(cudaMemcpyAsync(h.qB, qB, sizeof(float) * n, cudaMemcpyDeviceToDevice, st))) ||
+            (e = cuda_ok(cudaMemcpyAsync(h.site, site, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st))))
+            return e;
+    }
+    if (K > 0 && (e = cuda_ok(cudaMemcpyAsync(h.lam, lambda, sizeof(float) * K, cudaMemcpyDeviceToDevice, st))))
+        return e;
+    h.n = n;
+    h.K = K;
+    h.charges_set = true;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_lambda(fmm_handle* H, const float* lambda, void* stream) {
+    if (!H) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    if (!h.charges_set) return FMM_ERR_STATE;
+    if (h.K == 0) return FMM_OK;
+    if (!lambda) return FMM_ERR_ARG;
+    return cuda_ok(cudaMemcpyAsync(h.lam, lambda, sizeof(float) * h.K, cudaMemcpyDeviceToDevice, S(stream)));
+}
+
+fmm_status fmm_bind_lambda(fmm_handle* H, const float* lambda) {
+    if (!H) return FMM_ERR_ARG;
+    H->h.lam_bound = lambda;
+    return FMM_OK;
+}
+
+fmm_status fmm_eval(fmm_handle* H, const float* x, double* E, float* F, float* dVdl, float* phi, void* stream) {
+    if (!H) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    if (!h.charges_set) return FMM_ERR_STATE;
+    if (h.n > 0 && !x) return FMM_ERR_ARG;
+    cudaGetLastError();
+    launch_eval(&h, x, E, F, dVdl, phi, S(stream));
+    return cuda_ok(cudaGetLastError());
+}
+
+fmm_status fmm_eval_host(fmm_handle* H, const float* x_host, double* E_host, float* F_host, float* dV_host,
+                         void* stream) {
+    if (!H) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    if (!h.charges_set) return FMM_ERR_STATE;
+    if (h.n > 0 && !x_host) return FMM_ERR_ARG;
+    cudaStream_t st = S(stream);
+    const int n = h.n;
+    if (n > h.host_cap || !h.hE_dev) {
+        dfree(h.hx_dev);
+        dfree(h.hF_dev);
+        dfree(h.hE_dev);
+        fmm_status e;
+        if ((e = dalloc(&h.hx_dev, 3L * n)) || (e = dalloc(&h.hF_dev, 3L * n)) || (e = dalloc(&h.hE_dev, 1)))
+            return e;
+        h.host_cap = n;
+    }
+    if (h.K > 0 && !h.hdV_dev) {
+        if (dalloc(&h.hdV_dev, h.lam_cap)) return FMM_ERR_OOM;
+    }
+    fmm_status e = FMM_OK;
+    if (n > 0 && (e = cuda_ok(cudaMemcpyAsync(h.hx_dev, x_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st))))
+        return e;
+    cudaGetLastError();
+    launch_eval(&h, h.hx_dev, h.hE_dev, F_host ? h.hF_dev : nullptr, dV_host ? h.hdV_dev : nullptr, nullptr, st);
+    if ((e = cuda_ok(cudaGetLastError()))) return e;
+    if (E_host && (e = cuda_ok(cudaMemcpyAsync(E_host, h.hE_dev, sizeof(double), cudaMemcpyDeviceToHost, st))))
+        return e;
+    if (F_host && n > 0 &&
+        (e = cuda_ok(cudaMemcpyAsync(F_host, h.hF_dev, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st))))
+        return e;
+    if (dV_host && h.K > 0 &&
+        (e = cuda_ok(cudaMemcpyAsync(dV_host, h.hdV_dev, sizeof(float) * h.K, cudaMemcpyDeviceToHost, st))))
+        return e;
+    return cuda_ok(cudaStreamSynchronize(st));
+}
+
+fmm_status fmm_adjoint(fmm_handle* H, const double* gbar, const float* F, const float* phi, const float* dVdl,
+                       float* gx, float* gqA, float* gqB, float* glam, void* stream) {
+    if (!H || !gbar) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    if (!h.charges_set) return FMM_ERR_STATE;
+    if (gx && !F) return FMM_ERR_ARG;
+    if ((gqA || gqB) && !phi) return FMM_ERR_ARG;
+    if (glam && h.K > 0 && !dVdl) return FMM_ERR_ARG;
+    cudaGetLastError();
+    launch_adjoint(&h, gbar, F, phi, dVdl, gx, gqA, gqB, glam, S(stream));
+    return cuda_ok(cudaGetLastError());
+}
+
+fmm_status fmm_get_binning(fmm_handle* H, uint32_t* key, uint32_t* perm, uint32_t* start, uint32_t* count,
+                           void* stream) {
+    if (!H) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    if (!h.charges_set || !h.perm) return FMM_ERR_STATE;
+    cudaStream_t st = S(stream);
+    const size_t nleaf = 1ul << (3 * h.depth);
+    fmm_status e = FMM_OK;
+    if (key && h.n && (e = cuda_ok(cudaMemcpyAsync(key, h.key, 4ul * h.n, cudaMemcpyDeviceToDevice, st)))) return e;
+    if (perm && h.n && (e = cuda_ok(cudaMemcpyAsync(perm, h.perm, 4ul * h.n, cudaMemcpyDeviceToDevice, st))))
+        return e;
+    if (start && (e = cuda_ok(cudaMemcpyAsync(start, h.start, 4ul * nleaf, cudaMemcpyDeviceToDevice, st)))) return e;
+    if (count && (e = cuda_ok(cudaMemcpyAsync(count, h.count, 4ul * nleaf, cudaMemcpyDeviceToDevice, st)))) return e;
+    return FMM_OK;
+}
+
+fmm_status fmm_status_word(fmm_handle* H, int* device_status, void* stream) {
+    if (!H || !device_status) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    cudaStream_t st = S(stream);
+    fmm_status e;
+    if ((e = cuda_ok(cudaStreamSynchronize(st)))) return e;
+    if ((e = cuda_ok(cudaMemcpy(device_status, h.status, sizeof(int), cudaMemcpyDeviceToHost)))) return e;
+    return cuda_ok(cudaMemset(h.status, 0, sizeof(int)));
+}
+
+fmm_status fmm_set_profiling(fmm_handle* H, int enable) {
+    if (!H) return FMM_ERR_ARG;
+    H->h.profiling = enable != 0;
+    return FMM_OK;
+}
+
+int fmm_stage_times(fmm_handle* H, float* ms, int n) {
+    if (!H || !ms || !H->h.profiling) return 0;
+    Handle& h = H->h;
+    if (cudaEventSynchronize(h.ev[kNumStages]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int k = 0;
+    for (; k < n && k < kNumStages; ++k) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, h.ev[k], h.ev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            t = -1.f;
+        }
+        ms[k] = t;
+    }
+    return k;
+}
+
+int fmm_launches_per_eval(const fmm_handle* H) { return H ? launches_per_eval(&H->h) : 0; }
+
+void fmm_destroy(fmm_handle* H) {
+    if (!H) return;
+    cudaDeviceSynchronize();
+    free_all(H->h);
+    delete H;
+}
+
+}  // extern "C"

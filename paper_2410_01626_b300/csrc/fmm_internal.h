@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/fmmcph.h"
+
+namespace fmmcph {
+
+constexpr int kMaxP = FMM_MAX_P;
+constexpr int kMaxDepth = 7;
+constexpr int kNumOps = 343;  // M2L offsets o in {-3..3}^3 (the inner 27 slots unused)
+constexpr int kNumStages = 8;
+
+inline int ncoef(int p) { return (p + 1) * (p + 1); }
+inline int ncoef_padded(int p) { return (ncoef(p) + 15) / 16 * 16; }
+inline int op_index(int ox, int oy, int oz) { return (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3); }
+
+struct M2LTile {
+    int level;
+    int cls;          // child octant class of the target boxes (0..7)
+    int parent0;      // first parent index (Morton, at level-1)
+    int nparents;     // parents in this tile
+};
+
+struct Handle {
+    int device = 0;
+    fmm_box box{};
+    int periodic = 0, p = 0, depth = 0;
+    int nc = 0, ncp = 0;
+    int precision = FMM_FP32;
+    double ke = 138.935458;
+    double s_bin = 0.0;  // 2^depth / L
+    int lmin = 2;        // first level with M2L
+    // operators (device)
+    float* T = nullptr;        // [343][ncp(k)][ncp(j)]  M2L, transposed (input row k, output col j)
+    float* A = nullptr;        // [8][ncp][ncp] M2M transposed
+    float* B = nullptr;        // [8][ncp][ncp] L2L transposed
+    double* Ad = nullptr;      // [8][nc][nc] M2M row-major, FP64 (root step)
+    double* Lam = nullptr;     // [nc][nc] lattice, FP64 row-major
+    M2LTile* tiles = nullptr;  // M2L work list
+    int ntiles = 0;
+    // tree storage
+    std::vector<long> lvl_off;  // box offset of each level
+    long nbox_total = 0;
+    float* M = nullptr;  // [nbox_total][ncp]
+    float* L = nullptr;
+    // atoms
+    int cap = 0, n = 0, K = 0;
+    float *qA = nullptr, *qB = nullptr, *lam = nullptr;
+    const float* lam_bound = nullptr;
+    int32_t* site = nullptr;
+    int* site_ptr = nullptr;    // [K+1]
+    int* site_atoms = nullptr;  // [#site atoms], input indices grouped by site, ascending
+    int site_cap = 0, lam_cap = 0;
+    uint32_t *key = nullptr, *kA = nullptr, *kB = nullptr, *vA = nullptr, *vB = nullptr;
+    uint32_t *perm = nullptr, *inv = nullptr, *sorted_key = nullptr;
+    uint32_t *start = nullptr, *count = nullptr;
+    uint32_t* sort_table = nullptr;
+    int sort_blocks_cap = 0;
+    float4* pos = nullptr;
+    float* dq = nullptr;
+    float* phis = nullptr;   // sorted-order potential (without k_e)
+    double* epart = nullptr; // per-block partial sums of q phi
+    int epart_cap = 0;
+    double* leafqdt = nullptr;  // [nleaf][5] periodic: Q, Dx, Dy, Dz, T per leaf
+    double* root = nullptr;     // [nc] FP64 root multipole, then [5] Q D T at root+nc
+    int* status = nullptr;
+    bool charges_set = false;
+    // profiling
+    bool profiling = false;
+    cudaEvent_t ev[kNumStages + 1]{};
+    bool ev_valid = false;
+    // host staging for fmm_eval_host
+    float* hx_dev = nullptr;
+    float* hF_dev = nullptr;
+    float* hdV_dev = nullptr;
+    double* hE_dev = nullptr;
+    int host_cap = 0;
+};
+
+// kernels.cu
+void upload_constants(int p);
+void configure_kernels(int ncp);
+int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, float* phi,
+                cudaStream_t st);
+int launches_per_eval(const Handle* h);
+void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi,
+                    const float* dVdl, float* gx, float* gqA, float* gqB, float* glam,
+                    cudaStream_t st);
+void launch_site_csr(Handle* h, cudaStream_t st);
+
+}  // namespace fmmcph

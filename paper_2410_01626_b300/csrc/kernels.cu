@@ -1,0 +1,927 @@
+// CUDA kernels of one FMM evaluation (sm_103a).
+//
+// Stages (all on the caller's stream):
+//   binning   k_keys -> LSD radix sort (k_sort_hist/scan/scatter) -> k_ranges -> k_gather
+//             (Morton keys of the leaf cells, stable on (key, index); the gather also forms
+//             q_i = qA_i + lambda_s (qB_i - qA_i), Sec. 2.1 Eq. 1 with charge-only forms)
+//   P2M       k_p2m<P>        one warp per leaf, butterfly reduce-scatter of the coefficients
+//   M2M       k_m2m           per level, dense 8-child operators
+//   root      k_root, k_lattice (periodic) FP64 root multipole and lattice operator
+//   M2L       k_m2l_fp32 (FP32 CUDA cores) or the tcgen05 kernel in m2l_tc.cu
+//   L2L       k_l2l           per level
+//   near      k_near<P>       L2P + P2P (27 neighbour leaves) + forces / potential / energy
+//   final     k_final         E (FP64, fixed-order reduction) and dV/dlambda per site
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+
+#include "fmm_internal.h"
+
+namespace fmmcph {
+
+// ---- constant tables of the normalised regular-harmonic recurrences ----
+__constant__ float c_dg[kMaxP + 2];                   // sqrt((2m-1)/(2m))
+__constant__ float c_ra[kMaxP + 2][kMaxP + 2];        // (2n-1)/sqrt((n+m)(n-m))
+__constant__ float c_rb[kMaxP + 2][kMaxP + 2];        // sqrt((n+m-1)(n-m-1)/((n+m)(n-m)))
+__constant__ float c_g1[kMaxP + 2][kMaxP + 2];        // sqrt((n+m+1)(n+m+2))
+__constant__ float c_g2[kMaxP + 2][kMaxP + 2];        // sqrt((n-m+1)(n-m+2))
+__constant__ float c_g3[kMaxP + 2][kMaxP + 2];        // sqrt((n+1+m)(n+1-m))
+
+void upload_constants(int /*p*/) {
+    float dg[kMaxP + 2] = {0};
+    static float ra[kMaxP + 2][kMaxP + 2], rb[kMaxP + 2][kMaxP + 2], g1[kMaxP + 2][kMaxP + 2],
+        g2[kMaxP + 2][kMaxP + 2], g3[kMaxP + 2][kMaxP + 2];
+    for (int m = 1; m < kMaxP + 2; ++m) dg[m] = (float)std::sqrt((2.0 * m - 1.0) / (2.0 * m));
+    for (int n = 0; n < kMaxP + 2; ++n)
+        for (int m = 0; m < kMaxP + 2; ++m) {
+            ra[n][m] = rb[n][m] = 0.f;
+            if (n > m) {
+                ra[n][m] = (float)((2.0 * n - 1.0) / std::sqrt(double(n + m) * (n - m)));
+                if (n >= m + 2)
+                    rb[n][m] = (float)std::sqrt(double(n + m - 1) * (n - m - 1) / (double(n + m) * (n - m)));
+            }
+            g1[n][m] = (float)std::sqrt(double(n + m + 1) * (n + m + 2));
+            g2[n][m] = (n >= m) ? (float)std::sqrt(double(n - m + 1) * (n - m + 2)) : 0.f;
+            g3[n][m] = (n + 1 >= m) ? (float)std::sqrt(double(n + 1 + m) * (n + 1 - m)) : 0.f;
+        }
+    cudaMemcpyToSymbol(c_dg, dg, sizeof(dg));
+    cudaMemcpyToSymbol(c_ra, ra, sizeof(ra));
+    cudaMemcpyToSymbol(c_rb, rb, sizeof(rb));
+    cudaMemcpyToSymbol(c_g1, g1, sizeof(g1));
+    cudaMemcpyToSymbol(c_g2, g2, sizeof(g2));
+    cudaMemcpyToSymbol(c_g3, g3, sizeof(g3));
+}
+
+// ---- Morton helpers (up to 10 bits per axis) ----
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {
+    v &= 0x09249249u;
+    v = (v ^ (v >> 2)) & 0x030C30C3u;
+    v = (v ^ (v >> 4)) & 0x0300F00Fu;
+    v = (v ^ (v >> 8)) & 0x030000FFu;
+    v = (v ^ (v >> 16)) & 0x000003FFu;
+    return v;
+}
+__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+struct BoxGeom {
+    double o0, o1, o2, L, s;
+    int nb, depth, periodic;
+};
+
+// Wrapped (periodic) or raw (open) coordinate relative to the origin, exactly
+// as the binning specification states it (FP64, no FMA contraction).
+__device__ __forceinline__ double wrap_coord(double x, double o, double L, int periodic) {
+    double u = __dsub_rn(x, o);
+    if (periodic) {
+        u = __dsub_rn(u, __dmul_rn(L, floor(__ddiv_rn(u, L))));
+        if (u < 0.0 || u >= L) u = 0.0;
+    }
+    return u;
+}
+
+__device__ __forceinline__ int cell_of(double u, double s, int nb) {
+    double f = floor(__dmul_rn(u, s));
+    if (!(f >= 0.0)) return 0;
+    if (f > (double)(nb - 1)) return nb - 1;
+    return (int)f;
+}
+
+__global__ void k_keys(int n, const float* __restrict__ x, BoxGeom g, uint32_t* __restrict__ key,
+                       uint32_t* __restrict__ val, int* __restrict__ status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double o[3] = {g.o0, g.o1, g.o2};
+    int c[3];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double u = wrap_coord((double)x[3 * i + a], o[a], g.L, g.periodic);
+        if (!g.periodic && !(u >= 0.0 && u <= g.L)) bad = true;
+        c[a] = cell_of(u, g.s, g.nb);
+    }
+    key[i] = morton3(c[0], c[1], c[2]);
+    val[i] = (uint32_t)i;
+    if (bad) atomicOr(status, FMM_DEV_DOMAIN);
+}
+
+// ---- stable LSD radix sort, 8-bit digits ----
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortSub = 512;  // keys per warp sub-chunk
+constexpr int kSortTile = kSortWarps * kSortSub;
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(int n, const uint32_t* __restrict__ keys,
+                                                            int shift, uint32_t* __restrict__ table,
+                                                            int nblk) {
+    __shared__ uint32_t hist[256];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile;
+    for (int j = threadIdx.x; j < kSortTile; j += kSortThreads) {
+        int i = base + j;
+        if (i < n) atomicAdd(&hist[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    table[threadIdx.x * nblk + blockIdx.x] = hist[threadIdx.x];
+}
+
+// exclusive scan of the digit-major table, one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ table, int total) {
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x;
+    const int seg = (total + 1023) / 1024;
+    const int b = t * seg, e = min(total, b + seg);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += table[i];
+    // block exclusive scan of s
+    uint32_t v = s;
+    const int lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += y;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t z = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, z, d);
+            if (lane >= d) z += y;
+        }
+        wsum[lane] = z;
+    }
+    __syncthreads();
+    uint32_t run = v - s + (w > 0 ? wsum[w - 1] : 0u);
+    for (int i = b; i < e; ++i) {
+        uint32_t c = table[i];
+        table[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(int n, const uint32_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin,
+                                                               uint32_t* __restrict__ kout,
+                                                               uint32_t* __restrict__ vout, int shift,
+                                                               const uint32_t* __restrict__ table,
+                                                               int nblk) {
+    __shared__ uint32_t woff[kSortWarps][256];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&woff[0][0])[d] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile + w * kSortSub;
+    for (int j = lane; j < kSortSub; j += 32) {
+        int i = base + j;
+        if (i < n) atomicAdd(&woff[w][(kin[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // 256 threads = 256 digits
+        uint32_t run = table[d * nblk + blockIdx.x];
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            uint32_t c = woff[ww][d];
+            woff[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int g = 0; g < kSortSub; g += 32) {
+        int i = base + g + lane;
+        bool valid = i < n;
+        uint32_t k = valid ? kin[i] : 0u;
+        uint32_t digit = valid ? ((k >> shift) & 255u) : (256u + lane);
+        uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        uint32_t rank = __popc(peers & lt);
+        if (valid) {
+            uint32_t pos = woff[w][digit] + rank;
+            kout[pos] = k;
+            vout[pos] = vin[i];
+        }
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) woff[w][digit] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// leaf ranges by binary search over the sorted keys (empty leaves start at their insertion point)
+__global__ void k_ranges(int n, int nleaf, const uint32_t* __restrict__ skey, uint32_t* __restrict__ start,
+                         uint32_t* __restrict__ count) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    auto lower = [&](uint32_t v) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (skey[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    int s = lower((uint32_t)b), e = lower((uint32_t)b + 1u);
+    start[b] = (uint32_t)s;
+    count[b] = (uint32_t)(e - s);
+}
+
+__global__ void k_gather(int n, const uint32_t* __restrict__ perm, const float* __restrict__ x, BoxGeom g,
+                         const float* __restrict__ qA, const float* __restrict__ qB,
+                         const int32_t* __restrict__ site, int K, const float* __restrict__ lam,
+                         float4* __restrict__ pos, float* __restrict__ dq, uint32_t* __restrict__ inv,
+                         int* __restrict__ status) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int i = (int)perm[s];
+    float ux = (float)wrap_coord((double)x[3 * i], g.o0, g.L, g.periodic);
+    float uy = (float)wrap_coord((double)x[3 * i + 1], g.o1, g.L, g.periodic);
+    float uz = (float)wrap_coord((double)x[3 * i + 2], g.o2, g.L, g.periodic);
+    float a = qA[i], b = qB[i];
+    int st = site[i];
+    float d = 0.f, q = a;
+    if (st >= 0) {
+        if (st < K) {
+            d = b - a;
+            q = fmaf(lam[st], d, a);
+        } else {
+            atomicOr(status, FMM_DEV_SITE);
+        }
+    }
+    pos[s] = make_float4(ux, uy, uz, q);
+    dq[s] = d;
+    inv[i] = (uint32_t)s;
+}
+
+// ---- normalised regular solid harmonics, real form ----
+// R_hat_n^m(u) for n = 0..P, m = 0..n via the column recurrences; `visit(n, m, re, im)`.
+template <int P, class F>
+__device__ __forceinline__ void regular_harmonics(float x, float y, float z, F&& visit) {
+    const float rho2 = x * x + y * y + z * z;
+    float dr = 1.f, di = 0.f;
+#pragma unroll
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) {
+            const float t = (dr * x + di * y) * c_dg[m];
+            di = (di * x - dr * y) * c_dg[m];
+            dr = t;
+        }
+        float pr = dr, pi = di, ppr = 0.f, ppi = 0.f;
+#pragma unroll
+        for (int n = m; n <= P; ++n) {
+            if (n > m) {
+                const float a = c_ra[n][m] * z, b = c_rb[n][m] * rho2;
+                const float nr = a * pr - b * ppr, ni = a * pi - b * ppi;
+                ppr = pr;
+                ppi = pi;
+                pr = nr;
+                pi = ni;
+            }
+            visit(n, m, pr, pi);
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m(int nleaf, float h, float half_box,
+                                             const uint32_t* __restrict__ start,
+                                             const uint32_t* __restrict__ count,
+                                             const float4* __restrict__ pos, float* __restrict__ M,
+                                             int ncp, double* __restrict__ leafqdt) {
+    constexpr int NC = (P + 1) * (P + 1);
+    constexpr int NG = (NC + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int leaf = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (leaf >= nleaf) return;
+    const uint32_t lx = compact3(leaf), ly = compact3(leaf >> 1), lz = compact3(leaf >> 2);
+    const float cx = (lx + 0.5f) * h, cy = (ly + 0.5f) * h, cz = (lz + 0.5f) * h;
+    const float ih = 1.0f / h;
+    const int st = start[leaf], cnt = count[leaf];
+    float v[NG * 32];
+#pragma unroll
+    for (int i = 0; i < NG * 32; ++i) v[i] = 0.f;
+    double qd0 = 0, qd1 = 0, qd2 = 0, qd3 = 0, qd4 = 0;
+    for (int b = 0; b < cnt; b += 32) {
+        const int j = b + lane;
+        float4 a = make_float4(cx, cy, cz, 0.f);
+        if (j < cnt) a = pos[st + j];
+        const float q = a.w;
+        regular_harmonics<P>((a.x - cx) * ih, (a.y - cy) * ih, (a.z - cz) * ih,
+                             [&](int n, int m, float re, float im) {
+                                 if (m == 0) {
+                                     v[n * n] += q * re;
+                                 } else {
+                                     v[n * n + 2 * m - 1] += q * re;
+                                     v[n * n + 2 * m] -= q * im;
+                                 }
+                             });
+        if (leafqdt) {
+            const double ux = (double)a.x - half_box, uy = (double)a.y - half_box, uz = (double)a.z - half_box;
+            const double qq = (double)q;
+            qd0 += qq;
+            qd1 += qq * ux;
+            qd2 += qq * uy;
+            qd3 += qq * uz;
+            qd4 += qq * (ux * ux + uy * uy + uz * uz);
+        }
+    }
+    // butterfly reduce-scatter: after it, group g's sum for coefficient g*32+lane sits in v[g*32]
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        float* w = v + g * 32;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const bool up = (lane & s) != 0;
+#pragma unroll
+            for (int i = 0; i < s; ++i) {
+                const float send = up ? w[i] : w[i + s];
+                const float keep = up ? w[i + s] : w[i];
+                w[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+            }
+        }
+    }
+    float* out = M + (long)leaf * ncp;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int idx = g * 32 + lane;
+        if (idx < ncp) out[idx] = (idx < NC) ? v[g * 32] : 0.f;
+    }
+    for (int idx = NG * 32 + lane; idx < ncp; idx += 32) out[idx] = 0.f;
+    if (leafqdt) {
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            qd0 += __shfl_xor_sync(0xffffffffu, qd0, s);
+            qd1 += __shfl_xor_sync(0xffffffffu, qd1, s);
+            qd2 += __shfl_xor_sync(0xffffffffu, qd2, s);
+            qd3 += __shfl_xor_sync(0xffffffffu, qd3, s);
+            qd4 += __shfl_xor_sync(0xffffffffu, qd4, s);
+        }
+        if (lane == 0) {
+            double* o = leafqdt + 5L * leaf;
+            o[0] = qd0;
+            o[1] = qd1;
+            o[2] = qd2;
+            o[3] = qd3;
+            o[4] = qd4;
+        }
+    }
+}
+
+// ---- M2M: parent = sum_c A_c child_c ; G parents per block, thread j = output coefficient ----
+constexpr int kM2MG = 8;
+__global__ void k_m2m(int nparent, int nc, int ncp, const float* __restrict__ AT,
+                      const float* __restrict__ Mchild, float* __restrict__ Mparent) {
+    extern __shared__ float sm[];  // [G][8][ncp]
+    const int p0 = blockIdx.x * kM2MG;
+    const int tot = kM2MG * 8 * ncp;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int g = e / (8 * ncp);
+        const int r = e - g * 8 * ncp;  // c*ncp + k
+        sm[e] = (p0 + g < nparent) ? Mchild[(long)(p0 + g) * 8 * ncp + r] : 0.f;
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    float acc[kM2MG];
+#pragma unroll
+    for (int g = 0; g < kM2MG; ++g) acc[g] = 0.f;
+    for (int c = 0; c < 8; ++c) {
+        const float* a = AT + (long)c * ncp * ncp + j;
+        for (int k = 0; k < nc; ++k) {
+            const float t = a[(long)k * ncp];
+#pragma unroll
+            for (int g = 0; g < kM2MG; ++g) acc[g] = fmaf(t, sm[(g * 8 + c) * ncp + k], acc[g]);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < kM2MG; ++g)
+        if (p0 + g < nparent) Mparent[(long)(p0 + g) * ncp + j] = acc[g];
+}
+
+// ---- L2L: child_c += B_c parent ----
+__global__ void k_l2l(int nparent, int nc, int ncp, const float* __restrict__ BT,
+                      const float* __restrict__ Lparent, float* __restrict__ Lchild) {
+    extern __shared__ float sm[];  // [G][ncp]
+    const int p0 = blockIdx.x * kM2MG;
+    for (int e = threadIdx.x; e < kM2MG * ncp; e += blockDim.x) {
+        const int g = e / ncp;
+        sm[e] = (p0 + g < nparent) ? Lparent[(long)p0 * ncp + e] : 0.f;
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    for (int c = 0; c < 8; ++c) {
+        float acc[kM2MG];
+#pragma unroll
+        for (int g = 0; g < kM2MG; ++g) acc[g] = 0.f;
+        const float* b = BT + (long)c * ncp * ncp + j;
+        for (int k = 0; k < nc; ++k) {
+            const float t = b[(long)k * ncp];
+#pragma unroll
+            for (int g = 0; g < kM2MG; ++g) acc[g] = fmaf(t, sm[g * ncp + k], acc[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < kM2MG; ++g)
+            if (p0 + g < nparent) Lchild[((long)(p0 + g) * 8 + c) * ncp + j] += acc[g];
+    }
+}
+
+// ---- periodic root: FP64 root multipole (M2M from level 1) and the Q, D, T sums ----
+// blocks [0, nrowblk): 4 warps each, warp = one output row; block nrowblk: Q/D/T reduction.
+__global__ void k_root(int nc, int ncp, int depth, const double* __restrict__ Ad,
+                       const float* __restrict__ M1, const float* __restrict__ M0, int nleaf,
+                       const double* __restrict__ leafqdt, double* __restrict__ root) {
+    const int nrowblk = (nc + 3) / 4;
+    if ((int)blockIdx.x == nrowblk) {
+        __shared__ double red[5][256];
+        double a[5] = {0, 0, 0, 0, 0};
+        for (int l = threadIdx.x; l < nleaf; l += blockDim.x)
+            for (int c = 0; c < 5; ++c) a[c] += leafqdt[5L * l + c];
+        for (int c = 0; c < 5; ++c) red[c][threadIdx.x] = a[c];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s)
+                for (int c = 0; c < 5; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x < 5) root[nc + threadIdx.x] = red[threadIdx.x][0];
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (j >= nc) return;
+    double s = 0.0;
+    if (depth == 0) {
+        s = (lane == 0) ? (double)M0[j] : 0.0;
+    } else {
+        for (int e = lane; e < 8 * nc; e += 32) {
+            const int c = e / nc, k = e - c * nc;
+            s += Ad[((long)c * nc + j) * nc + k] * (double)M1[(long)c * ncp + k];
+        }
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) root[j] = s;
+}
+
+// L0 = Lambda M0 (FP64), written as the FP32 level-0 local expansion
+__global__ void k_lattice(int nc, int ncp, const double* __restrict__ Lam, const double* __restrict__ root,
+                          float* __restrict__ L0) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (j >= ncp) return;
+    double s = 0.0;
+    if (j < nc)
+        for (int k = lane; k < nc; k += 32) s += Lam[(long)j * nc + k] * root[k];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) L0[j] = (float)s;
+}
+
+// ---- M2L, FP32 CUDA cores: a tile of target boxes of one level and octant class ----
+constexpr int kM2LTB = 16;
+struct LevelOffsets {
+    long off[kMaxDepth + 1];
+};
+
+__global__ void k_m2l_fp32(const M2LTile* __restrict__ tiles, int nc, int ncp, const float* __restrict__ TT,
+                           const float* __restrict__ M, float* __restrict__ L, LevelOffsets lo,
+                           int periodic) {
+    extern __shared__ float ms[];  // [TB][ncp]
+    const M2LTile t = tiles[blockIdx.x];
+    const int lev = t.level, cls = t.cls, np = t.nparents;
+    const int nb = 1 << lev;
+    const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
+    const float* Ml = M + lo.off[lev] * ncp;
+    float* Ll = L + lo.off[lev] * ncp;
+    const int j = threadIdx.x;
+    float acc[kM2LTB];
+#pragma unroll
+    for (int g = 0; g < kM2LTB; ++g) acc[g] = 0.f;
+    for (int idx = 0; idx < 216; ++idx) {
+        const int ox = idx / 36 - 2 - cx, oy = (idx / 6) % 6 - 2 - cy, oz = idx % 6 - 2 - cz;
+        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+        __syncthreads();
+        for (int e = threadIdx.x; e < kM2LTB * ncp; e += blockDim.x) {
+            const int g = e / ncp, k = e - g * ncp;
+            float v = 0.f;
+            if (g < np) {
+                const uint32_t b = ((uint32_t)(t.parent0 + g) << 3) | (uint32_t)cls;
+                int sx = (int)compact3(b) + ox, sy = (int)compact3(b >> 1) + oy, sz = (int)compact3(b >> 2) + oz;
+                bool ok = true;
+                if (periodic) {
+                    sx &= nb - 1;
+                    sy &= nb - 1;
+                    sz &= nb - 1;
+                } else {
+                    ok = sx >= 0 && sx < nb && sy >= 0 && sy < nb && sz >= 0 && sz < nb;
+                }
+                if (ok) v = Ml[(long)morton3(sx, sy, sz) * ncp + k];
+            }
+            ms[e] = v;
+        }
+        __syncthreads();
+        const float* top = TT + (long)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * ncp * ncp + j;
+        for (int k = 0; k < nc; ++k) {
+            const float tv = top[(long)k * ncp];
+#pragma unroll
+            for (int g = 0; g < kM2LTB; ++g) acc[g] = fmaf(tv, ms[g * ncp + k], acc[g]);
+        }
+    }
+    for (int g = 0; g < np; ++g) {
+        const uint32_t b = ((uint32_t)(t.parent0 + g) << 3) | (uint32_t)cls;
+        Ll[(long)b * ncp + j] = acc[g];
+    }
+}
+
+// ---- L2P: potential and gradient of the leaf local expansion at u (units of h) ----
+template <int P>
+__device__ __forceinline__ void l2p_eval(const float* __restrict__ Lb, float x, float y, float z, float& phi,
+                                         float& gx, float& gy, float& gz) {
+    phi = gx = gy = gz = 0.f;
+    regular_harmonics<P>(x, y, z, [&](int n, int m, float pr, float pi) {
+        const float w = (m == 0) ? 1.f : 2.f;
+        const float Lr = (m == 0) ? __ldg(Lb + n * n) : __ldg(Lb + n * n + 2 * m - 1);
+        const float Li = (m == 0) ? 0.f : __ldg(Lb + n * n + 2 * m);
+        phi += w * (Lr * pr - Li * pi);
+        if (n < P) {
+            const int q1 = (n + 1) * (n + 1);
+            const float apr = __ldg(Lb + q1 + 2 * (m + 1) - 1), api = __ldg(Lb + q1 + 2 * (m + 1));
+            float cr, ci, br, bi;
+            if (m == 0) {
+                cr = __ldg(Lb + q1);
+                ci = 0.f;
+                br = -apr;  // L_{n+1}^{-1} = -conj(L_{n+1}^{1})
+                bi = api;
+            } else {
+                cr = __ldg(Lb + q1 + 2 * m - 1);
+                ci = __ldg(Lb + q1 + 2 * m);
+                if (m == 1) {
+                    br = __ldg(Lb + q1);
+                    bi = 0.f;
+                } else {
+                    br = __ldg(Lb + q1 + 2 * (m - 1) - 1);
+                    bi = __ldg(Lb + q1 + 2 * (m - 1));
+                }
+            }
+            const float c1 = c_g1[n][m], c2 = c_g2[n][m], c3 = c_g3[n][m];
+            const float Ar = c1 * apr, Ai = c1 * api, Br = c2 * br, Bi = c2 * bi;
+            const float hw = 0.5f * w;
+            gx += hw * ((Ar - Br) * pr - (Ai - Bi) * pi);
+            gy += hw * ((Ar + Br) * pi + (Ai + Bi) * pr);
+            gz += w * c3 * (cr * pr - ci * pi);
+        }
+    });
+}
+
+struct NearParams {
+    int nleaf, depth, periodic, use_far, ncp;
+    float h, Lbox, ke;
+    const uint32_t* start;
+    const uint32_t* count;
+    const float4* pos;
+    const float* Lleaf;
+    const double* qdt;  // Q, Dx, Dy, Dz, T (periodic) or null
+    double vol;
+    const uint32_t* perm;
+    float* F;
+    float* phi_out;
+    float* phis;
+    double* epart;
+};
+
+template <int P>
+__global__ void __launch_bounds__(128) k_near(NearParams a) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int leaf = blockIdx.x * 4 + w;
+    double esum = 0.0;
+    if (leaf < a.nleaf) {
+        const int nb = 1 << a.depth;
+        const int ix = (int)compact3(leaf), iy = (int)compact3(leaf >> 1), iz = (int)compact3(leaf >> 2);
+        const float h = a.h;
+        const float cx = (ix + 0.5f) * h, cy = (iy + 0.5f) * h, cz = (iz + 0.5f) * h;
+        const int st = a.start[leaf], cnt = a.count[leaf];
+        float cq = 0.f, cdx = 0.f, cdy = 0.f, cdz = 0.f, ctr = 0.f, c2 = 0.f;
+        if (a.periodic && a.qdt) {
+            c2 = (float)(2.0 * M_PI / (3.0 * a.vol));
+            cq = (float)a.qdt[0];
+            cdx = (float)a.qdt[1];
+            cdy = (float)a.qdt[2];
+            cdz = (float)a.qdt[3];
+            ctr = (float)a.qdt[4];
+        }
+        for (int tb = 0; tb < cnt; tb += 32) {
+            const int ti = tb + lane;
+            const bool valid = ti < cnt;
+            float4 me = make_float4(cx, cy, cz, 0.f);
+            if (valid) me = a.pos[st + ti];
+            float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+            for (int o = 0; o < 27; ++o) {
+                int sx = ix + o / 9 - 1, sy = iy + (o / 3) % 3 - 1, sz = iz + o % 3 - 1;
+                float shx = 0.f, shy = 0.f, shz = 0.f;
+                if (a.periodic) {
+                    const int wx = (sx + nb) & (nb - 1), wy = (sy + nb) & (nb - 1), wz = (sz + nb) & (nb - 1);
+                    shx = (float)(sx - wx) * h;
+                    shy = (float)(sy - wy) * h;
+                    shz = (float)(sz - wz) * h;
+                    sx = wx;
+                    sy = wy;
+                    sz = wz;
+                } else if (sx < 0 || sx >= nb || sy < 0 || sy >= nb || sz < 0 || sz >= nb) {
+                    continue;
+                }
+                const uint32_t src = morton3(sx, sy, sz);
+                const int s0 = a.start[src], sc = a.count[src];
+                for (int sb = 0; sb < sc; sb += 32) {
+                    float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
+                    sp.x += shx;
+                    sp.y += shy;
+                    sp.z += shz;
+                    const int ns = min(32, sc - sb);
+                    for (int t = 0; t < ns; ++t) {
+                        const float xs = __shfl_sync(0xffffffffu, sp.x, t);
+                        const float ys = __shfl_sync(0xffffffffu, sp.y, t);
+                        const float zs = __shfl_sync(0xffffffffu, sp.z, t);
+                        const float qs = __shfl_sync(0xffffffffu, sp.w, t);
+                        const float dx = me.x - xs, dy = me.y - ys, dz = me.z - zs;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
+                        const float qri = qs * ri;
+                        pot += qri;
+                        const float qri3 = qri * ri * ri;
+                        gx = fmaf(-qri3, dx, gx);
+                        gy = fmaf(-qri3, dy, gy);
+                        gz = fmaf(-qri3, dz, gz);
+                    }
+                }
+            }
+            if (a.use_far) {
+                float pf, fx, fy, fz;
+                const float ih = 1.0f / h;
+                l2p_eval<P>(a.Lleaf + (long)leaf * a.ncp, (me.x - cx) * ih, (me.y - cy) * ih, (me.z - cz) * ih,
+                            pf, fx, fy, fz);
+                pot += pf * ih;
+                gx += fx * ih * ih;
+                gy += fy * ih * ih;
+                gz += fz * ih * ih;
+            }
+            if (a.periodic) {
+                const float hb = 0.5f * a.Lbox;
+                const float ux = me.x - hb, uy = me.y - hb, uz = me.z - hb;
+                pot += c2 * (cq * (ux * ux + uy * uy + uz * uz) - 2.f * (ux * cdx + uy * cdy + uz * cdz) + ctr);
+                gx += 2.f * c2 * (cq * ux - cdx);
+                gy += 2.f * c2 * (cq * uy - cdy);
+                gz += 2.f * c2 * (cq * uz - cdz);
+            }
+            if (valid) {
+                const int i = (int)a.perm[st + ti];
+                const float q = me.w;
+                if (a.F) {
+                    a.F[3L * i] = -a.ke * q * gx;
+                    a.F[3L * i + 1] = -a.ke * q * gy;
+                    a.F[3L * i + 2] = -a.ke * q * gz;
+                }
+                if (a.phi_out) a.phi_out[i] = a.ke * pot;
+                a.phis[st + ti] = pot;
+                esum += (double)q * (double)pot;
+            }
+        }
+    }
+    // block reduction of q phi (fixed order)
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, d);
+    __shared__ double red[4];
+    if (lane == 0) red[w] = esum;
+    __syncthreads();
+    if (threadIdx.x == 0) a.epart[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+__global__ void k_final(int nparts, const double* __restrict__ epart, double ke, double* __restrict__ E, int K,
+                        const int* __restrict__ site_ptr, const int* __restrict__ site_atoms,
+                        const uint32_t* __restrict__ inv, const float* __restrict__ dq,
+                        const float* __restrict__ phis, float* __restrict__ dVdl) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 256) s += epart[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int d = 128; d > 0; d >>= 1) {
+        if ((int)threadIdx.x < d) red[threadIdx.x] += red[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && E) E[0] = 0.5 * ke * red[0];
+    if (dVdl)
+        for (int k = threadIdx.x; k < K; k += 256) {
+            double v = 0.0;
+            for (int a = site_ptr[k]; a < site_ptr[k + 1]; ++a) {
+                const uint32_t si = inv[site_atoms[a]];
+                v += (double)dq[si] * (double)phis[si];
+            }
+            dVdl[k] = (float)(ke * v);
+        }
+}
+
+__global__ void k_adjoint(int n, int K, const double* __restrict__ gbar, const float* __restrict__ F,
+                          const float* __restrict__ phi, const float* __restrict__ dVdl,
+                          const int32_t* __restrict__ site, const float* __restrict__ lam,
+                          float* __restrict__ gx, float* __restrict__ gqA, float* __restrict__ gqB,
+                          float* __restrict__ glam) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float g = (float)gbar[0];
+    if (i < K && glam) glam[i] = dVdl[i] * g;
+    if (i >= n) return;
+    if (gx) {
+        gx[3L * i] = -F[3L * i] * g;
+        gx[3L * i + 1] = -F[3L * i + 1] * g;
+        gx[3L * i + 2] = -F[3L * i + 2] * g;
+    }
+    const int s = site[i];
+    const float l = (s >= 0 && s < K) ? lam[s] : 0.f;
+    if (gqA) gqA[i] = phi[i] * (1.f - l) * g;
+    if (gqB) gqB[i] = phi[i] * l * g;
+}
+
+// ---------------------------------------------------------------------------------------------
+template <int P>
+static void launch_p2m(int nleaf, float h, float half, const Handle* hd, float* Mleaf, double* qdt,
+                       cudaStream_t st) {
+    k_p2m<P><<<(nleaf + 3) / 4, 128, 0, st>>>(nleaf, h, half, hd->start, hd->count, hd->pos, Mleaf, hd->ncp,
+                                              qdt);
+}
+template <int P>
+static void launch_near(const NearParams& a, cudaStream_t st) {
+    k_near<P><<<(a.nleaf + 3) / 4, 128, 0, st>>>(a);
+}
+
+#define FMM_DISPATCH_P(p, FN, ...)         \
+    switch (p) {                            \
+        case 1: FN<1>(__VA_ARGS__); break;  \
+        case 2: FN<2>(__VA_ARGS__); break;  \
+        case 3: FN<3>(__VA_ARGS__); break;  \
+        case 4: FN<4>(__VA_ARGS__); break;  \
+        case 5: FN<5>(__VA_ARGS__); break;  \
+        case 6: FN<6>(__VA_ARGS__); break;  \
+        case 7: FN<7>(__VA_ARGS__); break;  \
+        case 8: FN<8>(__VA_ARGS__); break;  \
+        case 9: FN<9>(__VA_ARGS__); break;  \
+        case 10: FN<10>(__VA_ARGS__); break; \
+        case 11: FN<11>(__VA_ARGS__); break; \
+        case 12: FN<12>(__VA_ARGS__); break; \
+        case 13: FN<13>(__VA_ARGS__); break; \
+        case 14: FN<14>(__VA_ARGS__); break; \
+        default: break;                     \
+    }
+
+bool m2l_tc_supported(const Handle* h);
+void launch_m2l_tc(Handle* h, cudaStream_t st);
+
+static inline int sort_passes(int depth) { return (3 * depth + 7) / 8; }
+
+void configure_kernels(int ncp) {
+    cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * kM2MG * 8 * ncp));
+}
+
+int launches_per_eval(const Handle* h) {
+    const int d = h->depth;
+    int n = 1 /*keys*/ + 3 * sort_passes(d) + 1 /*ranges*/ + 1 /*gather*/ + 1 /*p2m*/;
+    const int lmin = h->periodic ? 1 : 2;
+    if (d >= lmin) n += d - lmin;  // M2M parent levels d-1 .. lmin
+    if (h->periodic) n += 2;       // root + lattice
+    if (d >= lmin) n += 1;         // M2L
+    if (d >= lmin) n += d - lmin + (h->periodic ? 1 : 0);  // L2L
+    n += 1 /*near*/ + 1 /*final*/;
+    return n;
+}
+
+static inline void stage(Handle* h, int i, cudaStream_t st) {
+    if (h->profiling) cudaEventRecord(h->ev[i], st);
+}
+
+int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, float* phi, cudaStream_t st) {
+    const int n = h->n, d = h->depth, nb = 1 << d;
+    const int nleaf = 1 << (3 * d);
+    const float hleaf = (float)(h->box.edge / nb);
+    BoxGeom g{h->box.origin[0], h->box.origin[1], h->box.origin[2], h->box.edge, h->s_bin, nb, d, h->periodic};
+    const float* lam = h->lam_bound ? h->lam_bound : h->lam;
+    stage(h, 0, st);
+    // --- binning ---
+    const int nblk = (n + kSortTile - 1) / kSortTile;
+    if (n > 0) k_keys<<<(n + 255) / 256, 256, 0, st>>>(n, x, g, h->key, h->vA, h->status);
+    const uint32_t* kin = h->key;
+    const uint32_t* vin = h->vA;
+    uint32_t* kbuf[2] = {h->kB, h->kA};
+    uint32_t* vbuf[2] = {h->vB, h->vA};
+    const int passes = sort_passes(d);
+    for (int ps = 0; ps < passes; ++ps) {
+        uint32_t* ko = kbuf[ps & 1];
+        uint32_t* vo = vbuf[ps & 1];
+        if (n > 0) {
+            k_sort_hist<<<nblk, kSortThreads, 0, st>>>(n, kin, 8 * ps, h->sort_table, nblk);
+            k_sort_scan<<<1, 1024, 0, st>>>(h->sort_table, 256 * nblk);
+            k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(n, kin, vin, ko, vo, 8 * ps, h->sort_table, nblk);
+        }
+        kin = ko;
+        vin = vo;
+    }
+    h->sorted_key = const_cast<uint32_t*>(kin);
+    h->perm = const_cast<uint32_t*>(vin);
+    k_ranges<<<(nleaf + 255) / 256, 256, 0, st>>>(n, nleaf, h->sorted_key, h->start, h->count);
+    if (n > 0)
+        k_gather<<<(n + 255) / 256, 256, 0, st>>>(n, h->perm, x, g, h->qA, h->qB, h->site, h->K, lam, h->pos,
+                                                  h->dq, h->inv, h->status);
+    stage(h, 1, st);
+    // --- P2M ---
+    float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
+    float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
+    FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, (float)(0.5 * h->box.edge), h, Mleaf,
+                   h->periodic ? h->leafqdt : nullptr, st);
+    stage(h, 2, st);
+    // --- M2M (FP32) for parent levels d-1 .. lmin ---
+    const int lmin = h->periodic ? 1 : 2;
+    const size_t sm_m2m = sizeof(float) * kM2MG * 8 * h->ncp;
+    for (int l = d - 1; l >= lmin; --l) {
+        const int np = 1 << (3 * l);
+        k_m2m<<<(np + kM2MG - 1) / kM2MG, h->ncp, sm_m2m, st>>>(np, h->nc, h->ncp, h->A,
+                                                                 h->M + h->lvl_off[l + 1] * h->ncp,
+                                                                 h->M + h->lvl_off[l] * h->ncp);
+    }
+    stage(h, 3, st);
+    // --- periodic root (FP64) ---
+    if (h->periodic) {
+        const int nrowblk = (h->nc + 3) / 4;
+        const float* M1 = (d >= 1) ? h->M + h->lvl_off[1] * h->ncp : nullptr;
+        k_root<<<nrowblk + 1, 128, 0, st>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, nleaf, h->leafqdt, h->root);
+        k_lattice<<<(h->ncp + 3) / 4, 128, 0, st>>>(h->nc, h->ncp, h->Lam, h->root, h->L);
+    }
+    stage(h, 4, st);
+    // --- M2L ---
+    if (d >= lmin && h->ntiles > 0) {
+        if (h->precision != FMM_FP32 && m2l_tc_supported(h)) {
+            launch_m2l_tc(h, st);
+        } else {
+            LevelOffsets lo{};
+            for (int l = 0; l <= d; ++l) lo.off[l] = h->lvl_off[l];
+            k_m2l_fp32<<<h->ntiles, h->ncp, sizeof(float) * kM2LTB * h->ncp, st>>>(
+                h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
+        }
+    }
+    stage(h, 5, st);
+    // --- L2L: levels lmin+1 .. d (periodic: 1 .. d from the lattice-filled root) ---
+    const size_t sm_l2l = sizeof(float) * kM2MG * h->ncp;
+    const int lfirst = h->periodic ? 1 : lmin + 1;
+    for (int l = lfirst; l <= d; ++l) {
+        const int np = 1 << (3 * (l - 1));
+        k_l2l<<<(np + kM2MG - 1) / kM2MG, h->ncp, sm_l2l, st>>>(np, h->nc, h->ncp, h->B,
+                                                                 h->L + h->lvl_off[l - 1] * h->ncp,
+                                                                 h->L + h->lvl_off[l] * h->ncp);
+    }
+    stage(h, 6, st);
+    // --- near field + L2P + outputs ---
+    NearParams a{};
+    a.nleaf = nleaf;
+    a.depth = d;
+    a.periodic = h->periodic;
+    a.use_far = h->periodic ? 1 : (d >= 2 ? 1 : 0);
+    a.ncp = h->ncp;
+    a.h = hleaf;
+    a.Lbox = (float)h->box.edge;
+    a.ke = (float)h->ke;
+    a.start = h->start;
+    a.count = h->count;
+    a.pos = h->pos;
+    a.Lleaf = Lleaf;
+    a.qdt = h->periodic ? h->root + h->nc : nullptr;
+    a.vol = h->box.edge * h->box.edge * h->box.edge;
+    a.perm = h->perm;
+    a.F = F;
+    a.phi_out = phi;
+    a.phis = h->phis;
+    a.epart = h->epart;
+    FMM_DISPATCH_P(h->p, launch_near, a, st);
+    stage(h, 7, st);
+    const int nparts = (nleaf + 3) / 4;
+    k_final<<<1, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,
+                               h->phis, dVdl);
+    stage(h, 8, st);
+    return 0;
+}
+
+void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi, const float* dVdl,
+                    float* gx, float* gqA, float* gqB, float* glam, cudaStream_t st) {
+    const int m = h->n > h->K ? h->n : h->K;
+    if (m == 0) return;
+    const float* lam = h->lam_bound ? h->lam_bound : h->lam;
+    k_adjoint<<<(m + 255) / 256, 256, 0, st>>>(h->n, h->K, gbar, F, phi, dVdl, h->site, lam, gx, gqA, gqB, glam);
+}
+
+}  // namespace fmmcph

@@ -1,0 +1,207 @@
+"""GPU parity of the CUDA FMM path against the FP64 oracle (direct sum / Ewald).
+
+Tolerances: binning is bit-exact.  Where the far field is absent (open box,
+depth <= 1) the result is a plain FP32 pair sum and must agree to FP32
+rounding (1e-5 relative: a sum of ~1e3 terms of unit roundoff 6e-8 with
+cancellation).  With the far field the multipole truncation dominates; the
+bars are the ones stated for the method: relative RMS force error <= 1e-3 at
+p = 6 and <= 1e-5 at p = 12, dV/dlambda within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from fmm_check import errors, make_solver, oracle_ref, run_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+# ---------------------------------------------------------------- binning (bit exact)
+def _binning_case(s, depth):
+    f, d = make_solver(s, depth=depth)
+    E, F, dV, _ = f.eval(d["x"])
+    key, perm, start, count = [t.cpu().numpy().view(np.uint32) for t in f.binning()]
+    f.close()
+    rk, rp, rs, rc, _ = oracle.binning(s["x"], s["origin"], s["L"], depth, s["periodic"])
+    np.testing.assert_array_equal(key, rk)
+    np.testing.assert_array_equal(perm, rp)
+    np.testing.assert_array_equal(start, rs)
+    np.testing.assert_array_equal(count, rc)
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2, 3, 5])
+def test_binning_bit_exact_open(depth):
+    _binning_case(synth.small_open(), depth)
+
+
+@pytest.mark.parametrize("depth", [1, 4])
+def test_binning_bit_exact_periodic_adversarial(depth):
+    s = synth.periodic_uniform(seed=2, n=3000, L=2.0)
+    x = s["x"].copy()
+    L = s["L"]
+    x[0] = [0, 0, 0]
+    x[1] = [L, L, L]
+    x[2] = [L / 2, L / 4, 3 * L / 8]
+    x[3] = [-1e-7, -3 * L, 7.3 * L]
+    x[4] = [2 * L, -L, 1.5 * L]
+    x[5] = [-0.5 * L, 10.25 * L, -4.125 * L]
+    s["x"] = x.astype(np.float32)
+    _binning_case(s, depth)
+
+
+def test_binning_large_stable():
+    """Many atoms per leaf and ties: the permutation must be the stable one."""
+    rng = np.random.default_rng(0)
+    s = synth.open_uniform(seed=1, n=200000, L=4.0, n_sites=1)
+    s["x"][: 100000] = np.round(s["x"][: 100000], 1)  # heavy duplication of positions
+    _binning_case(s, 5)
+
+
+# ---------------------------------------------------------------- near field only
+@pytest.mark.parametrize("depth", [0, 1])
+def test_open_near_field_only_equals_direct_sum(depth):
+    s = synth.small_open()
+    ref = oracle_ref(s)
+    g = run_gpu(s, depth=depth)
+    e = errors(g, ref)
+    assert e["E"] < 1e-5 and e["F"] < 1e-5 and e["dVdl"] < 1e-5, e
+    np.testing.assert_allclose(g["phi"], ref["phi"], rtol=0, atol=1e-5 * np.abs(ref["phi"]).max())
+    assert g["status"] == 0
+
+
+# ---------------------------------------------------------------- open boundary FMM
+@pytest.mark.parametrize("p,ftol", [(6, 1e-3), (8, 2e-4), (12, 1e-5)])
+def test_open_fmm_small(p, ftol):
+    s = synth.small_open()
+    ref = oracle_ref(s)
+    e = errors(run_gpu(s, p=p, depth=2), ref)
+    assert e["F"] < ftol, e
+    assert e["dVdl"] < 1e-4, e
+    assert e["E"] < 1e-4, e
+
+
+def test_open_fmm_depth3_ragged():
+    """Several levels of far field, empty leaves, a ragged leaf population."""
+    s = synth.open_uniform(seed=4, n=5003, L=6.0, n_sites=12, site_size=5)
+    ref = oracle_ref(s)
+    e = errors(run_gpu(s, p=10, depth=3), ref)
+    assert e["F"] < 1e-4 and e["dVdl"] < 1e-4 and e["E"] < 1e-4, e
+
+
+# ---------------------------------------------------------------- periodic FMM
+@pytest.mark.parametrize("neutral", [True, False])
+def test_periodic_fmm_small(neutral):
+    s = synth.periodic_uniform(seed=3, n=2000, L=3.0, n_sites=8, site_size=4, neutral=neutral, p=8, depth=3)
+    ref = oracle_ref(s)
+    e = errors(run_gpu(s), ref)
+    assert e["F"] < 2e-4 and e["dVdl"] < 1e-4 and e["E"] < 1e-4, e
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2])
+def test_periodic_shallow_trees(depth):
+    s = synth.periodic_uniform(seed=8, n=300, L=1.7, n_sites=3, site_size=4, neutral=False, p=10, depth=depth)
+    ref = oracle_ref(s)
+    e = errors(run_gpu(s), ref)
+    assert e["F"] < 1e-4 and e["dVdl"] < 1e-4 and e["E"] < 1e-4, e
+
+
+def test_periodic_single_charge_wigner():
+    s = synth.periodic_uniform(seed=0, n=1, L=2.0, n_sites=0, site_size=1, neutral=False, p=8, depth=2)
+    s["qA"][:] = 1.0
+    s["qB"][:] = 1.0
+    g = run_gpu(s)
+    E_ref = 0.5 * oracle.KE_DEFAULT * (-2.8372974794) / 2.0
+    assert g["E"] == pytest.approx(E_ref, rel=1e-5)
+    assert np.abs(g["F"]).max() < 1e-4
+
+
+def test_periodic_nacl_madelung():
+    a = 0.5640
+    base = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    na = np.concatenate([base + [i, j, k] for i in range(4) for j in range(4) for k in range(4)]) * a
+    x = np.concatenate([na, na + [0.5 * a, 0, 0]]).astype(np.float32)
+    q = np.concatenate([np.ones(len(na)), -np.ones(len(na))]).astype(np.float32)
+    s = {"name": "nacl", "x": x, "qA": q, "qB": q.copy(), "site": np.full(len(q), -1, np.int32),
+         "lam": np.zeros(0, np.float32), "L": 4 * a, "origin": (0.0, 0.0, 0.0), "periodic": True, "p": 10, "depth": 3}
+    g = run_gpu(s)
+    M = -g["E"] / oracle.KE_DEFAULT * (a / 2) / (len(q) / 2)
+    assert M == pytest.approx(1.747565, abs=2e-5)
+
+
+@pytest.mark.slow
+def test_periodic_solvated_30k():
+    s = synth.solvated_30k()
+    ref = oracle_ref(s, tol=1e-9)
+    g = run_gpu(s)
+    e = errors(g, ref)
+    assert e["F"] < 2e-4 and e["dVdl"] < 1e-4 and e["E"] < 1e-4, e
+    assert g["status"] == 0
+
+
+# ---------------------------------------------------------------- API behaviour
+def test_deterministic_bitwise():
+    s = synth.periodic_uniform(seed=3, n=4000, L=3.0, p=8, depth=3)
+    f, d = make_solver(s)
+    a = f.eval(d["x"], phi=True)
+    b = f.eval(d["x"], phi=True)
+    torch.cuda.synchronize()
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+    f.close()
+
+
+def test_eval_host_matches_device():
+    s = synth.periodic_uniform(seed=6, n=3000, L=3.0, p=8, depth=3)
+    f, d = make_solver(s)
+    E, F, dV, _ = f.eval(d["x"])
+    torch.cuda.synchronize()
+    xh = torch.from_numpy(s["x"]).pin_memory()
+    Eh = torch.empty(1, dtype=torch.float64).pin_memory()
+    Fh = torch.empty(len(s["x"]), 3).pin_memory()
+    dVh = torch.empty(len(s["lam"])).pin_memory()
+    f.eval_host(xh, Eh, Fh, dVh)
+    assert Eh.item() == E.item()
+    assert torch.equal(Fh, F.cpu()) and torch.equal(dVh, dV.cpu())
+    f.close()
+
+
+def test_open_domain_error_is_reported():
+    s = synth.small_open()
+    s["x"][5] = [4.5, 1.0, 1.0]
+    f, d = make_solver(s)
+    f.eval(d["x"])
+    assert f.status_word() & 1
+    assert f.status_word() == 0  # cleared by the read
+    f.close()
+
+
+def test_set_lambda_changes_only_charges():
+    s = synth.small_open()
+    f, d = make_solver(s)
+    lam2 = torch.rand_like(d["lam"])
+    f.set_lambda(lam2)
+    E, F, dV, _ = f.eval(d["x"])
+    s2 = dict(s, lam=lam2.cpu().numpy())
+    ref = oracle.evaluate(s2)
+    e = errors({"E": E.item(), "F": F.cpu().numpy(), "dVdl": dV.cpu().numpy()}, ref)
+    assert e["F"] < 2e-4 and e["dVdl"] < 1e-4, e
+    f.close()
+
+
+def test_bad_arguments_rejected_on_host():
+    from paper_2410_01626_b300 import FMM, FmmError
+    with pytest.raises(FmmError):
+        FMM(-1.0, False, 8, 2)
+    with pytest.raises(FmmError):
+        FMM(1.0, False, 0, 2)
+    with pytest.raises(FmmError):
+        FMM(1.0, False, 8, 9)
+    f = FMM(1.0, False, 4, 1)
+    q = torch.zeros(3, device="cuda")
+    with pytest.raises(FmmError):
+        f.set_charges(q, q, torch.tensor([0, 5, -1], dtype=torch.int32, device="cuda"), torch.zeros(2, device="cuda"))
+    with pytest.raises(FmmError):  # eval before charges
+        f.eval_into(torch.zeros(0, 3, device="cuda"), torch.zeros(1, dtype=torch.float64, device="cuda"))
+    f.close()
