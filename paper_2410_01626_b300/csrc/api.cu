@@ -169,6 +169,10 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     h.ke = ke;
     h.s_bin = std::ldexp(1.0, depth) / box->edge;
     h.lmin = periodic ? 1 : 2;
+    if (precision != FMM_FP32 && !m2l_tc_supported(&h)) {  // no silent fallback to another precision
+        delete H;
+        return FMM_ERR_ARG;
+    }
     upload_constants(p);
     configure_kernels(ncoef_padded(p));
 

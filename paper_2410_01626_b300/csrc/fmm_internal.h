@@ -89,6 +89,7 @@ int launches_per_eval(const Handle* h);
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi,
                     const float* dVdl, float* gx, float* gqA, float* gqB, float* glam,
                     cudaStream_t st);
-void launch_site_csr(Handle* h, cudaStream_t st);
+bool m2l_tc_supported(const Handle* h);  // m2l_tc.cu
+void launch_m2l_tc(Handle* h, cudaStream_t st);
 
 }  // namespace fmmcph

@@ -782,8 +782,6 @@ static void launch_near(const NearParams& a, cudaStream_t st) {
         default: break;                     \
     }
 
-bool m2l_tc_supported(const Handle* h);
-void launch_m2l_tc(Handle* h, cudaStream_t st);
 
 static inline int sort_passes(int depth) { return (3 * depth + 7) / 8; }
 

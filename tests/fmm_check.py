@@ -4,6 +4,8 @@ system and compare it with the FP64 oracle.
 Error metrics (relative): E |dE|/|E|; F sqrt(sum |dF|^2 / sum |F|^2) over the
 compared atoms; dV/dlambda ||d||_2 / ||ref||_2 over sites.
 """
+import hashlib
+
 import numpy as np
 import torch
 
@@ -55,8 +57,17 @@ def errors(gpu, ref, idx=None):
 _cache = {}
 
 
-def oracle_ref(s, key=None, targets=None, tol=1e-11):
-    k = key or (s["name"], None if targets is None else len(targets), tol)
+def system_digest(s):
+    h = hashlib.sha1()
+    for k in ("x", "qA", "qB", "site", "lam"):
+        h.update(np.ascontiguousarray(s[k]).tobytes())
+    h.update(repr((s["L"], s["origin"], s["periodic"])).encode())
+    return h.hexdigest()
+
+
+def oracle_ref(s, targets=None, tol=1e-11):
+    t = None if targets is None else hashlib.sha1(np.asarray(targets, np.int64).tobytes()).hexdigest()
+    k = (system_digest(s), t, tol)
     if k not in _cache:
         _cache[k] = oracle.evaluate(s, targets=targets, tol=tol)
     return _cache[k]
