@@ -107,13 +107,16 @@ def test_periodic_shallow_trees(depth):
     assert e["F"] < 1e-4 and e["dVdl"] < 1e-4 and e["E"] < 1e-4, e
 
 
-def test_periodic_single_charge_wigner():
-    s = synth.periodic_uniform(seed=0, n=1, L=2.0, n_sites=0, site_size=1, neutral=False, p=8, depth=2)
+@pytest.mark.parametrize("p,tol", [(8, 5e-5), (12, 5e-6)])
+def test_periodic_single_charge_wigner(p, tol):
+    """One charge and its images: E = k q^2 xi / (2L).  A wrong background or
+    self-image convention is an O(1) error; what remains is FMM truncation."""
+    s = synth.periodic_uniform(seed=0, n=1, L=2.0, n_sites=0, site_size=1, neutral=False, p=p, depth=2)
     s["qA"][:] = 1.0
     s["qB"][:] = 1.0
     g = run_gpu(s)
     E_ref = 0.5 * oracle.KE_DEFAULT * (-2.8372974794) / 2.0
-    assert g["E"] == pytest.approx(E_ref, rel=1e-5)
+    assert g["E"] == pytest.approx(E_ref, rel=tol)
     assert np.abs(g["F"]).max() < 1e-4
 
 
