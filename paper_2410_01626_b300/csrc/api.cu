@@ -182,6 +182,8 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     {
         std::vector<double> op((size_t)nc * nc);
         std::vector<float> T((size_t)kNumOps * ncp * ncp, 0.f);
+        std::vector<float> Trm;  // output-major copy for the tensor-core layout
+        if (precision != FMM_FP32) Trm.assign((size_t)kNumOps * nc * nc, 0.f);
         for (int ox = -3; ox <= 3; ++ox)
             for (int oy = -3; oy <= 3; ++oy)
                 for (int oz = -3; oz <= 3; ++oz) {
@@ -191,6 +193,9 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
                     float* dst = T.data() + (size_t)op_index(ox, oy, oz) * ncp * ncp;
                     for (int j = 0; j < nc; ++j)
                         for (int k = 0; k < nc; ++k) dst[(size_t)k * ncp + j] = (float)op[(size_t)j * nc + k];
+                    if (!Trm.empty())
+                        for (size_t e = 0; e < (size_t)nc * nc; ++e)
+                            Trm[(size_t)op_index(ox, oy, oz) * nc * nc + e] = (float)op[e];
                 }
         std::vector<float> A((size_t)8 * ncp * ncp, 0.f), B((size_t)8 * ncp * ncp, 0.f);
         std::vector<double> Ad((size_t)8 * nc * nc);
@@ -221,6 +226,21 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
                 return st;
             }
             cudaMemcpy(h.Lam, op.data(), sizeof(double) * op.size(), cudaMemcpyHostToDevice);
+        }
+        if (!Trm.empty()) {
+            h.lvl_off.assign(depth + 2, 0);
+            long a2 = 0;
+            for (int l = 0; l <= depth; ++l) {
+                h.lvl_off[l] = a2;
+                a2 += 1L << (3 * l);
+            }
+            const int e = m2l_tc_setup(&h, Trm);
+            if (e != FMM_OK) {
+                m2l_tc_free(&h);
+                free_all(h);
+                delete H;
+                return (fmm_status)e;
+            }
         }
     }
     // ---- tree storage and work lists ----
@@ -468,6 +488,7 @@ int fmm_launches_per_eval(const fmm_handle* H) { return H ? launches_per_eval(&H
 void fmm_destroy(fmm_handle* H) {
     if (!H) return;
     cudaDeviceSynchronize();
+    m2l_tc_free(&H->h);
     free_all(H->h);
     delete H;
 }

@@ -78,6 +78,7 @@ struct Handle {
     float* hdV_dev = nullptr;
     double* hE_dev = nullptr;
     int host_cap = 0;
+    void* tc = nullptr;  // tensor-core M2L state (m2l_tc.cu)
 };
 
 // kernels.cu
@@ -89,7 +90,11 @@ int launches_per_eval(const Handle* h);
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi,
                     const float* dVdl, float* gx, float* gqA, float* gqB, float* glam,
                     cudaStream_t st);
-bool m2l_tc_supported(const Handle* h);  // m2l_tc.cu
+// m2l_tc.cu
+bool m2l_tc_supported(const Handle* h);
+int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor);  // [343][nc][nc], output-major
+void m2l_tc_free(Handle* h);
+int m2l_tc_launches(const Handle* h);
 void launch_m2l_tc(Handle* h, cudaStream_t st);
 
 }  // namespace fmmcph

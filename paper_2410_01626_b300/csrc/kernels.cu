@@ -795,7 +795,7 @@ int launches_per_eval(const Handle* h) {
     const int lmin = h->periodic ? 1 : 2;
     if (d >= lmin) n += d - lmin;  // M2M parent levels d-1 .. lmin
     if (h->periodic) n += 2;       // root + lattice
-    if (d >= lmin) n += 1;         // M2L
+    if (d >= lmin) n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? m2l_tc_launches(h) : 1;  // M2L
     if (d >= lmin) n += d - lmin + (h->periodic ? 1 : 0);  // L2L
     n += 1 /*near*/ + 1 /*final*/;
     return n;

@@ -117,7 +117,8 @@ def test_periodic_single_charge_wigner(p, tol):
     g = run_gpu(s)
     E_ref = 0.5 * oracle.KE_DEFAULT * (-2.8372974794) / 2.0
     assert g["E"] == pytest.approx(E_ref, rel=tol)
-    assert np.abs(g["F"]).max() < 1e-4
+    # the exact force vanishes by symmetry; compare with the natural scale k q^2 / L^2
+    assert np.abs(g["F"]).max() < 20 * tol * oracle.KE_DEFAULT / 2.0 ** 2
 
 
 def test_periodic_nacl_madelung():
@@ -208,3 +209,26 @@ def test_bad_arguments_rejected_on_host():
     with pytest.raises(FmmError):  # eval before charges
         f.eval_into(torch.zeros(0, 3, device="cuda"), torch.zeros(1, dtype=torch.float64, device="cuda"))
     f.close()
+
+
+# ---------------------------------------------------------------- tensor-core M2L (TF32)
+@pytest.mark.parametrize("periodic,p,depth", [(True, 8, 3), (True, 10, 3), (False, 8, 2), (False, 10, 4), (True, 10, 1)])
+def test_tf32_m2l_parity(periodic, p, depth):
+    """TF32 operands (rounded to nearest) with FP32 accumulation: forces stay within
+    1e-4 of the oracle; the potential (E, dV/dlambda) carries the operand rounding
+    (2^-11 relative per operand), measured at about 1e-3 and bounded here by 5e-3."""
+    if periodic:
+        s = synth.periodic_uniform(seed=3, n=3000, L=3.0, n_sites=8, site_size=4, p=p, depth=depth)
+    else:
+        s = synth.open_uniform(seed=5, n=3000, L=5.0, n_sites=8, site_size=4, p=p, depth=depth)
+    ref = oracle_ref(s)
+    g = run_gpu(s, precision="tf32")
+    e = errors(g, ref)
+    assert g["status"] == 0
+    assert e["F"] < 1e-4 and e["E"] < 5e-3 and e["dVdl"] < 5e-3, e
+
+
+def test_tf32_mode_unavailable_is_refused():
+    from paper_2410_01626_b300 import FMM, FmmError
+    with pytest.raises(FmmError):
+        FMM(1.0, True, 12, 3, precision="tf32")  # 169 coefficients exceed one 128-row MMA
