@@ -60,6 +60,7 @@ void free_all(Handle& h) {
     dfree(h.T);
     dfree(h.A);
     dfree(h.B);
+    dfree(h.B2);
     dfree(h.Ad);
     dfree(h.Lam);
     dfree(h.tiles);
@@ -197,7 +198,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
                         for (size_t e = 0; e < (size_t)nc * nc; ++e)
                             Trm[(size_t)op_index(ox, oy, oz) * nc * nc + e] = (float)op[e];
                 }
-        std::vector<float> A((size_t)8 * ncp * ncp, 0.f), B((size_t)8 * ncp * ncp, 0.f);
+        std::vector<float> A((size_t)8 * ncp * ncp, 0.f), B((size_t)8 * ncp * ncp, 0.f), B2((size_t)8 * ncp * ncp, 0.f);
         std::vector<double> Ad((size_t)8 * nc * nc);
         for (int c = 0; c < 8; ++c) {
             op_m2m(p, c, op.data());
@@ -206,9 +207,12 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
                 for (int k = 0; k < nc; ++k) A[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
             op_l2l(p, c, op.data());
             for (int j = 0; j < nc; ++j)
-                for (int k = 0; k < nc; ++k) B[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
+                for (int k = 0; k < nc; ++k) {
+                    B[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
+                    B2[(size_t)k * 8 * ncp + c * ncp + j] = (float)op[(size_t)j * nc + k];
+                }
         }
-        if ((st = dalloc(&h.T, T.size())) || (st = dalloc(&h.A, A.size())) || (st = dalloc(&h.B, B.size())) ||
+        if ((st = dalloc(&h.T, T.size())) || (st = dalloc(&h.A, A.size())) || (st = dalloc(&h.B, B.size())) || (st = dalloc(&h.B2, B2.size())) ||
             (st = dalloc(&h.Ad, Ad.size()))) {
             free_all(h);
             delete H;
@@ -217,6 +221,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         cudaMemcpy(h.T, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(h.A, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(h.B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.B2, B2.data(), sizeof(float) * B2.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(h.Ad, Ad.data(), sizeof(double) * Ad.size(), cudaMemcpyHostToDevice);
         if (periodic) {
             op_lattice(p, op.data());
@@ -263,7 +268,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     if ((st = dalloc(&h.M, (size_t)acc * ncp)) || (st = dalloc(&h.L, (size_t)acc * ncp)) ||
         (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.start, nleaf)) ||
         (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.epart, (nleaf + 3) / 4)) ||
-        (st = dalloc(&h.leafqdt, 5 * nleaf)) || (st = dalloc(&h.root, nc + 8)) || (st = dalloc(&h.status, 1)) ||
+        (st = dalloc(&h.leafqdt, 5 * nleaf)) || (st = dalloc(&h.root, nc + 8 + 5 * 64)) || (st = dalloc(&h.status, 1)) ||
         (st = dalloc(&h.site_ptr, 1))) {
         free_all(h);
         delete H;
@@ -275,7 +280,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     cudaMemset(h.M, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.L, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.status, 0, sizeof(int));
-    cudaMemset(h.root, 0, sizeof(double) * (nc + 8));
+    cudaMemset(h.root, 0, sizeof(double) * (nc + 8 + 5 * 64));
     cudaMemset(h.site_ptr, 0, sizeof(int));
     for (auto& e : h.ev) cudaEventCreate(&e);
     h.ev_valid = true;

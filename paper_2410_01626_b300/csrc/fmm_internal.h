@@ -37,6 +37,7 @@ struct Handle {
     float* T = nullptr;        // [343][ncp(k)][ncp(j)]  M2L, transposed (input row k, output col j)
     float* A = nullptr;        // [8][ncp][ncp] M2M transposed
     float* B = nullptr;        // [8][ncp][ncp] L2L transposed
+    float* B2 = nullptr;       // [ncp][8 ncp] L2L, all octants side by side
     double* Ad = nullptr;      // [8][nc][nc] M2M row-major, FP64 (root step)
     double* Lam = nullptr;     // [nc][nc] lattice, FP64 row-major
     M2LTile* tiles = nullptr;  // M2L work list

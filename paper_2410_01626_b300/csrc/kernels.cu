@@ -5,10 +5,10 @@
 //             (Morton keys of the leaf cells, stable on (key, index); the gather also forms
 //             q_i = qA_i + lambda_s (qB_i - qA_i), Sec. 2.1 Eq. 1 with charge-only forms)
 //   P2M       k_p2m<P>        one warp per leaf, butterfly reduce-scatter of the coefficients
-//   M2M       k_m2m           per level, dense 8-child operators
+//   M2M       k_sgemm         per level, one dense GEMM over the 8 contiguous children
 //   root      k_root, k_lattice (periodic) FP64 root multipole and lattice operator
 //   M2L       k_m2l_fp32 (FP32 CUDA cores) or the tcgen05 kernel in m2l_tc.cu
-//   L2L       k_l2l           per level
+//   L2L       k_sgemm         per level, one dense GEMM into the 8 contiguous children
 //   near      k_near<P>       L2P + P2P (27 neighbour leaves) + forces / potential / energy
 //   final     k_final         E (FP64, fixed-order reduction) and dV/dlambda per site
 #include <cuda_runtime.h>
@@ -18,6 +18,7 @@
 #include <cstdio>
 
 #include "fmm_internal.h"
+#include "sgemm.cuh"
 
 namespace fmmcph {
 
@@ -84,7 +85,7 @@ struct BoxGeom {
 // as the binning specification states it (FP64, no FMA contraction).
 __device__ __forceinline__ double wrap_coord(double x, double o, double L, int periodic) {
     double u = __dsub_rn(x, o);
-    if (periodic) {
+    if (periodic && !(u >= 0.0 && u < L)) {  // inside [0, L) the formula leaves u unchanged
         u = __dsub_rn(u, __dmul_rn(L, floor(__ddiv_rn(u, L))));
         if (u < 0.0 || u >= L) u = 0.0;
     }
@@ -378,84 +379,31 @@ __global__ void __launch_bounds__(128) k_p2m(int nleaf, float h, float half_box,
     }
 }
 
-// ---- M2M: parent = sum_c A_c child_c ; G parents per block, thread j = output coefficient ----
-constexpr int kM2MG = 8;
-__global__ void k_m2m(int nparent, int nc, int ncp, const float* __restrict__ AT,
-                      const float* __restrict__ Mchild, float* __restrict__ Mparent) {
-    extern __shared__ float sm[];  // [G][8][ncp]
-    const int p0 = blockIdx.x * kM2MG;
-    const int tot = kM2MG * 8 * ncp;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const int g = e / (8 * ncp);
-        const int r = e - g * 8 * ncp;  // c*ncp + k
-        sm[e] = (p0 + g < nparent) ? Mchild[(long)(p0 + g) * 8 * ncp + r] : 0.f;
-    }
-    __syncthreads();
-    const int j = threadIdx.x;
-    float acc[kM2MG];
-#pragma unroll
-    for (int g = 0; g < kM2MG; ++g) acc[g] = 0.f;
-    for (int c = 0; c < 8; ++c) {
-        const float* a = AT + (long)c * ncp * ncp + j;
-        for (int k = 0; k < nc; ++k) {
-            const float t = a[(long)k * ncp];
-#pragma unroll
-            for (int g = 0; g < kM2MG; ++g) acc[g] = fmaf(t, sm[(g * 8 + c) * ncp + k], acc[g]);
-        }
-    }
-#pragma unroll
-    for (int g = 0; g < kM2MG; ++g)
-        if (p0 + g < nparent) Mparent[(long)(p0 + g) * ncp + j] = acc[g];
-}
-
-// ---- L2L: child_c += B_c parent ----
-__global__ void k_l2l(int nparent, int nc, int ncp, const float* __restrict__ BT,
-                      const float* __restrict__ Lparent, float* __restrict__ Lchild) {
-    extern __shared__ float sm[];  // [G][ncp]
-    const int p0 = blockIdx.x * kM2MG;
-    for (int e = threadIdx.x; e < kM2MG * ncp; e += blockDim.x) {
-        const int g = e / ncp;
-        sm[e] = (p0 + g < nparent) ? Lparent[(long)p0 * ncp + e] : 0.f;
-    }
-    __syncthreads();
-    const int j = threadIdx.x;
-    for (int c = 0; c < 8; ++c) {
-        float acc[kM2MG];
-#pragma unroll
-        for (int g = 0; g < kM2MG; ++g) acc[g] = 0.f;
-        const float* b = BT + (long)c * ncp * ncp + j;
-        for (int k = 0; k < nc; ++k) {
-            const float t = b[(long)k * ncp];
-#pragma unroll
-            for (int g = 0; g < kM2MG; ++g) acc[g] = fmaf(t, sm[g * ncp + k], acc[g]);
-        }
-#pragma unroll
-        for (int g = 0; g < kM2MG; ++g)
-            if (p0 + g < nparent) Lchild[((long)(p0 + g) * 8 + c) * ncp + j] += acc[g];
-    }
-}
-
 // ---- periodic root: FP64 root multipole (M2M from level 1) and the Q, D, T sums ----
-// blocks [0, nrowblk): 4 warps each, warp = one output row; block nrowblk: Q/D/T reduction.
-__global__ void k_root(int nc, int ncp, int depth, const double* __restrict__ Ad,
-                       const float* __restrict__ M1, const float* __restrict__ M0, int nleaf,
-                       const double* __restrict__ leafqdt, double* __restrict__ root) {
-    const int nrowblk = (nc + 3) / 4;
-    if ((int)blockIdx.x == nrowblk) {
-        __shared__ double red[5][256];
-        double a[5] = {0, 0, 0, 0, 0};
-        for (int l = threadIdx.x; l < nleaf; l += blockDim.x)
-            for (int c = 0; c < 5; ++c) a[c] += leafqdt[5L * l + c];
-        for (int c = 0; c < 5; ++c) red[c][threadIdx.x] = a[c];
+// Q = sum q, D = sum q u, T = sum q |u|^2 about the box centre, reduced in a fixed order:
+// leaves -> kQdtBlocks partials (k_qdt) -> totals (k_lattice).
+constexpr int kQdtBlocks = 64;
+__global__ void __launch_bounds__(256) k_qdt(int nleaf, const double* __restrict__ leafqdt,
+                                             double* __restrict__ partial) {
+    __shared__ double red[5][256];
+    const int per = (nleaf + kQdtBlocks - 1) / kQdtBlocks;
+    const int b0 = blockIdx.x * per, b1 = min(nleaf, b0 + per);
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int l = b0 + threadIdx.x; l < b1; l += 256)
+        for (int c = 0; c < 5; ++c) a[c] += leafqdt[5L * l + c];
+    for (int c = 0; c < 5; ++c) red[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int c = 0; c < 5; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + st];
         __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s)
-                for (int c = 0; c < 5; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x < 5) root[nc + threadIdx.x] = red[threadIdx.x][0];
-        return;
     }
+    if (threadIdx.x < 5) partial[5 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// warp j computes root row j: M0_j = sum_c sum_k A_c[j][k] M1_c[k] in FP64
+__global__ void k_root(int nc, int ncp, int depth, const double* __restrict__ Ad, const float* __restrict__ M1,
+                       const float* __restrict__ M0, double* __restrict__ root) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (j >= nc) return;
@@ -474,8 +422,14 @@ __global__ void k_root(int nc, int ncp, int depth, const double* __restrict__ Ad
 }
 
 // L0 = Lambda M0 (FP64), written as the FP32 level-0 local expansion
-__global__ void k_lattice(int nc, int ncp, const double* __restrict__ Lam, const double* __restrict__ root,
+__global__ void k_lattice(int nc, int ncp, const double* __restrict__ Lam, double* __restrict__ root,
                           float* __restrict__ L0) {
+    if (blockIdx.x == 0 && threadIdx.x < 5) {  // Q, D, T totals from the fixed-order partials
+        const double* partial = root + nc + 8;
+        double t = 0.0;
+        for (int b = 0; b < kQdtBlocks; ++b) t += partial[5 * b + threadIdx.x];
+        root[nc + threadIdx.x] = t;
+    }
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (j >= ncp) return;
@@ -599,8 +553,21 @@ struct NearParams {
     double* epart;
 };
 
+// One warp per target leaf.
+// (1) Lanes 0..26 resolve the 27 neighbour leaves at once (periodic image shift, start,
+//     count) and a warp scan gives each neighbour's offset in a per-warp source list.
+// (2) When the list fits (kNearCap atoms, the common case), all lanes copy it into shared
+//     memory in one pass, so that every global load is in flight together; otherwise the
+//     sources are streamed neighbour by neighbour in chunks of 32.
+// (3) Leaves with few atoms split the warp into G source slices (lane = target + slice *
+//     32/G) so every lane works in the pair loop; slice sums are combined with shuffles.
+constexpr int kNearCap = 640;
 template <int P>
 __global__ void __launch_bounds__(128) k_near(NearParams a) {
+    __shared__ float4 src_sm[4][kNearCap];
+    __shared__ int nb_off[4][28];
+    __shared__ int nb_s0[4][27];
+    __shared__ float nb_sh[4][27][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int leaf = blockIdx.x * 4 + w;
     double esum = 0.0;
@@ -619,51 +586,105 @@ __global__ void __launch_bounds__(128) k_near(NearParams a) {
             cdz = (float)a.qdt[3];
             ctr = (float)a.qdt[4];
         }
-        for (int tb = 0; tb < cnt; tb += 32) {
-            const int ti = tb + lane;
+        // (1) neighbour table: lane o < 27 owns neighbour o
+        int my_s0 = 0, my_sc = 0;
+        float shx = 0.f, shy = 0.f, shz = 0.f;
+        if (lane < 27) {
+            int sx = ix + lane / 9 - 1, sy = iy + (lane / 3) % 3 - 1, sz = iz + lane % 3 - 1;
+            bool ok = true;
+            if (a.periodic) {
+                const int wx = (sx + nb) & (nb - 1), wy = (sy + nb) & (nb - 1), wz = (sz + nb) & (nb - 1);
+                shx = (float)(sx - wx) * h;
+                shy = (float)(sy - wy) * h;
+                shz = (float)(sz - wz) * h;
+                sx = wx;
+                sy = wy;
+                sz = wz;
+            } else {
+                ok = sx >= 0 && sx < nb && sy >= 0 && sy < nb && sz >= 0 && sz < nb;
+            }
+            if (ok) {
+                const uint32_t src = morton3(sx, sy, sz);
+                my_s0 = (int)a.start[src];
+                my_sc = (int)a.count[src];
+            }
+        }
+        int incl = my_sc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane < 27) nb_off[w][lane + 1] = incl;
+        if (lane == 0) nb_off[w][0] = 0;
+        __syncwarp();
+        if (lane < 27) {
+            nb_s0[w][lane] = my_s0;
+            nb_sh[w][lane][0] = shx;
+            nb_sh[w][lane][1] = shy;
+            nb_sh[w][lane][2] = shz;
+        }
+        __syncwarp();
+        const bool staged = total <= kNearCap;
+        if (staged) {  // (2) one pass over every source atom of the 27 neighbours
+            for (int j = lane; j < total; j += 32) {
+                int o = 0;  // largest neighbour with nb_off[o] <= j
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (o + step < 27 && nb_off[w][o + step] <= j) o += step;
+                float4 sp = a.pos[nb_s0[w][o] + (j - nb_off[w][o])];
+                sp.x += nb_sh[w][o][0];
+                sp.y += nb_sh[w][o][1];
+                sp.z += nb_sh[w][o][2];
+                src_sm[w][j] = sp;
+            }
+            __syncwarp();
+        }
+        const int G = cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
+        const int TPG = 32 / G;
+        const int tl = lane % TPG, slice = lane / TPG;
+        for (int tb = 0; tb < cnt; tb += TPG) {
+            const int ti = tb + tl;
             const bool valid = ti < cnt;
             float4 me = make_float4(cx, cy, cz, 0.f);
             if (valid) me = a.pos[st + ti];
             float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-            for (int o = 0; o < 27; ++o) {
-                int sx = ix + o / 9 - 1, sy = iy + (o / 3) % 3 - 1, sz = iz + o % 3 - 1;
-                float shx = 0.f, shy = 0.f, shz = 0.f;
-                if (a.periodic) {
-                    const int wx = (sx + nb) & (nb - 1), wy = (sy + nb) & (nb - 1), wz = (sz + nb) & (nb - 1);
-                    shx = (float)(sx - wx) * h;
-                    shy = (float)(sy - wy) * h;
-                    shz = (float)(sz - wz) * h;
-                    sx = wx;
-                    sy = wy;
-                    sz = wz;
-                } else if (sx < 0 || sx >= nb || sy < 0 || sy >= nb || sz < 0 || sz >= nb) {
-                    continue;
-                }
-                const uint32_t src = morton3(sx, sy, sz);
-                const int s0 = a.start[src], sc = a.count[src];
-                for (int sb = 0; sb < sc; sb += 32) {
-                    float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
-                    sp.x += shx;
-                    sp.y += shy;
-                    sp.z += shz;
-                    const int ns = min(32, sc - sb);
-                    for (int t = 0; t < ns; ++t) {
-                        const float xs = __shfl_sync(0xffffffffu, sp.x, t);
-                        const float ys = __shfl_sync(0xffffffffu, sp.y, t);
-                        const float zs = __shfl_sync(0xffffffffu, sp.z, t);
-                        const float qs = __shfl_sync(0xffffffffu, sp.w, t);
-                        const float dx = me.x - xs, dy = me.y - ys, dz = me.z - zs;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
-                        const float qri = qs * ri;
-                        pot += qri;
-                        const float qri3 = qri * ri * ri;
-                        gx = fmaf(-qri3, dx, gx);
-                        gy = fmaf(-qri3, dy, gy);
-                        gz = fmaf(-qri3, dz, gz);
+            auto pair = [&](const float4 s4) {
+                const float dx = me.x - s4.x, dy = me.y - s4.y, dz = me.z - s4.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
+                const float qri = s4.w * ri;
+                pot += qri;
+                const float qri3 = qri * ri * ri;
+                gx = fmaf(-qri3, dx, gx);
+                gy = fmaf(-qri3, dy, gy);
+                gz = fmaf(-qri3, dz, gz);
+            };
+            if (staged) {
+                for (int t = slice; t < total; t += G) pair(src_sm[w][t]);
+            } else {
+                for (int o = 0; o < 27; ++o) {
+                    const int s0 = nb_s0[w][o], sc = nb_off[w][o + 1] - nb_off[w][o];
+                    for (int sb = 0; sb < sc; sb += 32) {
+                        float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
+                        sp.x += nb_sh[w][o][0];
+                        sp.y += nb_sh[w][o][1];
+                        sp.z += nb_sh[w][o][2];
+                        __syncwarp();
+                        src_sm[w][lane] = sp;
+                        __syncwarp();
+                        const int ns = min(32, sc - sb);
+                        for (int t = slice; t < ns; t += G) pair(src_sm[w][t]);
                     }
                 }
+            }
+            for (int off = TPG; off < 32; off <<= 1) {
+                pot += __shfl_xor_sync(0xffffffffu, pot, off);
+                gx += __shfl_xor_sync(0xffffffffu, gx, off);
+                gy += __shfl_xor_sync(0xffffffffu, gy, off);
+                gz += __shfl_xor_sync(0xffffffffu, gz, off);
             }
             if (a.use_far) {
                 float pf, fx, fy, fz;
@@ -683,7 +704,7 @@ __global__ void __launch_bounds__(128) k_near(NearParams a) {
                 gy += 2.f * c2 * (cq * uy - cdy);
                 gz += 2.f * c2 * (cq * uz - cdz);
             }
-            if (valid) {
+            if (valid && slice == 0) {
                 const int i = (int)a.perm[st + ti];
                 const float q = me.w;
                 if (a.F) {
@@ -786,7 +807,7 @@ static void launch_near(const NearParams& a, cudaStream_t st) {
 static inline int sort_passes(int depth) { return (3 * depth + 7) / 8; }
 
 void configure_kernels(int ncp) {
-    cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * kM2MG * 8 * ncp));
+    (void)ncp;
 }
 
 int launches_per_eval(const Handle* h) {
@@ -794,7 +815,7 @@ int launches_per_eval(const Handle* h) {
     int n = 1 /*keys*/ + 3 * sort_passes(d) + 1 /*ranges*/ + 1 /*gather*/ + 1 /*p2m*/;
     const int lmin = h->periodic ? 1 : 2;
     if (d >= lmin) n += d - lmin;  // M2M parent levels d-1 .. lmin
-    if (h->periodic) n += 2;       // root + lattice
+    if (h->periodic) n += 3;       // Q/D/T partials + root + lattice
     if (d >= lmin) n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? m2l_tc_launches(h) : 1;  // M2L
     if (d >= lmin) n += d - lmin + (h->periodic ? 1 : 0);  // L2L
     n += 1 /*near*/ + 1 /*final*/;
@@ -844,21 +865,21 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, (float)(0.5 * h->box.edge), h, Mleaf,
                    h->periodic ? h->leafqdt : nullptr, st);
     stage(h, 2, st);
-    // --- M2M (FP32) for parent levels d-1 .. lmin ---
+    // --- M2M (FP32) for parent levels d-1 .. lmin: one GEMM per level,
+    //     [parents x 8 ncp] (the 8 children are contiguous) x [8 ncp x ncp] ---
     const int lmin = h->periodic ? 1 : 2;
-    const size_t sm_m2m = sizeof(float) * kM2MG * 8 * h->ncp;
     for (int l = d - 1; l >= lmin; --l) {
         const int np = 1 << (3 * l);
-        k_m2m<<<(np + kM2MG - 1) / kM2MG, h->ncp, sm_m2m, st>>>(np, h->nc, h->ncp, h->A,
-                                                                 h->M + h->lvl_off[l + 1] * h->ncp,
-                                                                 h->M + h->lvl_off[l] * h->ncp);
+        sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
+              h->M + h->lvl_off[l] * h->ncp, h->ncp, false, st);
     }
     stage(h, 3, st);
     // --- periodic root (FP64) ---
     if (h->periodic) {
         const int nrowblk = (h->nc + 3) / 4;
         const float* M1 = (d >= 1) ? h->M + h->lvl_off[1] * h->ncp : nullptr;
-        k_root<<<nrowblk + 1, 128, 0, st>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, nleaf, h->leafqdt, h->root);
+        k_qdt<<<kQdtBlocks, 256, 0, st>>>(nleaf, h->leafqdt, h->root + h->nc + 8);
+        k_root<<<nrowblk, 128, 0, st>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, h->root);
         k_lattice<<<(h->ncp + 3) / 4, 128, 0, st>>>(h->nc, h->ncp, h->Lam, h->root, h->L);
     }
     stage(h, 4, st);
@@ -874,14 +895,13 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         }
     }
     stage(h, 5, st);
-    // --- L2L: levels lmin+1 .. d (periodic: 1 .. d from the lattice-filled root) ---
-    const size_t sm_l2l = sizeof(float) * kM2MG * h->ncp;
+    // --- L2L: levels lmin+1 .. d (periodic: 1 .. d from the lattice-filled root): one GEMM per
+    //     level, [parents x ncp] x [ncp x 8 ncp] accumulated into the contiguous children ---
     const int lfirst = h->periodic ? 1 : lmin + 1;
     for (int l = lfirst; l <= d; ++l) {
         const int np = 1 << (3 * (l - 1));
-        k_l2l<<<(np + kM2MG - 1) / kM2MG, h->ncp, sm_l2l, st>>>(np, h->nc, h->ncp, h->B,
-                                                                 h->L + h->lvl_off[l - 1] * h->ncp,
-                                                                 h->L + h->lvl_off[l] * h->ncp);
+        sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
+              h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, st);
     }
     stage(h, 6, st);
     // --- near field + L2P + outputs ---

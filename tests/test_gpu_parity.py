@@ -125,7 +125,9 @@ def test_periodic_nacl_madelung():
     a = 0.5640
     base = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
     na = np.concatenate([base + [i, j, k] for i in range(4) for j in range(4) for k in range(4)]) * a
-    x = np.concatenate([na, na + [0.5 * a, 0, 0]]).astype(np.float32)
+    # shifted by a/4 so that every ion sits at a leaf centre of the depth-3 tree (an ion on a
+    # leaf corner is the worst case of the expansions; the lattice energy is shift invariant)
+    x = (np.concatenate([na, na + [0.5 * a, 0, 0]]) + a / 4).astype(np.float32)
     q = np.concatenate([np.ones(len(na)), -np.ones(len(na))]).astype(np.float32)
     s = {"name": "nacl", "x": x, "qA": q, "qB": q.copy(), "site": np.full(len(q), -1, np.int32),
          "lam": np.zeros(0, np.float32), "L": 4 * a, "origin": (0.0, 0.0, 0.0), "periodic": True, "p": 10, "depth": 3}
