@@ -34,10 +34,16 @@ namespace {
 
 constexpr int kTcRows = 256;    // virtual rows (N) per CTA
 constexpr int kTcStages = 3;    // operator-chunk ring depth
-constexpr int kTcChunk = 32;    // input coefficients per K chunk (4 MMAs of K = 8)
-constexpr int kTcKG = kTcChunk / 4;
-constexpr uint32_t kTcTBytes = 128 * kTcChunk * 4;  // one operator chunk: 128 x 32 fp32
+constexpr uint32_t kTcTBytes = 16384;  // one ring stage: 128 rows x 32 coefficients (or hi+lo x 16)
 constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
+// K chunk (input coefficients per slab / operator chunk): 32 for TF32, 16 for the split
+// 3xTF32 form, whose hi and lo slabs then share the same shared memory.
+template <bool SPLIT>
+struct TcCfg {
+    static constexpr int kChunk = SPLIT ? 16 : 32;
+    static constexpr int kKG = kChunk / 4;
+    static constexpr uint32_t kPartBytes = 128u * kChunk * 4u;  // one operator part (hi or lo)
+};
 
 struct TcLevels {
     int n[kMaxDepth + 1];
@@ -61,7 +67,7 @@ __device__ __forceinline__ uint32_t spread3_tc(uint32_t v) {
 // Pack one level's multipoles into [class][kgroup][(n+2)^3 rows][4], rounded to TF32
 // (round to nearest: the tensor core itself would truncate).
 __global__ void k_m2l_pack(int n, int R, int NKG, int ncp, int periodic, const float* __restrict__ Mlev,
-                           float* __restrict__ Mtc) {
+                           float* __restrict__ Mtc, float* __restrict__ Mtc_lo) {
     const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long total = 8L * NKG * R;
     if (tid >= total) return;
@@ -70,7 +76,7 @@ __global__ void k_m2l_pack(int n, int R, int NKG, int ncp, int periodic, const f
     const int cls = (int)(tid / ((long)R * NKG));
     const int m2 = n + 2;
     int i = row / (m2 * m2) - 1, j = (row / m2) % m2 - 1, k = row % m2 - 1;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f), lo = v;
     bool ok = 4 * g < ncp;
     if (periodic) {
         i = (i + n) % n;
@@ -81,33 +87,53 @@ __global__ void k_m2l_pack(int n, int R, int NKG, int ncp, int periodic, const f
     }
     if (ok) {
         const uint32_t box = ((spread3_tc(i) | (spread3_tc(j) << 1) | (spread3_tc(k) << 2)) << 3) | (uint32_t)cls;
-        v = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + 4 * g);
-        v.x = tc::round_tf32(v.x);
-        v.y = tc::round_tf32(v.y);
-        v.z = tc::round_tf32(v.z);
-        v.w = tc::round_tf32(v.w);
+        const float4 x = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + 4 * g);
+        v.x = tc::round_tf32(x.x);
+        v.y = tc::round_tf32(x.y);
+        v.z = tc::round_tf32(x.z);
+        v.w = tc::round_tf32(x.w);
+        lo.x = tc::round_tf32(x.x - v.x);
+        lo.y = tc::round_tf32(x.y - v.y);
+        lo.z = tc::round_tf32(x.z - v.z);
+        lo.w = tc::round_tf32(x.w - v.w);
     }
     reinterpret_cast<float4*>(Mtc)[tid] = v;
+    if (Mtc_lo) reinterpret_cast<float4*>(Mtc_lo)[tid] = lo;
 }
 
 struct TcTile {
     int level, cls, r0, pad;
 };
 
-__global__ void __launch_bounds__(128, 1)
+// Warp roles (10 warps): warp 0 lane 0 = bulk-copy producer, warp 1 lane 0 = MMA issuer,
+// warps 2..9 = accumulator drains.  The tensor core aligns addends to the largest and
+// truncates, so a long chain of MMAs into one FP32 accumulator drifts; here each source
+// class pi is accumulated into one of two TMEM accumulators (ping-pong, 2 x 256 columns)
+// and then added by the drain warps into FP32 registers (round to nearest), which bounds
+// every tensor-core chain to one class (about 1/8 of the work).
+constexpr int kTcThreads = 320;
+constexpr int kTcDrainWarps = 8;
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const TcTile* __restrict__ tiles, TcLevels lv, const float* __restrict__ Mtc,
-             const float* __restrict__ Ttc, float* __restrict__ L, int ncp, int NKC, int slab_rows,
-             int* __restrict__ status) {
+             const float* __restrict__ Mtc_lo, const float* __restrict__ Ttc, float* __restrict__ L, int ncp,
+             int NKC, int slab_rows, int* __restrict__ status) {
+    using Cfg = TcCfg<SPLIT>;
+    constexpr int kTcChunk = Cfg::kChunk;
+    constexpr int kTcKG = Cfg::kKG;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* slab = smem;
-    uint8_t* tring = smem + (size_t)slab_rows * kTcKG * 16;
+    uint8_t* slab = smem;                                          // hi (or only) slab
+    uint8_t* slab_lo = smem + (size_t)slab_rows * kTcKG * 16;     // lo slab (SPLIT)
+    uint8_t* tring = smem + (size_t)slab_rows * kTcKG * 16 * (SPLIT ? 2 : 1);
     uint64_t* bars = reinterpret_cast<uint64_t*>(tring + (size_t)kTcStages * kTcTBytes);
     uint64_t* slab_full = bars + 0;
     uint64_t* slab_empty = bars + 1;
-    uint64_t* done = bars + 2;
-    uint64_t* t_full = bars + 3;
-    uint64_t* t_empty = bars + 3 + kTcStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 + 2 * kTcStages);
+    uint64_t* acc_full = bars + 2;               // [2]
+    uint64_t* acc_empty = bars + 4;              // [2]
+    uint64_t* t_full = bars + 6;                 // [kTcStages]
+    uint64_t* t_empty = bars + 6 + kTcStages;    // [kTcStages]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6 + 2 * kTcStages);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const TcTile tile = tiles[blockIdx.x];
@@ -121,7 +147,10 @@ __global__ void __launch_bounds__(128, 1)
     if (threadIdx.x == 0) {
         tc::mbar_init(slab_full, 1);
         tc::mbar_init(slab_empty, 1);
-        tc::mbar_init(done, 1);
+        for (int a2 = 0; a2 < 2; ++a2) {
+            tc::mbar_init(acc_full + a2, 1);
+            tc::mbar_init(acc_empty + a2, kTcDrainWarps);
+        }
         for (int s = 0; s < kTcStages; ++s) {
             tc::mbar_init(t_full + s, 1);
             tc::mbar_init(t_empty + s, 1);
@@ -129,8 +158,8 @@ __global__ void __launch_bounds__(128, 1)
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, kTcRows);
+    if (warp == 2) {
+        tc::tmem_alloc(tmem_slot, 2 * kTcRows);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -141,129 +170,178 @@ __global__ void __launch_bounds__(128, 1)
     const int slab_row0 = r0 - S;  // >= 0 by construction of the tile list
     const int rows_load = min(slab_rows, R - slab_row0);
     const float* Mlev = Mtc + lv.mtc_off[lev];
+    const float* Mlev_lo = SPLIT ? Mtc_lo + lv.mtc_off[lev] : nullptr;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- producer ----------------
-        int it = 0, tcount = 0;
-        bool ok = true;
-        for (int pi = 0; pi < 8 && ok; ++pi) {
-            const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-            for (int ch = 0; ch < NKC && ok; ++ch) {
-                if (it > 0 && !tc::mbar_wait(slab_empty, (it - 1) & 1, kWaitLimit)) {
-                    ok = false;
-                    break;
-                }
-                tc::mbar_arrive_expect_tx(slab_full, (uint32_t)rows_load * 16u * kTcKG);
-                for (int g = 0; g < kTcKG; ++g) {
-                    const float* src = Mlev + (((long)pi * NKG + ch * kTcKG + g) * R + slab_row0) * 4;
-                    tc::bulk_g2s(slab + (size_t)g * slab_rows * 16, src, (uint32_t)rows_load * 16u, slab_full);
-                }
-                ++it;
-                for (int d = 0; d < 27 && ok; ++d) {
-                    const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                    const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
-                    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                    const int s = tcount % kTcStages, u = tcount / kTcStages;
-                    if (u > 0 && !tc::mbar_wait(t_empty + s, (u - 1) & 1, kWaitLimit)) {
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer ----------------
+            int it = 0, tcount = 0;
+            bool ok = true;
+            for (int pi = 0; pi < 8 && ok; ++pi) {
+                const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
+                for (int ch = 0; ch < NKC && ok; ++ch) {
+                    if (it > 0 && (!tc::mbar_wait(slab_empty, (it - 1) & 1, kWaitLimit) || *abort_flag)) {
                         ok = false;
                         break;
                     }
-                    const int op = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
-                    tc::mbar_arrive_expect_tx(t_full + s, kTcTBytes);
-                    tc::bulk_g2s(tring + (size_t)s * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
-                                 kTcTBytes, t_full + s);
-                    ++tcount;
+                    tc::mbar_arrive_expect_tx(slab_full, (uint32_t)rows_load * 16u * kTcKG * (SPLIT ? 2u : 1u));
+                    for (int g = 0; g < kTcKG; ++g) {
+                        const long e = (((long)pi * NKG + ch * kTcKG + g) * R + slab_row0) * 4;
+                        tc::bulk_g2s(slab + (size_t)g * slab_rows * 16, Mlev + e, (uint32_t)rows_load * 16u,
+                                     slab_full);
+                        if (SPLIT)
+                            tc::bulk_g2s(slab_lo + (size_t)g * slab_rows * 16, Mlev_lo + e, (uint32_t)rows_load * 16u,
+                                         slab_full);
+                    }
+                    ++it;
+                    for (int d = 0; d < 27 && ok; ++d) {
+                        const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+                        const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
+                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                        const int s = tcount % kTcStages, u = tcount / kTcStages;
+                        if (u > 0 && (!tc::mbar_wait(t_empty + s, (u - 1) & 1, kWaitLimit) || *abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        const int op = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+                        tc::mbar_arrive_expect_tx(t_full + s, kTcTBytes);
+                        tc::bulk_g2s(tring + (size_t)s * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
+                                     kTcTBytes, t_full + s);  // hi (+ lo) operator chunk
+                        ++tcount;
+                    }
                 }
             }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicOr(status, FMM_DEV_TIMEOUT);
+            }
         }
-        if (!ok) {
-            *abort_flag = 1;
-            atomicOr(status, FMM_DEV_TIMEOUT);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        const uint32_t idesc = tc::idesc_tf32(128, kTcRows);
-        const uint32_t slab_a = tc::smem_u32(slab), ring_a = tc::smem_u32(tring);
-        const uint32_t kg_stride = (uint32_t)slab_rows * 16u;
-        int it = 0, tcount = 0;
-        uint32_t acc = 0;
-        bool ok = true;
-        for (int pi = 0; pi < 8 && ok; ++pi) {
-            const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-            for (int ch = 0; ch < NKC && ok; ++ch) {
-                if (!tc::mbar_wait(slab_full, it & 1, kWaitLimit) || *abort_flag) {
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = tc::idesc_tf32(128, kTcRows);
+            const uint32_t slab_a = tc::smem_u32(slab), slab_lo_a = tc::smem_u32(slab_lo),
+                           ring_a = tc::smem_u32(tring);
+            const uint32_t kg_stride = (uint32_t)slab_rows * 16u;
+            int it = 0, tcount = 0;
+            bool ok = true;
+            for (int pi = 0; pi < 8 && ok; ++pi) {
+                const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
+                const int ab = pi & 1;  // accumulator of this source class
+                const uint32_t dacc = tmem + (uint32_t)(ab * kTcRows);
+                if (pi >= 2 && (!tc::mbar_wait(acc_empty + ab, ((pi >> 1) - 1) & 1, kWaitLimit) || *abort_flag)) {
                     ok = false;
                     break;
                 }
-                ++it;
                 tc::fence_after_sync();
-                for (int d = 0; d < 27 && ok; ++d) {
-                    const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                    const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
-                    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                    const int s = tcount % kTcStages, u = tcount / kTcStages;
-                    if (!tc::mbar_wait(t_full + s, u & 1, kWaitLimit) || *abort_flag) {
+                uint32_t acc = 0;
+                for (int ch = 0; ch < NKC && ok; ++ch) {
+                    if (!tc::mbar_wait(slab_full, it & 1, kWaitLimit) || *abort_flag) {
                         ok = false;
                         break;
                     }
+                    ++it;
                     tc::fence_after_sync();
-                    const int shift = dx * m2 * m2 + dy * m2 + dz;
-                    const uint32_t b_row = (uint32_t)(S + shift) * 16u;
-                    const uint32_t a_base = ring_a + (uint32_t)s * kTcTBytes;
+                    for (int d = 0; d < 27 && ok; ++d) {
+                        const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+                        const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
+                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                        const int s = tcount % kTcStages, u = tcount / kTcStages;
+                        if (!tc::mbar_wait(t_full + s, u & 1, kWaitLimit) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const int shift = dx * m2 * m2 + dy * m2 + dz;
+                        const uint32_t b_row = (uint32_t)(S + shift) * 16u;
+                        const uint32_t a_base = ring_a + (uint32_t)s * kTcTBytes;
 #pragma unroll
-                    for (int ks = 0; ks < kTcChunk / 8; ++ks) {
-                        const uint64_t ad = tc::smem_desc_kmajor(a_base + ks * 2 * 2048u, 2048u, 128u);
-                        const uint64_t bd = tc::smem_desc_kmajor(slab_a + ks * 2 * kg_stride + b_row, kg_stride, 128u);
-                        tc::mma_tf32(tmem, ad, bd, idesc, acc);
-                        acc = 1;
+                        for (int ks = 0; ks < kTcChunk / 8; ++ks) {
+                            const uint64_t ad = tc::smem_desc_kmajor(a_base + ks * 2 * 2048u, 2048u, 128u);
+                            const uint64_t bd =
+                                tc::smem_desc_kmajor(slab_a + ks * 2 * kg_stride + b_row, kg_stride, 128u);
+                            tc::mma_tf32(dacc, ad, bd, idesc, acc);
+                            acc = 1;
+                            if (SPLIT) {  // 3xTF32: + hi(T) lo(M) + lo(T) hi(M)
+                                const uint64_t bl =
+                                    tc::smem_desc_kmajor(slab_lo_a + ks * 2 * kg_stride + b_row, kg_stride, 128u);
+                                const uint64_t al =
+                                    tc::smem_desc_kmajor(a_base + Cfg::kPartBytes + ks * 2 * 2048u, 2048u, 128u);
+                                tc::mma_tf32(dacc, ad, bl, idesc, 1);
+                                tc::mma_tf32(dacc, al, bd, idesc, 1);
+                            }
+                        }
+                        tc::mma_commit(t_empty + s);
+                        ++tcount;
                     }
-                    tc::mma_commit(t_empty + s);
-                    ++tcount;
+                    tc::mma_commit(slab_empty);
                 }
-                tc::mma_commit(slab_empty);
+                tc::mma_commit(acc_full + ab);  // this class's partial sum is complete
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicOr(status, FMM_DEV_TIMEOUT);
+                for (int pi2 = 0; pi2 < 8; ++pi2) tc::mma_commit(acc_full + (pi2 & 1));  // release the drains
             }
         }
-        if (!ok) {
-            *abort_flag = 1;
-            atomicOr(status, FMM_DEV_TIMEOUT);
-        }
-        tc::mma_commit(done);  // arrives once every issued MMA has completed
-    }
-    __syncwarp();
-
-    // ---------------- epilogue: TMEM -> L (Morton order) ----------------
-    const bool done_ok = tc::mbar_wait(done, 0, kWaitLimit);
-    tc::fence_after_sync();
-    if (done_ok && !*abort_flag) {
-        const int j = warp * 32 + lane;  // output coefficient = TMEM lane
-        float* Ll = L + lv.l_off[lev] * (long)ncp;
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int cb = 0; cb < kTcRows; cb += 16) {
-            float v[16];
-            tc::tmem_ld16(taddr + cb, v);
+        __syncwarp();
+    } else {
+        // ---------------- accumulator drains (warps 2..9) ----------------
+        const int q = warp & 3;                    // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;          // column half (0: rows 0-127, 1: rows 128-255)
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        float sum[kTcRows / 2];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int r = r0 + cb + q;
+        for (int i = 0; i < kTcRows / 2; ++i) sum[i] = 0.f;
+        bool ok = true;
+        for (int pi = 0; pi < 8; ++pi) {
+            const int ab = pi & 1;
+            if (!tc::mbar_wait(acc_full + ab, (pi >> 1) & 1, kWaitLimit) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t base = tmem + lane_base + (uint32_t)(ab * kTcRows + half * (kTcRows / 2));
+#pragma unroll
+            for (int cb = 0; cb < kTcRows / 2; cb += 16) {
+                float v[16];
+                tc::tmem_ld16(base + cb, v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) sum[cb + e] += v[e];
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(acc_empty + ab);
+        }
+        if (ok && !*abort_flag) {
+            const int j = q * 32 + lane;  // output coefficient = TMEM lane
+            float* Ll = L + lv.l_off[lev] * (long)ncp;
+#pragma unroll
+            for (int e = 0; e < kTcRows / 2; ++e) {
+                const int r = r0 + half * (kTcRows / 2) + e;
                 if (r >= R) continue;
                 const int ip = r / (m2 * m2), jp = (r / m2) % m2, kp = r % m2;
                 if (ip < 1 || ip > n || jp < 1 || jp > n || kp < 1 || kp > n) continue;
                 const uint32_t box =
                     ((spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1) | (spread3_tc(kp - 1) << 2)) << 3) | (uint32_t)c;
-                if (j < ncp) Ll[(long)box * ncp + j] = v[q];
+                if (j < ncp) Ll[(long)box * ncp + j] = sum[e];
             }
+        } else if (lane == 0) {
+            atomicOr(status, FMM_DEV_TIMEOUT);
         }
-    } else if (threadIdx.x == 0) {
-        atomicOr(status, FMM_DEV_TIMEOUT);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 1) tc::tmem_dealloc(tmem, kTcRows);
+    if (warp == 2) tc::tmem_dealloc(tmem, 2 * kTcRows);
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
 struct TcState {
+    bool split = false;
+    float* Mtc_lo = nullptr;
     float* Mtc = nullptr;
     float* Ttc = nullptr;
     TcTile* tiles = nullptr;
@@ -277,7 +355,7 @@ struct TcState {
 
 bool m2l_tc_supported(const Handle* h) {
     // M = 128 output coefficients per MMA; the slab of the deepest level fits in shared memory
-    return h->precision == FMM_MIXED_TF32 && h->ncp <= 128 && h->depth <= 5;
+    return (h->precision == FMM_MIXED_TF32 || h->precision == FMM_MIXED_3XTF32) && h->ncp <= 128 && h->depth <= 5;
 }
 
 static TcState* tc_state(Handle* h) { return reinterpret_cast<TcState*>(h->tc); }
@@ -286,10 +364,15 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     TcState* st = new TcState();
     h->tc = st;
     const int nc = h->nc, ncp = h->ncp, d = h->depth;
+    st->split = h->precision == FMM_MIXED_3XTF32;
+    const int kTcChunk = st->split ? TcCfg<true>::kChunk : TcCfg<false>::kChunk;
+    const int kTcKG = kTcChunk / 4;
+    const int nparts = st->split ? 2 : 1;
     st->NKC = (ncp + kTcChunk - 1) / kTcChunk;
     const int NKG = st->NKC * kTcKG;
-    // operator chunks [op][chunk][kgroup][j(128)][4], rounded to TF32 (nearest, ties away)
-    std::vector<float> T((size_t)kNumOps * st->NKC * 128 * kTcChunk, 0.f);
+    // operator chunks [op][chunk][part][kgroup][j(128)][4]; part 0 = TF32 rounding (nearest,
+    // ties away), part 1 (3xTF32) = TF32 rounding of the remainder
+    std::vector<float> T((size_t)kNumOps * st->NKC * nparts * 128 * kTcChunk, 0.f);
     auto tf32 = [](float x) {
         uint32_t u;
         std::memcpy(&u, &x, 4);
@@ -303,7 +386,9 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
             for (int k = 0; k < nc; ++k) {
                 const float v = T_rowmajor[((size_t)op * nc + jj) * nc + k];
                 const int ch = k / kTcChunk, g = (k % kTcChunk) / 4, e = k % 4;
-                T[((((size_t)op * st->NKC + ch) * kTcKG + g) * 128 + jj) * 4 + e] = tf32(v);
+                const float hi = tf32(v);
+                T[(((((size_t)op * st->NKC + ch) * nparts + 0) * kTcKG + g) * 128 + jj) * 4 + e] = hi;
+                if (nparts == 2) T[(((((size_t)op * st->NKC + ch) * nparts + 1) * kTcKG + g) * 128 + jj) * 4 + e] = tf32(v - hi);
             }
     // packed multipole levels
     long off = 0;
@@ -329,10 +414,11 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
             for (int r0 = S; r0 < R - S; r0 += kTcRows) tiles.push_back({l, c, r0, 0});
     }
     st->slab_rows = kTcRows + 2 * max_S;
-    st->smem = (size_t)st->slab_rows * kTcKG * 16 + (size_t)kTcStages * kTcTBytes + 256;
+    st->smem = (size_t)st->slab_rows * kTcKG * 16 * nparts + (size_t)kTcStages * kTcTBytes + 256;
     st->ntiles = (int)tiles.size();
     if (cudaMalloc(&st->Ttc, sizeof(float) * T.size()) != cudaSuccess ||
         cudaMalloc(&st->Mtc, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess ||
+        (st->split && cudaMalloc(&st->Mtc_lo, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess) ||
         cudaMalloc(&st->tiles, sizeof(TcTile) * (tiles.empty() ? 1 : tiles.size())) != cudaSuccess) {
         cudaGetLastError();
         return FMM_ERR_OOM;
@@ -340,7 +426,8 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     cudaMemcpy(st->Ttc, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice);
     if (!tiles.empty()) cudaMemcpy(st->tiles, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice);
     if (st->smem > 227 * 1024) return FMM_ERR_ARG;
-    cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem);
+    if (st->split) cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem);
+    else cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem);
     return FMM_OK;
 }
 
@@ -348,6 +435,7 @@ void m2l_tc_free(Handle* h) {
     TcState* st = tc_state(h);
     if (!st) return;
     if (st->Mtc) cudaFree(st->Mtc);
+    if (st->Mtc_lo) cudaFree(st->Mtc_lo);
     if (st->Ttc) cudaFree(st->Ttc);
     if (st->tiles) cudaFree(st->tiles);
     delete st;
@@ -360,16 +448,21 @@ int m2l_tc_launches(const Handle* h) {
 
 void launch_m2l_tc(Handle* h, cudaStream_t stream) {
     TcState* st = tc_state(h);
-    const int NKG = st->NKC * kTcKG;
+    const int NKG = st->NKC * (st->split ? TcCfg<true>::kKG : TcCfg<false>::kKG);
     for (int l = h->lmin; l <= h->depth; ++l) {
         const long total = 8L * NKG * st->lv.R[l];
         k_m2l_pack<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(
             st->lv.n[l], st->lv.R[l], NKG, h->ncp, h->periodic, h->M + h->lvl_off[l] * h->ncp,
-            st->Mtc + st->lv.mtc_off[l]);
+            st->Mtc + st->lv.mtc_off[l], st->split ? st->Mtc_lo + st->lv.mtc_off[l] : nullptr);
     }
-    if (st->ntiles > 0)
-        k_m2l_tc<<<st->ntiles, 128, st->smem, stream>>>(st->tiles, st->lv, st->Mtc, st->Ttc, h->L, h->ncp, st->NKC,
-                                                         st->slab_rows, h->status);
+    if (st->ntiles > 0) {
+        if (st->split)
+            k_m2l_tc<true><<<st->ntiles, kTcThreads, st->smem, stream>>>(st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L,
+                                                                   h->ncp, st->NKC, st->slab_rows, h->status);
+        else
+            k_m2l_tc<false><<<st->ntiles, kTcThreads, st->smem, stream>>>(st->tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L,
+                                                                    h->ncp, st->NKC, st->slab_rows, h->status);
+    }
 }
 
 }  // namespace fmmcph

@@ -234,3 +234,18 @@ def test_tf32_mode_unavailable_is_refused():
     from paper_2410_01626_b300 import FMM, FmmError
     with pytest.raises(FmmError):
         FMM(1.0, True, 12, 3, precision="tf32")  # 169 coefficients exceed one 128-row MMA
+
+
+@pytest.mark.parametrize("periodic,p,depth", [(True, 8, 3), (True, 10, 3), (False, 10, 4), (True, 10, 1)])
+def test_3xtf32_m2l_parity(periodic, p, depth):
+    """Split TF32 (hi*hi + hi*lo + lo*hi) restores FP32-level operands: E, F and
+    dV/dlambda all within 1e-4 of the oracle, like the FP32 path."""
+    if periodic:
+        s = synth.periodic_uniform(seed=3, n=3000, L=3.0, n_sites=8, site_size=4, p=p, depth=depth)
+    else:
+        s = synth.open_uniform(seed=5, n=3000, L=5.0, n_sites=8, site_size=4, p=p, depth=depth)
+    ref = oracle_ref(s)
+    g = run_gpu(s, precision="3xtf32")
+    e = errors(g, ref)
+    assert g["status"] == 0
+    assert e["F"] < 1e-4 and e["E"] < 1e-4 and e["dVdl"] < 1e-4, e
