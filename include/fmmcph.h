@@ -182,6 +182,27 @@ fmm_status fmm_host_operator(int kind, int p, const int* o, double* out);
  * (p+1)^2) on the host -- the basis P2M and L2P use.  Test helper. */
 fmm_status fmm_host_regular(int p, const double* u, double* out);
 
+/* Binning with no device allocation, for callers that cannot call cudaMalloc: code running
+ * while a CUDA stream is being captured into a graph, processes whose device memory comes from
+ * a fixed budget or a foreign allocator, and real-time loops that must not allocate.  The paper
+ * has no counterpart; it is the binning step of fmm_eval (Morton keys, stable sort, leaf
+ * ranges) on its own.
+ *   box, periodic, depth: as for fmm_create (0 <= depth <= 7)
+ *   n_atoms:  0 <= n_atoms <= FMM_NOALLOC_MAX_ATOMS, else FMM_ERR_ARG
+ *   x:        [n_atoms][3] float positions
+ *   key, perm:[n_atoms] uint32 outputs, start, count: [8^depth] uint32 outputs -- the same
+ *             values fmm_get_binning returns after fmm_eval on the same positions
+ * The sort scratch is a static device array inside the library, sized for
+ * FMM_NOALLOC_MAX_ATOMS atoms (about 6.5 MB per GPU that loads the library, held until the
+ * process exits).  The first call on a device looks up that array's device address; make that
+ * first call before any stream capture.  Every call shares the array and keeps the last call's
+ * contents, so calls that overlap on the GPU (unordered streams) race; calls on one stream are
+ * ordered.  No device memory is allocated or freed.  Atoms outside an open box are clamped into
+ * the boundary leaves (use fmm_status_word after fmm_eval to detect them). */
+#define FMM_NOALLOC_MAX_ATOMS 524288
+fmm_status fmm_binning_noalloc(const fmm_box* box, int periodic, int depth, int n_atoms, const float* x,
+                               uint32_t* key, uint32_t* perm, uint32_t* start, uint32_t* count, void* stream);
+
 void fmm_destroy(fmm_handle* h);
 const char* fmm_error_string(fmm_status s);
 

@@ -48,6 +48,7 @@ EXPORTS = {
     "fmm_launches_per_eval": (I, [P]),
     "fmm_host_operator": (I, [I, I, P, P]),
     "fmm_host_regular": (I, [I, P, P]),
+    "fmm_binning_noalloc": (I, [ctypes.POINTER(FmmBox), I, I, I, P, P, P, P, P, P]),
     "fmm_destroy": (None, [P]),
     "fmm_error_string": (ctypes.c_char_p, [I]),
 }

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 
 #include "fmm_internal.h"
 #include "sgemm.cuh"
@@ -932,6 +933,86 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
                                h->phis, dVdl);
     stage(h, 8, st);
     return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Binning with no device allocation (fmm_binning_noalloc).
+// The sort's scratch -- two key buffers, one value buffer and the digit table -- lives in a
+// file-scope device array sized for FMM_NOALLOC_MAX_ATOMS atoms; every GPU that loads the
+// library holds it until the process exits.  Calls share it, so calls that overlap on the GPU
+// (different streams, no ordering between them) race; calls on one stream are ordered.
+constexpr int kNoAllocSortBlocks = (FMM_NOALLOC_MAX_ATOMS + kSortTile - 1) / kSortTile;
+constexpr size_t kNoAllocWords = 3ull * FMM_NOALLOC_MAX_ATOMS + 256ull * kNoAllocSortBlocks + 64;
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+// Device address of the scratch array on the current device.  Host code may not use the
+// array's name as a device pointer (it is a host-side stand-in), so the address is looked up
+// once per device, with that device current, and cached.
+static fmm_status noalloc_scratch(uint32_t** out) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static uint32_t* addr[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return FMM_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return FMM_ERR_CUDA;
+        }
+        addr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = addr[dev];
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_binning_noalloc(const fmm_box* box, int periodic, int depth, int n, const float* x,
+                                          uint32_t* key, uint32_t* perm, uint32_t* start, uint32_t* count,
+                                          void* stream) {
+    if (!box || !(box->edge > 0.0) || !std::isfinite(box->edge)) return FMM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(box->origin[a])) return FMM_ERR_ARG;
+    if ((periodic != 0 && periodic != 1) || depth < 0 || depth > kMaxDepth) return FMM_ERR_ARG;
+    if (n < 0 || n > FMM_NOALLOC_MAX_ATOMS) return FMM_ERR_ARG;  // beyond the static scratch
+    if (!start || !count || (n > 0 && (!x || !key || !perm))) return FMM_ERR_ARG;
+    uint32_t* scr = nullptr;
+    fmm_status e = noalloc_scratch(&scr);
+    if (e != FMM_OK) return e;
+    uint32_t* kB = scr;
+    uint32_t* kC = scr + FMM_NOALLOC_MAX_ATOMS;
+    uint32_t* vS = scr + 2L * FMM_NOALLOC_MAX_ATOMS;
+    uint32_t* table = scr + 3L * FMM_NOALLOC_MAX_ATOMS;
+    int* status = reinterpret_cast<int*>(table + 256L * kNoAllocSortBlocks);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = 1 << depth, nleaf = 1 << (3 * depth);
+    BoxGeom g{box->origin[0], box->origin[1], box->origin[2], box->edge, std::ldexp(1.0, depth) / box->edge,
+              nb, depth, periodic};
+    const int passes = sort_passes(depth);
+    // values ping-pong between the scratch and the caller's perm so that the last pass lands in perm
+    uint32_t* vbuf[2] = {(passes & 1) ? vS : perm, (passes & 1) ? perm : vS};
+    cudaGetLastError();
+    const uint32_t* kin = key;
+    const uint32_t* vin = vbuf[0];
+    if (n > 0) {
+        k_keys<<<(n + 255) / 256, 256, 0, st>>>(n, x, g, key, vbuf[0], status);
+        const int nblk = (n + kSortTile - 1) / kSortTile;
+        uint32_t* kout[2] = {kB, kC};
+        for (int ps = 0; ps < passes; ++ps) {
+            uint32_t* ko = kout[ps & 1];
+            uint32_t* vo = vbuf[(ps + 1) & 1];
+            k_sort_hist<<<nblk, kSortThreads, 0, st>>>(n, kin, 8 * ps, table, nblk);
+            k_sort_scan<<<1, 1024, 0, st>>>(table, 256 * nblk);
+            k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(n, kin, vin, ko, vo, 8 * ps, table, nblk);
+            kin = ko;
+            vin = vo;
+        }
+    }
+    k_ranges<<<(nleaf + 255) / 256, 256, 0, st>>>(n, nleaf, kin, start, count);
+    return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
 }
 
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi, const float* dVdl,
