@@ -49,6 +49,7 @@ void free_atoms(Handle& h) {
     dfree(h.pos);
     dfree(h.dq);
     dfree(h.phis);
+    dfree(h.far);
     dfree(h.sort_table);
     h.perm = nullptr;
     h.sorted_key = nullptr;
@@ -75,6 +76,7 @@ void free_all(Handle& h) {
     dfree(h.leafqdt);
     dfree(h.root);
     dfree(h.status);
+    dfree(h.work);
     dfree(h.hx_dev);
     dfree(h.hF_dev);
     dfree(h.hdV_dev);
@@ -269,7 +271,8 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.start, nleaf)) ||
         (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.epart, (nleaf + 3) / 4)) ||
         (st = dalloc(&h.leafqdt, 5 * nleaf)) || (st = dalloc(&h.root, nc + 8 + 5 * 64)) || (st = dalloc(&h.status, 1)) ||
-        (st = dalloc(&h.site_ptr, 1))) {
+        (st = dalloc(&h.site_ptr, 1)) ||
+        (st = dalloc(&h.work, 8L * (depth >= 1 ? (1L << (3 * (depth - 1))) : 1) * ncp))) {
         free_all(h);
         delete H;
         return st;
@@ -308,7 +311,7 @@ fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const f
         if ((e = dalloc(&h.qA, n)) || (e = dalloc(&h.qB, n)) || (e = dalloc(&h.site, n)) || (e = dalloc(&h.key, n)) ||
             (e = dalloc(&h.kA, n)) || (e = dalloc(&h.kB, n)) || (e = dalloc(&h.vA, n)) || (e = dalloc(&h.vB, n)) ||
             (e = dalloc(&h.inv, n)) || (e = dalloc(&h.pos, n)) || (e = dalloc(&h.dq, n)) ||
-            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.sort_table, 256L * (nblk > 0 ? nblk : 1)))) {
+            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.far, n)) || (e = dalloc(&h.sort_table, 256L * (nblk > 0 ? nblk : 1)))) {
             free_atoms(h);
             h.charges_set = false;
             return e;

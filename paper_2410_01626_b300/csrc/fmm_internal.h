@@ -63,11 +63,13 @@ struct Handle {
     float4* pos = nullptr;
     float* dq = nullptr;
     float* phis = nullptr;   // sorted-order potential (without k_e)
+    float4* far = nullptr;   // sorted-order far-field potential and gradient
     double* epart = nullptr; // per-block partial sums of q phi
     int epart_cap = 0;
     double* leafqdt = nullptr;  // [nleaf][5] periodic: Q, Dx, Dy, Dz, T per leaf
     double* root = nullptr;     // [nc] FP64 root multipole, then [5] Q D T at root+nc
     int* status = nullptr;
+    float* work = nullptr;  // split-K partial products (8 x the largest M2M output level)
     bool charges_set = false;
     // profiling
     bool profiling = false;

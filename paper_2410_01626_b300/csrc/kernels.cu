@@ -9,7 +9,8 @@
 //   root      k_root, k_lattice (periodic) FP64 root multipole and lattice operator
 //   M2L       k_m2l_fp32 (FP32 CUDA cores) or the tcgen05 kernel in m2l_tc.cu
 //   L2L       k_sgemm         per level, one dense GEMM into the 8 contiguous children
-//   near      k_near<P>       L2P + P2P (27 neighbour leaves) + forces / potential / energy
+//   near      k_l2p<P>        far field per atom (L2P + periodic background term)
+//             k_p2p           P2P over the 27 neighbour leaves + forces / potential / energy
 //   final     k_final         E (FP64, fixed-order reduction) and dV/dlambda per site
 #include <cuda_runtime.h>
 
@@ -139,40 +140,53 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(int n, const uint32_
     table[threadIdx.x * nblk + blockIdx.x] = hist[threadIdx.x];
 }
 
-// exclusive scan of the digit-major table, one block of 1024 threads
+// exclusive scan of the digit-major table [256 digits][nblk], one block of 1024 threads:
+// each warp scans whole digit rows with coalesced loads, then the 256 digit totals are scanned
+// and added back.
 __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ table, int total) {
+    __shared__ uint32_t dtot[256];
     __shared__ uint32_t wsum[32];
-    const int t = threadIdx.x;
-    const int seg = (total + 1023) / 1024;
-    const int b = t * seg, e = min(total, b + seg);
-    uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += table[i];
-    // block exclusive scan of s
-    uint32_t v = s;
-    const int lane = t & 31, w = t >> 5;
+    const int nblk = total / 256;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = w; d < 256; d += 32) {  // row d: exclusive scan within the row
+        uint32_t carry = 0;
+        for (int b0 = 0; b0 < nblk; b0 += 32) {
+            const int b = b0 + lane;
+            const uint32_t v = (b < nblk) ? table[d * nblk + b] : 0u;
+            uint32_t x = v;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += y;
+            for (int k = 1; k < 32; k <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, k);
+                if (lane >= k) x += y;
+            }
+            if (b < nblk) table[d * nblk + b] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) dtot[d] = carry;
     }
-    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    // exclusive scan of the 256 digit totals (threads 0..255)
+    uint32_t v = (threadIdx.x < 256) ? dtot[threadIdx.x] : 0u, x = v;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, k);
+        if (lane >= k) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
     if (w == 0) {
-        uint32_t z = wsum[lane];
+        uint32_t z = (lane < 8) ? wsum[lane] : 0u;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, z, d);
-            if (lane >= d) z += y;
+        for (int k = 1; k < 8; k <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, z, k);
+            if (lane >= k) z += y;
         }
-        wsum[lane] = z;
+        if (lane < 8) wsum[lane] = z;
     }
     __syncthreads();
-    uint32_t run = v - s + (w > 0 ? wsum[w - 1] : 0u);
-    for (int i = b; i < e; ++i) {
-        uint32_t c = table[i];
-        table[i] = run;
-        run += c;
-    }
+    if (threadIdx.x < 256) dtot[threadIdx.x] = x - v + (w > 0 ? wsum[w - 1] : 0u);
+    __syncthreads();
+    for (int e = threadIdx.x; e < total; e += 1024) table[e] += dtot[e / nblk];
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(int n, const uint32_t* __restrict__ kin,
@@ -554,17 +568,53 @@ struct NearParams {
     double* epart;
 };
 
-// One warp per target leaf.
+// Far field per atom: L2P of the leaf's local expansion plus the periodic background term,
+// one thread per atom in leaf order; far[s] = (phi, dphi/dx, dphi/dy, dphi/dz).
+template <int P>
+__global__ void __launch_bounds__(128) k_l2p(int n, int use_far, NearParams a, const uint32_t* __restrict__ skey,
+                                             float4* __restrict__ far) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t leaf = skey[s];
+    const float h = a.h;
+    const float cx = (compact3(leaf) + 0.5f) * h, cy = (compact3(leaf >> 1) + 0.5f) * h,
+                cz = (compact3(leaf >> 2) + 0.5f) * h;
+    const float4 me = a.pos[s];
+    float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    if (use_far) {
+        const float ih = 1.0f / h;
+        l2p_eval<P>(a.Lleaf + (long)leaf * a.ncp, (me.x - cx) * ih, (me.y - cy) * ih, (me.z - cz) * ih, pot, gx, gy,
+                    gz);
+        pot *= ih;
+        gx *= ih * ih;
+        gy *= ih * ih;
+        gz *= ih * ih;
+    }
+    if (a.periodic && a.qdt) {
+        const float c2 = (float)(2.0 * M_PI / (3.0 * a.vol));
+        const float cq = (float)a.qdt[0], cdx = (float)a.qdt[1], cdy = (float)a.qdt[2], cdz = (float)a.qdt[3],
+                    ctr = (float)a.qdt[4];
+        const float hb = 0.5f * a.Lbox;
+        const float ux = me.x - hb, uy = me.y - hb, uz = me.z - hb;
+        pot += c2 * (cq * (ux * ux + uy * uy + uz * uz) - 2.f * (ux * cdx + uy * cdy + uz * cdz) + ctr);
+        gx += 2.f * c2 * (cq * ux - cdx);
+        gy += 2.f * c2 * (cq * uy - cdy);
+        gz += 2.f * c2 * (cq * uz - cdz);
+    }
+    far[s] = make_float4(pot, gx, gy, gz);
+}
+
+// Near field, one warp per target leaf.
 // (1) Lanes 0..26 resolve the 27 neighbour leaves at once (periodic image shift, start,
 //     count) and a warp scan gives each neighbour's offset in a per-warp source list.
 // (2) When the list fits (kNearCap atoms, the common case), all lanes copy it into shared
 //     memory in one pass, so that every global load is in flight together; otherwise the
 //     sources are streamed neighbour by neighbour in chunks of 32.
-// (3) Leaves with few atoms split the warp into G source slices (lane = target + slice *
-//     32/G) so every lane works in the pair loop; slice sums are combined with shuffles.
+// (3) The warp is split into G = 32/TPG source slices (lane = target + slice * TPG), TPG in
+//     {4, 8, 16, 32} chosen per leaf to minimise padded target slots x source iterations;
+//     slice sums are combined with shuffles, then the far field (k_l2p) is added.
 constexpr int kNearCap = 640;
-template <int P>
-__global__ void __launch_bounds__(128) k_near(NearParams a) {
+__global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restrict__ far) {
     __shared__ float4 src_sm[4][kNearCap];
     __shared__ int nb_off[4][28];
     __shared__ int nb_s0[4][27];
@@ -576,17 +626,7 @@ __global__ void __launch_bounds__(128) k_near(NearParams a) {
         const int nb = 1 << a.depth;
         const int ix = (int)compact3(leaf), iy = (int)compact3(leaf >> 1), iz = (int)compact3(leaf >> 2);
         const float h = a.h;
-        const float cx = (ix + 0.5f) * h, cy = (iy + 0.5f) * h, cz = (iz + 0.5f) * h;
         const int st = a.start[leaf], cnt = a.count[leaf];
-        float cq = 0.f, cdx = 0.f, cdy = 0.f, cdz = 0.f, ctr = 0.f, c2 = 0.f;
-        if (a.periodic && a.qdt) {
-            c2 = (float)(2.0 * M_PI / (3.0 * a.vol));
-            cq = (float)a.qdt[0];
-            cdx = (float)a.qdt[1];
-            cdy = (float)a.qdt[2];
-            cdz = (float)a.qdt[3];
-            ctr = (float)a.qdt[4];
-        }
         // (1) neighbour table: lane o < 27 owns neighbour o
         int my_s0 = 0, my_sc = 0;
         float shx = 0.f, shy = 0.f, shz = 0.f;
@@ -617,15 +657,14 @@ __global__ void __launch_bounds__(128) k_near(NearParams a) {
             if (lane >= d) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (lane < 27) nb_off[w][lane + 1] = incl;
-        if (lane == 0) nb_off[w][0] = 0;
-        __syncwarp();
         if (lane < 27) {
+            nb_off[w][lane + 1] = incl;
             nb_s0[w][lane] = my_s0;
             nb_sh[w][lane][0] = shx;
             nb_sh[w][lane][1] = shy;
             nb_sh[w][lane][2] = shz;
         }
+        if (lane == 0) nb_off[w][0] = 0;
         __syncwarp();
         const bool staged = total <= kNearCap;
         if (staged) {  // (2) one pass over every source atom of the 27 neighbours
@@ -642,13 +681,23 @@ __global__ void __launch_bounds__(128) k_near(NearParams a) {
             }
             __syncwarp();
         }
-        const int G = cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
-        const int TPG = 32 / G;
+        // (3) slice shape: cost = target passes x (source iterations + combine overhead)
+        int TPG = 32, best = 1 << 30;
+#pragma unroll
+        for (int tpg = 4; tpg <= 32; tpg <<= 1) {
+            const int g = 32 / tpg;
+            const int cost = ((cnt + tpg - 1) / tpg) * ((total + g - 1) / g + 8 * (31 - __clz(g)) + 24);
+            if (cost < best) {
+                best = cost;
+                TPG = tpg;
+            }
+        }
+        const int G = 32 / TPG;
         const int tl = lane % TPG, slice = lane / TPG;
         for (int tb = 0; tb < cnt; tb += TPG) {
             const int ti = tb + tl;
             const bool valid = ti < cnt;
-            float4 me = make_float4(cx, cy, cz, 0.f);
+            float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) me = a.pos[st + ti];
             float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
             auto pair = [&](const float4 s4) {
@@ -663,7 +712,14 @@ __global__ void __launch_bounds__(128) k_near(NearParams a) {
                 gz = fmaf(-qri3, dz, gz);
             };
             if (staged) {
-                for (int t = slice; t < total; t += G) pair(src_sm[w][t]);
+                int t = slice;
+                for (; t + 3 * G < total; t += 4 * G) {
+                    pair(src_sm[w][t]);
+                    pair(src_sm[w][t + G]);
+                    pair(src_sm[w][t + 2 * G]);
+                    pair(src_sm[w][t + 3 * G]);
+                }
+                for (; t < total; t += G) pair(src_sm[w][t]);
             } else {
                 for (int o = 0; o < 27; ++o) {
                     const int s0 = nb_s0[w][o], sc = nb_off[w][o + 1] - nb_off[w][o];
@@ -687,25 +743,14 @@ __global__ void __launch_bounds__(128) k_near(NearParams a) {
                 gy += __shfl_xor_sync(0xffffffffu, gy, off);
                 gz += __shfl_xor_sync(0xffffffffu, gz, off);
             }
-            if (a.use_far) {
-                float pf, fx, fy, fz;
-                const float ih = 1.0f / h;
-                l2p_eval<P>(a.Lleaf + (long)leaf * a.ncp, (me.x - cx) * ih, (me.y - cy) * ih, (me.z - cz) * ih,
-                            pf, fx, fy, fz);
-                pot += pf * ih;
-                gx += fx * ih * ih;
-                gy += fy * ih * ih;
-                gz += fz * ih * ih;
-            }
-            if (a.periodic) {
-                const float hb = 0.5f * a.Lbox;
-                const float ux = me.x - hb, uy = me.y - hb, uz = me.z - hb;
-                pot += c2 * (cq * (ux * ux + uy * uy + uz * uz) - 2.f * (ux * cdx + uy * cdy + uz * cdz) + ctr);
-                gx += 2.f * c2 * (cq * ux - cdx);
-                gy += 2.f * c2 * (cq * uy - cdy);
-                gz += 2.f * c2 * (cq * uz - cdz);
-            }
             if (valid && slice == 0) {
+                if (far) {
+                    const float4 f4 = far[st + ti];
+                    pot += f4.x;
+                    gx += f4.y;
+                    gy += f4.z;
+                    gz += f4.w;
+                }
                 const int i = (int)a.perm[st + ti];
                 const float q = me.w;
                 if (a.F) {
@@ -781,8 +826,8 @@ static void launch_p2m(int nleaf, float h, float half, const Handle* hd, float* 
                                               qdt);
 }
 template <int P>
-static void launch_near(const NearParams& a, cudaStream_t st) {
-    k_near<P><<<(a.nleaf + 3) / 4, 128, 0, st>>>(a);
+static void launch_l2p(int n, int use_far, const NearParams& a, const uint32_t* skey, float4* far, cudaStream_t st) {
+    k_l2p<P><<<(n + 127) / 128, 128, 0, st>>>(n, use_far, a, skey, far);
 }
 
 #define FMM_DISPATCH_P(p, FN, ...)         \
@@ -815,11 +860,12 @@ int launches_per_eval(const Handle* h) {
     const int d = h->depth;
     int n = 1 /*keys*/ + 3 * sort_passes(d) + 1 /*ranges*/ + 1 /*gather*/ + 1 /*p2m*/;
     const int lmin = h->periodic ? 1 : 2;
-    if (d >= lmin) n += d - lmin;  // M2M parent levels d-1 .. lmin
+    if (d >= lmin) n += 2 * (d - lmin);  // M2M parent levels d-1 .. lmin (split-K product + sum)
     if (h->periodic) n += 3;       // Q/D/T partials + root + lattice
     if (d >= lmin) n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? m2l_tc_launches(h) : 1;  // M2L
     if (d >= lmin) n += d - lmin + (h->periodic ? 1 : 0);  // L2L
-    n += 1 /*near*/ + 1 /*final*/;
+    n += 1 /*p2p*/ + 1 /*final*/;
+    if (h->periodic || d >= 2) n += 1;  // l2p
     return n;
 }
 
@@ -872,7 +918,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     for (int l = d - 1; l >= lmin; --l) {
         const int np = 1 << (3 * l);
         sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
-              h->M + h->lvl_off[l] * h->ncp, h->ncp, false, st);
+              h->M + h->lvl_off[l] * h->ncp, h->ncp, false, st, 8, h->work);  // split K by child octant
     }
     stage(h, 3, st);
     // --- periodic root (FP64) ---
@@ -926,7 +972,9 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.phi_out = phi;
     a.phis = h->phis;
     a.epart = h->epart;
-    FMM_DISPATCH_P(h->p, launch_near, a, st);
+    const bool has_far = a.use_far || h->periodic;
+    if (has_far && n > 0) FMM_DISPATCH_P(h->p, launch_l2p, n, a.use_far, a, h->sorted_key, h->far, st);
+    k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, has_far ? h->far : nullptr);
     stage(h, 7, st);
     const int nparts = (nleaf + 3) / 4;
     k_final<<<1, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,

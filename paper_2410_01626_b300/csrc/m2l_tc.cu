@@ -32,7 +32,9 @@ namespace fmmcph {
 
 namespace {
 
-constexpr int kTcRows = 256;    // virtual rows (N) per CTA
+constexpr int kTcRows = 192;    // virtual rows (N) per CTA: 280 CTAs = two full waves at depth 5
+constexpr int kTcTmemCols = 512; // two accumulators, 256 columns apart
+constexpr int kTcAccStride = 256;
 constexpr int kTcStages = 3;    // operator-chunk ring depth
 constexpr uint32_t kTcTBytes = 16384;  // one ring stage: 128 rows x 32 coefficients (or hi+lo x 16)
 constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
@@ -108,9 +110,10 @@ struct TcTile {
 // Warp roles (10 warps): warp 0 lane 0 = bulk-copy producer, warp 1 lane 0 = MMA issuer,
 // warps 2..9 = accumulator drains.  The tensor core aligns addends to the largest and
 // truncates, so a long chain of MMAs into one FP32 accumulator drifts; here each source
-// class pi is accumulated into one of two TMEM accumulators (ping-pong, 2 x 256 columns)
+// class pi and K chunk is accumulated into one of two TMEM accumulators (ping-pong)
 // and then added by the drain warps into FP32 registers (round to nearest), which bounds
-// every tensor-core chain to one class (about 1/8 of the work).
+// every tensor-core chain to one (source class, K chunk) group: at most 27 offsets x 4 K steps
+// (x 3 products in the split form).
 constexpr int kTcThreads = 320;
 constexpr int kTcDrainWarps = 8;
 
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc::fence_mbar_init();
     }
     if (warp == 2) {
-        tc::tmem_alloc(tmem_slot, 2 * kTcRows);
+        tc::tmem_alloc(tmem_slot, kTcTmemCols);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -228,15 +231,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bool ok = true;
             for (int pi = 0; pi < 8 && ok; ++pi) {
                 const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-                const int ab = pi & 1;  // accumulator of this source class
-                const uint32_t dacc = tmem + (uint32_t)(ab * kTcRows);
-                if (pi >= 2 && (!tc::mbar_wait(acc_empty + ab, ((pi >> 1) - 1) & 1, kWaitLimit) || *abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc::fence_after_sync();
-                uint32_t acc = 0;
                 for (int ch = 0; ch < NKC && ok; ++ch) {
+                    const int grp = pi * NKC + ch;  // one accumulator chain per (source class, K chunk)
+                    const int ab = grp & 1;
+                    const uint32_t dacc = tmem + (uint32_t)(ab * kTcAccStride);
+                    if (grp >= 2 && (!tc::mbar_wait(acc_empty + ab, ((grp >> 1) - 1) & 1, kWaitLimit) || *abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    uint32_t acc = 0;
                     if (!tc::mbar_wait(slab_full, it & 1, kWaitLimit) || *abort_flag) {
                         ok = false;
                         break;
@@ -276,13 +280,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         ++tcount;
                     }
                     tc::mma_commit(slab_empty);
+                    tc::mma_commit(acc_full + ab);  // this group's partial sum is complete
                 }
-                tc::mma_commit(acc_full + ab);  // this class's partial sum is complete
             }
             if (!ok) {
                 *abort_flag = 1;
                 atomicOr(status, FMM_DEV_TIMEOUT);
-                for (int pi2 = 0; pi2 < 8; ++pi2) tc::mma_commit(acc_full + (pi2 & 1));  // release the drains
+                for (int g2 = 0; g2 < 2; ++g2) tc::mma_commit(acc_full + g2);  // release the drains
             }
         }
         __syncwarp();
@@ -295,14 +299,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int i = 0; i < kTcRows / 2; ++i) sum[i] = 0.f;
         bool ok = true;
-        for (int pi = 0; pi < 8; ++pi) {
-            const int ab = pi & 1;
-            if (!tc::mbar_wait(acc_full + ab, (pi >> 1) & 1, kWaitLimit) || *abort_flag) {
+        for (int grp = 0; grp < 8 * NKC; ++grp) {
+            const int ab = grp & 1;
+            if (!tc::mbar_wait(acc_full + ab, (grp >> 1) & 1, kWaitLimit) || *abort_flag) {
                 ok = false;
                 break;
             }
             tc::fence_after_sync();
-            const uint32_t base = tmem + lane_base + (uint32_t)(ab * kTcRows + half * (kTcRows / 2));
+            const uint32_t base = tmem + lane_base + (uint32_t)(ab * kTcAccStride + half * (kTcRows / 2));
 #pragma unroll
             for (int cb = 0; cb < kTcRows / 2; cb += 16) {
                 float v[16];
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 2) tc::tmem_dealloc(tmem, 2 * kTcRows);
+    if (warp == 2) tc::tmem_dealloc(tmem, kTcTmemCols);
 }
 
 }  // namespace

@@ -9,11 +9,20 @@
 
 namespace fmmcph {
 
+// blockIdx.z selects one of gridDim.z equal slices of K; slice z writes (or adds) its partial
+// product to C + z * cstride (split-K, summed afterwards in a fixed order by k_sum_slices).
 template <int BM, int TM>
 __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
                                                const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
-                                               int accumulate) {
+                                               int accumulate, long cstride) {
     constexpr int BN = 128, BK = 16, TN = 4;
+    {
+        const int kslice = K / gridDim.z;
+        A += (long)blockIdx.z * kslice;
+        B += (long)blockIdx.z * kslice * ldb;
+        C += (long)blockIdx.z * cstride;
+        K = kslice;
+    }
     static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
     constexpr int A_F4 = BM * BK / 4;          // float4 elements of an A tile
     constexpr int A_LD = (A_F4 + 255) / 256;   // float4 loads of A per thread
@@ -121,17 +130,41 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
     }
 }
 
+// C (=|+=) sum_z P_z, P_z = slice z of a split-K product, fixed summation order
+__global__ void k_sum_slices(int M, int N, int ldc, int nz, const float* __restrict__ P, long pstride,
+                             float* __restrict__ C, int accumulate) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)M * N) return;
+    const int m = (int)(e / N), nn = (int)(e % N);
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += P[z * pstride + (long)m * N + nn];
+    float* cp = C + (long)m * ldc + nn;
+    *cp = accumulate ? *cp + s : s;
+}
+
 // C = A B (+C): chooses the row tile so that small-M problems still spread over the SMs.
+// With `work` (>= ksplit * M * N floats) and ksplit > 1 the K range is split over blockIdx.z
+// -- long, thin products are latency bound otherwise -- and summed in a fixed order.
 inline void sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                  bool accumulate, cudaStream_t st) {
+                  bool accumulate, cudaStream_t st, int ksplit = 1, float* work = nullptr) {
     if (M <= 0 || N <= 0) return;
     const int nbn = (N + 127) / 128;
-    if ((long)((M + 63) / 64) * nbn >= 148) {
-        dim3 grid(nbn, (M + 63) / 64);
-        k_sgemm<64, 8><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
+    const bool split = ksplit > 1 && work && K % (4 * ksplit) == 0;
+    const int nz = split ? ksplit : 1;
+    float* out = split ? work : C;
+    const int ldo = split ? N : ldc;
+    const long cst = split ? (long)M * N : 0;
+    const int acc = split ? 0 : (accumulate ? 1 : 0);
+    if ((long)((M + 63) / 64) * nbn * nz >= 148) {
+        dim3 grid(nbn, (M + 63) / 64, nz);
+        k_sgemm<64, 8><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, acc, cst);
     } else {
-        dim3 grid(nbn, (M + 31) / 32);
-        k_sgemm<32, 4><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
+        dim3 grid(nbn, (M + 31) / 32, nz);
+        k_sgemm<32, 4><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, acc, cst);
+    }
+    if (split) {
+        const long tot = (long)M * N;
+        k_sum_slices<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, ldc, nz, work, cst, C, accumulate ? 1 : 0);
     }
 }
 
