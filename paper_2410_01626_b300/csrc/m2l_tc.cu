@@ -38,13 +38,16 @@ constexpr int kTcAccStride = 256;
 constexpr int kTcStages = 3;    // operator-chunk ring depth
 constexpr uint32_t kTcTBytes = 16384;  // one ring stage: 128 rows x 32 coefficients (or hi+lo x 16)
 constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
-// K chunk (input coefficients per slab / operator chunk): 32 for TF32, 16 for the split
-// 3xTF32 form, whose hi and lo slabs then share the same shared memory.
+// K chunk (input coefficients per slab / operator chunk): 32 for TF32, 16 for the split 3xTF32
+// form (hi and lo slabs), so one ring stage is 16 KB and one slab buffer about 86 KB in both
+// forms, and two slab buffers fit next to a 3-stage ring.
 template <bool SPLIT>
 struct TcCfg {
     static constexpr int kChunk = SPLIT ? 16 : 32;
     static constexpr int kKG = kChunk / 4;
+    static constexpr int kParts = SPLIT ? 2 : 1;
     static constexpr uint32_t kPartBytes = 128u * kChunk * 4u;  // one operator part (hi or lo)
+    static constexpr uint32_t kStageBytes = kParts * kPartBytes;  // 16 KB
 };
 
 struct TcLevels {
@@ -125,18 +128,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     using Cfg = TcCfg<SPLIT>;
     constexpr int kTcChunk = Cfg::kChunk;
     constexpr int kTcKG = Cfg::kKG;
+    static_assert(Cfg::kStageBytes == kTcTBytes, "ring stage size");
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* slab = smem;                                          // hi (or only) slab
-    uint8_t* slab_lo = smem + (size_t)slab_rows * kTcKG * 16;     // lo slab (SPLIT)
-    uint8_t* tring = smem + (size_t)slab_rows * kTcKG * 16 * (SPLIT ? 2 : 1);
+    // two slab buffers, each [part][kgroup][3 ranges][slab_rows][16 B]; range dx+1 holds the source
+    // rows r0 + dx (n+2)^2 - (n+3) .. + slab_rows, i.e. every delta_y, delta_z shift of one delta_x
+    const uint32_t kg_stride = 3u * (uint32_t)slab_rows * 16u;
+    const uint32_t part_bytes = kg_stride * kTcKG;
+    const uint32_t slab_bytes = part_bytes * Cfg::kParts;
+    uint8_t* slab0 = smem;
+    uint8_t* tring = smem + 2 * (size_t)slab_bytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(tring + (size_t)kTcStages * kTcTBytes);
-    uint64_t* slab_full = bars + 0;
-    uint64_t* slab_empty = bars + 1;
-    uint64_t* acc_full = bars + 2;               // [2]
-    uint64_t* acc_empty = bars + 4;              // [2]
-    uint64_t* t_full = bars + 6;                 // [kTcStages]
-    uint64_t* t_empty = bars + 6 + kTcStages;    // [kTcStages]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6 + 2 * kTcStages);
+    uint64_t* slab_full = bars + 0;    // [2]
+    uint64_t* slab_empty = bars + 2;   // [2]
+    uint64_t* acc_full = bars + 4;     // [2]
+    uint64_t* acc_empty = bars + 6;    // [2]
+    uint64_t* t_full = bars + 8;                 // [kTcStages]
+    uint64_t* t_empty = bars + 8 + kTcStages;    // [kTcStages]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8 + 2 * kTcStages);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const TcTile tile = tiles[blockIdx.x];
@@ -144,15 +152,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int n = lv.n[lev], R = lv.R[lev], S = lv.S[lev];
     const int m2 = n + 2;
     const int NKG = NKC * kTcKG;
+    const int ngroups = 8 * NKC;  // (source class, K chunk) groups
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
 
     if (threadIdx.x == 0) {
-        tc::mbar_init(slab_full, 1);
-        tc::mbar_init(slab_empty, 1);
-        for (int a2 = 0; a2 < 2; ++a2) {
-            tc::mbar_init(acc_full + a2, 1);
-            tc::mbar_init(acc_empty + a2, kTcDrainWarps);
+        for (int q = 0; q < 2; ++q) {
+            tc::mbar_init(slab_full + q, 1);
+            tc::mbar_init(slab_empty + q, 1);
+            tc::mbar_init(acc_full + q, 1);
+            tc::mbar_init(acc_empty + q, kTcDrainWarps);
         }
         for (int s = 0; s < kTcStages; ++s) {
             tc::mbar_init(t_full + s, 1);
@@ -170,47 +179,66 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    const int slab_row0 = r0 - S;  // >= 0 by construction of the tile list
-    const int rows_load = min(slab_rows, R - slab_row0);
+    const int hal = m2 + 1;  // rows before/after the tile within one delta_x range
+    int rs[3], rl[3];
+    for (int q = 0; q < 3; ++q) {
+        rs[q] = r0 + (q - 1) * m2 * m2 - hal;          // >= 0: r0 >= S = m2^2 + hal
+        rl[q] = min(kTcRows + 2 * hal, R - rs[q]);     // > 0:  r0 < R - S
+    }
     const float* Mlev = Mtc + lv.mtc_off[lev];
     const float* Mlev_lo = SPLIT ? Mtc_lo + lv.mtc_off[lev] : nullptr;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer ----------------
-            int it = 0, tcount = 0;
+            auto load_slab = [&](int g) {
+                const int pi = g / NKC, ch = g % NKC, buf = g & 1;
+                uint8_t* dst = slab0 + (size_t)buf * slab_bytes;
+                tc::mbar_arrive_expect_tx(slab_full + buf,
+                                          (uint32_t)(rl[0] + rl[1] + rl[2]) * 16u * kTcKG * Cfg::kParts);
+                for (int kg = 0; kg < kTcKG; ++kg)
+                    for (int q = 0; q < 3; ++q) {
+                        const long e = (((long)pi * NKG + ch * kTcKG + kg) * R + rs[q]) * 4;
+                        uint8_t* dq = dst + (size_t)kg * kg_stride + (size_t)q * slab_rows * 16;
+                        tc::bulk_g2s(dq, Mlev + e, (uint32_t)rl[q] * 16u, slab_full + buf);
+                        if (SPLIT) tc::bulk_g2s(dq + part_bytes, Mlev_lo + e, (uint32_t)rl[q] * 16u, slab_full + buf);
+                    }
+            };
+            int stage = 0;
+            uint32_t ephase = 0;
+            bool first_round = true;
             bool ok = true;
-            for (int pi = 0; pi < 8 && ok; ++pi) {
-                const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-                for (int ch = 0; ch < NKC && ok; ++ch) {
-                    if (it > 0 && (!tc::mbar_wait(slab_empty, (it - 1) & 1, kWaitLimit) || *abort_flag)) {
+            load_slab(0);
+            for (int g = 0; g < ngroups && ok; ++g) {
+                const int pi = g / NKC, ch = g % NKC;
+                const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
+                bool next_issued = false;
+#pragma unroll
+                for (int d = 0; d < 27; ++d) {
+                    const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+                    const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
+                    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                    if (!first_round && !tc::mbar_wait(t_empty + stage, ephase, kWaitLimit)) {
                         ok = false;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(slab_full, (uint32_t)rows_load * 16u * kTcKG * (SPLIT ? 2u : 1u));
-                    for (int g = 0; g < kTcKG; ++g) {
-                        const long e = (((long)pi * NKG + ch * kTcKG + g) * R + slab_row0) * 4;
-                        tc::bulk_g2s(slab + (size_t)g * slab_rows * 16, Mlev + e, (uint32_t)rows_load * 16u,
-                                     slab_full);
-                        if (SPLIT)
-                            tc::bulk_g2s(slab_lo + (size_t)g * slab_rows * 16, Mlev_lo + e, (uint32_t)rows_load * 16u,
-                                         slab_full);
+                    const int op = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+                    tc::mbar_arrive_expect_tx(t_full + stage, kTcTBytes);
+                    tc::bulk_g2s(tring + (size_t)stage * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
+                                 kTcTBytes, t_full + stage);  // hi (+ lo) operator chunk
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        if (!first_round) ephase ^= 1u;
+                        first_round = false;
                     }
-                    ++it;
-                    for (int d = 0; d < 27 && ok; ++d) {
-                        const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                        const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
-                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                        const int s = tcount % kTcStages, u = tcount / kTcStages;
-                        if (u > 0 && (!tc::mbar_wait(t_empty + s, (u - 1) & 1, kWaitLimit) || *abort_flag)) {
+                    if (!next_issued && g + 1 < ngroups) {  // prefetch the next group's slab
+                        next_issued = true;
+                        const int gn = g + 1;
+                        if (gn >= 2 && !tc::mbar_wait(slab_empty + (gn & 1), ((gn >> 1) - 1) & 1, kWaitLimit)) {
                             ok = false;
                             break;
                         }
-                        const int op = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
-                        tc::mbar_arrive_expect_tx(t_full + s, kTcTBytes);
-                        tc::bulk_g2s(tring + (size_t)s * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
-                                     kTcTBytes, t_full + s);  // hi (+ lo) operator chunk
-                        ++tcount;
+                        load_slab(gn);
                     }
                 }
             }
@@ -223,65 +251,61 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
+            // Lean loop: the 27 shifts are unrolled (constant delta), the ring position is a
+            // running counter, and the abort flag is only consulted when a wait expires.
             const uint32_t idesc = tc::idesc_tf32(128, kTcRows);
-            const uint32_t slab_a = tc::smem_u32(slab), slab_lo_a = tc::smem_u32(slab_lo),
-                           ring_a = tc::smem_u32(tring);
-            const uint32_t kg_stride = (uint32_t)slab_rows * 16u;
-            int it = 0, tcount = 0;
+            // descriptors are built once and advanced by adding (byte offset >> 4) to the address field
+            const uint64_t a_base = tc::smem_desc_kmajor(tc::smem_u32(tring), 2048u, 128u);
+            const uint64_t b_base = tc::smem_desc_kmajor(tc::smem_u32(slab0), kg_stride, 128u);
+            int stage = 0;
+            uint32_t tphase = 0;
             bool ok = true;
-            for (int pi = 0; pi < 8 && ok; ++pi) {
-                const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-                for (int ch = 0; ch < NKC && ok; ++ch) {
-                    const int grp = pi * NKC + ch;  // one accumulator chain per (source class, K chunk)
-                    const int ab = grp & 1;
-                    const uint32_t dacc = tmem + (uint32_t)(ab * kTcAccStride);
-                    if (grp >= 2 && (!tc::mbar_wait(acc_empty + ab, ((grp >> 1) - 1) & 1, kWaitLimit) || *abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    uint32_t acc = 0;
-                    if (!tc::mbar_wait(slab_full, it & 1, kWaitLimit) || *abort_flag) {
-                        ok = false;
-                        break;
-                    }
-                    ++it;
-                    tc::fence_after_sync();
-                    for (int d = 0; d < 27 && ok; ++d) {
-                        const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                        const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
-                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                        const int s = tcount % kTcStages, u = tcount / kTcStages;
-                        if (!tc::mbar_wait(t_full + s, u & 1, kWaitLimit) || *abort_flag) {
-                            ok = false;
-                            break;
-                        }
-                        tc::fence_after_sync();
-                        const int shift = dx * m2 * m2 + dy * m2 + dz;
-                        const uint32_t b_row = (uint32_t)(S + shift) * 16u;
-                        const uint32_t a_base = ring_a + (uint32_t)s * kTcTBytes;
-#pragma unroll
-                        for (int ks = 0; ks < kTcChunk / 8; ++ks) {
-                            const uint64_t ad = tc::smem_desc_kmajor(a_base + ks * 2 * 2048u, 2048u, 128u);
-                            const uint64_t bd =
-                                tc::smem_desc_kmajor(slab_a + ks * 2 * kg_stride + b_row, kg_stride, 128u);
-                            tc::mma_tf32(dacc, ad, bd, idesc, acc);
-                            acc = 1;
-                            if (SPLIT) {  // 3xTF32: + hi(T) lo(M) + lo(T) hi(M)
-                                const uint64_t bl =
-                                    tc::smem_desc_kmajor(slab_lo_a + ks * 2 * kg_stride + b_row, kg_stride, 128u);
-                                const uint64_t al =
-                                    tc::smem_desc_kmajor(a_base + Cfg::kPartBytes + ks * 2 * 2048u, 2048u, 128u);
-                                tc::mma_tf32(dacc, ad, bl, idesc, 1);
-                                tc::mma_tf32(dacc, al, bd, idesc, 1);
-                            }
-                        }
-                        tc::mma_commit(t_empty + s);
-                        ++tcount;
-                    }
-                    tc::mma_commit(slab_empty);
-                    tc::mma_commit(acc_full + ab);  // this group's partial sum is complete
+            for (int g = 0; g < ngroups && ok; ++g) {
+                const int pi = g / NKC, buf = g & 1;
+                const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
+                const int ab = g & 1;
+                const uint32_t dacc = tmem + (uint32_t)(ab * kTcAccStride);
+                if (g >= 2 && !tc::mbar_wait(acc_empty + ab, ((g >> 1) - 1) & 1, kWaitLimit)) {
+                    ok = false;
+                    break;
                 }
+                if (!tc::mbar_wait(slab_full + buf, (g >> 1) & 1, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint64_t b_buf = b_base + (((uint64_t)buf * slab_bytes) >> 4) + (uint64_t)hal;
+                uint32_t acc = 0;
+#pragma unroll
+                for (int d = 0; d < 27; ++d) {
+                    const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+                    const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
+                    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                    if (!tc::mbar_wait(t_full + stage, tphase, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
+                    const uint64_t bd0 = b_buf + (uint64_t)((dx + 1) * slab_rows + dy * m2 + dz);
+#pragma unroll
+                    for (int ks = 0; ks < kTcChunk / 8; ++ks) {
+                        const uint64_t ad = ad0 + (uint64_t)ks * (4096u >> 4);
+                        const uint64_t bd = bd0 + (uint64_t)ks * ((2u * kg_stride) >> 4);
+                        tc::mma_tf32(dacc, ad, bd, idesc, acc);
+                        acc = 1;
+                        if (SPLIT) {  // 3xTF32: + hi(T) lo(M) + lo(T) hi(M)
+                            tc::mma_tf32(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
+                            tc::mma_tf32(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
+                        }
+                    }
+                    tc::mma_commit(t_empty + stage);
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        tphase ^= 1u;
+                    }
+                }
+                tc::mma_commit(slab_empty + buf);
+                tc::mma_commit(acc_full + ab);  // this group's partial sum is complete
             }
             if (!ok) {
                 *abort_flag = 1;
@@ -293,13 +317,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else {
         // ---------------- accumulator drains (warps 2..9) ----------------
         const int q = warp & 3;                    // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;          // column half (0: rows 0-127, 1: rows 128-255)
+        const int half = (warp - 2) >> 2;          // column half of the tile
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         float sum[kTcRows / 2];
 #pragma unroll
         for (int i = 0; i < kTcRows / 2; ++i) sum[i] = 0.f;
         bool ok = true;
-        for (int grp = 0; grp < 8 * NKC; ++grp) {
+        for (int grp = 0; grp < ngroups; ++grp) {
             const int ab = grp & 1;
             if (!tc::mbar_wait(acc_full + ab, (grp >> 1) & 1, kWaitLimit) || *abort_flag) {
                 ok = false;
@@ -417,8 +441,9 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
         for (int c = 0; c < 8; ++c)
             for (int r0 = S; r0 < R - S; r0 += kTcRows) tiles.push_back({l, c, r0, 0});
     }
-    st->slab_rows = kTcRows + 2 * max_S;
-    st->smem = (size_t)st->slab_rows * kTcKG * 16 * nparts + (size_t)kTcStages * kTcTBytes + 256;
+    (void)max_S;
+    st->slab_rows = kTcRows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
+    st->smem = 2 * (size_t)3 * st->slab_rows * kTcKG * 16 * nparts + (size_t)kTcStages * kTcTBytes + 256;
     st->ntiles = (int)tiles.size();
     if (cudaMalloc(&st->Ttc, sizeof(float) * T.size()) != cudaSuccess ||
         cudaMalloc(&st->Mtc, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess ||
