@@ -182,6 +182,31 @@ fmm_status fmm_host_operator(int kind, int p, const int* o, double* out);
  * (p+1)^2) on the host -- the basis P2M and L2P use.  Test helper. */
 fmm_status fmm_host_regular(int p, const double* u, double* out);
 
+/* One Langevin (BAOAB) step of the lambda particles on the device, driven by the force
+ * -dV/dlambda of the preceding fmm_eval (Sec. 2.1, Eq. 1; lambda particle of mass m, Sec. 2.7).
+ *   lambda, velocity: [n_sites] float, updated in place; dVdlambda: [n_sites] float
+ *   dt (ps), mass (u), gamma (1/ps), kT (kJ/mol); reflecting walls at lo < hi
+ *   seed, step: counter-based Philox4x32-10 stream (reproducible, resumable from a step)
+ *   first: nonzero on the first step (half kick)
+ * With fmm_bind_lambda(h, lambda) the next fmm_eval uses the new charges directly, so an
+ * eval + step loop runs without host involvement and can be captured in a CUDA graph. */
+fmm_status fmm_lambda_step(int n_sites, float* lambda, float* velocity, const float* dVdlambda, double dt,
+                           double mass, double gamma, double kT, unsigned long long seed,
+                           unsigned long long step, int first, double lo, double hi, void* stream);
+
+/* Batches of independent replicas (different sizes, boxes, depths, precisions).
+ * fmm_batch_create takes n existing handles (charges already set; the batch does not own
+ * them).  fmm_batch_eval evaluates every replica; x, E, F, dVdlambda are HOST arrays of n
+ * DEVICE pointers (F, dVdlambda and their entries may be NULL).  The replicas run as
+ * parallel branches of one CUDA graph, captured on the first call and re-captured whenever
+ * a pointer changes; later calls are one graph launch on `stream`.  Each replica's result is
+ * bitwise identical to its own fmm_eval. */
+typedef struct fmm_batch fmm_batch;
+fmm_status fmm_batch_create(int n, fmm_handle* const* handles, fmm_batch** out);
+fmm_status fmm_batch_eval(fmm_batch* b, const float* const* x, double* const* E, float* const* F,
+                          float* const* dVdlambda, void* stream);
+void fmm_batch_destroy(fmm_batch* b);
+
 /* Binning with no device allocation, for callers that cannot call cudaMalloc: code running
  * while a CUDA stream is being captured into a graph, processes whose device memory comes from
  * a fixed budget or a foreign allocator, and real-time loops that must not allocate.  The paper
@@ -205,6 +230,9 @@ fmm_status fmm_binning_noalloc(const fmm_box* box, int periodic, int depth, int 
 
 void fmm_destroy(fmm_handle* h);
 const char* fmm_error_string(fmm_status s);
+/* Detail of the last CUDA failure reported by this thread (the failing call and CUDA's
+ * message); an empty string when none has been recorded. */
+const char* fmm_last_error(void);
 
 #ifdef __cplusplus
 }

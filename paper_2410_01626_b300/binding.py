@@ -49,8 +49,14 @@ EXPORTS = {
     "fmm_host_operator": (I, [I, I, P, P]),
     "fmm_host_regular": (I, [I, P, P]),
     "fmm_binning_noalloc": (I, [ctypes.POINTER(FmmBox), I, I, I, P, P, P, P, P, P]),
+    "fmm_lambda_step": (I, [I, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_ulonglong, ctypes.c_ulonglong, I, ctypes.c_double, ctypes.c_double, P]),
+    "fmm_batch_create": (I, [I, P, ctypes.POINTER(P)]),
+    "fmm_batch_eval": (I, [P, P, P, P, P, P]),
+    "fmm_batch_destroy": (None, [P]),
     "fmm_destroy": (None, [P]),
     "fmm_error_string": (ctypes.c_char_p, [I]),
+    "fmm_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -80,7 +86,8 @@ def load(build_if_missing: bool = True):
 class FmmError(RuntimeError):
     def __init__(self, code, what=""):
         msg = load().fmm_error_string(code).decode()
-        super().__init__(f"{what}: {msg} (status {code})")
+        detail = load().fmm_last_error().decode() if code == 3 else ""
+        super().__init__(f"{what}: {msg} (status {code})" + (f" [{detail}]" if detail else ""))
         self.code = code
 
 
@@ -245,3 +252,40 @@ def host_regular(p, u):
     _check(lib.fmm_host_regular(int(p), uu.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p)),
            "fmm_host_regular")
     return out
+
+
+def lambda_step(lam, vel, dVdl, step, seed, dt=0.002, mass=60.0, gamma=1.0, kT=2.494339, first=False,
+                lo=-0.1, hi=1.1):
+    """One device-side BAOAB step of the lambda particles (in place)."""
+    _dev(lam, torch.float32, "lambda"), _dev(vel, torch.float32, "velocity"), _dev(dVdl, torch.float32, "dVdl")
+    _check(load().fmm_lambda_step(lam.numel(), _ptr(lam), _ptr(vel), _ptr(dVdl), dt, mass, gamma, kT, int(seed),
+                                  int(step), int(bool(first)), lo, hi, _stream()), "fmm_lambda_step")
+
+
+class Batch:
+    """Independent replicas evaluated as parallel branches of one CUDA graph."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        b = ctypes.c_void_p()
+        _check(load().fmm_batch_create(len(self.solvers), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(b)),
+               "fmm_batch_create")
+        self._b = b
+
+    def eval_into(self, xs, Es, Fs=None, dVs=None):
+        n = len(self.solvers)
+        def arr(ts):
+            if ts is None:
+                return None
+            a = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None and t.numel() else None) for t in ts])
+            return ctypes.cast(a, ctypes.c_void_p)
+        self._keep = (arr(xs), arr(Es), arr(Fs), arr(dVs))
+        _check(load().fmm_batch_eval(self._b, *self._keep, _stream()), "fmm_batch_eval")
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            load().fmm_batch_destroy(self._b)
+        self._b = None
+
+    __del__ = close

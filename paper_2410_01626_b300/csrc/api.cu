@@ -3,9 +3,11 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
+#include <algorithm>
 
 #include "fmm_internal.h"
 #include "operators.h"
@@ -17,6 +19,15 @@ struct fmm_handle {
 };
 
 namespace {
+
+thread_local char g_last_error[256] = "";
+
+// Records the failing call and CUDA's message for fmm_last_error(); returns FMM_ERR_CUDA.
+fmm_status cuda_fail(const char* what, cudaError_t e) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;
+}
 
 template <class T>
 fmm_status dalloc(T** p, size_t count) {
@@ -97,6 +108,8 @@ fmm_status cuda_ok(cudaError_t e) {
 }  // namespace
 
 extern "C" {
+
+const char* fmm_last_error(void) { return g_last_error; }
 
 const char* fmm_error_string(fmm_status s) {
     switch (s) {
@@ -499,6 +512,130 @@ void fmm_destroy(fmm_handle* H) {
     m2l_tc_free(&H->h);
     free_all(H->h);
     delete H;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Batches of independent replicas.  One fmm_batch_eval runs every replica's evaluation as a
+// parallel branch of one CUDA graph (captured on first use, re-captured when the caller's
+// pointers change), so uneven replicas share the GPU and the whole batch is one launch.
+struct fmm_batch {
+    std::vector<fmm_handle*> reps;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;  // [0] fork, [1..n] joins
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;     // pointers the graph was captured with
+};
+
+extern "C" {
+
+fmm_status fmm_batch_create(int n, fmm_handle* const* handles, fmm_batch** out) {
+    if (!out || n <= 0 || !handles) return FMM_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!handles[i]) return FMM_ERR_ARG;
+    fmm_batch* b = new (std::nothrow) fmm_batch();
+    if (!b) return FMM_ERR_OOM;
+    b->reps.assign(handles, handles + n);
+    b->streams.resize(n);
+    b->events.resize(n + 1);
+    for (int i = 0; i < n; ++i)
+        if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            fmm_batch_destroy(b);
+            return FMM_ERR_CUDA;
+        }
+    for (auto& e : b->events)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            fmm_batch_destroy(b);
+            return FMM_ERR_CUDA;
+        }
+    *out = b;
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_eval(fmm_batch* b, const float* const* x, double* const* E, float* const* F,
+                          float* const* dVdlambda, void* stream) {
+    if (!b || !x || !E) return FMM_ERR_ARG;
+    const int n = (int)b->reps.size();
+    for (int i = 0; i < n; ++i) {
+        if (!b->reps[i]->h.charges_set) return FMM_ERR_STATE;
+        if (!E[i] || (b->reps[i]->h.n > 0 && !x[i])) return FMM_ERR_ARG;
+    }
+    std::vector<const void*> key;
+    for (int i = 0; i < n; ++i) {
+        key.push_back(x[i]);
+        key.push_back(E[i]);
+        key.push_back(F ? F[i] : nullptr);
+        key.push_back(dVdlambda ? dVdlambda[i] : nullptr);
+        key.push_back(b->reps[i]->h.lam_bound);
+        key.push_back(b->reps[i]->h.perm);  // buffer growth re-captures
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaGetLastError();
+    if (!b->exec || key != b->key) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        // capture on a private stream: fork to one stream per replica, join back
+        cudaStream_t origin = nullptr;
+        cudaError_t ce = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return cuda_fail("fmm_batch_eval: stream", ce);
+        fmm_status e = FMM_OK;
+        ce = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) e = cuda_fail("fmm_batch_eval: begin capture", ce);
+        if (e == FMM_OK) {
+            char where[96] = "";
+            cudaError_t le = cudaEventRecord(b->events[0], origin);
+            if (le != cudaSuccess) snprintf(where, sizeof(where), "fork record");
+            for (int i = 0; i < n && le == cudaSuccess; ++i) {
+                le = cudaStreamWaitEvent(b->streams[i], b->events[0], 0);
+                if (le != cudaSuccess) { snprintf(where, sizeof(where), "fork wait, replica %d", i); break; }
+                launch_eval(&b->reps[i]->h, x[i], E[i], F ? F[i] : nullptr, dVdlambda ? dVdlambda[i] : nullptr,
+                            nullptr, b->streams[i]);
+                le = cudaGetLastError();
+                if (le != cudaSuccess) { snprintf(where, sizeof(where), "kernels of replica %d", i); break; }
+                le = cudaEventRecord(b->events[i + 1], b->streams[i]);
+                if (le != cudaSuccess) { snprintf(where, sizeof(where), "join record, replica %d", i); break; }
+                le = cudaStreamWaitEvent(origin, b->events[i + 1], 0);
+                if (le != cudaSuccess) { snprintf(where, sizeof(where), "join wait, replica %d", i); break; }
+            }
+            ce = cudaStreamEndCapture(origin, &b->graph);
+            if (le != cudaSuccess) {
+                char msg[160];
+                snprintf(msg, sizeof(msg), "fmm_batch_eval: capture (%s)", where);
+                e = cuda_fail(msg, le);
+            } else if (ce != cudaSuccess) {
+                e = cuda_fail("fmm_batch_eval: end capture", ce);
+            }
+        }
+        if (e == FMM_OK) {
+            ce = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            if (ce != cudaSuccess) e = cuda_fail("fmm_batch_eval: instantiate", ce);
+        }
+        cudaStreamDestroy(origin);
+        if (e != FMM_OK) return e;
+        b->key = key;
+    }
+    const cudaError_t le = cudaGraphLaunch(b->exec, st);
+    if (le != cudaSuccess) return cuda_fail("fmm_batch_eval: graph launch", le);
+    return FMM_OK;
+}
+
+void fmm_batch_destroy(fmm_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (auto e : b->events)
+        if (e) cudaEventDestroy(e);
+    delete b;
 }
 
 }  // extern "C"

@@ -455,8 +455,11 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     cudaMemcpy(st->Ttc, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice);
     if (!tiles.empty()) cudaMemcpy(st->tiles, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice);
     if (st->smem > 227 * 1024) return FMM_ERR_ARG;
-    if (st->split) cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem);
-    else cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem);
+    // The attribute is process wide per kernel: set it to the per-block maximum once, so that
+    // handles of different depths (different slab sizes) never lower each other's limit.
+    constexpr int kMaxDynSmem = 227 * 1024;
+    cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     return FMM_OK;
 }
 

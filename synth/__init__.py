@@ -120,14 +120,19 @@ def _cluster(rng, n, radius, center, min_dist=0.1):
 
 
 def _compact_sites(rng, pts, n_sites, site_size, seed_sep=0.5):
+    """Seeds at least seed_sep apart (relaxed step by step when the cluster is too small to
+    hold that many), each with its nearest unused cluster atoms."""
     order = rng.permutation(len(pts))
-    seeds = []
-    for i in order:
-        if all(np.sum((pts[i] - pts[j]) ** 2) >= seed_sep ** 2 for j in seeds):
-            seeds.append(i)
-            if len(seeds) == n_sites:
-                break
-    if len(seeds) < n_sites:
+    for sep in (seed_sep, 0.35, 0.25, 0.0):
+        seeds = []
+        for i in order:
+            if all(np.sum((pts[i] - pts[j]) ** 2) >= sep ** 2 for j in seeds):
+                seeds.append(i)
+                if len(seeds) == n_sites:
+                    break
+        if len(seeds) == n_sites:
+            break
+    if len(seeds) < n_sites or n_sites * site_size > len(pts):
         raise ValueError("cluster too small for the requested number of sites")
     used = np.zeros(len(pts), bool)
     used[seeds] = True
