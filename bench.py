@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="30k-atom system (for profiling runs)")
+    ap.add_argument("--workload", default="solvated_500k", choices=["solvated_500k", "batch64", "loop1000"],
+                    help="batch64: 64 uneven replicas in one graph; loop1000: lambda-dynamics loop")
     return ap.parse_args()
 
 
@@ -386,10 +388,145 @@ def run_native(args):
     return 0
 
 
+def _timed_region(fn, steps, stream, local, flush=None):
+    """Run fn() `steps` times between CUDA events (L2 flushed before each step when given);
+    returns per-step ms and the sampled clocks."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], clk.stop()
+
+
+def run_batch(args):
+    """64 independent replicas (N log-uniform in 5k..50k) evaluated as one CUDA graph; depths
+    chosen per replica by the autotuner."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2410_01626_b300 import Batch, FMM
+    from paper_2410_01626_b300.autotune import tune_depth
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = "tf32" if args.precision == "auto" else args.precision
+    reps = synth.replicas(64, first_seed=100 + 64 * rank)
+    solvers, xs, depths = [], [], []
+    for s in reps:
+        t = {k: torch.from_numpy(np.ascontiguousarray(s[k])).to(dev) for k in ("x", "qA", "qB", "site", "lam")}
+        d, _ = tune_depth(s["L"], True, s["p"], prec, t["x"], t["qA"], t["qB"], t["site"], t["lam"], reps=2)
+        f = FMM(s["L"], True, s["p"], d, precision=prec)
+        f.set_charges(t["qA"], t["qB"], t["site"], t["lam"])
+        solvers.append(f)
+        xs.append(t["x"])
+        depths.append(d)
+    outs = [f.outputs(dev) for f in solvers]
+    b = Batch(solvers)
+    stream = torch.cuda.current_stream()
+    fn = lambda: b.eval_into(xs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    for _ in range(max(args.warmup, 3)):
+        fn()
+    ms_list, clocks = _timed_region(fn, args.steps, stream, local)
+    ms = sum(ms_list) / len(ms_list)
+    atoms = sum(len(s["x"]) for s in reps)
+    line = {"metric": "replica FMM evals/s (64 replicas, 5k-50k atoms, one CUDA graph)", "value": ws * 64 * 1000.0 / ms,
+            "unit": "replica-evals/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": "batch64: replicas seeds 100..163, periodic, p=8, autotuned depths",
+                       "atoms_total": atoms, "depths": depths, "precision": prec,
+                       "l2": "working set of all replicas (~0.6 GB) exceeds L2"},
+            "atom_evals_per_s": ws * atoms * 1000.0 / ms,
+            "gpu_launches": sum(f.launches_per_eval() for f in solvers) * args.steps, "clocks": clocks,
+            "roofline": None, "cpu_baseline": None, "e2e": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    for f in solvers:
+        f.close()
+    return 0
+
+
+def run_loop(args):
+    """lambda dynamics on the 500k system: per step one FMM evaluation (CUDA graph) and one
+    device Langevin step; lambda is bound to the solver so charges refresh every step."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2410_01626_b300 import FMM, lambda_step
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = "3xtf32" if args.precision == "auto" else args.precision
+    s = synth.solvated_500k()
+    t = {k: torch.from_numpy(np.ascontiguousarray(s[k])).to(dev) for k in ("x", "qA", "qB", "site", "lam")}
+    f = FMM(s["L"], True, s["p"], s["depth"], precision=prec)
+    f.set_charges(t["qA"], t["qB"], t["site"], t["lam"])
+    lam = t["lam"].clone()
+    vel = torch.zeros_like(lam)
+    f.bind_lambda(lam)
+    E, F, dV, _ = f.outputs(dev)
+    f.eval_into(t["x"], E, F, dV)
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(g, stream=cs):
+            f.eval_into(t["x"], E, F, dV)
+    torch.cuda.current_stream().wait_stream(cs)
+    n_steps = 1000
+    step = [0]
+
+    def one():
+        g.replay()
+        lambda_step(lam, vel, dV, step[0], 5, first=(step[0] == 0))
+        step[0] += 1
+
+    for _ in range(max(args.warmup, 3)):
+        one()
+    torch.cuda.synchronize()
+    a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    a.record()
+    for _ in range(n_steps):
+        one()
+    b2.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = a.elapsed_time(b2) / n_steps
+    lam_np = lam.cpu().numpy()
+    line = {"metric": "lambda-dynamics steps/s (500k atoms: FMM eval + Langevin step, graph replay)",
+            "value": ws * 1000.0 / ms, "unit": "steps/s", "n_gpus": ws, "steps": n_steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+            "data": "synthetic",
+            "config": {"workload": "loop1000: " + WORKLOAD, "langevin": "BAOAB m=60 u, dt=2 fs, gamma=1/ps, 300 K",
+                       "l2": "working set > L2 per step"},
+            "lambda_range": [float(lam_np.min()), float(lam_np.max())],
+            "gpu_launches": (f.launches_per_eval() + 1) * n_steps, "clocks": clocks,
+            "roofline": None, "cpu_baseline": None, "e2e": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    f.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "loop1000":
+        return run_loop(args)
     return run_native(args)
 
 

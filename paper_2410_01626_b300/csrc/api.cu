@@ -8,6 +8,9 @@
 #include <new>
 #include <vector>
 #include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
 
 #include "fmm_internal.h"
 #include "operators.h"
@@ -107,6 +110,59 @@ fmm_status cuda_ok(cudaError_t e) {
 
 }  // namespace
 
+// Host-built operator banks depend only on (p, periodic); handles in one process share them.
+struct HostOps {
+    std::vector<float> T, Trm, A, B, B2;
+    std::vector<double> Ad, Lam;
+};
+
+static std::shared_ptr<const HostOps> host_ops(int p, int periodic, bool want_rowmajor) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, std::shared_ptr<HostOps>> cache;
+    const int nc = ncoef(p), ncp = ncoef_padded(p);
+    std::lock_guard<std::mutex> lock(mu);
+    auto& slot = cache[{p, periodic}];
+    if (slot && (!want_rowmajor || !slot->Trm.empty())) return slot;
+    auto o = std::make_shared<HostOps>();
+    std::vector<double> op((size_t)nc * nc);
+    o->T.assign((size_t)kNumOps * ncp * ncp, 0.f);
+    o->Trm.assign((size_t)kNumOps * nc * nc, 0.f);
+    for (int ox = -3; ox <= 3; ++ox)
+        for (int oy = -3; oy <= 3; ++oy)
+            for (int oz = -3; oz <= 3; ++oz) {
+                if (std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz))) < 2) continue;
+                const int oo[3] = {ox, oy, oz};
+                op_m2l(p, oo, op.data());
+                float* dst = o->T.data() + (size_t)op_index(ox, oy, oz) * ncp * ncp;
+                for (int j = 0; j < nc; ++j)
+                    for (int k = 0; k < nc; ++k) dst[(size_t)k * ncp + j] = (float)op[(size_t)j * nc + k];
+                for (size_t e = 0; e < (size_t)nc * nc; ++e)
+                    o->Trm[(size_t)op_index(ox, oy, oz) * nc * nc + e] = (float)op[e];
+            }
+    o->A.assign((size_t)8 * ncp * ncp, 0.f);
+    o->B.assign((size_t)8 * ncp * ncp, 0.f);
+    o->B2.assign((size_t)8 * ncp * ncp, 0.f);
+    o->Ad.resize((size_t)8 * nc * nc);
+    for (int c = 0; c < 8; ++c) {
+        op_m2m(p, c, op.data());
+        std::memcpy(o->Ad.data() + (size_t)c * nc * nc, op.data(), sizeof(double) * nc * nc);
+        for (int j = 0; j < nc; ++j)
+            for (int k = 0; k < nc; ++k) o->A[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
+        op_l2l(p, c, op.data());
+        for (int j = 0; j < nc; ++j)
+            for (int k = 0; k < nc; ++k) {
+                o->B[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
+                o->B2[(size_t)k * 8 * ncp + c * ncp + j] = (float)op[(size_t)j * nc + k];
+            }
+    }
+    if (periodic) {
+        o->Lam.resize((size_t)nc * nc);
+        op_lattice(p, o->Lam.data());
+    }
+    slot = o;
+    return slot;
+}
+
 extern "C" {
 
 const char* fmm_last_error(void) { return g_last_error; }
@@ -194,67 +250,30 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
 
     const int nc = h.nc, ncp = h.ncp;
     fmm_status st = FMM_OK;
-    // ---- operators ----
+    // ---- operators (host banks cached per (p, periodic)) ----
     {
-        std::vector<double> op((size_t)nc * nc);
-        std::vector<float> T((size_t)kNumOps * ncp * ncp, 0.f);
-        std::vector<float> Trm;  // output-major copy for the tensor-core layout
-        if (precision != FMM_FP32) Trm.assign((size_t)kNumOps * nc * nc, 0.f);
-        for (int ox = -3; ox <= 3; ++ox)
-            for (int oy = -3; oy <= 3; ++oy)
-                for (int oz = -3; oz <= 3; ++oz) {
-                    if (std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz))) < 2) continue;
-                    const int o[3] = {ox, oy, oz};
-                    op_m2l(p, o, op.data());
-                    float* dst = T.data() + (size_t)op_index(ox, oy, oz) * ncp * ncp;
-                    for (int j = 0; j < nc; ++j)
-                        for (int k = 0; k < nc; ++k) dst[(size_t)k * ncp + j] = (float)op[(size_t)j * nc + k];
-                    if (!Trm.empty())
-                        for (size_t e = 0; e < (size_t)nc * nc; ++e)
-                            Trm[(size_t)op_index(ox, oy, oz) * nc * nc + e] = (float)op[e];
-                }
-        std::vector<float> A((size_t)8 * ncp * ncp, 0.f), B((size_t)8 * ncp * ncp, 0.f), B2((size_t)8 * ncp * ncp, 0.f);
-        std::vector<double> Ad((size_t)8 * nc * nc);
-        for (int c = 0; c < 8; ++c) {
-            op_m2m(p, c, op.data());
-            std::memcpy(Ad.data() + (size_t)c * nc * nc, op.data(), sizeof(double) * nc * nc);
-            for (int j = 0; j < nc; ++j)
-                for (int k = 0; k < nc; ++k) A[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
-            op_l2l(p, c, op.data());
-            for (int j = 0; j < nc; ++j)
-                for (int k = 0; k < nc; ++k) {
-                    B[((size_t)c * ncp + k) * ncp + j] = (float)op[(size_t)j * nc + k];
-                    B2[(size_t)k * 8 * ncp + c * ncp + j] = (float)op[(size_t)j * nc + k];
-                }
-        }
-        if ((st = dalloc(&h.T, T.size())) || (st = dalloc(&h.A, A.size())) || (st = dalloc(&h.B, B.size())) || (st = dalloc(&h.B2, B2.size())) ||
-            (st = dalloc(&h.Ad, Ad.size()))) {
+        const std::shared_ptr<const HostOps> ops = host_ops(p, periodic, precision != FMM_FP32);
+        if ((st = dalloc(&h.T, ops->T.size())) || (st = dalloc(&h.A, ops->A.size())) ||
+            (st = dalloc(&h.B, ops->B.size())) || (st = dalloc(&h.B2, ops->B2.size())) ||
+            (st = dalloc(&h.Ad, ops->Ad.size())) || (periodic && (st = dalloc(&h.Lam, ops->Lam.size())))) {
             free_all(h);
             delete H;
             return st;
         }
-        cudaMemcpy(h.T, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice);
-        cudaMemcpy(h.A, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice);
-        cudaMemcpy(h.B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice);
-        cudaMemcpy(h.B2, B2.data(), sizeof(float) * B2.size(), cudaMemcpyHostToDevice);
-        cudaMemcpy(h.Ad, Ad.data(), sizeof(double) * Ad.size(), cudaMemcpyHostToDevice);
-        if (periodic) {
-            op_lattice(p, op.data());
-            if ((st = dalloc(&h.Lam, op.size()))) {
-                free_all(h);
-                delete H;
-                return st;
-            }
-            cudaMemcpy(h.Lam, op.data(), sizeof(double) * op.size(), cudaMemcpyHostToDevice);
-        }
-        if (!Trm.empty()) {
+        cudaMemcpy(h.T, ops->T.data(), sizeof(float) * ops->T.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.A, ops->A.data(), sizeof(float) * ops->A.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.B, ops->B.data(), sizeof(float) * ops->B.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.B2, ops->B2.data(), sizeof(float) * ops->B2.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(h.Ad, ops->Ad.data(), sizeof(double) * ops->Ad.size(), cudaMemcpyHostToDevice);
+        if (periodic) cudaMemcpy(h.Lam, ops->Lam.data(), sizeof(double) * ops->Lam.size(), cudaMemcpyHostToDevice);
+        if (precision != FMM_FP32) {
             h.lvl_off.assign(depth + 2, 0);
             long a2 = 0;
             for (int l = 0; l <= depth; ++l) {
                 h.lvl_off[l] = a2;
                 a2 += 1L << (3 * l);
             }
-            const int e = m2l_tc_setup(&h, Trm);
+            const int e = m2l_tc_setup(&h, ops->Trm);
             if (e != FMM_OK) {
                 m2l_tc_free(&h);
                 free_all(h);
