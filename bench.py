@@ -49,6 +49,17 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_ms(pg, ms: float, device=None) -> float:
+    """Max of a per-rank time over the process group (the job is as fast as its slowest rank);
+    the whole-job throughput is then world_size * units / max_ms."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,9 +267,7 @@ def run_native(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
     if pg:
-        tt = torch.tensor([ms], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = aggregate_ms(pg, ms, dev)
         pg.barrier()
     value = ws * 1000.0 / ms
 
@@ -308,9 +317,7 @@ def run_native(args):
             e_ms.append((time.perf_counter() - a) * 1e3)
         em = sum(e_ms) / len(e_ms)
         if pg:
-            tt = torch.tensor([em], device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            em = float(tt.item())
+            em = aggregate_ms(pg, em, dev)
         e2e = {"value": ws * 1000.0 / em, "unit": "evals/s", "h2d_bytes_per_step": 12 * n,
                "d2h_bytes_per_step": 8 + 12 * n + 4 * K, "ms_per_step": em}
 
