@@ -301,7 +301,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     const long nleaf = 1L << (3 * depth);
     if ((st = dalloc(&h.M, (size_t)acc * ncp)) || (st = dalloc(&h.L, (size_t)acc * ncp)) ||
         (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.start, nleaf)) ||
-        (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.epart, (nleaf + 3) / 4)) ||
+        (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.epart, nleaf)) ||
         (st = dalloc(&h.leafqdt, 5 * nleaf)) || (st = dalloc(&h.root, nc + 8 + 5 * 64)) || (st = dalloc(&h.status, 1)) ||
         (st = dalloc(&h.site_ptr, 1)) ||
         (st = dalloc(&h.work, 8L * (depth >= 1 ? (1L << (3 * (depth - 1))) : 1) * ncp))) {
@@ -309,7 +309,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         delete H;
         return st;
     }
-    h.epart_cap = (int)((nleaf + 3) / 4);
+    h.epart_cap = (int)nleaf;
     if (!tiles.empty())
         cudaMemcpy(h.tiles, tiles.data(), sizeof(M2LTile) * tiles.size(), cudaMemcpyHostToDevice);
     cudaMemset(h.M, 0, sizeof(float) * acc * ncp);

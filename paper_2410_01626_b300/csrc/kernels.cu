@@ -604,20 +604,56 @@ __global__ void __launch_bounds__(128) k_l2p(int n, int use_far, NearParams a, c
     far[s] = make_float4(pot, gx, gy, gz);
 }
 
+// ---- packed two-wide FP32 arithmetic (f32x2) ----
+__device__ __forceinline__ unsigned long long f2pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2unpack(unsigned long long v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Near field, one warp per target leaf.
 // (1) Lanes 0..26 resolve the 27 neighbour leaves at once (periodic image shift, start,
-//     count) and a warp scan gives each neighbour's offset in a per-warp source list.
+//     count); the target's own leaf is listed first, its count rounded up to even.  A warp
+//     scan gives each neighbour's offset in a per-warp source list.
 // (2) When the list fits (kNearCap atoms, the common case), all lanes copy it into shared
-//     memory in one pass, so that every global load is in flight together; otherwise the
-//     sources are streamed neighbour by neighbour in chunks of 32.
+//     memory in one pass as packed pairs (x0 x1 y0 y1 | z0 z1 q0 q1), so that every global
+//     load is in flight together; otherwise the sources are streamed neighbour by neighbour.
 // (3) The warp is split into G = 32/TPG source slices (lane = target + slice * TPG), TPG in
-//     {4, 8, 16, 32} chosen per leaf to minimise padded target slots x source iterations;
-//     slice sums are combined with shuffles, then the far field (k_l2p) is added.
-constexpr int kNearCap = 640;
+//     {4, 8, 16, 32} chosen per leaf to minimise padded target slots x source iterations.
+//     Each iteration takes two sources with f32x2 arithmetic; only the own leaf's pairs need
+//     the r > 0 test (self, coincident atoms), since equal positions always share a leaf.
+//     Slice sums are combined with shuffles, then the far field (k_l2p) is added.
+constexpr int kNearCap = 512;
 __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restrict__ far) {
-    __shared__ float4 src_sm[4][kNearCap];
+    __shared__ float4 src_sm[4][kNearCap];  // packed pairs: [2j] = (x x y y), [2j+1] = (z z q q)
     __shared__ int nb_off[4][28];
     __shared__ int nb_s0[4][27];
+    __shared__ int nb_sc[4][27];
     __shared__ float nb_sh[4][27][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int leaf = blockIdx.x * 4 + w;
@@ -627,11 +663,12 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
         const int ix = (int)compact3(leaf), iy = (int)compact3(leaf >> 1), iz = (int)compact3(leaf >> 2);
         const float h = a.h;
         const int st = a.start[leaf], cnt = a.count[leaf];
-        // (1) neighbour table: lane o < 27 owns neighbour o
+        // (1) neighbour table: lane 0 = own leaf (offset 13), lanes 1..26 = the others
         int my_s0 = 0, my_sc = 0;
         float shx = 0.f, shy = 0.f, shz = 0.f;
         if (lane < 27) {
-            int sx = ix + lane / 9 - 1, sy = iy + (lane / 3) % 3 - 1, sz = iz + lane % 3 - 1;
+            const int o = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);
+            int sx = ix + o / 9 - 1, sy = iy + (o / 3) % 3 - 1, sz = iz + o % 3 - 1;
             bool ok = true;
             if (a.periodic) {
                 const int wx = (sx + nb) & (nb - 1), wy = (sy + nb) & (nb - 1), wz = (sz + nb) & (nb - 1);
@@ -650,43 +687,63 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
                 my_sc = (int)a.count[src];
             }
         }
-        int incl = my_sc;
+        const int slot = (lane == 0) ? ((my_sc + 1) & ~1) : my_sc;  // own leaf padded to even
+        int incl = slot;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += y;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int own_pairs = __shfl_sync(0xffffffffu, slot, 0) >> 1;
         if (lane < 27) {
             nb_off[w][lane + 1] = incl;
             nb_s0[w][lane] = my_s0;
+            nb_sc[w][lane] = my_sc;
             nb_sh[w][lane][0] = shx;
             nb_sh[w][lane][1] = shy;
             nb_sh[w][lane][2] = shz;
         }
         if (lane == 0) nb_off[w][0] = 0;
         __syncwarp();
-        const bool staged = total <= kNearCap;
+        const int npairs = (total + 1) >> 1;
+        const bool staged = 2 * npairs <= kNearCap;
         if (staged) {  // (2) one pass over every source atom of the 27 neighbours
-            for (int j = lane; j < total; j += 32) {
-                int o = 0;  // largest neighbour with nb_off[o] <= j
+            for (int j0 = 0; j0 < 2 * npairs; j0 += 32) {  // uniform trip count: shuffles below
+                const int j = j0 + lane;
+                int o = 0;  // largest neighbour slot with nb_off[o] <= j
 #pragma unroll
                 for (int step = 16; step >= 1; step >>= 1)
                     if (o + step < 27 && nb_off[w][o + step] <= j) o += step;
-                float4 sp = a.pos[nb_s0[w][o] + (j - nb_off[w][o])];
-                sp.x += nb_sh[w][o][0];
-                sp.y += nb_sh[w][o][1];
-                sp.z += nb_sh[w][o][2];
-                src_sm[w][j] = sp;
+                const int k = j - nb_off[w][o];
+                // padding (own leaf odd, list odd): a zero charge far away contributes nothing
+                float4 sp = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+                if (j < total && k < nb_sc[w][o]) {
+                    sp = a.pos[nb_s0[w][o] + k];
+                    sp.x += nb_sh[w][o][0];
+                    sp.y += nb_sh[w][o][1];
+                    sp.z += nb_sh[w][o][2];
+                }
+                // lane pair (2i, 2i+1) holds one source pair; each lane writes one float4 of it
+                const float4 nb4 = make_float4(__shfl_xor_sync(0xffffffffu, sp.x, 1), __shfl_xor_sync(0xffffffffu, sp.y, 1),
+                                               __shfl_xor_sync(0xffffffffu, sp.z, 1), __shfl_xor_sync(0xffffffffu, sp.w, 1));
+                const bool even = (lane & 1) == 0;
+                const float4 lo = even ? sp : nb4, hi = even ? nb4 : sp;  // sources 2i and 2i+1
+                if (j < 2 * npairs) {
+                    float4* dst = src_sm[w] + 2 * (j >> 1);
+                    if (even) dst[0] = make_float4(lo.x, hi.x, lo.y, hi.y);
+                    else dst[1] = make_float4(lo.z, hi.z, lo.w, hi.w);
+                }
             }
             __syncwarp();
         }
         // (3) slice shape: cost = target passes x (source iterations + combine overhead)
+        const int work = staged ? npairs : total;
         int TPG = 32, best = 1 << 30;
 #pragma unroll
         for (int tpg = 4; tpg <= 32; tpg <<= 1) {
             const int g = 32 / tpg;
-            const int cost = ((cnt + tpg - 1) / tpg) * ((total + g - 1) / g + 8 * (31 - __clz(g)) + 24);
+            const int cost = ((cnt + tpg - 1) / tpg) * ((work + g - 1) / g + 8 * (31 - __clz(g)) + 24);
             if (cost < best) {
                 best = cost;
                 TPG = tpg;
@@ -699,30 +756,47 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
             const bool valid = ti < cnt;
             float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) me = a.pos[st + ti];
-            float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-            auto pair = [&](const float4 s4) {
-                const float dx = me.x - s4.x, dy = me.y - s4.y, dz = me.z - s4.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
-                const float qri = s4.w * ri;
-                pot += qri;
-                const float qri3 = qri * ri * ri;
-                gx = fmaf(-qri3, dx, gx);
-                gy = fmaf(-qri3, dy, gy);
-                gz = fmaf(-qri3, dz, gz);
-            };
+            float pot, gx, gy, gz;
             if (staged) {
+                const unsigned long long mx = f2pack(me.x, me.x), my = f2pack(me.y, me.y), mz = f2pack(me.z, me.z);
+                unsigned long long P = 0ull, GX = 0ull, GY = 0ull, GZ = 0ull;
+                const float4* sp4 = src_sm[w];
+                // sources minus target: the gradient of q/r at the target is q (s - x) / r^3
+                auto pair2 = [&](const float4 A, const float4 B, const bool check) {
+                    const unsigned long long dx = f2sub(f2pack(A.x, A.y), mx);
+                    const unsigned long long dy = f2sub(f2pack(A.z, A.w), my);
+                    const unsigned long long dz = f2sub(f2pack(B.x, B.y), mz);
+                    const float2 r2 = f2unpack(f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx))));
+                    float r0 = rsqrtf(r2.x), r1 = rsqrtf(r2.y);
+                    if (check) {
+                        r0 = (r2.x > 0.f) ? r0 : 0.f;
+                        r1 = (r2.y > 0.f) ? r1 : 0.f;
+                    }
+                    const unsigned long long ri = f2pack(r0, r1);
+                    const unsigned long long qri = f2mul(f2pack(B.z, B.w), ri);
+                    P = f2add(P, qri);
+                    const unsigned long long qri3 = f2mul(qri, f2mul(ri, ri));
+                    GX = f2fma(qri3, dx, GX);
+                    GY = f2fma(qri3, dy, GY);
+                    GZ = f2fma(qri3, dz, GZ);
+                };
                 int t = slice;
-                for (; t + 3 * G < total; t += 4 * G) {
-                    pair(src_sm[w][t]);
-                    pair(src_sm[w][t + G]);
-                    pair(src_sm[w][t + 2 * G]);
-                    pair(src_sm[w][t + 3 * G]);
+                for (; t < own_pairs; t += G) pair2(sp4[2 * t], sp4[2 * t + 1], true);
+                for (; t + G < npairs; t += 2 * G) {
+                    pair2(sp4[2 * t], sp4[2 * t + 1], false);
+                    pair2(sp4[2 * (t + G)], sp4[2 * (t + G) + 1], false);
                 }
-                for (; t < total; t += G) pair(src_sm[w][t]);
+                for (; t < npairs; t += G) pair2(sp4[2 * t], sp4[2 * t + 1], false);
+                const float2 p2 = f2unpack(P), x2 = f2unpack(GX), y2 = f2unpack(GY), z2 = f2unpack(GZ);
+                pot = p2.x + p2.y;
+                gx = x2.x + x2.y;
+                gy = y2.x + y2.y;
+                gz = z2.x + z2.y;
             } else {
+                pot = gx = gy = gz = 0.f;
+                float4* stage = src_sm[w];
                 for (int o = 0; o < 27; ++o) {
-                    const int s0 = nb_s0[w][o], sc = nb_off[w][o + 1] - nb_off[w][o];
+                    const int s0 = nb_s0[w][o], sc = nb_sc[w][o];
                     for (int sb = 0; sb < sc; sb += 32) {
                         float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
@@ -730,10 +804,21 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
                         sp.y += nb_sh[w][o][1];
                         sp.z += nb_sh[w][o][2];
                         __syncwarp();
-                        src_sm[w][lane] = sp;
+                        stage[lane] = sp;
                         __syncwarp();
                         const int ns = min(32, sc - sb);
-                        for (int t = slice; t < ns; t += G) pair(src_sm[w][t]);
+                        for (int t = slice; t < ns; t += G) {
+                            const float4 s4 = stage[t];
+                            const float dx = s4.x - me.x, dy = s4.y - me.y, dz = s4.z - me.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
+                            const float qri = s4.w * ri;
+                            pot += qri;
+                            const float qri3 = qri * ri * ri;
+                            gx = fmaf(qri3, dx, gx);
+                            gy = fmaf(qri3, dy, gy);
+                            gz = fmaf(qri3, dz, gz);
+                        }
                     }
                 }
             }
@@ -764,13 +849,11 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
             }
         }
     }
-    // block reduction of q phi (fixed order)
+    // warp reduction of q phi (fixed order), one partial per leaf: no block barrier, so a
+    // warp with a small leaf does not wait for its neighbours
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, d);
-    __shared__ double red[4];
-    if (lane == 0) red[w] = esum;
-    __syncthreads();
-    if (threadIdx.x == 0) a.epart[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+    if (lane == 0 && leaf < a.nleaf) a.epart[leaf] = esum;
 }
 
 __global__ void k_final(int nparts, const double* __restrict__ epart, double ke, double* __restrict__ E, int K,
@@ -976,7 +1059,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     if (has_far && n > 0) FMM_DISPATCH_P(h->p, launch_l2p, n, a.use_far, a, h->sorted_key, h->far, st);
     k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, has_far ? h->far : nullptr);
     stage(h, 7, st);
-    const int nparts = (nleaf + 3) / 4;
+    const int nparts = nleaf;  // one q phi partial per leaf
     k_final<<<1, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,
                                h->phis, dVdl);
     stage(h, 8, st);
