@@ -62,7 +62,10 @@ typedef enum {
 typedef enum {
     FMM_FP32 = 0,        /* every stage in FP32 on CUDA cores (root/lattice FP64) */
     FMM_MIXED_TF32 = 1,  /* M2L on tcgen05 tensor cores in TF32, FP32 accumulate  */
-    FMM_MIXED_3XTF32 = 2 /* M2L as three TF32 products (split operands)           */
+    FMM_MIXED_3XTF32 = 2, /* M2L as three TF32 products (split operands)          */
+    FMM_MIXED_3XBF16 = 3  /* M2L as three BF16 products hi*hi + hi*lo + lo*hi of
+                             split operands (about 16 significant bits, twice the
+                             tensor rate of TF32), FP32 accumulate                  */
 } fmm_precision;
 
 typedef struct {

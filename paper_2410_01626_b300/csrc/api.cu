@@ -223,7 +223,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     if (opt) {
         for (int r : opt->reserved)
             if (r != 0) return FMM_ERR_ARG;
-        if (opt->precision < FMM_FP32 || opt->precision > FMM_MIXED_3XTF32) return FMM_ERR_ARG;
+        if (opt->precision < FMM_FP32 || opt->precision > FMM_MIXED_3XBF16) return FMM_ERR_ARG;
         precision = opt->precision;
         if (opt->coulomb_k > 0.0) ke = opt->coulomb_k;
     }

@@ -1,4 +1,6 @@
-// M2L on the 5th-generation tensor cores: tcgen05.mma kind::tf32, FP32 accumulation in TMEM.
+// M2L on the 5th-generation tensor cores: tcgen05.mma kind::tf32 (one TF32 product, or three
+// products of hi/lo TF32 parts) or kind::f16 (three products of hi/lo BF16 parts), FP32
+// accumulation in TMEM.
 //
 // The multipole-to-local translation of one level is, for every target box b,
 //     L_b = sum_{o in IL(b)} T_o M_{b+o}
@@ -10,14 +12,17 @@
 // images or zeros) and linearised row-major, so for a fixed (c, pi) every delta is a
 // constant row shift  delta_x (n+2)^2 + delta_y (n+2) + delta_z.
 //
-// A CTA owns 256 consecutive "virtual rows" r0..r0+255 of the target class (interior rows
+// A CTA owns 192 consecutive "virtual rows" r0..r0+191 of the target class (interior rows
 // are targets, ghost rows are discarded) and accumulates D[coef_out][row] in TMEM:
-//   A = T_o chunk      (M = 128 output coefficients x K = 32 input coefficients), smem
-//   B = source slab    (N = 256 rows x K = 32) -- one slab per (pi, K chunk) serves all
-//                      deltas: the B descriptor just starts delta rows further in.
+//   A = T_o chunk      (M = 128 output coefficients x one K chunk of input coefficients), smem
+//   B = source slab    (N = 192 rows x the same K chunk) -- one slab per (pi, K chunk) serves
+//                      all deltas: the B descriptor just starts delta rows further in.
+// Operands are stored in 16-byte core-matrix rows ("cells": 4 TF32 or 8 BF16 coefficients),
+// so every mode has the same byte layout; one MMA consumes 32 bytes of K (8 TF32 or 16 BF16).
 // Warp 0 lane 0 streams slabs and operator chunks with cp.async.bulk into a 3-stage ring;
-// warp 1 lane 0 issues the MMAs; all four warps drain TMEM into the Morton-ordered L.
+// warp 1 lane 0 issues the MMAs; warps 2..9 drain TMEM into the Morton-ordered L.
 // Every wait is bounded; on expiry the CTA flags FMM_DEV_TIMEOUT and returns cleanly.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,18 +41,24 @@ constexpr int kTcRows = 192;    // virtual rows (N) per CTA: 280 CTAs = two full
 constexpr int kTcTmemCols = 512; // two accumulators, 256 columns apart
 constexpr int kTcAccStride = 256;
 constexpr int kTcStages = 3;    // operator-chunk ring depth
-constexpr uint32_t kTcTBytes = 16384;  // one ring stage: 128 rows x 32 coefficients (or hi+lo x 16)
+constexpr uint32_t kTcTBytes = 16384;  // one ring stage: one operator chunk, hi (+ lo) parts
 constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
-// K chunk (input coefficients per slab / operator chunk): 32 for TF32, 16 for the split 3xTF32
-// form (hi and lo slabs), so one ring stage is 16 KB and one slab buffer about 86 KB in both
-// forms, and two slab buffers fit next to a 3-stage ring.
-template <bool SPLIT>
+// Operand forms.  K chunk (input coefficients per slab / operator chunk): 32 for TF32, 16 for
+// the split 3xTF32 form (hi and lo parts), 32 for the split 3xBF16 form; in every form one ring
+// stage is 16 KB and one slab buffer about 86 KB, so two slab buffers fit next to a 3-stage ring.
+enum TcMode { kTf32 = 0, kTf32x3 = 1, kBf16x3 = 2 };
+template <int MODE>
 struct TcCfg {
-    static constexpr int kChunk = SPLIT ? 16 : 32;
-    static constexpr int kKG = kChunk / 4;
-    static constexpr int kParts = SPLIT ? 2 : 1;
-    static constexpr uint32_t kPartBytes = 128u * kChunk * 4u;  // one operator part (hi or lo)
-    static constexpr uint32_t kStageBytes = kParts * kPartBytes;  // 16 KB
+    static constexpr bool kSplit = MODE != kTf32;
+    static constexpr bool kBf16 = MODE == kBf16x3;
+    static constexpr int kElem = kBf16 ? 2 : 4;             // bytes per operand element
+    static constexpr int kPerCell = 16 / kElem;             // coefficients per 16-byte cell
+    static constexpr int kChunk = kBf16 ? 32 : (kSplit ? 16 : 32);
+    static constexpr int kKG = kChunk / kPerCell;           // cells per chunk row (8, 4, 4)
+    static constexpr int kKSteps = kChunk * kElem / 32;     // MMAs per chunk (32 bytes of K each)
+    static constexpr int kParts = kSplit ? 2 : 1;
+    static constexpr uint32_t kPartBytes = 128u * kChunk * kElem;  // one operator part (hi or lo)
+    static constexpr uint32_t kStageBytes = kParts * kPartBytes;   // 16 KB
 };
 
 struct TcLevels {
@@ -69,8 +80,18 @@ __device__ __forceinline__ uint32_t spread3_tc(uint32_t v) {
     return v;
 }
 
-// Pack one level's multipoles into [class][kgroup][(n+2)^3 rows][4], rounded to TF32
-// (round to nearest: the tensor core itself would truncate).
+// Pack one level's multipoles into [class][cell][(n+2)^3 rows][16 bytes].  TF32 forms: a cell
+// holds 4 coefficients rounded to TF32 (round to nearest: the tensor core itself would
+// truncate), and the lo part is the TF32 rounding of the remainder.  BF16 form: a cell holds
+// 8 coefficients rounded to BF16 (nearest even), lo = BF16 rounding of the remainder.
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {  // a in the low half (first in memory)
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+__device__ __forceinline__ float bf16_lo_of(uint32_t pair) { return __uint_as_float(pair << 16); }
+__device__ __forceinline__ float bf16_hi_of(uint32_t pair) { return __uint_as_float(pair & 0xFFFF0000u); }
+
+template <bool BF16>
 __global__ void k_m2l_pack(int n, int R, int NKG, int ncp, int periodic, const float* __restrict__ Mlev,
                            float* __restrict__ Mtc, float* __restrict__ Mtc_lo) {
     const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,7 +103,8 @@ __global__ void k_m2l_pack(int n, int R, int NKG, int ncp, int periodic, const f
     const int m2 = n + 2;
     int i = row / (m2 * m2) - 1, j = (row / m2) % m2 - 1, k = row % m2 - 1;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f), lo = v;
-    bool ok = 4 * g < ncp;
+    constexpr int kPerCell = BF16 ? 8 : 4;
+    bool ok = kPerCell * g < ncp;
     if (periodic) {
         i = (i + n) % n;
         j = (j + n) % n;
@@ -92,6 +114,20 @@ __global__ void k_m2l_pack(int n, int R, int NKG, int ncp, int periodic, const f
     }
     if (ok) {
         const uint32_t box = ((spread3_tc(i) | (spread3_tc(j) << 1) | (spread3_tc(k) << 2)) << 3) | (uint32_t)cls;
+        if (BF16) {
+            const float4 x0 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + 8 * g);
+            const float4 x1 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + 8 * g + 4);
+            const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            uint32_t hi[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                hi[e] = bf16_pair(xs[2 * e], xs[2 * e + 1]);
+                lw[e] = bf16_pair(xs[2 * e] - bf16_lo_of(hi[e]), xs[2 * e + 1] - bf16_hi_of(hi[e]));
+            }
+            reinterpret_cast<uint4*>(Mtc)[tid] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            reinterpret_cast<uint4*>(Mtc_lo)[tid] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            return;
+        }
         const float4 x = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + 4 * g);
         v.x = tc::round_tf32(x.x);
         v.y = tc::round_tf32(x.y);
@@ -120,12 +156,13 @@ struct TcTile {
 constexpr int kTcThreads = 320;
 constexpr int kTcDrainWarps = 8;
 
-template <bool SPLIT>
+template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const TcTile* __restrict__ tiles, TcLevels lv, const float* __restrict__ Mtc,
              const float* __restrict__ Mtc_lo, const float* __restrict__ Ttc, float* __restrict__ L, int ncp,
              int NKC, int slab_rows, int* __restrict__ status) {
-    using Cfg = TcCfg<SPLIT>;
+    using Cfg = TcCfg<MODE>;
+    constexpr bool SPLIT = Cfg::kSplit;
     constexpr int kTcChunk = Cfg::kChunk;
     constexpr int kTcKG = Cfg::kKG;
     static_assert(Cfg::kStageBytes == kTcTBytes, "ring stage size");
@@ -253,7 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // ---------------- MMA issuer ----------------
             // Lean loop: the 27 shifts are unrolled (constant delta), the ring position is a
             // running counter, and the abort flag is only consulted when a wait expires.
-            const uint32_t idesc = tc::idesc_tf32(128, kTcRows);
+            const uint32_t idesc = Cfg::kBf16 ? tc::idesc_bf16(128, kTcRows) : tc::idesc_tf32(128, kTcRows);
             // descriptors are built once and advanced by adding (byte offset >> 4) to the address field
             const uint64_t a_base = tc::smem_desc_kmajor(tc::smem_u32(tring), 2048u, 128u);
             const uint64_t b_base = tc::smem_desc_kmajor(tc::smem_u32(slab0), kg_stride, 128u);
@@ -288,15 +325,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
                     const uint64_t bd0 = b_buf + (uint64_t)((dx + 1) * slab_rows + dy * m2 + dz);
 #pragma unroll
-                    for (int ks = 0; ks < kTcChunk / 8; ++ks) {
+                    for (int ks = 0; ks < Cfg::kKSteps; ++ks) {  // 32 bytes of K = two cells per MMA
                         const uint64_t ad = ad0 + (uint64_t)ks * (4096u >> 4);
                         const uint64_t bd = bd0 + (uint64_t)ks * ((2u * kg_stride) >> 4);
-                        tc::mma_tf32(dacc, ad, bd, idesc, acc);
-                        acc = 1;
-                        if (SPLIT) {  // 3xTF32: + hi(T) lo(M) + lo(T) hi(M)
-                            tc::mma_tf32(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
-                            tc::mma_tf32(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
+                        if (Cfg::kBf16) {  // 3xBF16: hi(T) hi(M) + hi(T) lo(M) + lo(T) hi(M)
+                            tc::mma_bf16(dacc, ad, bd, idesc, acc);
+                            tc::mma_bf16(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
+                            tc::mma_bf16(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
+                        } else {
+                            tc::mma_tf32(dacc, ad, bd, idesc, acc);
+                            if (SPLIT) {  // 3xTF32: + hi(T) lo(M) + lo(T) hi(M)
+                                tc::mma_tf32(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
+                                tc::mma_tf32(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
+                            }
                         }
+                        acc = 1;
                     }
                     tc::mma_commit(t_empty + stage);
                     if (++stage == kTcStages) {
@@ -368,56 +411,102 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ------------------------------------------------------------------------------------------
 struct TcState {
-    bool split = false;
+    int mode = kTf32;
     float* Mtc_lo = nullptr;
     float* Mtc = nullptr;
     float* Ttc = nullptr;
     TcTile* tiles = nullptr;
     int ntiles = 0;
     int NKC = 0;
+    int KG = 0;  // 16-byte cells per K chunk
     int slab_rows = 0;
     size_t smem = 0;
     TcLevels lv{};
-    std::vector<long> pack_off;
 };
 
 bool m2l_tc_supported(const Handle* h) {
     // M = 128 output coefficients per MMA; the slab of the deepest level fits in shared memory
-    return (h->precision == FMM_MIXED_TF32 || h->precision == FMM_MIXED_3XTF32) && h->ncp <= 128 && h->depth <= 5;
+    const bool mixed = h->precision == FMM_MIXED_TF32 || h->precision == FMM_MIXED_3XTF32 ||
+                       h->precision == FMM_MIXED_3XBF16;
+    return mixed && h->ncp <= 128 && h->depth <= 5;
 }
 
 static TcState* tc_state(Handle* h) { return reinterpret_cast<TcState*>(h->tc); }
+
+namespace {
+// Host roundings of the operator parts, matching the device packing of the multipoles.
+float host_tf32(float x) {  // nearest, ties away from zero (cvt.rna.tf32.f32)
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+uint16_t host_bf16_bits(float x) {  // nearest, ties to even (cvt.rn.bf16.f32); finite inputs
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float host_bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
+template <int MODE>
+void pack_operators(const std::vector<float>& Trm, int nc, int NKC, std::vector<uint8_t>& out) {
+    using Cfg = TcCfg<MODE>;
+    // [op][chunk][part][cell][j (128)][16 bytes]; part 0 = hi rounding, part 1 = rounding of the remainder
+    out.assign((size_t)kNumOps * NKC * Cfg::kStageBytes, 0);
+    for (int op = 0; op < kNumOps; ++op)
+        for (int jj = 0; jj < nc; ++jj)
+            for (int k = 0; k < nc; ++k) {
+                const float v = Trm[((size_t)op * nc + jj) * nc + k];
+                const int ch = k / Cfg::kChunk, g = (k % Cfg::kChunk) / Cfg::kPerCell, e = k % Cfg::kPerCell;
+                for (int part = 0; part < Cfg::kParts; ++part) {
+                    const size_t cell = ((((size_t)op * NKC + ch) * Cfg::kParts + part) * Cfg::kKG + g) * 128 + jj;
+                    uint8_t* dst = out.data() + cell * 16 + (size_t)e * Cfg::kElem;
+                    if (Cfg::kBf16) {
+                        const uint16_t hi = host_bf16_bits(v);
+                        const uint16_t w = part == 0 ? hi : host_bf16_bits(v - host_bf16_value(hi));
+                        std::memcpy(dst, &w, 2);
+                    } else {
+                        const float hi = host_tf32(v);
+                        const float w = part == 0 ? hi : host_tf32(v - hi);
+                        std::memcpy(dst, &w, 4);
+                    }
+                }
+            }
+}
+}  // namespace
 
 int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc] j-major*/) {
     TcState* st = new TcState();
     h->tc = st;
     const int nc = h->nc, ncp = h->ncp, d = h->depth;
-    st->split = h->precision == FMM_MIXED_3XTF32;
-    const int kTcChunk = st->split ? TcCfg<true>::kChunk : TcCfg<false>::kChunk;
-    const int kTcKG = kTcChunk / 4;
-    const int nparts = st->split ? 2 : 1;
-    st->NKC = (ncp + kTcChunk - 1) / kTcChunk;
-    const int NKG = st->NKC * kTcKG;
-    // operator chunks [op][chunk][part][kgroup][j(128)][4]; part 0 = TF32 rounding (nearest,
-    // ties away), part 1 (3xTF32) = TF32 rounding of the remainder
-    std::vector<float> T((size_t)kNumOps * st->NKC * nparts * 128 * kTcChunk, 0.f);
-    auto tf32 = [](float x) {
-        uint32_t u;
-        std::memcpy(&u, &x, 4);
-        u = (u + 0x1000u) & 0xFFFFE000u;
-        float y;
-        std::memcpy(&y, &u, 4);
-        return y;
-    };
-    for (int op = 0; op < kNumOps; ++op)
-        for (int jj = 0; jj < nc; ++jj)
-            for (int k = 0; k < nc; ++k) {
-                const float v = T_rowmajor[((size_t)op * nc + jj) * nc + k];
-                const int ch = k / kTcChunk, g = (k % kTcChunk) / 4, e = k % 4;
-                const float hi = tf32(v);
-                T[(((((size_t)op * st->NKC + ch) * nparts + 0) * kTcKG + g) * 128 + jj) * 4 + e] = hi;
-                if (nparts == 2) T[(((((size_t)op * st->NKC + ch) * nparts + 1) * kTcKG + g) * 128 + jj) * 4 + e] = tf32(v - hi);
-            }
+    st->mode = h->precision == FMM_MIXED_3XTF32 ? kTf32x3 : h->precision == FMM_MIXED_3XBF16 ? kBf16x3 : kTf32;
+    int chunk = 0, nparts = 1;
+    std::vector<uint8_t> T;
+    switch (st->mode) {
+        case kTf32x3:
+            chunk = TcCfg<kTf32x3>::kChunk, st->KG = TcCfg<kTf32x3>::kKG, nparts = 2;
+            st->NKC = (ncp + chunk - 1) / chunk;
+            pack_operators<kTf32x3>(T_rowmajor, nc, st->NKC, T);
+            break;
+        case kBf16x3:
+            chunk = TcCfg<kBf16x3>::kChunk, st->KG = TcCfg<kBf16x3>::kKG, nparts = 2;
+            st->NKC = (ncp + chunk - 1) / chunk;
+            pack_operators<kBf16x3>(T_rowmajor, nc, st->NKC, T);
+            break;
+        default:
+            chunk = TcCfg<kTf32>::kChunk, st->KG = TcCfg<kTf32>::kKG, nparts = 1;
+            st->NKC = (ncp + chunk - 1) / chunk;
+            pack_operators<kTf32>(T_rowmajor, nc, st->NKC, T);
+    }
+    const int NKG = st->NKC * st->KG;
     // packed multipole levels
     long off = 0;
     for (int l = 0; l <= kMaxDepth; ++l) {
@@ -426,7 +515,6 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
         st->lv.l_off[l] = 0;
     }
     std::vector<TcTile> tiles;
-    int max_S = 0;
     for (int l = h->lmin; l <= d; ++l) {
         const int n = 1 << (l - 1);
         const int R = (n + 2) * (n + 2) * (n + 2);
@@ -436,30 +524,29 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
         st->lv.S[l] = S;
         st->lv.mtc_off[l] = off;
         st->lv.l_off[l] = h->lvl_off[l];
-        off += 8L * NKG * R * 4;
-        max_S = std::max(max_S, S);
+        off += 8L * NKG * R * 4;  // 16-byte cells, counted in floats
         for (int c = 0; c < 8; ++c)
             for (int r0 = S; r0 < R - S; r0 += kTcRows) tiles.push_back({l, c, r0, 0});
     }
-    (void)max_S;
     st->slab_rows = kTcRows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
-    st->smem = 2 * (size_t)3 * st->slab_rows * kTcKG * 16 * nparts + (size_t)kTcStages * kTcTBytes + 256;
+    st->smem = 2 * (size_t)3 * st->slab_rows * st->KG * 16 * nparts + (size_t)kTcStages * kTcTBytes + 256;
     st->ntiles = (int)tiles.size();
-    if (cudaMalloc(&st->Ttc, sizeof(float) * T.size()) != cudaSuccess ||
+    if (cudaMalloc(&st->Ttc, T.size()) != cudaSuccess ||
         cudaMalloc(&st->Mtc, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess ||
-        (st->split && cudaMalloc(&st->Mtc_lo, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess) ||
+        (nparts == 2 && cudaMalloc(&st->Mtc_lo, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess) ||
         cudaMalloc(&st->tiles, sizeof(TcTile) * (tiles.empty() ? 1 : tiles.size())) != cudaSuccess) {
         cudaGetLastError();
         return FMM_ERR_OOM;
     }
-    cudaMemcpy(st->Ttc, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(st->Ttc, T.data(), T.size(), cudaMemcpyHostToDevice);
     if (!tiles.empty()) cudaMemcpy(st->tiles, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice);
     if (st->smem > 227 * 1024) return FMM_ERR_ARG;
     // The attribute is process wide per kernel: set it to the per-block maximum once, so that
     // handles of different depths (different slab sizes) never lower each other's limit.
     constexpr int kMaxDynSmem = 227 * 1024;
-    cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_m2l_tc<kTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_m2l_tc<kTf32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_m2l_tc<kBf16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     return FMM_OK;
 }
 
@@ -480,20 +567,32 @@ int m2l_tc_launches(const Handle* h) {
 
 void launch_m2l_tc(Handle* h, cudaStream_t stream) {
     TcState* st = tc_state(h);
-    const int NKG = st->NKC * (st->split ? TcCfg<true>::kKG : TcCfg<false>::kKG);
+    const int NKG = st->NKC * st->KG;
+    const bool bf16 = st->mode == kBf16x3;
     for (int l = h->lmin; l <= h->depth; ++l) {
         const long total = 8L * NKG * st->lv.R[l];
-        k_m2l_pack<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(
-            st->lv.n[l], st->lv.R[l], NKG, h->ncp, h->periodic, h->M + h->lvl_off[l] * h->ncp,
-            st->Mtc + st->lv.mtc_off[l], st->split ? st->Mtc_lo + st->lv.mtc_off[l] : nullptr);
-    }
-    if (st->ntiles > 0) {
-        if (st->split)
-            k_m2l_tc<true><<<st->ntiles, kTcThreads, st->smem, stream>>>(st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L,
-                                                                   h->ncp, st->NKC, st->slab_rows, h->status);
+        const unsigned grid = (unsigned)((total + 255) / 256);
+        float* lo = st->Mtc_lo ? st->Mtc_lo + st->lv.mtc_off[l] : nullptr;
+        if (bf16)
+            k_m2l_pack<true><<<grid, 256, 0, stream>>>(st->lv.n[l], st->lv.R[l], NKG, h->ncp, h->periodic,
+                                                       h->M + h->lvl_off[l] * h->ncp, st->Mtc + st->lv.mtc_off[l], lo);
         else
-            k_m2l_tc<false><<<st->ntiles, kTcThreads, st->smem, stream>>>(st->tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L,
-                                                                    h->ncp, st->NKC, st->slab_rows, h->status);
+            k_m2l_pack<false><<<grid, 256, 0, stream>>>(st->lv.n[l], st->lv.R[l], NKG, h->ncp, h->periodic,
+                                                        h->M + h->lvl_off[l] * h->ncp, st->Mtc + st->lv.mtc_off[l], lo);
+    }
+    if (st->ntiles == 0) return;
+    switch (st->mode) {
+        case kTf32x3:
+            k_m2l_tc<kTf32x3><<<st->ntiles, kTcThreads, st->smem, stream>>>(
+                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, h->status);
+            break;
+        case kBf16x3:
+            k_m2l_tc<kBf16x3><<<st->ntiles, kTcThreads, st->smem, stream>>>(
+                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, h->status);
+            break;
+        default:
+            k_m2l_tc<kTf32><<<st->ntiles, kTcThreads, st->smem, stream>>>(
+                st->tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, h->status);
     }
 }
 

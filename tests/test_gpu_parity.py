@@ -249,3 +249,37 @@ def test_3xtf32_m2l_parity(periodic, p, depth):
     e = errors(g, ref)
     assert g["status"] == 0
     assert e["F"] < 1e-4 and e["E"] < 1e-4 and e["dVdl"] < 1e-4, e
+
+
+# ---------------------------------------------------------------- tensor-core M2L (split BF16)
+@pytest.mark.parametrize("periodic,p,depth", [(True, 8, 3), (True, 10, 3), (False, 8, 2), (False, 10, 4), (True, 10, 1)])
+def test_3xbf16_m2l_parity(periodic, p, depth):
+    """Split BF16 (hi*hi + hi*lo + lo*hi, about 16 significant bits per operand, products
+    exact in FP32): E, F and dV/dlambda within 1e-4 of the oracle."""
+    if periodic:
+        s = synth.periodic_uniform(seed=3, n=3000, L=3.0, n_sites=8, site_size=4, p=p, depth=depth)
+    else:
+        s = synth.open_uniform(seed=5, n=3000, L=5.0, n_sites=8, site_size=4, p=p, depth=depth)
+    ref = oracle_ref(s)
+    g = run_gpu(s, precision="3xbf16")
+    e = errors(g, ref)
+    print(f"3xbf16 periodic={periodic} p={p} depth={depth}: {e}")
+    assert g["status"] == 0
+    assert e["F"] < 1e-4 and e["E"] < 1e-4 and e["dVdl"] < 1e-4, e
+
+
+def test_3xbf16_close_to_fp32_path():
+    """Each split BF16 operand carries up to 2^-16 relative error (hi and lo keep 8
+    significant bits each) and the dropped lo*lo product is of the same order, so the
+    local expansions differ from the FP32 path by about 1e-5 of the summed term sizes.
+    Forces are near-field dominated (measured 2e-7); E and dV/dlambda sum potentials whose
+    far-field terms cancel (measured 1.5e-6 and 4.5e-5).  A wrong cell layout or
+    descriptor shows as an O(1) difference."""
+    s = synth.periodic_uniform(seed=11, n=6000, L=3.5, n_sites=8, site_size=4, p=10, depth=3)
+    a = run_gpu(s, precision="fp32")
+    b = run_gpu(s, precision="3xbf16")
+    dF = np.sqrt(((a["F"] - b["F"]) ** 2).sum() / (a["F"] ** 2).sum())
+    dE = abs(a["E"] - b["E"]) / abs(a["E"])
+    dV = np.linalg.norm(a["dVdl"] - b["dVdl"]) / np.linalg.norm(a["dVdl"])
+    print(f"3xbf16 vs fp32: dF {dF:.2e} dE {dE:.2e} dVdl {dV:.2e}")
+    assert dF < 2e-6 and dE < 1e-5 and dV < 1e-4, (dF, dE, dV)
