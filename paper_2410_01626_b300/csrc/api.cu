@@ -64,7 +64,6 @@ void free_atoms(Handle& h) {
     dfree(h.dq);
     dfree(h.phis);
     dfree(h.far);
-    dfree(h.sort_table);
     h.perm = nullptr;
     h.sorted_key = nullptr;
     h.cap = 0;
@@ -86,8 +85,9 @@ void free_all(Handle& h) {
     dfree(h.site_atoms);
     dfree(h.start);
     dfree(h.count);
+    dfree(h.leafcnt);
     dfree(h.epart);
-    dfree(h.leafqdt);
+    dfree(h.leafmom);
     dfree(h.root);
     dfree(h.status);
     dfree(h.work);
@@ -246,7 +246,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         return FMM_ERR_ARG;
     }
     upload_constants(p);
-    configure_kernels(ncoef_padded(p));
+    configure_kernels(p);
 
     const int nc = h.nc, ncp = h.ncp;
     fmm_status st = FMM_OK;
@@ -301,8 +301,8 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     const long nleaf = 1L << (3 * depth);
     if ((st = dalloc(&h.M, (size_t)acc * ncp)) || (st = dalloc(&h.L, (size_t)acc * ncp)) ||
         (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.start, nleaf)) ||
-        (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.epart, nleaf)) ||
-        (st = dalloc(&h.leafqdt, 5 * nleaf)) || (st = dalloc(&h.root, nc + 8 + 5 * 64)) || (st = dalloc(&h.status, 1)) ||
+        (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.leafcnt, nleaf)) || (st = dalloc(&h.epart, nleaf)) ||
+        (st = dalloc(&h.leafmom, (long)kLeafMomStride * nleaf)) || (st = dalloc(&h.root, nc + kRootDoubles)) || (st = dalloc(&h.status, 1)) ||
         (st = dalloc(&h.site_ptr, 1)) ||
         (st = dalloc(&h.work, 8L * (depth >= 1 ? (1L << (3 * (depth - 1))) : 1) * ncp))) {
         free_all(h);
@@ -315,7 +315,8 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     cudaMemset(h.M, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.L, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.status, 0, sizeof(int));
-    cudaMemset(h.root, 0, sizeof(double) * (nc + 8 + 5 * 64));
+    cudaMemset(h.leafcnt, 0, sizeof(uint32_t) * nleaf);
+    cudaMemset(h.root, 0, sizeof(double) * (nc + kRootDoubles));
     cudaMemset(h.site_ptr, 0, sizeof(int));
     for (auto& e : h.ev) cudaEventCreate(&e);
     h.ev_valid = true;
@@ -336,14 +337,13 @@ fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const f
     if (K > 0 && !lambda) return FMM_ERR_ARG;
     Handle& h = H->h;
     cudaStream_t st = S(stream);
-    const int nblk = (n + 4095) / 4096;
     if (n > h.cap) {
         free_atoms(h);
         fmm_status e;
         if ((e = dalloc(&h.qA, n)) || (e = dalloc(&h.qB, n)) || (e = dalloc(&h.site, n)) || (e = dalloc(&h.key, n)) ||
             (e = dalloc(&h.kA, n)) || (e = dalloc(&h.kB, n)) || (e = dalloc(&h.vA, n)) || (e = dalloc(&h.vB, n)) ||
             (e = dalloc(&h.inv, n)) || (e = dalloc(&h.pos, n)) || (e = dalloc(&h.dq, n)) ||
-            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.far, n)) || (e = dalloc(&h.sort_table, 256L * (nblk > 0 ? nblk : 1)))) {
+            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.far, n))) {
             free_atoms(h);
             h.charges_set = false;
             return e;

@@ -10,6 +10,8 @@ namespace fmmcph {
 
 constexpr int kMaxP = FMM_MAX_P;
 constexpr int kMaxDepth = 7;
+constexpr int kLeafMomStride = 8;  // floats per leaf in Handle::leafmom
+constexpr int kRootDoubles = 8 + 5 * 64 + 4 + 40;  // Handle::root beyond nc: Q D T, k_qdt partials, FP32 copies, k_final totals + ticket
 constexpr int kNumOps = 343;  // M2L offsets o in {-3..3}^3 (the inner 27 slots unused)
 constexpr int kNumStages = 8;
 
@@ -58,15 +60,14 @@ struct Handle {
     uint32_t *key = nullptr, *kA = nullptr, *kB = nullptr, *vA = nullptr, *vB = nullptr;
     uint32_t *perm = nullptr, *inv = nullptr, *sorted_key = nullptr;
     uint32_t *start = nullptr, *count = nullptr;
-    uint32_t* sort_table = nullptr;
-    int sort_blocks_cap = 0;
+    uint32_t* leafcnt = nullptr;  // [nleaf] per-leaf counters of the binning step, zero between calls
     float4* pos = nullptr;
     float* dq = nullptr;
     float* phis = nullptr;   // sorted-order potential (without k_e)
     float4* far = nullptr;   // sorted-order far-field potential and gradient
-    double* epart = nullptr; // per-block partial sums of q phi
+    float* epart = nullptr;  // per-leaf partial sums of q phi
     int epart_cap = 0;
-    double* leafqdt = nullptr;  // [nleaf][5] periodic: Q, Dx, Dy, Dz, T per leaf
+    float* leafmom = nullptr;   // [nleaf][kLeafMomStride] periodic: leaf moments for the Q, D, T sums
     double* root = nullptr;     // [nc] FP64 root multipole, then [5] Q D T at root+nc
     int* status = nullptr;
     float* work = nullptr;  // split-K partial products (8 x the largest M2M output level)
@@ -86,7 +87,7 @@ struct Handle {
 
 // kernels.cu
 void upload_constants(int p);
-void configure_kernels(int ncp);
+void configure_kernels(int p);  // per-kernel launch attributes for expansion degree p
 int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, float* phi,
                 cudaStream_t st);
 int launches_per_eval(const Handle* h);

@@ -1,10 +1,10 @@
 // CUDA kernels of one FMM evaluation (sm_103a).
 //
 // Stages (all on the caller's stream):
-//   binning   k_keys -> LSD radix sort (k_sort_hist/scan/scatter) -> k_ranges -> k_gather
+//   binning   k_bin_count -> k_bin_scan -> k_bin_place -> k_bin_order_gather (counting sort by leaf)
 //             (Morton keys of the leaf cells, stable on (key, index); the gather also forms
 //             q_i = qA_i + lambda_s (qB_i - qA_i), Sec. 2.1 Eq. 1 with charge-only forms)
-//   P2M       k_p2m<P>        one warp per leaf, butterfly reduce-scatter of the coefficients
+//   P2M       k_p2m<P>        one block per 8 sibling leaves: per-atom harmonics in shared memory, fixed-order leaf sums
 //   M2M       k_sgemm         per level, one dense GEMM over the 8 contiguous children
 //   root      k_root, k_lattice (periodic) FP64 root multipole and lattice operator
 //   M2L       k_m2l_fp32 (FP32 CUDA cores) or the tcgen05 kernel in m2l_tc.cu
@@ -101,22 +101,188 @@ __device__ __forceinline__ int cell_of(double u, double s, int nb) {
     return (int)f;
 }
 
+// Leaf cell of one coordinate, bit-identical to the FP64 specification above.  FP32 first:
+// with of = fl32(o), sf = fl32(s), u32 = fl32(x - of), t32 = fl32(u32 sf),
+//   |u32 - (x - o)| <= 2^-24 (|o| + |x - of|)                    <= E_u = 2^-23 (|x| + 2|o|),
+//   |t32 - (x - o) s| <= 2^-24 |u32| (sf + s) + s E_u            <= E_t = s (2^-22 |u32| + E_u),
+// and the FP64 value differs from (x - o) s by far less than E_t.  When u32 is more than E_u
+// (plus the rounding of L) inside (0, L) -- so FP64 neither wraps nor flags the domain -- and
+// t32 is more than E_t from both integers around it, floor(t32) is the FP64 cell; otherwise
+// the FP64 arithmetic decides.  *bad is set for an open-box coordinate outside [0, L].
+__device__ __forceinline__ int cell_fast(float xf, double o, float of, BoxGeom g, float Lf, float sf, bool& bad) {
+    const float u32 = xf - of;
+    const float eu = 1.1920929e-7f * (fabsf(xf) + 2.f * fabsf(of)) + 1e-30f;  // 2^-23 (|x| + 2|o|)
+    if (u32 > eu && u32 < Lf - eu - 1.1920929e-7f * Lf) {
+        const float t32 = u32 * sf;
+        const float et = sf * (2.3841858e-7f * u32 + eu) * 1.0001f;             // 2^-22 |u32| + E_u
+        const float c = floorf(t32);
+        if (t32 - c > et && c + 1.f - t32 > et) return min((int)c, g.nb - 1);
+    }
+    const double u = wrap_coord((double)xf, o, g.L, g.periodic);
+    if (!g.periodic && !(u >= 0.0 && u <= g.L)) bad = true;
+    return cell_of(u, g.s, g.nb);
+}
+
+__device__ __forceinline__ uint32_t leaf_key(const float* __restrict__ x, int i, const BoxGeom& g, bool& bad) {
+    const float Lf = (float)g.L, sf = (float)g.s;
+    const int cx = cell_fast(x[3 * i], g.o0, (float)g.o0, g, Lf, sf, bad);
+    const int cy = cell_fast(x[3 * i + 1], g.o1, (float)g.o1, g, Lf, sf, bad);
+    const int cz = cell_fast(x[3 * i + 2], g.o2, (float)g.o2, g, Lf, sf, bad);
+    return morton3(cx, cy, cz);
+}
+
 __global__ void k_keys(int n, const float* __restrict__ x, BoxGeom g, uint32_t* __restrict__ key,
                        uint32_t* __restrict__ val, int* __restrict__ status) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double o[3] = {g.o0, g.o1, g.o2};
-    int c[3];
     bool bad = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double u = wrap_coord((double)x[3 * i + a], o[a], g.L, g.periodic);
-        if (!g.periodic && !(u >= 0.0 && u <= g.L)) bad = true;
-        c[a] = cell_of(u, g.s, g.nb);
-    }
-    key[i] = morton3(c[0], c[1], c[2]);
+    key[i] = leaf_key(x, i, g, bad);
     val[i] = (uint32_t)i;
     if (bad) atomicOr(status, FMM_DEV_DOMAIN);
+}
+
+// ---- binning as a counting sort by leaf ----
+// (1) k_bin_count: key of every atom and a claim on a slot of its leaf (atomic, so the slot
+//     order inside a leaf is arbitrary); (2) k_bin_scan: exclusive scan of the leaf counts ->
+//     start, count (and the counters are cleared for the next call); (3) k_bin_place: atom i
+//     goes to start[key] + slot; (4) k_bin_order_gather: one warp per leaf puts the leaf's
+//     atoms in ascending input index -- exactly the order of a stable sort on (key, index) --
+//     and gathers positions and charges in that order.
+__global__ void k_bin_count(int n, const float* __restrict__ x, BoxGeom g, uint32_t* __restrict__ key,
+                            uint32_t* __restrict__ slot, uint32_t* __restrict__ leafcnt, int* __restrict__ status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool bad = false;
+    const uint32_t k = leaf_key(x, i, g, bad);
+    key[i] = k;
+    slot[i] = atomicAdd(leafcnt + k, 1u);
+    if (bad) atomicOr(status, FMM_DEV_DOMAIN);
+}
+
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_bin_scan(int nleaf, uint32_t* __restrict__ leafcnt,
+                                                           uint32_t* __restrict__ start, uint32_t* __restrict__ count) {
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t carry = 0;
+    for (int base = 0; base < nleaf; base += 4 * kScanThreads) {
+        uint32_t v[4], tot = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int l = base + 4 * t + e;
+            v[e] = l < nleaf ? leafcnt[l] : 0u;
+            tot += v[e];
+        }
+        uint32_t x = tot;  // inclusive scan of the thread totals
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, k);
+            if (lane >= k) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t z = wsum[lane];
+#pragma unroll
+            for (int k = 1; k < 32; k <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, k);
+                if (lane >= k) z += y;
+            }
+            wsum[lane] = z;
+        }
+        __syncthreads();
+        uint32_t run = carry + x - tot + (w > 0 ? wsum[w - 1] : 0u);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int l = base + 4 * t + e;
+            if (l < nleaf) {
+                start[l] = run;
+                count[l] = v[e];
+                leafcnt[l] = 0u;
+            }
+            run += v[e];
+        }
+        carry += wsum[31];
+        __syncthreads();
+    }
+}
+
+__global__ void k_bin_place(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
+                            const uint32_t* __restrict__ start, uint32_t* __restrict__ placed) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    placed[start[key[i]] + slot[i]] = (uint32_t)i;
+}
+
+// Position and charges of input atom i at sorted slot s (the gather of the binning step).
+__device__ __forceinline__ void gather_atom(int i, int s, const float* __restrict__ x, const BoxGeom& g,
+                                            const float* __restrict__ qA, const float* __restrict__ qB,
+                                            const int32_t* __restrict__ site, int K, const float* __restrict__ lam,
+                                            float4* __restrict__ pos, float* __restrict__ dq,
+                                            uint32_t* __restrict__ inv, int* __restrict__ status) {
+    float u[3];
+    const double o[3] = {g.o0, g.o1, g.o2};
+    const float Lf = (float)g.L;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float xf = x[3 * i + a], of = (float)o[a];
+        const float u32 = xf - of;
+        const float eu = 1.1920929e-7f * (fabsf(xf) + 2.f * fabsf(of)) + 1e-30f;
+        if (g.periodic && !(u32 > eu && u32 < Lf - eu - 1.1920929e-7f * Lf))
+            u[a] = (float)wrap_coord((double)xf, o[a], g.L, 1);
+        else
+            u[a] = u32;
+    }
+    const float a = qA[i], b = qB[i];
+    const int st = site[i];
+    float d = 0.f, q = a;
+    if (st >= 0) {
+        if (st < K) {
+            d = b - a;
+            q = fmaf(lam[st], d, a);
+        } else {
+            atomicOr(status, FMM_DEV_SITE);
+        }
+    }
+    pos[s] = make_float4(u[0], u[1], u[2], q);
+    dq[s] = d;
+    inv[i] = (uint32_t)s;
+}
+
+__global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint32_t* __restrict__ start,
+                                                          const uint32_t* __restrict__ count,
+                                                          const uint32_t* __restrict__ placed,
+                                                          uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
+                                                          const float* __restrict__ x, BoxGeom g,
+                                                          const float* __restrict__ qA, const float* __restrict__ qB,
+                                                          const int32_t* __restrict__ site, int K,
+                                                          const float* __restrict__ lam, float4* __restrict__ pos,
+                                                          float* __restrict__ dq, uint32_t* __restrict__ inv,
+                                                          int* __restrict__ status) {
+    const int leaf = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (leaf >= nleaf) return;
+    const int st = (int)start[leaf], c = (int)count[leaf];
+    if (c <= 32) {  // the whole leaf in one register per lane: rank = number of smaller indices
+        const uint32_t v = lane < c ? placed[st + lane] : 0xFFFFFFFFu;
+        int r = 0;
+        for (int k = 0; k < c; ++k) r += __shfl_sync(0xffffffffu, v, k) < v ? 1 : 0;
+        if (lane < c) {
+            perm[st + r] = v;
+            skey[st + r] = (uint32_t)leaf;
+            gather_atom((int)v, st + r, x, g, qA, qB, site, K, lam, pos, dq, inv, status);
+        }
+        return;
+    }
+    // larger leaves: the same ranks by a pass over the leaf per element (O(c^2 / 32) per warp,
+    // the order of the leaf's own near-field work)
+    for (int e = lane; e < c; e += 32) {
+        const uint32_t v = placed[st + e];
+        int r = 0;
+        for (int k = 0; k < c; ++k) r += placed[st + k] < v ? 1 : 0;
+        perm[st + r] = v;
+        skey[st + r] = (uint32_t)leaf;
+        gather_atom((int)v, st + r, x, g, qA, qB, site, K, lam, pos, dq, inv, status);
+    }
 }
 
 // ---- stable LSD radix sort, 8-bit digits ----
@@ -253,33 +419,6 @@ __global__ void k_ranges(int n, int nleaf, const uint32_t* __restrict__ skey, ui
     count[b] = (uint32_t)(e - s);
 }
 
-__global__ void k_gather(int n, const uint32_t* __restrict__ perm, const float* __restrict__ x, BoxGeom g,
-                         const float* __restrict__ qA, const float* __restrict__ qB,
-                         const int32_t* __restrict__ site, int K, const float* __restrict__ lam,
-                         float4* __restrict__ pos, float* __restrict__ dq, uint32_t* __restrict__ inv,
-                         int* __restrict__ status) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int i = (int)perm[s];
-    float ux = (float)wrap_coord((double)x[3 * i], g.o0, g.L, g.periodic);
-    float uy = (float)wrap_coord((double)x[3 * i + 1], g.o1, g.L, g.periodic);
-    float uz = (float)wrap_coord((double)x[3 * i + 2], g.o2, g.L, g.periodic);
-    float a = qA[i], b = qB[i];
-    int st = site[i];
-    float d = 0.f, q = a;
-    if (st >= 0) {
-        if (st < K) {
-            d = b - a;
-            q = fmaf(lam[st], d, a);
-        } else {
-            atomicOr(status, FMM_DEV_SITE);
-        }
-    }
-    pos[s] = make_float4(ux, uy, uz, q);
-    dq[s] = d;
-    inv[i] = (uint32_t)s;
-}
-
 // ---- normalised regular solid harmonics, real form ----
 // R_hat_n^m(u) for n = 0..P, m = 0..n via the column recurrences; `visit(n, m, re, im)`.
 template <int P, class F>
@@ -309,103 +448,200 @@ __device__ __forceinline__ void regular_harmonics(float x, float y, float z, F&&
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(128) k_p2m(int nleaf, float h, float half_box,
-                                             const uint32_t* __restrict__ start,
-                                             const uint32_t* __restrict__ count,
-                                             const float4* __restrict__ pos, float* __restrict__ M,
-                                             int ncp, double* __restrict__ leafqdt) {
-    constexpr int NC = (P + 1) * (P + 1);
-    constexpr int NG = (NC + 31) / 32;
-    const int lane = threadIdx.x & 31;
-    const int leaf = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (leaf >= nleaf) return;
-    const uint32_t lx = compact3(leaf), ly = compact3(leaf >> 1), lz = compact3(leaf >> 2);
-    const float cx = (lx + 0.5f) * h, cy = (ly + 0.5f) * h, cz = (lz + 0.5f) * h;
-    const float ih = 1.0f / h;
-    const int st = start[leaf], cnt = count[leaf];
-    float v[NG * 32];
+// Columns m in [M0, M1] only (the m = 0 .. M1 diagonal chain is still walked).
+template <int P, int M0, int M1, class F>
+__device__ __forceinline__ void regular_harmonics_cols(float x, float y, float z, F&& visit) {
+    const float rho2 = x * x + y * y + z * z;
+    float dr = 1.f, di = 0.f;
 #pragma unroll
-    for (int i = 0; i < NG * 32; ++i) v[i] = 0.f;
-    double qd0 = 0, qd1 = 0, qd2 = 0, qd3 = 0, qd4 = 0;
-    for (int b = 0; b < cnt; b += 32) {
-        const int j = b + lane;
-        float4 a = make_float4(cx, cy, cz, 0.f);
-        if (j < cnt) a = pos[st + j];
-        const float q = a.w;
-        regular_harmonics<P>((a.x - cx) * ih, (a.y - cy) * ih, (a.z - cz) * ih,
-                             [&](int n, int m, float re, float im) {
-                                 if (m == 0) {
-                                     v[n * n] += q * re;
-                                 } else {
-                                     v[n * n + 2 * m - 1] += q * re;
-                                     v[n * n + 2 * m] -= q * im;
-                                 }
-                             });
-        if (leafqdt) {
-            const double ux = (double)a.x - half_box, uy = (double)a.y - half_box, uz = (double)a.z - half_box;
-            const double qq = (double)q;
-            qd0 += qq;
-            qd1 += qq * ux;
-            qd2 += qq * uy;
-            qd3 += qq * uz;
-            qd4 += qq * (ux * ux + uy * uy + uz * uz);
+    for (int m = 0; m <= M1; ++m) {
+        if (m > 0) {
+            const float t = (dr * x + di * y) * c_dg[m];
+            di = (di * x - dr * y) * c_dg[m];
+            dr = t;
         }
-    }
-    // butterfly reduce-scatter: after it, group g's sum for coefficient g*32+lane sits in v[g*32]
+        if (m < M0) continue;
+        float pr = dr, pi = di, ppr = 0.f, ppi = 0.f;
 #pragma unroll
-    for (int g = 0; g < NG; ++g) {
-        float* w = v + g * 32;
-#pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) {
-            const bool up = (lane & s) != 0;
-#pragma unroll
-            for (int i = 0; i < s; ++i) {
-                const float send = up ? w[i] : w[i + s];
-                const float keep = up ? w[i + s] : w[i];
-                w[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        for (int n = m; n <= P; ++n) {
+            if (n > m) {
+                const float a = c_ra[n][m] * z, b = c_rb[n][m] * rho2;
+                const float nr = a * pr - b * ppr, ni = a * pi - b * ppi;
+                ppr = pr;
+                ppi = pi;
+                pr = nr;
+                pi = ni;
             }
-        }
-    }
-    float* out = M + (long)leaf * ncp;
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-        const int idx = g * 32 + lane;
-        if (idx < ncp) out[idx] = (idx < NC) ? v[g * 32] : 0.f;
-    }
-    for (int idx = NG * 32 + lane; idx < ncp; idx += 32) out[idx] = 0.f;
-    if (leafqdt) {
-#pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) {
-            qd0 += __shfl_xor_sync(0xffffffffu, qd0, s);
-            qd1 += __shfl_xor_sync(0xffffffffu, qd1, s);
-            qd2 += __shfl_xor_sync(0xffffffffu, qd2, s);
-            qd3 += __shfl_xor_sync(0xffffffffu, qd3, s);
-            qd4 += __shfl_xor_sync(0xffffffffu, qd4, s);
-        }
-        if (lane == 0) {
-            double* o = leafqdt + 5L * leaf;
-            o[0] = qd0;
-            o[1] = qd1;
-            o[2] = qd2;
-            o[3] = qd3;
-            o[4] = qd4;
+            visit(n, m, pr, pi);
         }
     }
 }
 
+// P2M, one 256-thread block per 8 consecutive leaves (the children of one parent, whose atoms
+// are contiguous in leaf order).  Atoms are taken 128 at a time.  For atom t of the chunk,
+// thread t (warps 0-3) writes q R_hat_n^m(u) for the columns m < MS and thread 128 + t (warps
+// 4-7) the columns m >= MS plus the atom's moments, into shared memory (row stride NC rounded
+// up to odd, so the column writes are conflict free); the two halves cost about the same.
+// Then thread t sums "virtual coefficient" v = t % 128 (+ 128, ...) over the atoms of leaves
+// 4 (t / 128) .. +3 in order: v < NC is a multipole coefficient, v = NC + k (k < kMom) is
+// moment k of the leaf for the periodic correction, about the leaf centre: q_hi, q_lo
+// (q_hi = q rounded to a multiple of 2^-11, so the FP32 sum of q_hi is exact and
+// Q = sum q_hi + sum q_lo is good to FP64 level), q dx, q dy, q dz, q |d|^2.  k_qdt turns them
+// into Q, D, T about the box centre in FP64 with all lanes busy: this GPU's FP64 pipe is
+// narrow, so no FP64 instruction runs per atom or per leaf thread.  Every sum runs in a fixed
+// order, so the result is deterministic.
+constexpr int kP2mThreads = 256;
+constexpr int kP2mChunk = 128;
+constexpr int kP2mLeaves = 8;
+constexpr int kMom = 6;        // leaf moments for the periodic correction
+constexpr int kMomStride = kLeafMomStride;  // floats per leaf in the moment array
+template <int P>
+struct P2mCfg {
+    static constexpr int NC = (P + 1) * (P + 1);
+    static constexpr int NCS = NC | 1;
+    static constexpr int kSlots = (NC + kMom + kP2mChunk - 1) / kP2mChunk;
+    // column split: sum over m < MS of (P - m + 1), plus the chain to MS - 1, against the rest
+    static constexpr int split() {
+        int best = 1, bestd = 1 << 30;
+        for (int ms = 1; ms <= P; ++ms) {
+            int a = ms - 1, b = P;
+            for (int m = 0; m <= P; ++m) (m < ms ? a : b) += P - m + 1;
+            const int d = a > b ? a - b : b - a;
+            if (d < bestd) {
+                bestd = d;
+                best = ms;
+            }
+        }
+        return best;
+    }
+    static constexpr int MS = P >= 1 ? split() : 1;
+    static constexpr size_t kSmem = sizeof(float) * kP2mChunk * (NCS + kMom);
+};
+
+template <int P>
+__global__ void __launch_bounds__(kP2mThreads) k_p2m(int nleaf, float h, const uint32_t* __restrict__ start,
+                                                     const uint32_t* __restrict__ count,
+                                                     const float4* __restrict__ pos, float* __restrict__ M,
+                                                     int ncp, float* __restrict__ leafmom) {
+    using Cfg = P2mCfg<P>;
+    constexpr int NC = Cfg::NC, NCS = Cfg::NCS, SL = Cfg::kSlots, MS = Cfg::MS;
+    constexpr int kLPT = kP2mLeaves / 2;  // leaves per reducing thread
+    extern __shared__ __align__(16) float p2m_smem[];
+    float* hsm = p2m_smem;                         // [chunk][NCS] harmonics
+    float* msm = p2m_smem + kP2mChunk * NCS;       // [kMom][chunk] moments
+    const int t = threadIdx.x;
+    const int L0 = blockIdx.x * kP2mLeaves;
+    const int nl = min(kP2mLeaves, nleaf - L0);
+    __shared__ int lo_s[kP2mLeaves], hi_s[kP2mLeaves];
+    if (t < kP2mLeaves) {
+        const int l = L0 + min(t, nl - 1);
+        lo_s[t] = t < nl ? (int)start[l] : 0;
+        hi_s[t] = t < nl ? (int)(start[l] + count[l]) : 0;
+    }
+    __syncthreads();
+    const int a0 = lo_s[0], a1 = hi_s[nl - 1];
+    const float ih = 1.0f / h;
+    const int role = t >> 7, ct = t & (kP2mChunk - 1);
+    const int jbase = role * kLPT;
+    float acc[SL][kLPT];
+#pragma unroll
+    for (int j = 0; j < kLPT; ++j)
+#pragma unroll
+        for (int c = 0; c < SL; ++c) acc[c][j] = 0.f;
+    for (int base = a0; base < a1; base += kP2mChunk) {
+        const int a = base + ct;
+        if (a < a1) {
+            const float4 p4 = pos[a];
+            int j = 0;  // the atom's leaf: the last k with lo_s[k] <= a (empty leaves share starts)
+#pragma unroll
+            for (int k = 1; k < kP2mLeaves; ++k)
+                if (k < nl && lo_s[k] <= a) j = k;
+            const uint32_t lf = (uint32_t)(L0 + j);
+            const float cx = (compact3(lf) + 0.5f) * h, cy = (compact3(lf >> 1) + 0.5f) * h,
+                        cz = (compact3(lf >> 2) + 0.5f) * h;
+            const float q = p4.w;
+            const float dx = p4.x - cx, dy = p4.y - cy, dz = p4.z - cz;
+            float* row = hsm + ct * NCS;
+            auto put = [&](int n, int m, float re, float im) {
+                if (m == 0) {
+                    row[n * n] = q * re;
+                } else {
+                    row[n * n + 2 * m - 1] = q * re;
+                    row[n * n + 2 * m] = -q * im;
+                }
+            };
+            if (role == 0) {
+                regular_harmonics_cols<P, 0, MS - 1>(dx * ih, dy * ih, dz * ih, put);
+            } else {
+                regular_harmonics_cols<P, MS, P>(dx * ih, dy * ih, dz * ih, put);
+                const float qhi = rintf(q * 2048.f) * (1.f / 2048.f);
+                msm[0 * kP2mChunk + ct] = qhi;
+                msm[1 * kP2mChunk + ct] = q - qhi;
+                msm[2 * kP2mChunk + ct] = q * dx;
+                msm[3 * kP2mChunk + ct] = q * dy;
+                msm[4 * kP2mChunk + ct] = q * dz;
+                msm[5 * kP2mChunk + ct] = q * (dx * dx + dy * dy + dz * dz);
+            }
+        }
+        __syncthreads();
+        const int top = min(a1, base + kP2mChunk);
+#pragma unroll
+        for (int c = 0; c < SL; ++c) {
+            const int v = ct + c * kP2mChunk;
+            if (v >= NC + (leafmom ? kMom : 0)) continue;
+            // coefficient v: column v of the harmonics rows; moment v - NC: its own row
+            const float* src = v < NC ? hsm + v : msm + (v - NC) * kP2mChunk;
+            const int stride = v < NC ? NCS : 1;
+#pragma unroll
+            for (int jj = 0; jj < kLPT; ++jj) {
+                const int j = jbase + jj;
+                const int s0 = max(lo_s[j], base), s1 = min(hi_s[j], top);
+                float sum = acc[c][jj];
+                for (int b = s0; b < s1; ++b) sum += src[(b - base) * stride];
+                acc[c][jj] = sum;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int jj = 0; jj < kLPT; ++jj) {
+        const int j = jbase + jj;
+        if (j >= nl) break;
+        float* out = M + (long)(L0 + j) * ncp;
+#pragma unroll
+        for (int c = 0; c < SL; ++c) {
+            const int v = ct + c * kP2mChunk;
+            if (v < NC) out[v] = acc[c][jj];
+            else if (leafmom && v < NC + kMom) leafmom[(long)(L0 + j) * kMomStride + (v - NC)] = acc[c][jj];
+        }
+        for (int v = NC + ct; v < ncp; v += kP2mChunk) out[v] = 0.f;
+    }
+}
+
 // ---- periodic root: FP64 root multipole (M2M from level 1) and the Q, D, T sums ----
-// Q = sum q, D = sum q u, T = sum q |u|^2 about the box centre, reduced in a fixed order:
-// leaves -> kQdtBlocks partials (k_qdt) -> totals (k_lattice).
+// Q = sum q, D = sum q u, T = sum q |u|^2 about the box centre, from the leaf moments about
+// the leaf centres c (d = u - c):  D = sum q d + Q c,  T = sum q |d|^2 + 2 c . sum q d + Q |c|^2,
+// in FP64, reduced in a fixed order: leaves -> kQdtBlocks partials (k_qdt) -> totals (k_lattice).
 constexpr int kQdtBlocks = 64;
-__global__ void __launch_bounds__(256) k_qdt(int nleaf, const double* __restrict__ leafqdt,
+__global__ void __launch_bounds__(256) k_qdt(int nleaf, double h, double half_box, const float* __restrict__ leafmom,
                                              double* __restrict__ partial) {
     __shared__ double red[5][256];
     const int per = (nleaf + kQdtBlocks - 1) / kQdtBlocks;
     const int b0 = blockIdx.x * per, b1 = min(nleaf, b0 + per);
     double a[5] = {0, 0, 0, 0, 0};
-    for (int l = b0 + threadIdx.x; l < b1; l += 256)
-        for (int c = 0; c < 5; ++c) a[c] += leafqdt[5L * l + c];
+    for (int l = b0 + threadIdx.x; l < b1; l += 256) {
+        const float4 m0 = *reinterpret_cast<const float4*>(leafmom + (long)l * kMomStride);
+        const float2 m1 = *reinterpret_cast<const float2*>(leafmom + (long)l * kMomStride + 4);
+        const double Q = (double)m0.x + (double)m0.y;
+        const double mx = m0.z, my = m0.w, mz = m1.x, mt = m1.y;
+        const double cx = (compact3((uint32_t)l) + 0.5) * h - half_box, cy = (compact3((uint32_t)l >> 1) + 0.5) * h - half_box,
+                     cz = (compact3((uint32_t)l >> 2) + 0.5) * h - half_box;
+        a[0] += Q;
+        a[1] += mx + Q * cx;
+        a[2] += my + Q * cy;
+        a[3] += mz + Q * cz;
+        a[4] += mt + 2.0 * (cx * mx + cy * my + cz * mz) + Q * (cx * cx + cy * cy + cz * cz);
+    }
     for (int c = 0; c < 5; ++c) red[c][threadIdx.x] = a[c];
     __syncthreads();
     for (int st = 128; st > 0; st >>= 1) {
@@ -436,14 +672,17 @@ __global__ void k_root(int nc, int ncp, int depth, const double* __restrict__ Ad
     if (lane == 0) root[j] = s;
 }
 
-// L0 = Lambda M0 (FP64), written as the FP32 level-0 local expansion
+// L0 = Lambda M0 (FP64), written as the FP32 level-0 local expansion.  Block 0 also totals
+// Q, D, T from the fixed-order partials and leaves c2 (Q, D, T), c2 = 2 pi / (3 V), in FP32 for
+// the per-atom correction (qdtf).
 __global__ void k_lattice(int nc, int ncp, const double* __restrict__ Lam, double* __restrict__ root,
-                          float* __restrict__ L0) {
-    if (blockIdx.x == 0 && threadIdx.x < 5) {  // Q, D, T totals from the fixed-order partials
+                          float* __restrict__ L0, double c2, float* __restrict__ qdtf) {
+    if (blockIdx.x == 0 && threadIdx.x < 5) {
         const double* partial = root + nc + 8;
         double t = 0.0;
         for (int b = 0; b < kQdtBlocks; ++b) t += partial[5 * b + threadIdx.x];
         root[nc + threadIdx.x] = t;
+        qdtf[threadIdx.x] = (float)(c2 * t);
     }
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -559,13 +798,12 @@ struct NearParams {
     const uint32_t* count;
     const float4* pos;
     const float* Lleaf;
-    const double* qdt;  // Q, Dx, Dy, Dz, T (periodic) or null
-    double vol;
+    const float* qdtf;  // c2 (Q, Dx, Dy, Dz, T), c2 = 2 pi / (3 V) (periodic) or null
     const uint32_t* perm;
     float* F;
     float* phi_out;
     float* phis;
-    double* epart;
+    float* epart;  // per-leaf sum of q phi (FP32, ~15 terms); totalled in FP64 by k_final
 };
 
 // Far field per atom: L2P of the leaf's local expansion plus the periodic background term,
@@ -590,16 +828,14 @@ __global__ void __launch_bounds__(128) k_l2p(int n, int use_far, NearParams a, c
         gy *= ih * ih;
         gz *= ih * ih;
     }
-    if (a.periodic && a.qdt) {
-        const float c2 = (float)(2.0 * M_PI / (3.0 * a.vol));
-        const float cq = (float)a.qdt[0], cdx = (float)a.qdt[1], cdy = (float)a.qdt[2], cdz = (float)a.qdt[3],
-                    ctr = (float)a.qdt[4];
+    if (a.periodic && a.qdtf) {
+        const float cq = a.qdtf[0], cdx = a.qdtf[1], cdy = a.qdtf[2], cdz = a.qdtf[3], ctr = a.qdtf[4];
         const float hb = 0.5f * a.Lbox;
         const float ux = me.x - hb, uy = me.y - hb, uz = me.z - hb;
-        pot += c2 * (cq * (ux * ux + uy * uy + uz * uz) - 2.f * (ux * cdx + uy * cdy + uz * cdz) + ctr);
-        gx += 2.f * c2 * (cq * ux - cdx);
-        gy += 2.f * c2 * (cq * uy - cdy);
-        gz += 2.f * c2 * (cq * uz - cdz);
+        pot += cq * (ux * ux + uy * uy + uz * uz) - 2.f * (ux * cdx + uy * cdy + uz * cdz) + ctr;
+        gx += 2.f * (cq * ux - cdx);
+        gy += 2.f * (cq * uy - cdy);
+        gz += 2.f * (cq * uz - cdz);
     }
     far[s] = make_float4(pot, gx, gy, gz);
 }
@@ -657,7 +893,7 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
     __shared__ float nb_sh[4][27][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int leaf = blockIdx.x * 4 + w;
-    double esum = 0.0;
+    float esum = 0.f;
     if (leaf < a.nleaf) {
         const int nb = 1 << a.depth;
         const int ix = (int)compact3(leaf), iy = (int)compact3(leaf >> 1), iz = (int)compact3(leaf >> 2);
@@ -845,7 +1081,7 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
                 }
                 if (a.phi_out) a.phi_out[i] = a.ke * pot;
                 a.phis[st + ti] = pot;
-                esum += (double)q * (double)pot;
+                esum = fmaf(q, pot, esum);
             }
         }
     }
@@ -856,22 +1092,45 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
     if (lane == 0 && leaf < a.nleaf) a.epart[leaf] = esum;
 }
 
-__global__ void k_final(int nparts, const double* __restrict__ epart, double ke, double* __restrict__ E, int K,
-                        const int* __restrict__ site_ptr, const int* __restrict__ site_atoms,
-                        const uint32_t* __restrict__ inv, const float* __restrict__ dq,
-                        const float* __restrict__ phis, float* __restrict__ dVdl) {
+// E = 1/2 k sum of the FP32 per-leaf partials of q phi, totalled in FP64: each of the
+// kFinalBlocks blocks sums a fixed slice, and the last block to finish (atomic ticket) adds the
+// block totals in block order, so the result is deterministic.  dV/dlambda_k = k sum over the
+// site's atoms of dq phi (FP64), one thread per site.
+constexpr int kFinalBlocks = 32;
+static_assert(8 + 5 * kQdtBlocks + 4 + kFinalBlocks + 1 <= kRootDoubles, "root scratch layout");
+__global__ void __launch_bounds__(256) k_final(int nparts, const float* __restrict__ epart, double ke,
+                                               double* __restrict__ E, int K, const int* __restrict__ site_ptr,
+                                               const int* __restrict__ site_atoms, const uint32_t* __restrict__ inv,
+                                               const float* __restrict__ dq, const float* __restrict__ phis,
+                                               float* __restrict__ dVdl, double* __restrict__ blocksum,
+                                               unsigned int* __restrict__ ticket) {
     __shared__ double red[256];
+    __shared__ bool last;
+    const int per = (nparts + kFinalBlocks - 1) / kFinalBlocks;
+    const int b0 = blockIdx.x * per, b1 = min(nparts, b0 + per);
     double s = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += 256) s += epart[i];
+    for (int i = b0 + threadIdx.x; i < b1; i += 256) s += (double)epart[i];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int d = 128; d > 0; d >>= 1) {
         if ((int)threadIdx.x < d) red[threadIdx.x] += red[threadIdx.x + d];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && E) E[0] = 0.5 * ke * red[0];
+    if (threadIdx.x == 0) {
+        blocksum[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == kFinalBlocks - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (int b = 0; b < kFinalBlocks; ++b) t += ((volatile double*)blocksum)[b];
+        if (E) E[0] = 0.5 * ke * t;
+        *ticket = 0u;  // ready for the next call
+    }
     if (dVdl)
-        for (int k = threadIdx.x; k < K; k += 256) {
+        for (int k = blockIdx.x * 256 + threadIdx.x; k < K; k += kFinalBlocks * 256) {
             double v = 0.0;
             for (int a = site_ptr[k]; a < site_ptr[k + 1]; ++a) {
                 const uint32_t si = inv[site_atoms[a]];
@@ -903,10 +1162,10 @@ __global__ void k_adjoint(int n, int K, const double* __restrict__ gbar, const f
 
 // ---------------------------------------------------------------------------------------------
 template <int P>
-static void launch_p2m(int nleaf, float h, float half, const Handle* hd, float* Mleaf, double* qdt,
+static void launch_p2m(int nleaf, float h, const Handle* hd, float* Mleaf, float* mom,
                        cudaStream_t st) {
-    k_p2m<P><<<(nleaf + 3) / 4, 128, 0, st>>>(nleaf, h, half, hd->start, hd->count, hd->pos, Mleaf, hd->ncp,
-                                              qdt);
+    k_p2m<P><<<(nleaf + kP2mLeaves - 1) / kP2mLeaves, kP2mThreads, P2mCfg<P>::kSmem, st>>>(
+        nleaf, h, hd->start, hd->count, hd->pos, Mleaf, hd->ncp, mom);
 }
 template <int P>
 static void launch_l2p(int n, int use_far, const NearParams& a, const uint32_t* skey, float4* far, cudaStream_t st) {
@@ -935,13 +1194,16 @@ static void launch_l2p(int n, int use_far, const NearParams& a, const uint32_t* 
 
 static inline int sort_passes(int depth) { return (3 * depth + 7) / 8; }
 
-void configure_kernels(int ncp) {
-    (void)ncp;
+template <int P>
+static void configure_p2m() {
+    cudaFuncSetAttribute(k_p2m<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2mCfg<P>::kSmem);
 }
+
+void configure_kernels(int p) { FMM_DISPATCH_P(p, configure_p2m); }
 
 int launches_per_eval(const Handle* h) {
     const int d = h->depth;
-    int n = 1 /*keys*/ + 3 * sort_passes(d) + 1 /*ranges*/ + 1 /*gather*/ + 1 /*p2m*/;
+    int n = 4 /*count, scan, place, order+gather*/ + 1 /*p2m*/;
     const int lmin = h->periodic ? 1 : 2;
     if (d >= lmin) n += 2 * (d - lmin);  // M2M parent levels d-1 .. lmin (split-K product + sum)
     if (h->periodic) n += 3;       // Q/D/T partials + root + lattice
@@ -951,6 +1213,9 @@ int launches_per_eval(const Handle* h) {
     if (h->periodic || d >= 2) n += 1;  // l2p
     return n;
 }
+
+// FP32 copies of c2 (Q, D, T) for the per-atom correction, after the FP64 totals and partials
+static inline float* qdt_float(Handle* h) { return reinterpret_cast<float*>(h->root + h->nc + 8 + 5 * kQdtBlocks); }
 
 static inline void stage(Handle* h, int i, cudaStream_t st) {
     if (h->profiling) cudaEventRecord(h->ev[i], st);
@@ -963,37 +1228,22 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     BoxGeom g{h->box.origin[0], h->box.origin[1], h->box.origin[2], h->box.edge, h->s_bin, nb, d, h->periodic};
     const float* lam = h->lam_bound ? h->lam_bound : h->lam;
     stage(h, 0, st);
-    // --- binning ---
-    const int nblk = (n + kSortTile - 1) / kSortTile;
-    if (n > 0) k_keys<<<(n + 255) / 256, 256, 0, st>>>(n, x, g, h->key, h->vA, h->status);
-    const uint32_t* kin = h->key;
-    const uint32_t* vin = h->vA;
-    uint32_t* kbuf[2] = {h->kB, h->kA};
-    uint32_t* vbuf[2] = {h->vB, h->vA};
-    const int passes = sort_passes(d);
-    for (int ps = 0; ps < passes; ++ps) {
-        uint32_t* ko = kbuf[ps & 1];
-        uint32_t* vo = vbuf[ps & 1];
-        if (n > 0) {
-            k_sort_hist<<<nblk, kSortThreads, 0, st>>>(n, kin, 8 * ps, h->sort_table, nblk);
-            k_sort_scan<<<1, 1024, 0, st>>>(h->sort_table, 256 * nblk);
-            k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(n, kin, vin, ko, vo, 8 * ps, h->sort_table, nblk);
-        }
-        kin = ko;
-        vin = vo;
+    // --- binning: counting sort by leaf (see k_bin_count .. k_bin_order_gather) ---
+    if (n > 0) k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(n, x, g, h->key, h->vA, h->leafcnt, h->status);
+    k_bin_scan<<<1, kScanThreads, 0, st>>>(nleaf, h->leafcnt, h->start, h->count);
+    h->perm = h->kA;
+    h->sorted_key = h->kB;
+    if (n > 0) {
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(n, h->key, h->vA, h->start, h->vB);
+        k_bin_order_gather<<<(nleaf + 3) / 4, 128, 0, st>>>(nleaf, h->start, h->count, h->vB, h->perm,
+                                                            h->sorted_key, x, g, h->qA, h->qB, h->site, h->K, lam,
+                                                            h->pos, h->dq, h->inv, h->status);
     }
-    h->sorted_key = const_cast<uint32_t*>(kin);
-    h->perm = const_cast<uint32_t*>(vin);
-    k_ranges<<<(nleaf + 255) / 256, 256, 0, st>>>(n, nleaf, h->sorted_key, h->start, h->count);
-    if (n > 0)
-        k_gather<<<(n + 255) / 256, 256, 0, st>>>(n, h->perm, x, g, h->qA, h->qB, h->site, h->K, lam, h->pos,
-                                                  h->dq, h->inv, h->status);
     stage(h, 1, st);
     // --- P2M ---
     float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
     float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
-    FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, (float)(0.5 * h->box.edge), h, Mleaf,
-                   h->periodic ? h->leafqdt : nullptr, st);
+    FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, h, Mleaf, h->periodic ? h->leafmom : nullptr, st);
     stage(h, 2, st);
     // --- M2M (FP32) for parent levels d-1 .. lmin: one GEMM per level,
     //     [parents x 8 ncp] (the 8 children are contiguous) x [8 ncp x ncp] ---
@@ -1008,9 +1258,11 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     if (h->periodic) {
         const int nrowblk = (h->nc + 3) / 4;
         const float* M1 = (d >= 1) ? h->M + h->lvl_off[1] * h->ncp : nullptr;
-        k_qdt<<<kQdtBlocks, 256, 0, st>>>(nleaf, h->leafqdt, h->root + h->nc + 8);
+        k_qdt<<<kQdtBlocks, 256, 0, st>>>(nleaf, h->box.edge / nb, 0.5 * h->box.edge, h->leafmom, h->root + h->nc + 8);
         k_root<<<nrowblk, 128, 0, st>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, h->root);
-        k_lattice<<<(h->ncp + 3) / 4, 128, 0, st>>>(h->nc, h->ncp, h->Lam, h->root, h->L);
+        k_lattice<<<(h->ncp + 3) / 4, 128, 0, st>>>(h->nc, h->ncp, h->Lam, h->root, h->L,
+                                                     2.0 * M_PI / (3.0 * h->box.edge * h->box.edge * h->box.edge),
+                                                     qdt_float(h));
     }
     stage(h, 4, st);
     // --- M2L ---
@@ -1048,8 +1300,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.count = h->count;
     a.pos = h->pos;
     a.Lleaf = Lleaf;
-    a.qdt = h->periodic ? h->root + h->nc : nullptr;
-    a.vol = h->box.edge * h->box.edge * h->box.edge;
+    a.qdtf = h->periodic ? qdt_float(h) : nullptr;
     a.perm = h->perm;
     a.F = F;
     a.phi_out = phi;
@@ -1060,8 +1311,9 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, has_far ? h->far : nullptr);
     stage(h, 7, st);
     const int nparts = nleaf;  // one q phi partial per leaf
-    k_final<<<1, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,
-                               h->phis, dVdl);
+    double* fin = h->root + h->nc + 8 + 5 * kQdtBlocks + 4;  // [kFinalBlocks] block totals, then the ticket
+    k_final<<<kFinalBlocks, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,
+                                          h->phis, dVdl, fin, reinterpret_cast<unsigned int*>(fin + kFinalBlocks));
     stage(h, 8, st);
     return 0;
 }

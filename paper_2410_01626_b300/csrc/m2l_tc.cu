@@ -163,7 +163,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
              int NKC, int slab_rows, int* __restrict__ status) {
     using Cfg = TcCfg<MODE>;
     constexpr bool SPLIT = Cfg::kSplit;
-    constexpr int kTcChunk = Cfg::kChunk;
     constexpr int kTcKG = Cfg::kKG;
     static_assert(Cfg::kStageBytes == kTcTBytes, "ring stage size");
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -186,7 +185,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     const TcTile tile = tiles[blockIdx.x];
     const int lev = tile.level, c = tile.cls, r0 = tile.r0;
-    const int n = lv.n[lev], R = lv.R[lev], S = lv.S[lev];
+    const int n = lv.n[lev], R = lv.R[lev];
     const int m2 = n + 2;
     const int NKG = NKC * kTcKG;
     const int ngroups = 8 * NKC;  // (source class, K chunk) groups

@@ -51,6 +51,30 @@ def test_binning_bit_exact_periodic_adversarial(depth):
     _binning_case(s, depth)
 
 
+@pytest.mark.parametrize("periodic", [True, False])
+def test_binning_bit_exact_cell_faces(periodic):
+    """Coordinates on cell faces and one or two float ulps either side of them, with a
+    non-zero origin: the cases where single-precision key arithmetic would disagree with
+    the FP64 specification."""
+    depth, L, o = 4, 3.7, (-1.25, 0.5, 2.0)
+    s = synth.open_uniform(seed=9, n=4000, L=L, n_sites=2)
+    s["origin"] = o
+    h = L / 2 ** depth
+    rng = np.random.default_rng(4)
+    x = (s["x"].astype(np.float64) + np.asarray(o)).astype(np.float32)
+    k = rng.integers(0, 2 ** depth + 1, size=(3000, 3))
+    face = (np.asarray(o) + k * h).astype(np.float32)
+    ulps = rng.integers(-2, 3, size=face.shape)
+    face = np.nextafter(face, np.where(ulps > 0, np.inf, -np.inf).astype(np.float32))
+    face = np.where(ulps == 0, (np.asarray(o) + k * h).astype(np.float32), face)
+    x[:3000] = face
+    if not periodic:  # keep the open box's atoms inside [origin, origin + L]
+        x = np.clip(x, np.asarray(o, np.float32), np.asarray(o) + L).astype(np.float32)
+    s["x"] = x
+    s["periodic"] = periodic
+    _binning_case(s, depth)
+
+
 def test_binning_large_stable():
     """Many atoms per leaf and ties: the permutation must be the stable one."""
     rng = np.random.default_rng(0)
