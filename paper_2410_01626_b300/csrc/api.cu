@@ -77,6 +77,8 @@ void free_all(Handle& h) {
     dfree(h.B2);
     dfree(h.Ad);
     dfree(h.Lam);
+    translate_free(h.m2m_tc);
+    translate_free(h.l2l_tc);
     dfree(h.tiles);
     dfree(h.M);
     dfree(h.L);
@@ -273,7 +275,20 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
                 h.lvl_off[l] = a2;
                 a2 += 1L << (3 * l);
             }
-            const int e = m2l_tc_setup(&h, ops->Trm);
+            int e = m2l_tc_setup(&h, ops->Trm);
+            if (e == FMM_OK) {  // M2M [ncp][8 ncp] and L2L [8 ncp][ncp] as row-major W[m][k]
+                std::vector<float> W((size_t)8 * ncp * ncp);
+                for (int c = 0; c < 8; ++c)
+                    for (int k = 0; k < ncp; ++k)
+                        for (int j = 0; j < ncp; ++j)
+                            W[(size_t)j * 8 * ncp + c * ncp + k] = ops->A[((size_t)c * ncp + k) * ncp + j];
+                h.m2m_tc = translate_pack(W, ncp, 8 * ncp);
+                for (int k = 0; k < ncp; ++k)
+                    for (int cj = 0; cj < 8 * ncp; ++cj) W[(size_t)cj * ncp + k] = ops->B2[(size_t)k * 8 * ncp + cj];
+                h.l2l_tc = translate_pack(W, 8 * ncp, ncp);
+                if (!h.m2m_tc.dev || !h.l2l_tc.dev) e = FMM_ERR_OOM;
+                translate_configure();
+            }
             if (e != FMM_OK) {
                 m2l_tc_free(&h);
                 free_all(h);

@@ -26,6 +26,13 @@ struct M2LTile {
     int nparents;     // parents in this tile
 };
 
+// A fixed translation operator packed for the tensor-core M2M / L2L (translate_tc.cu)
+struct TranslateOp {
+    uint8_t* dev = nullptr;
+    size_t bytes = 0;
+    int Mtot = 0, K = 0, nmt = 0, nkc = 0;
+};
+
 struct Handle {
     int device = 0;
     fmm_box box{};
@@ -42,6 +49,7 @@ struct Handle {
     float* B2 = nullptr;       // [ncp][8 ncp] L2L, all octants side by side
     double* Ad = nullptr;      // [8][nc][nc] M2M row-major, FP64 (root step)
     double* Lam = nullptr;     // [nc][nc] lattice, FP64 row-major
+    TranslateOp m2m_tc, l2l_tc;  // mixed precisions: M2M and L2L on the tensor cores
     M2LTile* tiles = nullptr;  // M2L work list
     int ntiles = 0;
     // tree storage
@@ -94,6 +102,12 @@ int launches_per_eval(const Handle* h);
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi,
                     const float* dVdl, float* gx, float* gqA, float* gqB, float* glam,
                     cudaStream_t st);
+// translate_tc.cu
+TranslateOp translate_pack(const std::vector<float>& W, int Mtot, int K);  // W row-major [Mtot][K]
+void translate_free(TranslateOp& op);
+void translate_configure();
+void translate_tc(const TranslateOp& op, const float* X, int ldx, int N, float* C, int ldc, bool accumulate,
+                  int* status, cudaStream_t st, int ksplit = 1, float* work = nullptr);
 // m2l_tc.cu
 bool m2l_tc_supported(const Handle* h);
 int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor);  // [343][nc][nc], output-major

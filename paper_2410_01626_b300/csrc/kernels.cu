@@ -1250,8 +1250,12 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lmin = h->periodic ? 1 : 2;
     for (int l = d - 1; l >= lmin; --l) {
         const int np = 1 << (3 * l);
-        sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
-              h->M + h->lvl_off[l] * h->ncp, h->ncp, false, st, 8, h->work);  // split K by child octant
+        if (h->m2m_tc.dev)
+            translate_tc(h->m2m_tc, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, np, h->M + h->lvl_off[l] * h->ncp,
+                         h->ncp, false, h->status, st, 8, h->work);  // split K by child octant
+        else
+            sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
+                  h->M + h->lvl_off[l] * h->ncp, h->ncp, false, st, 8, h->work);  // split K by child octant
     }
     stage(h, 3, st);
     // --- periodic root (FP64) ---
@@ -1282,8 +1286,12 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lfirst = h->periodic ? 1 : lmin + 1;
     for (int l = lfirst; l <= d; ++l) {
         const int np = 1 << (3 * (l - 1));
-        sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
-              h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, st);
+        if (h->l2l_tc.dev)
+            translate_tc(h->l2l_tc, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, np, h->L + h->lvl_off[l] * h->ncp,
+                         8 * h->ncp, true, h->status, st);
+        else
+            sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
+                  h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, st);
     }
     stage(h, 6, st);
     // --- near field + L2P + outputs ---

@@ -182,6 +182,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t* t_empty = bars + 8 + kTcStages;    // [kTcStages]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8 + 2 * kTcStages);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    // copies issued (operator chunks, slabs) by the producer and consumed by the MMA issuer,
+    // so that after an abort the outstanding copies are waited for before the CTA exits
+    volatile int* copy_count = abort_flag + 1;  // [4]: t issued, slabs issued, t taken, slabs taken
 
     const TcTile tile = tiles[blockIdx.x];
     const int lev = tile.level, c = tile.cls, r0 = tile.r0;
@@ -204,6 +207,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc::mbar_init(t_empty + s, 1);
         }
         *abort_flag = 0;
+        for (int q = 0; q < 4; ++q) copy_count[q] = 0;
         tc::fence_mbar_init();
     }
     if (warp == 2) {
@@ -227,7 +231,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer ----------------
+            int t_issued = 0, slabs_issued = 0;
             auto load_slab = [&](int g) {
+                ++slabs_issued;
                 const int pi = g / NKC, ch = g % NKC, buf = g & 1;
                 uint8_t* dst = slab0 + (size_t)buf * slab_bytes;
                 tc::mbar_arrive_expect_tx(slab_full + buf,
@@ -262,6 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc::mbar_arrive_expect_tx(t_full + stage, kTcTBytes);
                     tc::bulk_g2s(tring + (size_t)stage * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
                                  kTcTBytes, t_full + stage);  // hi (+ lo) operator chunk
+                    ++t_issued;
                     if (++stage == kTcStages) {
                         stage = 0;
                         if (!first_round) ephase ^= 1u;
@@ -282,6 +289,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 *abort_flag = 1;
                 atomicOr(status, FMM_DEV_TIMEOUT);
             }
+            copy_count[0] = t_issued;
+            copy_count[1] = slabs_issued;
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -296,6 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int stage = 0;
             uint32_t tphase = 0;
             bool ok = true;
+            int t_taken = 0, slabs_taken = 0;
             for (int g = 0; g < ngroups && ok; ++g) {
                 const int pi = g / NKC, buf = g & 1;
                 const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
@@ -309,6 +319,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     ok = false;
                     break;
                 }
+                ++slabs_taken;
                 tc::fence_after_sync();
                 const uint64_t b_buf = b_base + (((uint64_t)buf * slab_bytes) >> 4) + (uint64_t)hal;
                 uint32_t acc = 0;
@@ -321,6 +332,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         ok = false;
                         break;
                     }
+                    ++t_taken;
                     const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
                     const uint64_t bd0 = b_buf + (uint64_t)((dx + 1) * slab_rows + dy * m2 + dz);
 #pragma unroll
@@ -354,6 +366,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 atomicOr(status, FMM_DEV_TIMEOUT);
                 for (int g2 = 0; g2 < 2; ++g2) tc::mma_commit(acc_full + g2);  // release the drains
             }
+            copy_count[2] = t_taken;
+            copy_count[3] = slabs_taken;
         }
         __syncwarp();
     } else {
@@ -402,6 +416,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     }
     tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        // copies issued but never consumed may still be landing in shared memory: wait for them
+        // (bounded) before the CTA exits; ring use j is stage j % 3 with phase parity (j / 3) & 1
+        for (int j = copy_count[2]; j < copy_count[0]; ++j)
+            tc::mbar_wait(t_full + j % kTcStages, (uint32_t)((j / kTcStages) & 1), kWaitLimit);
+        for (int g = copy_count[3]; g < copy_count[1]; ++g)
+            tc::mbar_wait(slab_full + (g & 1), (uint32_t)((g >> 1) & 1), kWaitLimit);
+    }
     __syncthreads();
     if (warp == 2) tc::tmem_dealloc(tmem, kTcTmemCols);
 }
