@@ -879,12 +879,41 @@ __device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsign
 // (2) When the list fits (kNearCap atoms, the common case), all lanes copy it into shared
 //     memory in one pass as packed pairs (x0 x1 y0 y1 | z0 z1 q0 q1), so that every global
 //     load is in flight together; otherwise the sources are streamed neighbour by neighbour.
-// (3) The warp is split into G = 32/TPG source slices (lane = target + slice * TPG), TPG in
-//     {4, 8, 16, 32} chosen per leaf to minimise padded target slots x source iterations.
-//     Each iteration takes two sources with f32x2 arithmetic; only the own leaf's pairs need
-//     the r > 0 test (self, coincident atoms), since equal positions always share a leaf.
-//     Slice sums are combined with shuffles, then the far field (k_l2p) is added.
-constexpr int kNearCap = 512;
+// (3) Every lane holds two targets.  The warp is split into G source slices of TPG lanes
+//     (lane = target lane + slice * TPG; TPG need not be a power of two), over as many passes
+//     as the leaf needs; (passes, TPG) is chosen per leaf to minimise padded slots x source
+//     iterations.  Each iteration loads one source pair and applies it to both targets with
+//     f32x2 arithmetic; only the own leaf's pairs need the r > 0 test (self, coincident
+//     atoms), since equal positions always share a leaf.  Slice sums are combined by a
+//     fixed-order shuffle tree, then the far field (k_l2p) is added.
+constexpr int kNearCap = 640;
+__device__ __forceinline__ float rsqrt_approx(float x) {  // MUFU reciprocal square root
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// Target atom at sorted slot s: add the far field, write F (input order), phi and the sorted
+// potential, and add q phi to the leaf's energy partial.
+__device__ __forceinline__ void near_output(const NearParams& a, const float4* __restrict__ far, int s, float q,
+                                            float pot, float gx, float gy, float gz, float& esum) {
+    if (far) {
+        const float4 f4 = far[s];
+        pot += f4.x;
+        gx += f4.y;
+        gy += f4.z;
+        gz += f4.w;
+    }
+    const int i = (int)a.perm[s];
+    if (a.F) {
+        a.F[3L * i] = -a.ke * q * gx;
+        a.F[3L * i + 1] = -a.ke * q * gy;
+        a.F[3L * i + 2] = -a.ke * q * gz;
+    }
+    if (a.phi_out) a.phi_out[i] = a.ke * pot;
+    a.phis[s] = pot;
+    esum = fmaf(q, pot, esum);
+}
+
 __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restrict__ far) {
     __shared__ float4 src_sm[4][kNearCap];  // packed pairs: [2j] = (x x y y), [2j+1] = (z z q q)
     __shared__ int nb_off[4][28];
@@ -973,63 +1002,12 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
             }
             __syncwarp();
         }
-        // (3) slice shape: cost = target passes x (source iterations + combine overhead)
-        const int work = staged ? npairs : total;
-        int TPG = 32, best = 1 << 30;
-#pragma unroll
-        for (int tpg = 4; tpg <= 32; tpg <<= 1) {
-            const int g = 32 / tpg;
-            const int cost = ((cnt + tpg - 1) / tpg) * ((work + g - 1) / g + 8 * (31 - __clz(g)) + 24);
-            if (cost < best) {
-                best = cost;
-                TPG = tpg;
-            }
-        }
-        const int G = 32 / TPG;
-        const int tl = lane % TPG, slice = lane / TPG;
-        for (int tb = 0; tb < cnt; tb += TPG) {
-            const int ti = tb + tl;
-            const bool valid = ti < cnt;
-            float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid) me = a.pos[st + ti];
-            float pot, gx, gy, gz;
-            if (staged) {
-                const unsigned long long mx = f2pack(me.x, me.x), my = f2pack(me.y, me.y), mz = f2pack(me.z, me.z);
-                unsigned long long P = 0ull, GX = 0ull, GY = 0ull, GZ = 0ull;
-                const float4* sp4 = src_sm[w];
-                // sources minus target: the gradient of q/r at the target is q (s - x) / r^3
-                auto pair2 = [&](const float4 A, const float4 B, const bool check) {
-                    const unsigned long long dx = f2sub(f2pack(A.x, A.y), mx);
-                    const unsigned long long dy = f2sub(f2pack(A.z, A.w), my);
-                    const unsigned long long dz = f2sub(f2pack(B.x, B.y), mz);
-                    const float2 r2 = f2unpack(f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx))));
-                    float r0 = rsqrtf(r2.x), r1 = rsqrtf(r2.y);
-                    if (check) {
-                        r0 = (r2.x > 0.f) ? r0 : 0.f;
-                        r1 = (r2.y > 0.f) ? r1 : 0.f;
-                    }
-                    const unsigned long long ri = f2pack(r0, r1);
-                    const unsigned long long qri = f2mul(f2pack(B.z, B.w), ri);
-                    P = f2add(P, qri);
-                    const unsigned long long qri3 = f2mul(qri, f2mul(ri, ri));
-                    GX = f2fma(qri3, dx, GX);
-                    GY = f2fma(qri3, dy, GY);
-                    GZ = f2fma(qri3, dz, GZ);
-                };
-                int t = slice;
-                for (; t < own_pairs; t += G) pair2(sp4[2 * t], sp4[2 * t + 1], true);
-                for (; t + G < npairs; t += 2 * G) {
-                    pair2(sp4[2 * t], sp4[2 * t + 1], false);
-                    pair2(sp4[2 * (t + G)], sp4[2 * (t + G) + 1], false);
-                }
-                for (; t < npairs; t += G) pair2(sp4[2 * t], sp4[2 * t + 1], false);
-                const float2 p2 = f2unpack(P), x2 = f2unpack(GX), y2 = f2unpack(GY), z2 = f2unpack(GZ);
-                pot = p2.x + p2.y;
-                gx = x2.x + x2.y;
-                gy = y2.x + y2.y;
-                gz = z2.x + z2.y;
-            } else {
-                pot = gx = gy = gz = 0.f;
+        if (!staged) {  // streamed sources (rare): one target per lane, 32 targets per pass
+            for (int tb = 0; tb < cnt; tb += 32) {
+                const int ti = tb + lane;
+                const bool valid = ti < cnt;
+                const float4 me = valid ? a.pos[st + ti] : make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
+                float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
                 float4* stage = src_sm[w];
                 for (int o = 0; o < 27; ++o) {
                     const int s0 = nb_s0[w][o], sc = nb_sc[w][o];
@@ -1043,11 +1021,11 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
                         stage[lane] = sp;
                         __syncwarp();
                         const int ns = min(32, sc - sb);
-                        for (int t = slice; t < ns; t += G) {
+                        for (int t = 0; t < ns; ++t) {
                             const float4 s4 = stage[t];
                             const float dx = s4.x - me.x, dy = s4.y - me.y, dz = s4.z - me.z;
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const float ri = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
+                            const float ri = (r2 > 0.f) ? rsqrt_approx(r2) : 0.f;
                             const float qri = s4.w * ri;
                             pot += qri;
                             const float qri3 = qri * ri * ri;
@@ -1057,31 +1035,97 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
                         }
                     }
                 }
+                if (valid) near_output(a, far, st + ti, me.w, pot, gx, gy, gz, esum);
             }
-            for (int off = TPG; off < 32; off <<= 1) {
-                pot += __shfl_xor_sync(0xffffffffu, pot, off);
-                gx += __shfl_xor_sync(0xffffffffu, gx, off);
-                gy += __shfl_xor_sync(0xffffffffu, gy, off);
-                gz += __shfl_xor_sync(0xffffffffu, gz, off);
+        } else if (cnt > 0) {
+            // (3) mapping: passes x TPG lanes (2 targets each) x G slices
+            int TPG = 32, G = 1, passes = (cnt + 63) / 64, best = 1 << 30;
+            const int p0 = passes;
+            for (int ps = p0; ps < p0 + 4; ++ps) {
+                const int tpg = (cnt + 2 * ps - 1) / (2 * ps);
+                const int g = 32 / tpg;
+                const int cost = ps * ((npairs + g - 1) / g + 4 * g + 16);
+                if (cost < best) {
+                    best = cost;
+                    TPG = tpg;
+                    G = g;
+                    passes = ps;
+                }
             }
-            if (valid && slice == 0) {
-                if (far) {
-                    const float4 f4 = far[st + ti];
-                    pot += f4.x;
-                    gx += f4.y;
-                    gy += f4.z;
-                    gz += f4.w;
+            const int tl = lane % TPG, slice = lane / TPG;
+            const bool active = slice < G;
+            const float4* sp4 = src_sm[w];
+            for (int ps = 0; ps < passes; ++ps) {
+                const int ti0 = ps * 2 * TPG + tl, ti1 = ti0 + TPG;
+                const bool v0 = active && ti0 < cnt, v1 = active && ti1 < cnt;
+                const float4 far_pt = make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
+                const float4 me0 = v0 ? a.pos[st + ti0] : far_pt, me1 = v1 ? a.pos[st + ti1] : far_pt;
+                const unsigned long long mx0 = f2pack(me0.x, me0.x), my0 = f2pack(me0.y, me0.y),
+                                         mz0 = f2pack(me0.z, me0.z), mx1 = f2pack(me1.x, me1.x),
+                                         my1 = f2pack(me1.y, me1.y), mz1 = f2pack(me1.z, me1.z);
+                unsigned long long P0 = 0ull, X0 = 0ull, Y0 = 0ull, Z0 = 0ull, P1 = 0ull, X1 = 0ull, Y1 = 0ull, Z1 = 0ull;
+                // sources minus target: the gradient of q/r at the target is q (s - x) / r^3
+                auto apply = [&](const unsigned long long sx, const unsigned long long sy, const unsigned long long sz,
+                                 const unsigned long long sq, const unsigned long long mx, const unsigned long long my,
+                                 const unsigned long long mz, unsigned long long& P, unsigned long long& GX,
+                                 unsigned long long& GY, unsigned long long& GZ, const bool check) {
+                    const unsigned long long dx = f2sub(sx, mx), dy = f2sub(sy, my), dz = f2sub(sz, mz);
+                    const float2 r2 = f2unpack(f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx))));
+                    float r0 = rsqrt_approx(r2.x), r1 = rsqrt_approx(r2.y);
+                    if (check) {
+                        r0 = (r2.x > 0.f) ? r0 : 0.f;
+                        r1 = (r2.y > 0.f) ? r1 : 0.f;
+                    }
+                    const unsigned long long ri = f2pack(r0, r1);
+                    const unsigned long long qri = f2mul(sq, ri);
+                    P = f2add(P, qri);
+                    const unsigned long long qri3 = f2mul(qri, f2mul(ri, ri));
+                    GX = f2fma(qri3, dx, GX);
+                    GY = f2fma(qri3, dy, GY);
+                    GZ = f2fma(qri3, dz, GZ);
+                };
+                auto step = [&](int t, const bool check) {
+                    const float4 A = sp4[2 * t], B = sp4[2 * t + 1];
+                    const unsigned long long sx = f2pack(A.x, A.y), sy = f2pack(A.z, A.w), sz = f2pack(B.x, B.y),
+                                             sq = f2pack(B.z, B.w);
+                    apply(sx, sy, sz, sq, mx0, my0, mz0, P0, X0, Y0, Z0, check);
+                    apply(sx, sy, sz, sq, mx1, my1, mz1, P1, X1, Y1, Z1, check);
+                };
+                if (active) {
+                    int t = slice;
+                    for (; t < own_pairs; t += G) step(t, true);
+                    for (; t + G < npairs; t += 2 * G) {
+                        step(t, false);
+                        step(t + G, false);
+                    }
+                    for (; t < npairs; t += G) step(t, false);
                 }
-                const int i = (int)a.perm[st + ti];
-                const float q = me.w;
-                if (a.F) {
-                    a.F[3L * i] = -a.ke * q * gx;
-                    a.F[3L * i + 1] = -a.ke * q * gy;
-                    a.F[3L * i + 2] = -a.ke * q * gz;
+                float v[8];
+                {
+                    const float2 p0v = f2unpack(P0), x0v = f2unpack(X0), y0v = f2unpack(Y0), z0v = f2unpack(Z0);
+                    const float2 p1v = f2unpack(P1), x1v = f2unpack(X1), y1v = f2unpack(Y1), z1v = f2unpack(Z1);
+                    v[0] = p0v.x + p0v.y;
+                    v[1] = x0v.x + x0v.y;
+                    v[2] = y0v.x + y0v.y;
+                    v[3] = z0v.x + z0v.y;
+                    v[4] = p1v.x + p1v.y;
+                    v[5] = x1v.x + x1v.y;
+                    v[6] = y1v.x + y1v.y;
+                    v[7] = z1v.x + z1v.y;
                 }
-                if (a.phi_out) a.phi_out[i] = a.ke * pot;
-                a.phis[st + ti] = pot;
-                esum = fmaf(q, pot, esum);
+                // slice sums: fixed-order tree over the slices (slice 0 ends with the total)
+                for (int off = 1; off < G; off <<= 1) {
+                    const bool take = (slice % (2 * off)) == 0 && slice + off < G;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float o = __shfl_down_sync(0xffffffffu, v[e], off * TPG);
+                        if (take) v[e] += o;
+                    }
+                }
+                if (slice == 0) {
+                    if (v0) near_output(a, far, st + ti0, me0.w, v[0], v[1], v[2], v[3], esum);
+                    if (v1) near_output(a, far, st + ti1, me1.w, v[4], v[5], v[6], v[7], esum);
+                }
             }
         }
     }
