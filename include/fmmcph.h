@@ -161,9 +161,13 @@ fmm_status fmm_get_binning(fmm_handle* h, uint32_t* key, uint32_t* perm, uint32_
 fmm_status fmm_status_word(fmm_handle* h, int* device_status, void* stream);
 
 /* Per-stage device times of the last fmm_eval when profiling is enabled
- * (CUDA events between the stages, on the eval's stream): ms[0..n) =
- * binning, P2M, M2M, lattice, M2L, L2L, near field + L2P + outputs, final
- * reduction.  Synchronises.  Returns the number of stages written. */
+ * (CUDA events between the stages): ms[0..n) = binning, P2M, M2M, lattice,
+ * M2L, L2L, outputs (the wait for the near field, then L2P, F, phi and the
+ * energy partials), final reduction -- consecutive intervals -- and, as
+ * ms[8], the near field (P2P), which runs on the eval's stream concurrently
+ * with P2M .. L2L (those run on an internal stream of the handle, forked from
+ * and joined back to the eval's stream, so graph capture of fmm_eval works).
+ * Synchronises.  Returns the number of stages written (at most 9). */
 int fmm_stage_times(fmm_handle* h, float* ms, int n);
 fmm_status fmm_set_profiling(fmm_handle* h, int enable);
 

@@ -22,7 +22,9 @@ FMM_FP32, FMM_MIXED_TF32, FMM_MIXED_3XTF32, FMM_MIXED_3XBF16 = 0, 1, 2, 3
 PRECISIONS = {"fp32": FMM_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF32, "3xbf16": FMM_MIXED_3XBF16}
 DEV_DOMAIN, DEV_SITE, DEV_TIMEOUT = 1, 2, 4
 KE_DEFAULT = 138.935458
-STAGES = ("binning", "p2m", "m2m", "root", "m2l", "l2l", "near", "final")
+# consecutive stages of one evaluation, then the near field, which runs on the caller's stream
+# concurrently with the chain p2m .. l2l ("outputs" includes the wait for it)
+STAGES = ("binning", "p2m", "m2m", "root", "m2l", "l2l", "outputs", "final", "p2p")
 
 
 class FmmBox(ctypes.Structure):

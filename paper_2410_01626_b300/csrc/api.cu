@@ -63,7 +63,7 @@ void free_atoms(Handle& h) {
     dfree(h.pos);
     dfree(h.dq);
     dfree(h.phis);
-    dfree(h.far);
+    dfree(h.near);
     h.perm = nullptr;
     h.sorted_key = nullptr;
     h.cap = 0;
@@ -97,9 +97,16 @@ void free_all(Handle& h) {
     dfree(h.hF_dev);
     dfree(h.hdV_dev);
     dfree(h.hE_dev);
-    if (h.ev_valid)
+    if (h.ev_valid) {
         for (auto& e : h.ev) cudaEventDestroy(e);
+        for (auto& e : h.ev_p2p) cudaEventDestroy(e);
+    }
     h.ev_valid = false;
+    if (h.fork_ev) cudaEventDestroy(h.fork_ev);
+    if (h.join_ev) cudaEventDestroy(h.join_ev);
+    if (h.chain) cudaStreamDestroy(h.chain);
+    h.fork_ev = h.join_ev = nullptr;
+    h.chain = nullptr;
 }
 
 inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
@@ -334,7 +341,20 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     cudaMemset(h.root, 0, sizeof(double) * (nc + kRootDoubles));
     cudaMemset(h.site_ptr, 0, sizeof(int));
     for (auto& e : h.ev) cudaEventCreate(&e);
+    for (auto& e : h.ev_p2p) cudaEventCreate(&e);
     h.ev_valid = true;
+    {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&h.chain, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            free_all(h);
+            delete H;
+            return FMM_ERR_CUDA;
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();
         free_all(h);
@@ -358,12 +378,24 @@ fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const f
         if ((e = dalloc(&h.qA, n)) || (e = dalloc(&h.qB, n)) || (e = dalloc(&h.site, n)) || (e = dalloc(&h.key, n)) ||
             (e = dalloc(&h.kA, n)) || (e = dalloc(&h.kB, n)) || (e = dalloc(&h.vA, n)) || (e = dalloc(&h.vB, n)) ||
             (e = dalloc(&h.inv, n)) || (e = dalloc(&h.pos, n)) || (e = dalloc(&h.dq, n)) ||
-            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.far, n))) {
+            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.near, n))) {
             free_atoms(h);
             h.charges_set = false;
             return e;
         }
         h.cap = n;
+    }
+    {  // one q phi partial per 128 atoms (k_far_out blocks)
+        const int nparts = (n + 127) / 128;
+        if (nparts > h.epart_cap) {
+            dfree(h.epart);
+            if (dalloc(&h.epart, nparts)) {
+                h.epart_cap = 0;
+                h.charges_set = false;
+                return FMM_ERR_OOM;
+            }
+            h.epart_cap = nparts;
+        }
     }
     if (K > h.lam_cap) {
         dfree(h.lam);
@@ -522,14 +554,16 @@ fmm_status fmm_set_profiling(fmm_handle* H, int enable) {
 int fmm_stage_times(fmm_handle* H, float* ms, int n) {
     if (!H || !ms || !H->h.profiling) return 0;
     Handle& h = H->h;
-    if (cudaEventSynchronize(h.ev[kNumStages]) != cudaSuccess) {
+    if (cudaEventSynchronize(h.ev[kNumStages - 1]) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int k = 0;
     for (; k < n && k < kNumStages; ++k) {
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, h.ev[k], h.ev[k + 1]) != cudaSuccess) {
+        const cudaError_t r = k < kNumStages - 1 ? cudaEventElapsedTime(&t, h.ev[k], h.ev[k + 1])
+                                                 : cudaEventElapsedTime(&t, h.ev_p2p[0], h.ev_p2p[1]);
+        if (r != cudaSuccess) {
             cudaGetLastError();
             t = -1.f;
         }

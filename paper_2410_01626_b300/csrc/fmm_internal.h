@@ -13,7 +13,7 @@ constexpr int kMaxDepth = 7;
 constexpr int kLeafMomStride = 8;  // floats per leaf in Handle::leafmom
 constexpr int kRootDoubles = 8 + 5 * 64 + 4 + 40;  // Handle::root beyond nc: Q D T, k_qdt partials, FP32 copies, k_final totals + ticket
 constexpr int kNumOps = 343;  // M2L offsets o in {-3..3}^3 (the inner 27 slots unused)
-constexpr int kNumStages = 8;
+constexpr int kNumStages = 9;  // 8 consecutive stage intervals, then the near field on the side branch
 
 inline int ncoef(int p) { return (p + 1) * (p + 1); }
 inline int ncoef_padded(int p) { return (ncoef(p) + 15) / 16 * 16; }
@@ -72,8 +72,8 @@ struct Handle {
     float4* pos = nullptr;
     float* dq = nullptr;
     float* phis = nullptr;   // sorted-order potential (without k_e)
-    float4* far = nullptr;   // sorted-order far-field potential and gradient
-    float* epart = nullptr;  // per-leaf partial sums of q phi
+    float4* near = nullptr;  // sorted-order near-field potential and gradient (k_p2p -> k_far_out)
+    float2* epart = nullptr;  // per-block (hi, lo) partial sums of q phi
     int epart_cap = 0;
     float* leafmom = nullptr;   // [nleaf][kLeafMomStride] periodic: leaf moments for the Q, D, T sums
     double* root = nullptr;     // [nc] FP64 root multipole, then [5] Q D T at root+nc
@@ -82,8 +82,13 @@ struct Handle {
     bool charges_set = false;
     // profiling
     bool profiling = false;
-    cudaEvent_t ev[kNumStages + 1]{};
+    cudaEvent_t ev[kNumStages + 1]{};  // ev[0..8]: boundaries of the 8 consecutive stages (ev[9] unused)
+    cudaEvent_t ev_p2p[2]{};           // the near field on the caller's stream, concurrent with the chain
     bool ev_valid = false;
+    // the multipole chain runs on `chain` (highest priority) while the near field runs on the
+    // caller's stream; fork/join by events
+    cudaStream_t chain = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // host staging for fmm_eval_host
     float* hx_dev = nullptr;
     float* hF_dev = nullptr;

@@ -9,7 +9,7 @@
 //   root      k_root, k_lattice (periodic) FP64 root multipole and lattice operator
 //   M2L       k_m2l_fp32 (FP32 CUDA cores) or the tcgen05 kernel in m2l_tc.cu
 //   L2L       k_sgemm         per level, one dense GEMM into the 8 contiguous children
-//   near      k_l2p<P>        far field per atom (L2P + periodic background term)
+//   outputs   k_far_out<P>    far field per atom (L2P + periodic background term) + near field -> F, phi, E partials
 //             k_p2p           P2P over the 27 neighbour leaves + forces / potential / energy
 //   final     k_final         E (FP64, fixed-order reduction) and dV/dlambda per site
 #include <cuda_runtime.h>
@@ -803,41 +803,81 @@ struct NearParams {
     float* F;
     float* phi_out;
     float* phis;
-    float* epart;  // per-leaf sum of q phi (FP32, ~15 terms); totalled in FP64 by k_final
+    float2* epart;  // per-block sum of q phi as a compensated (hi, lo) pair; totalled in FP64 by k_final
 };
 
-// Far field per atom: L2P of the leaf's local expansion plus the periodic background term,
-// one thread per atom in leaf order; far[s] = (phi, dphi/dx, dphi/dy, dphi/dz).
+// Outputs per atom, one thread per atom in leaf order: the far field (L2P of the leaf's local
+// expansion plus the periodic background term) added to the near field from k_p2p, then F in
+// input order, phi, the sorted potential, and the block's partial sum of q phi: a fixed-order
+// tree over the block's 128 atoms in compensated FP32 (exact products by FMA, TwoSum at every
+// level), kept as a (hi, lo) pair that k_final totals in FP64.
+constexpr int kOutThreads = 128;
+__device__ __forceinline__ float2 two_sum(float a, float b) {  // a + b = s + e exactly
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return make_float2(s, e);
+}
 template <int P>
-__global__ void __launch_bounds__(128) k_l2p(int n, int use_far, NearParams a, const uint32_t* __restrict__ skey,
-                                             float4* __restrict__ far) {
+__global__ void __launch_bounds__(kOutThreads) k_far_out(int n, int use_far, NearParams a,
+                                                         const uint32_t* __restrict__ skey,
+                                                         const float4* __restrict__ near) {
+    __shared__ float2 red[kOutThreads];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const uint32_t leaf = skey[s];
-    const float h = a.h;
-    const float cx = (compact3(leaf) + 0.5f) * h, cy = (compact3(leaf >> 1) + 0.5f) * h,
-                cz = (compact3(leaf >> 2) + 0.5f) * h;
-    const float4 me = a.pos[s];
-    float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-    if (use_far) {
-        const float ih = 1.0f / h;
-        l2p_eval<P>(a.Lleaf + (long)leaf * a.ncp, (me.x - cx) * ih, (me.y - cy) * ih, (me.z - cz) * ih, pot, gx, gy,
-                    gz);
-        pot *= ih;
-        gx *= ih * ih;
-        gy *= ih * ih;
-        gz *= ih * ih;
+    float2 e = make_float2(0.f, 0.f);
+    if (s < n) {
+        const uint32_t leaf = skey[s];
+        const float h = a.h;
+        const float cx = (compact3(leaf) + 0.5f) * h, cy = (compact3(leaf >> 1) + 0.5f) * h,
+                    cz = (compact3(leaf >> 2) + 0.5f) * h;
+        const float4 me = a.pos[s];
+        float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        if (use_far) {
+            const float ih = 1.0f / h;
+            l2p_eval<P>(a.Lleaf + (long)leaf * a.ncp, (me.x - cx) * ih, (me.y - cy) * ih, (me.z - cz) * ih, pot, gx,
+                        gy, gz);
+            pot *= ih;
+            gx *= ih * ih;
+            gy *= ih * ih;
+            gz *= ih * ih;
+        }
+        if (a.periodic && a.qdtf) {
+            const float cq = a.qdtf[0], cdx = a.qdtf[1], cdy = a.qdtf[2], cdz = a.qdtf[3], ctr = a.qdtf[4];
+            const float hb = 0.5f * a.Lbox;
+            const float ux = me.x - hb, uy = me.y - hb, uz = me.z - hb;
+            pot += cq * (ux * ux + uy * uy + uz * uz) - 2.f * (ux * cdx + uy * cdy + uz * cdz) + ctr;
+            gx += 2.f * (cq * ux - cdx);
+            gy += 2.f * (cq * uy - cdy);
+            gz += 2.f * (cq * uz - cdz);
+        }
+        const float4 nr = near[s];
+        pot += nr.x;
+        gx += nr.y;
+        gy += nr.z;
+        gz += nr.w;
+        const int i = (int)a.perm[s];
+        const float q = me.w;
+        if (a.F) {
+            a.F[3L * i] = -a.ke * q * gx;
+            a.F[3L * i + 1] = -a.ke * q * gy;
+            a.F[3L * i + 2] = -a.ke * q * gz;
+        }
+        if (a.phi_out) a.phi_out[i] = a.ke * pot;
+        a.phis[s] = pot;
+        const float qp = q * pot;
+        e = make_float2(qp, fmaf(q, pot, -qp));
     }
-    if (a.periodic && a.qdtf) {
-        const float cq = a.qdtf[0], cdx = a.qdtf[1], cdy = a.qdtf[2], cdz = a.qdtf[3], ctr = a.qdtf[4];
-        const float hb = 0.5f * a.Lbox;
-        const float ux = me.x - hb, uy = me.y - hb, uz = me.z - hb;
-        pot += cq * (ux * ux + uy * uy + uz * uz) - 2.f * (ux * cdx + uy * cdy + uz * cdz) + ctr;
-        gx += 2.f * (cq * ux - cdx);
-        gy += 2.f * (cq * uy - cdy);
-        gz += 2.f * (cq * uz - cdz);
+    red[threadIdx.x] = e;
+    __syncthreads();
+    for (int d = kOutThreads / 2; d > 0; d >>= 1) {
+        if ((int)threadIdx.x < d) {
+            const float2 u = red[threadIdx.x], v = red[threadIdx.x + d];
+            const float2 t = two_sum(u.x, v.x);
+            red[threadIdx.x] = make_float2(t.x, t.y + (u.y + v.y));
+        }
+        __syncthreads();
     }
-    far[s] = make_float4(pot, gx, gy, gz);
+    if (threadIdx.x == 0) a.epart[blockIdx.x] = red[0];
 }
 
 // ---- packed two-wide FP32 arithmetic (f32x2) ----
@@ -885,36 +925,21 @@ __device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsign
 //     iterations.  Each iteration loads one source pair and applies it to both targets with
 //     f32x2 arithmetic; only the own leaf's pairs need the r > 0 test (self, coincident
 //     atoms), since equal positions always share a leaf.  Slice sums are combined by a
-//     fixed-order shuffle tree, then the far field (k_l2p) is added.
+//     fixed-order shuffle tree; k_far_out adds the far field and writes the outputs.
 constexpr int kNearCap = 640;
 __device__ __forceinline__ float rsqrt_approx(float x) {  // MUFU reciprocal square root
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// Target atom at sorted slot s: add the far field, write F (input order), phi and the sorted
-// potential, and add q phi to the leaf's energy partial.
-__device__ __forceinline__ void near_output(const NearParams& a, const float4* __restrict__ far, int s, float q,
-                                            float pot, float gx, float gy, float gz, float& esum) {
-    if (far) {
-        const float4 f4 = far[s];
-        pot += f4.x;
-        gx += f4.y;
-        gy += f4.z;
-        gz += f4.w;
-    }
-    const int i = (int)a.perm[s];
-    if (a.F) {
-        a.F[3L * i] = -a.ke * q * gx;
-        a.F[3L * i + 1] = -a.ke * q * gy;
-        a.F[3L * i + 2] = -a.ke * q * gz;
-    }
-    if (a.phi_out) a.phi_out[i] = a.ke * pot;
-    a.phis[s] = pot;
-    esum = fmaf(q, pot, esum);
+// Near-field potential and gradient of the target atom at sorted slot s; k_far_out adds the far
+// field and writes the outputs.
+__device__ __forceinline__ void near_output(float4* __restrict__ near, int s, float pot, float gx, float gy,
+                                            float gz) {
+    near[s] = make_float4(pot, gx, gy, gz);
 }
 
-__global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restrict__ far) {
+__global__ void __launch_bounds__(128) k_p2p(NearParams a, float4* __restrict__ near) {
     __shared__ float4 src_sm[4][kNearCap];  // packed pairs: [2j] = (x x y y), [2j+1] = (z z q q)
     __shared__ int nb_off[4][28];
     __shared__ int nb_s0[4][27];
@@ -922,7 +947,6 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
     __shared__ float nb_sh[4][27][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int leaf = blockIdx.x * 4 + w;
-    float esum = 0.f;
     if (leaf < a.nleaf) {
         const int nb = 1 << a.depth;
         const int ix = (int)compact3(leaf), iy = (int)compact3(leaf >> 1), iz = (int)compact3(leaf >> 2);
@@ -1035,7 +1059,7 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
                         }
                     }
                 }
-                if (valid) near_output(a, far, st + ti, me.w, pot, gx, gy, gz, esum);
+                if (valid) near_output(near, st + ti, pot, gx, gy, gz);
             }
         } else if (cnt > 0) {
             // (3) mapping: passes x TPG lanes (2 targets each) x G slices
@@ -1123,26 +1147,21 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, const float4* __restr
                     }
                 }
                 if (slice == 0) {
-                    if (v0) near_output(a, far, st + ti0, me0.w, v[0], v[1], v[2], v[3], esum);
-                    if (v1) near_output(a, far, st + ti1, me1.w, v[4], v[5], v[6], v[7], esum);
+                    if (v0) near_output(near, st + ti0, v[0], v[1], v[2], v[3]);
+                    if (v1) near_output(near, st + ti1, v[4], v[5], v[6], v[7]);
                 }
             }
         }
     }
-    // warp reduction of q phi (fixed order), one partial per leaf: no block barrier, so a
-    // warp with a small leaf does not wait for its neighbours
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, d);
-    if (lane == 0 && leaf < a.nleaf) a.epart[leaf] = esum;
 }
 
-// E = 1/2 k sum of the FP32 per-leaf partials of q phi, totalled in FP64: each of the
+// E = 1/2 k sum of the per-block partials of q phi, totalled in FP64: each of the
 // kFinalBlocks blocks sums a fixed slice, and the last block to finish (atomic ticket) adds the
 // block totals in block order, so the result is deterministic.  dV/dlambda_k = k sum over the
 // site's atoms of dq phi (FP64), one thread per site.
 constexpr int kFinalBlocks = 32;
 static_assert(8 + 5 * kQdtBlocks + 4 + kFinalBlocks + 1 <= kRootDoubles, "root scratch layout");
-__global__ void __launch_bounds__(256) k_final(int nparts, const float* __restrict__ epart, double ke,
+__global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restrict__ epart, double ke,
                                                double* __restrict__ E, int K, const int* __restrict__ site_ptr,
                                                const int* __restrict__ site_atoms, const uint32_t* __restrict__ inv,
                                                const float* __restrict__ dq, const float* __restrict__ phis,
@@ -1153,7 +1172,7 @@ __global__ void __launch_bounds__(256) k_final(int nparts, const float* __restri
     const int per = (nparts + kFinalBlocks - 1) / kFinalBlocks;
     const int b0 = blockIdx.x * per, b1 = min(nparts, b0 + per);
     double s = 0.0;
-    for (int i = b0 + threadIdx.x; i < b1; i += 256) s += (double)epart[i];
+    for (int i = b0 + threadIdx.x; i < b1; i += 256) s += (double)epart[i].x + (double)epart[i].y;
     red[threadIdx.x] = s;
     __syncthreads();
     for (int d = 128; d > 0; d >>= 1) {
@@ -1212,8 +1231,9 @@ static void launch_p2m(int nleaf, float h, const Handle* hd, float* Mleaf, float
         nleaf, h, hd->start, hd->count, hd->pos, Mleaf, hd->ncp, mom);
 }
 template <int P>
-static void launch_l2p(int n, int use_far, const NearParams& a, const uint32_t* skey, float4* far, cudaStream_t st) {
-    k_l2p<P><<<(n + 127) / 128, 128, 0, st>>>(n, use_far, a, skey, far);
+static void launch_far_out(int n, int use_far, const NearParams& a, const uint32_t* skey, const float4* near,
+                           cudaStream_t st) {
+    k_far_out<P><<<(n + kOutThreads - 1) / kOutThreads, kOutThreads, 0, st>>>(n, use_far, a, skey, near);
 }
 
 #define FMM_DISPATCH_P(p, FN, ...)         \
@@ -1253,8 +1273,7 @@ int launches_per_eval(const Handle* h) {
     if (h->periodic) n += 3;       // Q/D/T partials + root + lattice
     if (d >= lmin) n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? m2l_tc_launches(h) : 1;  // M2L
     if (d >= lmin) n += d - lmin + (h->periodic ? 1 : 0);  // L2L
-    n += 1 /*p2p*/ + 1 /*final*/;
-    if (h->periodic || d >= 2) n += 1;  // l2p
+    n += 1 /*p2p*/ + 1 /*far field + outputs*/ + 1 /*final*/;
     return n;
 }
 
@@ -1283,62 +1302,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
                                                             h->sorted_key, x, g, h->qA, h->qB, h->site, h->K, lam,
                                                             h->pos, h->dq, h->inv, h->status);
     }
-    stage(h, 1, st);
-    // --- P2M ---
-    float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
-    float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
-    FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, h, Mleaf, h->periodic ? h->leafmom : nullptr, st);
-    stage(h, 2, st);
-    // --- M2M (FP32) for parent levels d-1 .. lmin: one GEMM per level,
-    //     [parents x 8 ncp] (the 8 children are contiguous) x [8 ncp x ncp] ---
-    const int lmin = h->periodic ? 1 : 2;
-    for (int l = d - 1; l >= lmin; --l) {
-        const int np = 1 << (3 * l);
-        if (h->m2m_tc.dev)
-            translate_tc(h->m2m_tc, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, np, h->M + h->lvl_off[l] * h->ncp,
-                         h->ncp, false, h->status, st, 8, h->work);  // split K by child octant
-        else
-            sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
-                  h->M + h->lvl_off[l] * h->ncp, h->ncp, false, st, 8, h->work);  // split K by child octant
-    }
-    stage(h, 3, st);
-    // --- periodic root (FP64) ---
-    if (h->periodic) {
-        const int nrowblk = (h->nc + 3) / 4;
-        const float* M1 = (d >= 1) ? h->M + h->lvl_off[1] * h->ncp : nullptr;
-        k_qdt<<<kQdtBlocks, 256, 0, st>>>(nleaf, h->box.edge / nb, 0.5 * h->box.edge, h->leafmom, h->root + h->nc + 8);
-        k_root<<<nrowblk, 128, 0, st>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, h->root);
-        k_lattice<<<(h->ncp + 3) / 4, 128, 0, st>>>(h->nc, h->ncp, h->Lam, h->root, h->L,
-                                                     2.0 * M_PI / (3.0 * h->box.edge * h->box.edge * h->box.edge),
-                                                     qdt_float(h));
-    }
-    stage(h, 4, st);
-    // --- M2L ---
-    if (d >= lmin && h->ntiles > 0) {
-        if (h->precision != FMM_FP32 && m2l_tc_supported(h)) {
-            launch_m2l_tc(h, st);
-        } else {
-            LevelOffsets lo{};
-            for (int l = 0; l <= d; ++l) lo.off[l] = h->lvl_off[l];
-            k_m2l_fp32<<<h->ntiles, h->ncp, sizeof(float) * kM2LTB * h->ncp, st>>>(
-                h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
-        }
-    }
-    stage(h, 5, st);
-    // --- L2L: levels lmin+1 .. d (periodic: 1 .. d from the lattice-filled root): one GEMM per
-    //     level, [parents x ncp] x [ncp x 8 ncp] accumulated into the contiguous children ---
-    const int lfirst = h->periodic ? 1 : lmin + 1;
-    for (int l = lfirst; l <= d; ++l) {
-        const int np = 1 << (3 * (l - 1));
-        if (h->l2l_tc.dev)
-            translate_tc(h->l2l_tc, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, np, h->L + h->lvl_off[l] * h->ncp,
-                         8 * h->ncp, true, h->status, st);
-        else
-            sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
-                  h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, st);
-    }
-    stage(h, 6, st);
-    // --- near field + L2P + outputs ---
+    // --- near field on the caller's stream, concurrent with the multipole chain ---
     NearParams a{};
     a.nleaf = nleaf;
     a.depth = d;
@@ -1351,18 +1315,81 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.start = h->start;
     a.count = h->count;
     a.pos = h->pos;
-    a.Lleaf = Lleaf;
+    a.Lleaf = h->L + h->lvl_off[d] * h->ncp;
     a.qdtf = h->periodic ? qdt_float(h) : nullptr;
     a.perm = h->perm;
     a.F = F;
     a.phi_out = phi;
     a.phis = h->phis;
     a.epart = h->epart;
-    const bool has_far = a.use_far || h->periodic;
-    if (has_far && n > 0) FMM_DISPATCH_P(h->p, launch_l2p, n, a.use_far, a, h->sorted_key, h->far, st);
-    k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, has_far ? h->far : nullptr);
+    stage(h, 1, st);
+    // fork: the chain P2M .. L2L on h->chain (highest priority), P2P here
+    cudaStream_t cs = h->chain;
+    cudaEventRecord(h->fork_ev, st);
+    cudaStreamWaitEvent(cs, h->fork_ev, 0);
+    if (h->profiling) cudaEventRecord(h->ev_p2p[0], st);
+    k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, h->near);
+    if (h->profiling) cudaEventRecord(h->ev_p2p[1], st);
+        // --- P2M ---
+    float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
+    float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
+    FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, h, Mleaf, h->periodic ? h->leafmom : nullptr, cs);
+    stage(h, 2, cs);
+    // --- M2M (FP32) for parent levels d-1 .. lmin: one GEMM per level,
+    //     [parents x 8 ncp] (the 8 children are contiguous) x [8 ncp x ncp] ---
+    const int lmin = h->periodic ? 1 : 2;
+    for (int l = d - 1; l >= lmin; --l) {
+        const int np = 1 << (3 * l);
+        if (h->m2m_tc.dev)
+            translate_tc(h->m2m_tc, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, np, h->M + h->lvl_off[l] * h->ncp,
+                         h->ncp, false, h->status, cs, 8, h->work);  // split K by child octant
+        else
+            sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
+                  h->M + h->lvl_off[l] * h->ncp, h->ncp, false, cs, 8, h->work);  // split K by child octant
+    }
+    stage(h, 3, cs);
+    // --- periodic root (FP64) ---
+    if (h->periodic) {
+        const int nrowblk = (h->nc + 3) / 4;
+        const float* M1 = (d >= 1) ? h->M + h->lvl_off[1] * h->ncp : nullptr;
+        k_qdt<<<kQdtBlocks, 256, 0, cs>>>(nleaf, h->box.edge / nb, 0.5 * h->box.edge, h->leafmom, h->root + h->nc + 8);
+        k_root<<<nrowblk, 128, 0, cs>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, h->root);
+        k_lattice<<<(h->ncp + 3) / 4, 128, 0, cs>>>(h->nc, h->ncp, h->Lam, h->root, h->L,
+                                                     2.0 * M_PI / (3.0 * h->box.edge * h->box.edge * h->box.edge),
+                                                     qdt_float(h));
+    }
+    stage(h, 4, cs);
+    // --- M2L ---
+    if (d >= lmin && h->ntiles > 0) {
+        if (h->precision != FMM_FP32 && m2l_tc_supported(h)) {
+            launch_m2l_tc(h, cs);
+        } else {
+            LevelOffsets lo{};
+            for (int l = 0; l <= d; ++l) lo.off[l] = h->lvl_off[l];
+            k_m2l_fp32<<<h->ntiles, h->ncp, sizeof(float) * kM2LTB * h->ncp, cs>>>(
+                h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
+        }
+    }
+    stage(h, 5, cs);
+    // --- L2L: levels lmin+1 .. d (periodic: 1 .. d from the lattice-filled root): one GEMM per
+    //     level, [parents x ncp] x [ncp x 8 ncp] accumulated into the contiguous children ---
+    const int lfirst = h->periodic ? 1 : lmin + 1;
+    for (int l = lfirst; l <= d; ++l) {
+        const int np = 1 << (3 * (l - 1));
+        if (h->l2l_tc.dev)
+            translate_tc(h->l2l_tc, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, np, h->L + h->lvl_off[l] * h->ncp,
+                         8 * h->ncp, true, h->status, cs);
+        else
+            sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
+                  h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, cs);
+    }
+    stage(h, 6, cs);
+    // join, then the far field and the outputs per atom
+    cudaEventRecord(h->join_ev, cs);
+    cudaStreamWaitEvent(st, h->join_ev, 0);
+    if (n > 0) FMM_DISPATCH_P(h->p, launch_far_out, n, a.use_far, a, h->sorted_key, h->near, st);
     stage(h, 7, st);
-    const int nparts = nleaf;  // one q phi partial per leaf
+    const int nparts = (n + kOutThreads - 1) / kOutThreads;  // one q phi partial per output block
     double* fin = h->root + h->nc + 8 + 5 * kQdtBlocks + 4;  // [kFinalBlocks] block totals, then the ticket
     k_final<<<kFinalBlocks, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,
                                           h->phis, dVdl, fin, reinterpret_cast<unsigned int*>(fin + kFinalBlocks));
