@@ -323,10 +323,13 @@ def run_native(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        xh = torch.from_numpy(np.ascontiguousarray(s["x"])).pin_memory()
-        Eh = torch.empty(1, dtype=torch.float64).pin_memory()
-        Fh = torch.empty(n, 3).pin_memory()
-        dVh = torch.empty(K).pin_memory()
+        # page-locked host buffers from the library's allocator (see fmm_host_alloc)
+        from paper_2410_01626_b300 import pinned_empty
+        xh = pinned_empty((n, 3))
+        xh.copy_(torch.from_numpy(np.ascontiguousarray(s["x"])))
+        Eh = pinned_empty(1, torch.float64)
+        Fh = pinned_empty((n, 3))
+        dVh = pinned_empty(max(K, 1))
         for _ in range(2):
             f.eval_host(xh, Eh, Fh, dVh)
         e_ms = []

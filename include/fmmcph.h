@@ -134,6 +134,17 @@ fmm_status fmm_eval(fmm_handle* h, const float* x, double* E, float* F, float* d
 fmm_status fmm_eval_host(fmm_handle* h, const float* x_host, double* E_host, float* F_host,
                          float* dVdlambda_host, void* stream);
 
+/* Page-locked host memory for the buffers of fmm_eval_host (not part of the
+ * method; a convenience for callers).  Copies from this memory run at full
+ * PCIe rate in both directions; on the B300 hosts measured here, page-locked
+ * memory obtained by other routes (e.g. a framework's pinned-tensor cache)
+ * fed host-to-device copies several times slower.  fmm_host_alloc writes the
+ * address to *out (NULL on failure) and returns FMM_ERR_ARG for bytes == 0 or
+ * out == NULL, FMM_ERR_OOM when the allocation fails.  Free with
+ * fmm_host_free (NULL is ignored). */
+fmm_status fmm_host_alloc(size_t bytes, void** out);
+void fmm_host_free(void* p);
+
 /* Adjoint of E(x, qA, qB, lambda) for reverse-mode differentiation.
  *   gbar:       [1] double, dL/dE (device)
  *   F, phi:     outputs of the preceding fmm_eval (input order)

@@ -7,10 +7,10 @@ behind a C ABI (``include/fmmcph.h``).  PyTorch supplies device memory and
 streams only.
 """
 from .binding import (FMM, Batch, FmmError, KE_DEFAULT, STAGES, host_operator, host_regular, lambda_step,
-                      library_path, load)
+                      library_path, load, pinned_empty)
 from .autograd import FMMEnergy, fmm_energy
 
 load()  # fail loudly at import when the native library is missing
 
 __all__ = ["FMM", "Batch", "lambda_step", "FmmError", "FMMEnergy", "fmm_energy", "KE_DEFAULT", "STAGES", "host_operator",
-           "host_regular", "library_path", "load"]
+           "host_regular", "library_path", "load", "pinned_empty"]

@@ -56,6 +56,8 @@ EXPORTS = {
     "fmm_batch_create": (I, [I, P, ctypes.POINTER(P)]),
     "fmm_batch_eval": (I, [P, P, P, P, P, P]),
     "fmm_batch_destroy": (None, [P]),
+    "fmm_host_alloc": (I, [ctypes.c_size_t, ctypes.POINTER(P)]),
+    "fmm_host_free": (None, [P]),
     "fmm_destroy": (None, [P]),
     "fmm_error_string": (ctypes.c_char_p, [I]),
     "fmm_last_error": (ctypes.c_char_p, []),
@@ -234,6 +236,23 @@ class FMM:
 
     def launches_per_eval(self):
         return int(self._lib.fmm_launches_per_eval(self._h))
+
+
+def pinned_empty(shape, dtype=torch.float32):
+    """Page-locked host tensor from the library's allocator (fmm_host_alloc), for the buffers of
+    FMM.eval_host; the memory is released (fmm_host_free) when the last tensor using it is gone."""
+    import weakref
+    import numpy as np
+    shape = tuple(int(d) for d in (shape if isinstance(shape, (tuple, list)) else (shape,)))
+    count = int(np.prod(shape)) if shape else 1
+    itemsize = torch.empty((), dtype=dtype).element_size()
+    nbytes = max(1, count * itemsize)
+    ptr = P()
+    _check(load().fmm_host_alloc(nbytes, ctypes.byref(ptr)), "fmm_host_alloc")
+    raw = (ctypes.c_uint8 * nbytes).from_address(ptr.value)
+    arr = np.frombuffer(raw, dtype=np.uint8)
+    weakref.finalize(arr, load().fmm_host_free, ptr.value)
+    return torch.from_numpy(arr)[: count * itemsize].view(dtype).view(shape)
 
 
 def host_operator(kind, p, o=(0, 0, 0)):

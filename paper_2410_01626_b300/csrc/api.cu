@@ -506,6 +506,22 @@ fmm_status fmm_eval_host(fmm_handle* H, const float* x_host, double* E_host, flo
     return cuda_ok(cudaStreamSynchronize(st));
 }
 
+fmm_status fmm_host_alloc(size_t bytes, void** out) {
+    if (!out) return FMM_ERR_ARG;
+    *out = nullptr;
+    if (bytes == 0) return FMM_ERR_ARG;
+    if (cudaHostAlloc(out, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return FMM_ERR_OOM;
+    }
+    return FMM_OK;
+}
+
+void fmm_host_free(void* p) {
+    if (p) cudaFreeHost(p);
+}
+
 fmm_status fmm_adjoint(fmm_handle* H, const double* gbar, const float* F, const float* phi, const float* dVdl,
                        float* gx, float* gqA, float* gqB, float* glam, void* stream) {
     if (!H || !gbar) return FMM_ERR_ARG;

@@ -194,6 +194,15 @@ def test_eval_host_matches_device():
     f.eval_host(xh, Eh, Fh, dVh)
     assert Eh.item() == E.item()
     assert torch.equal(Fh, F.cpu()) and torch.equal(dVh, dV.cpu())
+    # the same through buffers from the library's page-locked allocator
+    from paper_2410_01626_b300 import pinned_empty
+    xp = pinned_empty(xh.shape)
+    xp.copy_(xh)
+    Ep, Fp, dVp = pinned_empty(1, torch.float64), pinned_empty(Fh.shape), pinned_empty(dVh.shape)
+    f.eval_host(xp, Ep, Fp, dVp)
+    assert Ep.item() == E.item()
+    assert torch.equal(Fp, F.cpu()) and torch.equal(dVp, dV.cpu())
+    del xp, Ep, Fp, dVp  # released through fmm_host_free
     f.close()
 
 
