@@ -22,11 +22,25 @@ What it computes (citations are to arXiv 2410.01626):
   the site derivative that drives the lambda particle, Sec. 2.1).
 * ``binning``: the Morton-key leaf binning specification (keys, stable
   permutation, leaf ranges).
+* ``pair_potential`` / ``self_potential``: the pair potential psi(r) of the
+  energy above (1/r open; the Ewald pair potential periodic) and its
+  self-image limit psi_0 (0 open; xi / L periodic).
+* ``hamiltonian_correction``: the difference between interpolating the
+  Hamiltonian and interpolating the charges (Sec. 2.1, Eq. 1).  For atoms i, j
+  of one site k, (1 - lambda) qA_i qA_j + lambda qB_i qB_j - q_i(lambda) q_j(lambda)
+  = lambda (1 - lambda) dq_i dq_j, and pairs in different sites agree in both
+  forms, so E_H - E_q = k_e sum_k lambda_k (1 - lambda_k) [sum_{i<j in k}
+  dq_i dq_j psi(r_ij) + 1/2 sum_{i in k} dq_i^2 psi_0].  ``evaluate(...,
+  hamiltonian=True)`` adds it and its derivatives.
 
 Pins (tests/test_oracle.py): two-charge closed form, NaCl Madelung constant,
 Wigner constant of a single charge with background, alpha independence, the
 de Leeuw-Perram-Smith tinfoil/vacuum relation, finite differences in x and
-lambda, brute-force binning on tiny inputs.
+lambda, brute-force binning on tiny inputs; for the pair potential the Wigner
+constant (psi_0 L = xi), the small-r expansion 1/r + xi/L + (2 pi / 3V) r^2 and
+periodicity; for the Hamiltonian form, multilinearity in the site lambdas
+(the energy at any lambda is the multilinear interpolation of the
+charge-interpolated energies at lambda_k in {0, 1}, where the two forms agree).
 """
 from __future__ import annotations
 
@@ -70,6 +84,8 @@ def _load():
         _lib.orc_bin.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                  P, P, P, P, P]
         _lib.orc_nthreads.restype = ctypes.c_int
+        _lib.orc_ewald_pair.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, P, P]
     return _lib
 
 
@@ -142,8 +158,73 @@ def ewald(x, q, L, targets=None, tol=1e-11, alpha=None, rc=None, mmax=None):
     return phi, grad
 
 
-def evaluate(sys_, targets=None, ke=KE_DEFAULT, tol=1e-11, site_atoms=True):
-    """E, F, dV/dlambda for a synthetic system dict (keys of ``synth``).
+def _pair(r, L, periodic, self_term, tol):
+    if not periodic:
+        if self_term:
+            return 0.0, np.zeros(3)
+        r = np.asarray(r, np.float64)
+        d = float(np.sqrt(np.dot(r, r)))
+        return 1.0 / d, -r / d ** 3
+    alpha, rc, mmax = ewald_params(L, tol)
+    rr = np.ascontiguousarray(np.zeros(3) if r is None else r, np.float64)
+    psi = np.zeros(1)
+    grad = np.zeros(3)
+    _load().orc_ewald_pair(_p(rr), int(bool(self_term)), float(L), float(alpha), float(rc), int(mmax), _p(psi),
+                           _p(grad))
+    return float(psi[0]), grad
+
+
+def pair_potential(r, L=None, periodic=False, tol=1e-11):
+    """psi(r) and d psi / d r for displacement r (unit charges, k_e = 1)."""
+    return _pair(r, L, periodic, False, tol)
+
+
+def self_potential(L=None, periodic=False, tol=1e-11):
+    """psi_0 = lim_{r -> 0} (psi(r) - 1/|r|): 0 open, xi / L periodic."""
+    return _pair(None, L, periodic, True, tol)[0]
+
+
+def hamiltonian_correction(sys_, ke=KE_DEFAULT, tol=1e-11):
+    """E_H - E_q and its derivatives for a system dict: returns E (float), F [n,3]
+    (-dE/dx), dVdl [K] (dE/dlambda), phi_h [n] (dE/d dq_i = ke lambda (1 - lambda) phi_h_i)."""
+    x = np.asarray(sys_["x"], np.float32).astype(np.float64)
+    _, dq = charges(sys_["qA"], sys_["qB"], sys_["site"], sys_["lam"])
+    site = np.asarray(sys_["site"], np.int64)
+    lam = np.asarray(sys_["lam"], np.float32).astype(np.float64)
+    L, periodic = sys_["L"], bool(sys_["periodic"])
+    n, K = len(dq), len(lam)
+    F = np.zeros((n, 3))
+    phi_h = np.zeros(n)
+    dvdl = np.zeros(K)
+    E = 0.0
+    psi0 = self_potential(L, periodic, tol)
+    for k in range(K):
+        atoms = np.nonzero(site == k)[0]
+        w = lam[k] * (1.0 - lam[k])
+        e_site = 0.0
+        for a in atoms:
+            phi_h[a] += dq[a] * psi0
+            e_site += 0.5 * dq[a] ** 2 * psi0
+        for ia, a in enumerate(atoms):
+            for b in atoms[ia + 1:]:
+                r = x[a] - x[b]
+                if periodic:
+                    r = r - L * np.round(r / L)
+                psi, g = pair_potential(r, L, periodic, tol)
+                e_site += dq[a] * dq[b] * psi
+                phi_h[a] += dq[b] * psi
+                phi_h[b] += dq[a] * psi
+                F[a] -= ke * w * dq[a] * dq[b] * g
+                F[b] += ke * w * dq[a] * dq[b] * g
+        E += ke * w * e_site
+        dvdl[k] = ke * (1.0 - 2.0 * lam[k]) * e_site
+    return {"E": E, "F": F, "dVdl": dvdl, "phi_h": phi_h}
+
+
+def evaluate(sys_, targets=None, ke=KE_DEFAULT, tol=1e-11, site_atoms=True, hamiltonian=False):
+    """E, F, dV/dlambda for a synthetic system dict (keys of ``synth``); with
+    ``hamiltonian`` the Hamiltonian-interpolation form (charge-interpolation
+    energy plus ``hamiltonian_correction``).
 
     With ``targets`` given, phi/F are returned for those atoms only; E is then
     not computed (it needs every phi) and dV/dlambda is computed from the
@@ -173,6 +254,13 @@ def evaluate(sys_, targets=None, ke=KE_DEFAULT, tol=1e-11, site_atoms=True):
     sel = site[idx] >= 0
     np.add.at(dvdl, site[idx][sel], dq[idx][sel] * phi[sel])
     out["dVdl"] = ke * dvdl
+    if hamiltonian:
+        h = hamiltonian_correction(sys_, ke, tol)
+        out["F"] = out["F"] + h["F"][idx]
+        out["dVdl"] = out["dVdl"] + h["dVdl"]
+        if "E" in out:
+            out["E"] += h["E"]
+        out["phi_h"] = h["phi_h"][idx]
     return out
 
 

@@ -197,6 +197,67 @@ void orc_ewald(int n, const double* x, const double* q, double L, double alpha,
     free(Sim);
 }
 
+/* ---- Ewald pair potential (for the Hamiltonian-interpolation correction) ----
+ * psi(r): potential at displacement r of a unit charge and all its periodic
+ * images in a cube of edge L, tinfoil boundary, uniform neutralising
+ * background (the pair potential of the Ewald energy above):
+ *   psi(r) = sum_n erfc(alpha |r + nL|) / |r + nL|
+ *          + (4 pi / V) sum_{k != 0} exp(-k^2 / 4 alpha^2) / k^2 cos(k . r)
+ *          - pi / (V alpha^2).
+ * With self != 0 the result is the self-image term psi_0 = lim_{r -> 0}
+ * (psi(r) - 1/|r|): the n = 0 real-space term is replaced by its limit
+ * -2 alpha / sqrt(pi) (r is then ignored).  grad = d psi / d r (zero for
+ * self).  Images within rc, reciprocal indices |m| <= mmax. */
+void orc_ewald_pair(const double* r, int self, double L, double alpha, double rc, int mmax, double* psi,
+                    double* grad) {
+    const double V = L * L * L;
+    double d0[3] = {0.0, 0.0, 0.0};
+    if (!self)
+        for (int a = 0; a < 3; ++a) d0[a] = r[a];
+    double p = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int)ceil((-rc - d0[a]) / L) - 1;
+        hi[a] = (int)floor((rc - d0[a]) / L) + 1;
+    }
+    for (int nx = lo[0]; nx <= hi[0]; ++nx)
+        for (int ny = lo[1]; ny <= hi[1]; ++ny)
+            for (int nz = lo[2]; nz <= hi[2]; ++nz) {
+                const double dx = d0[0] + nx * L, dy = d0[1] + ny * L, dz = d0[2] + nz * L;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 > rc * rc) continue;
+                if (self && nx == 0 && ny == 0 && nz == 0) continue;
+                const double rn = sqrt(r2);
+                const double e = erfc(alpha * rn) / rn;
+                p += e;
+                const double f = (e + 2.0 * alpha / sqrt(M_PI) * exp(-alpha * alpha * r2)) / r2;
+                gx -= f * dx;
+                gy -= f * dy;
+                gz -= f * dz;
+            }
+    if (self) p -= 2.0 * alpha / sqrt(M_PI);
+    for (int mx = -mmax; mx <= mmax; ++mx)
+        for (int my = -mmax; my <= mmax; ++my)
+            for (int mz = -mmax; mz <= mmax; ++mz) {
+                const int m2 = mx * mx + my * my + mz * mz;
+                if (m2 == 0 || m2 > mmax * mmax) continue;
+                const double kx = 2.0 * M_PI / L * mx, ky = 2.0 * M_PI / L * my, kz = 2.0 * M_PI / L * mz;
+                const double k2 = kx * kx + ky * ky + kz * kz;
+                const double w = 4.0 * M_PI / V * exp(-k2 / (4.0 * alpha * alpha)) / k2;
+                const double ph = kx * d0[0] + ky * d0[1] + kz * d0[2];
+                p += w * cos(ph);
+                const double sw = -w * sin(ph);
+                gx += sw * kx;
+                gy += sw * ky;
+                gz += sw * kz;
+            }
+    p -= M_PI / (V * alpha * alpha);
+    *psi = p;
+    grad[0] = self ? 0.0 : gx;
+    grad[1] = self ? 0.0 : gy;
+    grad[2] = self ? 0.0 : gz;
+}
+
 /* ---- binning specification ----
  * Per axis: u = (double)x - origin; periodic: u -= L*floor(u/L), then u
  * outside [0, L) is folded to 0; open: u outside [0, L] flags the domain

@@ -258,3 +258,102 @@ def test_binning_open_domain_flag():
     x = np.array([[0.5, 0.5, 0.5], [1.2, 0.5, 0.5]], np.float32)
     *_, st = oracle.binning(x, (0, 0, 0), 1.0, 2, False)
     assert st == 1
+
+
+# ---------------------------------------------------------------- pair potential (Hamiltonian form)
+XI = -2.8372974794  # Wigner constant of the simple cubic lattice with background
+
+
+@pytest.mark.parametrize("L", [1.0, 2.5, 7.0])
+def test_pair_self_term_is_wigner(L):
+    assert oracle.self_potential(L, True) * L == pytest.approx(XI, abs=1e-9)
+    assert oracle.self_potential(None, False) == 0.0
+
+
+def test_pair_potential_small_r_expansion_and_periodicity():
+    """psi(r) = 1/r + xi/L + (2 pi / 3V) r^2 + O(r^4 / L^5) (degree 2 and odd harmonic
+    terms vanish by cubic symmetry), and psi is periodic."""
+    L = 2.0
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        for s in (0.02, 0.05):
+            r = s * L * d
+            psi, _ = oracle.pair_potential(r, L, True)
+            approx = 1.0 / np.linalg.norm(r) + XI / L + 2 * np.pi / (3 * L ** 3) * np.dot(r, r)
+            assert abs(psi - approx) < 40.0 * s ** 4 / L
+        r = rng.uniform(-0.5, 0.5, 3) * L
+        for shift in (np.array([L, 0, 0]), np.array([0, -L, L])):
+            assert oracle.pair_potential(r + shift, L, True)[0] == pytest.approx(oracle.pair_potential(r, L, True)[0],
+                                                                                 abs=1e-9)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_pair_potential_gradient_by_finite_differences(periodic):
+    L = 3.0
+    r = np.array([0.41, -0.27, 0.33])
+    _, g = oracle.pair_potential(r, L, periodic)
+    h = 1e-5
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        fd = (oracle.pair_potential(r + e, L, periodic)[0] - oracle.pair_potential(r - e, L, periodic)[0]) / (2 * h)
+        assert fd == pytest.approx(g[a], rel=1e-6, abs=1e-9)
+
+
+def _two_site_system(periodic):
+    if periodic:
+        s = synth.periodic_uniform(seed=14, n=80, L=2.2, n_sites=2, site_size=4, neutral=False, p=6, depth=1)
+    else:
+        s = synth.open_uniform(seed=14, n=80, L=2.2, n_sites=2, site_size=4, p=6, depth=1)
+    return s
+
+
+def _energy(s, lam, hamiltonian):
+    t = dict(s)
+    t["lam"] = np.asarray(lam, np.float32)
+    return oracle.evaluate(t, tol=1e-12, hamiltonian=hamiltonian)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_hamiltonian_form_is_multilinear_in_lambda(periodic):
+    """Interpolating the Hamiltonian makes E linear in each site lambda; at lambda_k in
+    {0, 1} it equals the charge-interpolated energy.  So E_H(l1, l2) is the bilinear
+    interpolation of the four corner energies of the (pinned) charge form, and
+    dE_H/dl_k is the corner difference."""
+    s = _two_site_system(periodic)
+    corner = {(a, b): _energy(s, [a, b], False)["E"] for a in (0.0, 1.0) for b in (0.0, 1.0)}
+    l1, l2 = 0.375, 0.8125  # exact in FP32, the precision of the lambda inputs
+    out = _energy(s, [l1, l2], True)
+    bil = ((1 - l1) * (1 - l2) * corner[0, 0] + l1 * (1 - l2) * corner[1, 0] + (1 - l1) * l2 * corner[0, 1]
+           + l1 * l2 * corner[1, 1])
+    scale = max(abs(v) for v in corner.values())
+    assert out["E"] == pytest.approx(bil, abs=1e-9 * scale)
+    d1 = (1 - l2) * (corner[1, 0] - corner[0, 0]) + l2 * (corner[1, 1] - corner[0, 1])
+    d2 = (1 - l1) * (corner[0, 1] - corner[0, 0]) + l1 * (corner[1, 1] - corner[1, 0])
+    assert out["dVdl"][0] == pytest.approx(d1, abs=1e-9 * scale)
+    assert out["dVdl"][1] == pytest.approx(d2, abs=1e-9 * scale)
+    # and it differs from the charge form away from the corners
+    assert abs(out["E"] - _energy(s, [l1, l2], False)["E"]) > 1e-6 * scale
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_hamiltonian_forces_by_finite_differences(periodic):
+    s = _two_site_system(periodic)
+    lam = [0.375, 0.625]
+    out = _energy(s, lam, True)
+    site_atoms = np.nonzero(s["site"] >= 0)[0][:3]
+    h = 1e-4
+    for i in site_atoms:
+        for a in range(3):
+            xp = s["x"].astype(np.float64).copy()
+            xm = xp.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            sp, sm = dict(s), dict(s)
+            sp["x"], sm["x"] = xp, xm
+            # positions are FP32 inputs: difference over the step the rounded coordinates take
+            h_eff = (float(np.float32(xp[i, a])) - float(np.float32(xm[i, a]))) / 2
+            fd = -(_energy(sp, lam, True)["E"] - _energy(sm, lam, True)["E"]) / (2 * h_eff)
+            assert fd == pytest.approx(out["F"][i, a], rel=1e-5, abs=1e-6 * np.abs(out["F"]).max())
