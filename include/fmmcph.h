@@ -73,10 +73,23 @@ typedef struct {
     double edge;      /* cube edge length L, nm > 0 */
 } fmm_box;
 
+/* How the energy depends on lambda within a site (Sec. 2.1, Eq. 1).
+ * CHARGE: the charges are interpolated, q_i = qA_i + lambda (qB_i - qA_i),
+ *   and E is the Coulomb energy of q(lambda).
+ * HAMILTONIAN: the Hamiltonian is interpolated; pairs in different sites (and
+ *   all pairs with other atoms) are the same as above, pairs i, j within one
+ *   site k differ by lambda_k (1 - lambda_k) dq_i dq_j psi(r_ij), where psi is
+ *   the pair potential of the box (1/r open; the periodic pair potential with
+ *   its self-image term for i = j).  E is then linear in every lambda_k, and
+ *   F and dV/dlambda include the correction.  phi (fmm_eval) stays the
+ *   potential of q(lambda). */
+typedef enum { FMM_INTERP_CHARGE = 0, FMM_INTERP_HAMILTONIAN = 1 } fmm_interpolation;
+
 typedef struct {
-    int precision;     /* fmm_precision                           */
-    double coulomb_k;  /* k_e; <= 0 selects 138.935458             */
-    int reserved[8];   /* must be zero                             */
+    int precision;      /* fmm_precision                           */
+    double coulomb_k;   /* k_e; <= 0 selects 138.935458             */
+    int interpolation;  /* fmm_interpolation                       */
+    int reserved[7];    /* must be zero                             */
 } fmm_options;
 
 typedef struct fmm_handle fmm_handle;

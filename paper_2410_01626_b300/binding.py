@@ -20,6 +20,8 @@ I = ctypes.c_int
 
 FMM_FP32, FMM_MIXED_TF32, FMM_MIXED_3XTF32, FMM_MIXED_3XBF16 = 0, 1, 2, 3
 PRECISIONS = {"fp32": FMM_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF32, "3xbf16": FMM_MIXED_3XBF16}
+# lambda dependence within a site (Sec. 2.1, Eq. 1): interpolated charges, or interpolated Hamiltonian
+INTERPOLATIONS = {"charge": 0, "hamiltonian": 1}
 DEV_DOMAIN, DEV_SITE, DEV_TIMEOUT = 1, 2, 4
 KE_DEFAULT = 138.935458
 # consecutive stages of one evaluation, then the near field, which runs on the caller's stream
@@ -32,7 +34,8 @@ class FmmBox(ctypes.Structure):
 
 
 class FmmOptions(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("coulomb_k", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+    _fields_ = [("precision", ctypes.c_int), ("coulomb_k", ctypes.c_double), ("interpolation", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 EXPORTS = {
@@ -123,11 +126,12 @@ def _dev(t, dtype, name):
 class FMM:
     """One solver handle: a cubic box, boundary, multipole order p and tree depth."""
 
-    def __init__(self, edge, periodic, p, depth, origin=(0.0, 0.0, 0.0), precision="fp32", ke=None):
+    def __init__(self, edge, periodic, p, depth, origin=(0.0, 0.0, 0.0), precision="fp32", ke=None,
+                 interpolation="charge"):
         lib = load()
         box = FmmBox((ctypes.c_double * 3)(*[float(o) for o in origin]), float(edge))
         opt = FmmOptions(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                         float(ke) if ke else 0.0, (ctypes.c_int * 8)())
+                         float(ke) if ke else 0.0, INTERPOLATIONS[interpolation], (ctypes.c_int * 7)())
         h = ctypes.c_void_p()
         _check(lib.fmm_create(ctypes.byref(box), int(bool(periodic)), int(p), int(depth), ctypes.byref(opt),
                               ctypes.byref(h)), "fmm_create")
@@ -136,6 +140,7 @@ class FMM:
         self.edge, self.periodic, self.p, self.depth = float(edge), bool(periodic), int(p), int(depth)
         self.origin = tuple(float(o) for o in origin)
         self.precision = precision
+        self.interpolation = interpolation
         self.ke = float(ke) if ke else KE_DEFAULT
         self.n = 0
         self.K = 0

@@ -90,6 +90,9 @@ void free_all(Handle& h) {
     dfree(h.leafcnt);
     dfree(h.epart);
     dfree(h.leafmom);
+    dfree(h.hi_coef);
+    dfree(h.hi_site);
+    dfree(h.hi_phi);
     dfree(h.root);
     dfree(h.status);
     dfree(h.work);
@@ -227,13 +230,16 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         if (!std::isfinite(box->origin[a])) return FMM_ERR_ARG;
     if (periodic != 0 && periodic != 1) return FMM_ERR_ARG;
     if (p < 1 || p > FMM_MAX_P || depth < 0 || depth > kMaxDepth) return FMM_ERR_ARG;
-    int precision = FMM_FP32;
+    int precision = FMM_FP32, interpolation = FMM_INTERP_CHARGE;
     double ke = 138.935458;
     if (opt) {
         for (int r : opt->reserved)
             if (r != 0) return FMM_ERR_ARG;
         if (opt->precision < FMM_FP32 || opt->precision > FMM_MIXED_3XBF16) return FMM_ERR_ARG;
+        if (opt->interpolation != FMM_INTERP_CHARGE && opt->interpolation != FMM_INTERP_HAMILTONIAN)
+            return FMM_ERR_ARG;
         precision = opt->precision;
+        interpolation = opt->interpolation;
         if (opt->coulomb_k > 0.0) ke = opt->coulomb_k;
     }
     fmm_handle* H = new (std::nothrow) fmm_handle();
@@ -247,6 +253,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     h.nc = ncoef(p);
     h.ncp = ncoef_padded(p);
     h.precision = precision;
+    h.hamiltonian = interpolation == FMM_INTERP_HAMILTONIAN;
     h.ke = ke;
     h.s_bin = std::ldexp(1.0, depth) / box->edge;
     h.lmin = periodic ? 1 : 2;
@@ -275,6 +282,18 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         cudaMemcpy(h.B2, ops->B2.data(), sizeof(float) * ops->B2.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(h.Ad, ops->Ad.data(), sizeof(double) * ops->Ad.size(), cudaMemcpyHostToDevice);
         if (periodic) cudaMemcpy(h.Lam, ops->Lam.data(), sizeof(double) * ops->Lam.size(), cudaMemcpyHostToDevice);
+        if (h.hamiltonian && periodic) {
+            // the harmonic remainder h of the periodic pair potential: the lattice operator's
+            // response to a unit charge at the root centre, i.e. its first column
+            std::vector<float> hc(ncp, 0.f);
+            for (int j = 0; j < nc; ++j) hc[j] = (float)ops->Lam[(size_t)j * nc];
+            if ((st = dalloc(&h.hi_coef, ncp))) {
+                free_all(h);
+                delete H;
+                return st;
+            }
+            cudaMemcpy(h.hi_coef, hc.data(), sizeof(float) * ncp, cudaMemcpyHostToDevice);
+        }
         if (precision != FMM_FP32) {
             h.lvl_off.assign(depth + 2, 0);
             long a2 = 0;
@@ -396,6 +415,17 @@ fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const f
             }
             h.epart_cap = nparts;
         }
+    }
+    if (h.hamiltonian && (n > h.hi_cap || K > h.hi_kcap)) {
+        dfree(h.hi_phi);
+        dfree(h.hi_site);
+        h.hi_cap = h.hi_kcap = 0;
+        if (dalloc(&h.hi_phi, n > 0 ? n : 1) || dalloc(&h.hi_site, 2L * (K > 0 ? K : 1))) {
+            h.charges_set = false;
+            return FMM_ERR_OOM;
+        }
+        h.hi_cap = n;
+        h.hi_kcap = K;
     }
     if (K > h.lam_cap) {
         dfree(h.lam);

@@ -39,6 +39,7 @@ struct Handle {
     int periodic = 0, p = 0, depth = 0;
     int nc = 0, ncp = 0;
     int precision = FMM_FP32;
+    bool hamiltonian = false;  // Hamiltonian interpolation within sites (intra-site correction)
     double ke = 138.935458;
     double s_bin = 0.0;  // 2^depth / L
     int lmin = 2;        // first level with M2L
@@ -77,6 +78,13 @@ struct Handle {
     int epart_cap = 0;
     float* leafmom = nullptr;   // [nleaf][kLeafMomStride] periodic: leaf moments for the Q, D, T sums
     double* root = nullptr;     // [nc] FP64 root multipole, then [5] Q D T at root+nc
+    // Hamiltonian interpolation: h of the periodic pair potential (normalised root local
+    // expansion, [ncp]), per-site energy and dV/dlambda corrections ([K][2]), and per-atom
+    // phi_h = sum_{j in site, j != i} dq_j psi_ij + dq_i psi_0 (input order) for the adjoint
+    float* hi_coef = nullptr;
+    double* hi_site = nullptr;
+    float* hi_phi = nullptr;
+    int hi_cap = 0, hi_kcap = 0;
     int* status = nullptr;
     float* work = nullptr;  // split-K partial products (8 x the largest M2M output level)
     bool charges_set = false;

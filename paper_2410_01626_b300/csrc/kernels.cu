@@ -880,6 +880,128 @@ __global__ void __launch_bounds__(kOutThreads) k_far_out(int n, int use_far, Nea
     if (threadIdx.x == 0) a.epart[blockIdx.x] = red[0];
 }
 
+// ---- Hamiltonian interpolation: the intra-site correction ----
+// For atoms i, j of one site k, interpolating the Hamiltonian instead of the charges changes
+// the pair term by lambda_k (1 - lambda_k) dq_i dq_j psi(r_ij) (Sec. 2.1, Eq. 1), including
+// i = j with the self-image term psi_0.  psi is the pair potential the FMM sums: 1/r open;
+// periodic, psi(r) = 1/|r| + sum over the 26 neighbouring images 1/|r - nL| + c2 |r|^2 + h(r),
+// with c2 = 2 pi / 3V and h the lattice remainder, evaluated as the root local expansion of a
+// unit charge at the root centre (the lattice operator's first column) at u = r / L.
+struct HiParams {
+    int K, periodic;
+    float L, ke, c2;
+    const float* coef;  // h, normalised root local expansion (periodic)
+    const int* site_ptr;
+    const int* site_atoms;
+    const uint32_t* inv;
+    const float4* pos;
+    const float* dq;
+    const float* lam;
+    float* F;           // input order, corrected in place (may be null)
+    double* site_out;   // [K][2]: energy and dV/dlambda corrections
+    float* phi_h;       // input order: sum_{j != i} dq_j psi_ij + dq_i psi_0
+};
+
+// psi(r) - [self ? 1/|r| : 0] and its gradient in r; r = 0 with self gives psi_0
+template <int P>
+__device__ void hi_pair(const HiParams& p, float rx, float ry, float rz, bool self, float& psi, float& gx,
+                        float& gy, float& gz) {
+    psi = gx = gy = gz = 0.f;
+    if (!self) {
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        const float ri = 1.0f / sqrtf(r2);
+        const float ri3 = ri * ri * ri;
+        psi = ri;
+        gx = -rx * ri3;
+        gy = -ry * ri3;
+        gz = -rz * ri3;
+    }
+    if (!p.periodic) return;
+    const float L = p.L;
+    for (int n = 0; n < 27; ++n) {
+        if (n == 13) continue;
+        const float dx = rx - (float)(n / 9 - 1) * L, dy = ry - (float)((n / 3) % 3 - 1) * L,
+                    dz = rz - (float)(n % 3 - 1) * L;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float ri = 1.0f / sqrtf(r2);
+        const float ri3 = ri * ri * ri;
+        psi += ri;
+        gx -= dx * ri3;
+        gy -= dy * ri3;
+        gz -= dz * ri3;
+    }
+    psi += p.c2 * (rx * rx + ry * ry + rz * rz);
+    gx += 2.f * p.c2 * rx;
+    gy += 2.f * p.c2 * ry;
+    gz += 2.f * p.c2 * rz;
+    const float iL = 1.0f / L;
+    float hp, hx, hy, hz;
+    l2p_eval<P>(p.coef, rx * iL, ry * iL, rz * iL, hp, hx, hy, hz);
+    psi += hp * iL;
+    gx += hx * iL * iL;
+    gy += hy * iL * iL;
+    gz += hz * iL * iL;
+}
+
+// one warp per site, one lane per site atom: each lane sums over the other atoms of its site
+// (every pair is evaluated from both sides, so no atomics and a fixed order)
+template <int P>
+__global__ void __launch_bounds__(128) k_hi(HiParams p) {
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (k >= p.K) return;
+    const int a0 = p.site_ptr[k], na = p.site_ptr[k + 1] - a0;
+    const float lam = p.lam[k];
+    const float w = lam * (1.f - lam);
+    float psi0, t0, t1, t2;
+    hi_pair<P>(p, 0.f, 0.f, 0.f, true, psi0, t0, t1, t2);
+    double e = 0.0;
+    for (int a = lane; a < na; a += 32) {
+        const int ia = p.site_atoms[a0 + a];
+        const uint32_t sa = p.inv[ia];
+        const float4 pa = p.pos[sa];
+        const float da = p.dq[sa];
+        float ph = da * psi0, gx = 0.f, gy = 0.f, gz = 0.f;
+        for (int b = 0; b < na; ++b) {
+            if (b == a) continue;
+            const uint32_t sb = p.inv[p.site_atoms[a0 + b]];
+            const float4 pb = p.pos[sb];
+            const float db = p.dq[sb];
+            float rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+            if (p.periodic) {  // minimum image: the truncated h is most accurate for small |r|
+                rx -= p.L * rintf(rx / p.L);
+                ry -= p.L * rintf(ry / p.L);
+                rz -= p.L * rintf(rz / p.L);
+            }
+            float psi, hx, hy, hz;
+            hi_pair<P>(p, rx, ry, rz, false, psi, hx, hy, hz);
+            ph += db * psi;
+            gx += db * hx;
+            gy += db * hy;
+            gz += db * hz;
+        }
+        if (p.F) {
+            const float c = p.ke * w * da;
+            p.F[3L * ia] -= c * gx;
+            p.F[3L * ia + 1] -= c * gy;
+            p.F[3L * ia + 2] -= c * gz;
+        }
+        p.phi_h[ia] = ph;
+        e += 0.5 * (double)da * (double)ph;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
+    if (lane == 0) {
+        p.site_out[2 * k] = (double)p.ke * (double)w * e;
+        p.site_out[2 * k + 1] = (double)p.ke * (1.0 - 2.0 * (double)lam) * e;
+    }
+}
+
+template <int P>
+static void launch_hi(const HiParams& hp, cudaStream_t st) {
+    k_hi<P><<<(hp.K + 3) / 4, 128, 0, st>>>(hp);
+}
+
 // ---- packed two-wide FP32 arithmetic (f32x2) ----
 __device__ __forceinline__ unsigned long long f2pack(float a, float b) {
     unsigned long long r;
@@ -1166,7 +1288,7 @@ __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restr
                                                const int* __restrict__ site_atoms, const uint32_t* __restrict__ inv,
                                                const float* __restrict__ dq, const float* __restrict__ phis,
                                                float* __restrict__ dVdl, double* __restrict__ blocksum,
-                                               unsigned int* __restrict__ ticket) {
+                                               unsigned int* __restrict__ ticket, const double* __restrict__ hi_site) {
     __shared__ double red[256];
     __shared__ bool last;
     const int per = (nparts + kFinalBlocks - 1) / kFinalBlocks;
@@ -1189,7 +1311,10 @@ __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restr
         __threadfence();
         double t = 0.0;
         for (int b = 0; b < kFinalBlocks; ++b) t += ((volatile double*)blocksum)[b];
-        if (E) E[0] = 0.5 * ke * t;
+        double hsum = 0.0;  // Hamiltonian interpolation: per-site corrections, in site order
+        if (hi_site)
+            for (int k = 0; k < K; ++k) hsum += hi_site[2 * k];
+        if (E) E[0] = 0.5 * ke * t + hsum;
         *ticket = 0u;  // ready for the next call
     }
     if (dVdl)
@@ -1199,7 +1324,7 @@ __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restr
                 const uint32_t si = inv[site_atoms[a]];
                 v += (double)dq[si] * (double)phis[si];
             }
-            dVdl[k] = (float)(ke * v);
+            dVdl[k] = (float)(ke * v + (hi_site ? hi_site[2 * k + 1] : 0.0));
         }
 }
 
@@ -1207,7 +1332,7 @@ __global__ void k_adjoint(int n, int K, const double* __restrict__ gbar, const f
                           const float* __restrict__ phi, const float* __restrict__ dVdl,
                           const int32_t* __restrict__ site, const float* __restrict__ lam,
                           float* __restrict__ gx, float* __restrict__ gqA, float* __restrict__ gqB,
-                          float* __restrict__ glam) {
+                          float* __restrict__ glam, float ke, const float* __restrict__ phi_h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float g = (float)gbar[0];
     if (i < K && glam) glam[i] = dVdl[i] * g;
@@ -1219,8 +1344,10 @@ __global__ void k_adjoint(int n, int K, const double* __restrict__ gbar, const f
     }
     const int s = site[i];
     const float l = (s >= 0 && s < K) ? lam[s] : 0.f;
-    if (gqA) gqA[i] = phi[i] * (1.f - l) * g;
-    if (gqB) gqB[i] = phi[i] * l * g;
+    // Hamiltonian interpolation adds dE/d dq_i = ke lambda (1 - lambda) phi_h_i (dq = qB - qA)
+    const float hterm = (phi_h && s >= 0 && s < K) ? ke * l * (1.f - l) * phi_h[i] : 0.f;
+    if (gqA) gqA[i] = (phi[i] * (1.f - l) - hterm) * g;
+    if (gqB) gqB[i] = (phi[i] * l + hterm) * g;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1274,6 +1401,7 @@ int launches_per_eval(const Handle* h) {
     if (d >= lmin) n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? m2l_tc_launches(h) : 1;  // M2L
     if (d >= lmin) n += d - lmin + (h->periodic ? 1 : 0);  // L2L
     n += 1 /*p2p*/ + 1 /*far field + outputs*/ + 1 /*final*/;
+    if (h->hamiltonian && h->K > 0) n += 1;  // intra-site correction
     return n;
 }
 
@@ -1388,11 +1516,32 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     cudaEventRecord(h->join_ev, cs);
     cudaStreamWaitEvent(st, h->join_ev, 0);
     if (n > 0) FMM_DISPATCH_P(h->p, launch_far_out, n, a.use_far, a, h->sorted_key, h->near, st);
+    const bool hi = h->hamiltonian && h->K > 0;
+    if (hi) {
+        HiParams hp{};
+        hp.K = h->K;
+        hp.periodic = h->periodic;
+        hp.L = (float)h->box.edge;
+        hp.ke = (float)h->ke;
+        hp.c2 = (float)(2.0 * M_PI / (3.0 * h->box.edge * h->box.edge * h->box.edge));
+        hp.coef = h->hi_coef;
+        hp.site_ptr = h->site_ptr;
+        hp.site_atoms = h->site_atoms;
+        hp.inv = h->inv;
+        hp.pos = h->pos;
+        hp.dq = h->dq;
+        hp.lam = lam;
+        hp.F = F;
+        hp.site_out = h->hi_site;
+        hp.phi_h = h->hi_phi;
+        FMM_DISPATCH_P(h->p, launch_hi, hp, st);
+    }
     stage(h, 7, st);
     const int nparts = (n + kOutThreads - 1) / kOutThreads;  // one q phi partial per output block
     double* fin = h->root + h->nc + 8 + 5 * kQdtBlocks + 4;  // [kFinalBlocks] block totals, then the ticket
     k_final<<<kFinalBlocks, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,
-                                          h->phis, dVdl, fin, reinterpret_cast<unsigned int*>(fin + kFinalBlocks));
+                                          h->phis, dVdl, fin, reinterpret_cast<unsigned int*>(fin + kFinalBlocks),
+                                          hi ? h->hi_site : nullptr);
     stage(h, 8, st);
     return 0;
 }
@@ -1482,7 +1631,8 @@ void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* 
     const int m = h->n > h->K ? h->n : h->K;
     if (m == 0) return;
     const float* lam = h->lam_bound ? h->lam_bound : h->lam;
-    k_adjoint<<<(m + 255) / 256, 256, 0, st>>>(h->n, h->K, gbar, F, phi, dVdl, h->site, lam, gx, gqA, gqB, glam);
+    k_adjoint<<<(m + 255) / 256, 256, 0, st>>>(h->n, h->K, gbar, F, phi, dVdl, h->site, lam, gx, gqA, gqB, glam,
+                                               (float)h->ke, h->hamiltonian ? h->hi_phi : nullptr);
 }
 
 }  // namespace fmmcph

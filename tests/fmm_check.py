@@ -23,16 +23,16 @@ def to_dev(s, dev="cuda"):
     }
 
 
-def make_solver(s, p=None, depth=None, precision="fp32"):
+def make_solver(s, p=None, depth=None, precision="fp32", interpolation="charge"):
     f = FMM(s["L"], s["periodic"], s["p"] if p is None else p, s["depth"] if depth is None else depth,
-            origin=s["origin"], precision=precision)
+            origin=s["origin"], precision=precision, interpolation=interpolation)
     d = to_dev(s)
     f.set_charges(d["qA"], d["qB"], d["site"], d["lam"])
     return f, d
 
 
-def run_gpu(s, p=None, depth=None, precision="fp32"):
-    f, d = make_solver(s, p, depth, precision)
+def run_gpu(s, p=None, depth=None, precision="fp32", interpolation="charge"):
+    f, d = make_solver(s, p, depth, precision, interpolation)
     E, F, dV, phi = f.eval(d["x"], phi=True)
     torch.cuda.synchronize()
     st = f.status_word()
@@ -65,9 +65,9 @@ def system_digest(s):
     return h.hexdigest()
 
 
-def oracle_ref(s, targets=None, tol=1e-11):
+def oracle_ref(s, targets=None, tol=1e-11, hamiltonian=False):
     t = None if targets is None else hashlib.sha1(np.asarray(targets, np.int64).tobytes()).hexdigest()
-    k = (system_digest(s), t, tol)
+    k = (system_digest(s), t, tol, hamiltonian)
     if k not in _cache:
-        _cache[k] = oracle.evaluate(s, targets=targets, tol=tol)
+        _cache[k] = oracle.evaluate(s, targets=targets, tol=tol, hamiltonian=hamiltonian)
     return _cache[k]
