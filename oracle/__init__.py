@@ -22,6 +22,9 @@ What it computes (citations are to arXiv 2410.01626):
   the site derivative that drives the lambda particle, Sec. 2.1).
 * ``binning``: the Morton-key leaf binning specification (keys, stable
   permutation, leaf ranges).
+* ``charges4`` / four-form systems (``forms`` = 4): sites with two lambda
+  coordinates over four charge forms (Sec. 2.1, Eq. 2), dV/dlambda per site
+  and coordinate; ``hamiltonian_correction4`` the Hamiltonian form of them.
 * ``pair_potential`` / ``self_potential``: the pair potential psi(r) of the
   energy above (1/r open; the Ewald pair potential periodic) and its
   self-image limit psi_0 (0 open; xi / L periodic).
@@ -108,6 +111,25 @@ def charges(qA, qB, site, lam):
     dq = np.empty(n)
     _load().orc_charges(n, _p(qA), _p(qB), _p(site), len(lam), _p(lam), _p(q), _p(dq))
     return q, dq
+
+
+def charges4(qA, qB, qC, qD, site, lam2):
+    """Sites with two lambda coordinates (Sec. 2.1, Eq. 2): with lp, lt of the atom's site,
+    q_i = (1 - lp)[(1 - lt) qA_i + lt qB_i] + lp[(1 - lt) qC_i + lt qD_i] (FP64 from FP32
+    inputs), and the derivatives dq/dlp, dq/dlt.  lam2 = [2K]: (lp, lt) per site.  Atoms
+    outside every site keep qA."""
+    a, b, c, d = (np.asarray(v, np.float32).astype(np.float64) for v in (qA, qB, qC, qD))
+    site = np.asarray(site, np.int64)
+    l2 = np.asarray(lam2, np.float32).astype(np.float64).reshape(-1, 2)
+    K = len(l2)
+    ins = (site >= 0) & (site < K)
+    k = np.where(ins, site, 0)
+    p = np.where(ins, l2[k, 0] if K else 0.0, 0.0)
+    t = np.where(ins, l2[k, 1] if K else 0.0, 0.0)
+    q = np.where(ins, (1 - p) * ((1 - t) * a + t * b) + p * ((1 - t) * c + t * d), a)
+    dqp = np.where(ins, ((1 - t) * c + t * d) - ((1 - t) * a + t * b), 0.0)
+    dqt = np.where(ins, (1 - p) * (b - a) + p * (d - c), 0.0)
+    return q, dqp, dqt
 
 
 def _targets(targets, n):
@@ -221,6 +243,56 @@ def hamiltonian_correction(sys_, ke=KE_DEFAULT, tol=1e-11):
     return {"E": E, "F": F, "dVdl": dvdl, "phi_h": phi_h}
 
 
+def hamiltonian_correction4(sys_, ke=KE_DEFAULT, tol=1e-11):
+    """The Hamiltonian-interpolation correction for sites with four forms (Eq. 2).  With
+    weights w_X(lp, lt) of the forms X in {A, B, C, D} and q_i = sum_X w_X q^X_i, the pair
+    term of atoms i, j of one site changes by C_ij = sum_X w_X q^X_i q^X_j - q_i q_j
+    = sum_X w_X (q^X_i - q_i)(q^X_j - q_j) (i = j with psi_0), and
+    dC_ij/dl = sum_X (dw_X/dl)(q^X_i - q_i)(q^X_j - q_j).  Returns E, F [n,3],
+    dVdl [2K] (lp, lt per site) and g_h [n,4]: dE/dq^X_i = ke w_X g_h[i, X]."""
+    x = np.asarray(sys_["x"], np.float32).astype(np.float64)
+    Q = np.stack([np.asarray(sys_[k], np.float32).astype(np.float64) for k in ("qA", "qB", "qC", "qD")], 1)
+    q, _, _ = charges4(sys_["qA"], sys_["qB"], sys_["qC"], sys_["qD"], sys_["site"], sys_["lam"])
+    site = np.asarray(sys_["site"], np.int64)
+    l2 = np.asarray(sys_["lam"], np.float32).astype(np.float64).reshape(-1, 2)
+    L, periodic = sys_["L"], bool(sys_["periodic"])
+    n, K = len(q), len(l2)
+    F = np.zeros((n, 3))
+    g_h = np.zeros((n, 4))
+    dvdl = np.zeros((K, 2))
+    E = 0.0
+    psi0 = self_potential(L, periodic, tol)
+    for k in range(K):
+        p, t = l2[k]
+        w = np.array([(1 - p) * (1 - t), (1 - p) * t, p * (1 - t), p * t])
+        wp = np.array([-(1 - t), -t, 1 - t, t])
+        wt = np.array([-(1 - p), 1 - p, -p, p])
+        atoms = np.nonzero(site == k)[0]
+        dev = Q[atoms] - q[atoms, None]  # q^X_i - q_i
+        for ia, a in enumerate(atoms):
+            c = np.dot(w, dev[ia] ** 2)
+            E += ke * 0.5 * c * psi0
+            dvdl[k, 0] += ke * 0.5 * np.dot(wp, dev[ia] ** 2) * psi0
+            dvdl[k, 1] += ke * 0.5 * np.dot(wt, dev[ia] ** 2) * psi0
+            g_h[a] += dev[ia] * psi0
+            for ib in range(ia + 1, len(atoms)):
+                b = atoms[ib]
+                r = x[a] - x[b]
+                if periodic:
+                    r = r - L * np.round(r / L)
+                psi, g = pair_potential(r, L, periodic, tol)
+                prod = dev[ia] * dev[ib]
+                cab = np.dot(w, prod)
+                E += ke * cab * psi
+                dvdl[k, 0] += ke * np.dot(wp, prod) * psi
+                dvdl[k, 1] += ke * np.dot(wt, prod) * psi
+                F[a] -= ke * cab * g
+                F[b] += ke * cab * g
+                g_h[a] += dev[ib] * psi
+                g_h[b] += dev[ia] * psi
+    return {"E": E, "F": F, "dVdl": dvdl.reshape(-1), "g_h": g_h}
+
+
 def evaluate(sys_, targets=None, ke=KE_DEFAULT, tol=1e-11, site_atoms=True, hamiltonian=False):
     """E, F, dV/dlambda for a synthetic system dict (keys of ``synth``); with
     ``hamiltonian`` the Hamiltonian-interpolation form (charge-interpolation
@@ -231,9 +303,14 @@ def evaluate(sys_, targets=None, ke=KE_DEFAULT, tol=1e-11, site_atoms=True, hami
     site atoms, which are added to the evaluated set when ``site_atoms``.
     """
     x = np.asarray(sys_["x"], np.float32).astype(np.float64)
-    q, dq = charges(sys_["qA"], sys_["qB"], sys_["site"], sys_["lam"])
+    four = sys_.get("forms", 2) == 4
+    if four:
+        q, dq, dqt = charges4(sys_["qA"], sys_["qB"], sys_["qC"], sys_["qD"], sys_["site"], sys_["lam"])
+        K = len(sys_["lam"]) // 2
+    else:
+        q, dq = charges(sys_["qA"], sys_["qB"], sys_["site"], sys_["lam"])
+        K = len(sys_["lam"])
     n = len(q)
-    K = len(sys_["lam"])
     site = np.asarray(sys_["site"], np.int64)
     if targets is None:
         idx = np.arange(n)
@@ -254,13 +331,20 @@ def evaluate(sys_, targets=None, ke=KE_DEFAULT, tol=1e-11, site_atoms=True, hami
     sel = site[idx] >= 0
     np.add.at(dvdl, site[idx][sel], dq[idx][sel] * phi[sel])
     out["dVdl"] = ke * dvdl
+    if four:  # (dE/dlp, dE/dlt) per site, interleaved
+        dvt = np.zeros(K)
+        np.add.at(dvt, site[idx][sel], dqt[idx][sel] * phi[sel])
+        out["dVdl"] = ke * np.stack([dvdl, dvt], 1).reshape(-1)
     if hamiltonian:
-        h = hamiltonian_correction(sys_, ke, tol)
+        h = hamiltonian_correction4(sys_, ke, tol) if four else hamiltonian_correction(sys_, ke, tol)
         out["F"] = out["F"] + h["F"][idx]
         out["dVdl"] = out["dVdl"] + h["dVdl"]
         if "E" in out:
             out["E"] += h["E"]
-        out["phi_h"] = h["phi_h"][idx]
+        if "phi_h" in h:
+            out["phi_h"] = h["phi_h"][idx]
+        if "g_h" in h:
+            out["g_h"] = h["g_h"][idx]
     return out
 
 

@@ -251,3 +251,31 @@ def replica(seed, p=8):
 
 def replicas(n=64, first_seed=100, p=8):
     return [replica(first_seed + i, p=p) for i in range(n)]
+
+
+def tautomer_sites(s, seed=0, tautomer_fraction=0.5):
+    """Four charge forms per site (Sec. 2.1, Eq. 2): A and B are the two protonated
+    tautomers, C = D the deprotonated form.  B redistributes A's charges within the site
+    (shift U(-0.3, 0.3), mean removed per site, so A and B carry the same net charge);
+    sites without a tautomer have B = A.  lam becomes [2K] = (lambda_p, lambda_t) per site,
+    both U(0, 1).  Returns a new system dict with keys qA, qB, qC, qD and forms = 4."""
+    rng = np.random.default_rng(seed)
+    t = dict(s)
+    site = s["site"]
+    K = len(s["lam"])
+    qA = s["qA"].astype(np.float64)
+    qB = qA.copy()
+    has_t = rng.uniform(size=K) < tautomer_fraction
+    for k in range(K):
+        g = np.nonzero(site == k)[0]
+        if has_t[k] and len(g):
+            d = rng.uniform(-0.3, 0.3, len(g))
+            qB[g] = qA[g] + d - d.mean()
+    t["qA"] = s["qA"].copy()
+    t["qB"] = np.ascontiguousarray(qB, np.float32)
+    t["qC"] = s["qB"].copy()
+    t["qD"] = s["qB"].copy()
+    t["lam"] = np.ascontiguousarray(rng.uniform(0.0, 1.0, 2 * K), np.float32)
+    t["forms"] = 4
+    t["name"] = s["name"] + "_tautomers"
+    return t

@@ -357,3 +357,86 @@ def test_hamiltonian_forces_by_finite_differences(periodic):
             h_eff = (float(np.float32(xp[i, a])) - float(np.float32(xm[i, a]))) / 2
             fd = -(_energy(sp, lam, True)["E"] - _energy(sm, lam, True)["E"]) / (2 * h_eff)
             assert fd == pytest.approx(out["F"][i, a], rel=1e-5, abs=1e-6 * np.abs(out["F"]).max())
+
+
+# ---------------------------------------------------------------- four-form sites (Eq. 2)
+def _four_form_system(periodic, tautomer_fraction=1.0):
+    return synth.tautomer_sites(_two_site_system(periodic), seed=3, tautomer_fraction=tautomer_fraction)
+
+
+def _energy4(s, lam2, hamiltonian):
+    t = dict(s)
+    t["lam"] = np.asarray(lam2, np.float32)
+    return oracle.evaluate(t, tol=1e-12, hamiltonian=hamiltonian)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_four_form_hamiltonian_is_multilinear(periodic):
+    """Eq. 2 makes E linear in each of the four coordinates (lp, lt of two sites): E_H
+    equals the multilinear interpolation of the sixteen corner energies, where every site
+    is in one pure form and both interpolations agree; dE/dl is the matching difference."""
+    import itertools
+    s = _four_form_system(periodic)
+    lam = np.array([0.375, 0.8125, 0.625, 0.25])  # exact in FP32
+    corners = {c: _energy4(s, np.array(c, float), False)["E"] for c in itertools.product((0.0, 1.0), repeat=4)}
+    out = _energy4(s, lam, True)
+
+    def interp(l):
+        return sum(np.prod([li if ci else 1 - li for ci, li in zip(c, l)]) * e for c, e in corners.items())
+
+    scale = max(abs(v) for v in corners.values())
+    assert out["E"] == pytest.approx(interp(lam), abs=1e-10 * scale)
+    for j in range(4):  # dE/dl_j of a multilinear function: interpolation of the corner differences
+        lo, hi = lam.copy(), lam.copy()
+        lo[j], hi[j] = 0.0, 1.0
+        assert out["dVdl"][j] == pytest.approx(interp(hi) - interp(lo), abs=1e-10 * scale)
+    assert abs(out["E"] - _energy4(s, lam, False)["E"]) > 1e-6 * scale
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_four_form_charge_derivatives_by_finite_differences(periodic):
+    """Charge interpolation: E is quadratic in each coordinate, so central differences
+    are exact up to rounding."""
+    s = _four_form_system(periodic)
+    lam = np.array([0.375, 0.8125, 0.625, 0.25])
+    out = _energy4(s, lam, False)
+    h = 0.125
+    for j in range(4):
+        lp, lm = lam.copy(), lam.copy()
+        lp[j] += h
+        lm[j] -= h
+        fd = (_energy4(s, lp, False)["E"] - _energy4(s, lm, False)["E"]) / (2 * h)
+        assert fd == pytest.approx(out["dVdl"][j], rel=1e-9, abs=1e-9 * abs(out["E"]))
+
+
+@pytest.mark.parametrize("hamiltonian", [False, True])
+def test_four_form_reduces_to_two_forms(hamiltonian):
+    """Sites without tautomers (qB = qA, qD = qC) are the two-form sites of Eq. 1 with
+    lambda = lp; their lt derivative vanishes."""
+    s2 = _two_site_system(True)
+    s4 = _four_form_system(True, tautomer_fraction=0.0)
+    lam4 = np.array([0.375, 0.8125, 0.625, 0.25])
+    a = _energy4(s4, lam4, hamiltonian)
+    b = _energy(s2, lam4[0::2], hamiltonian)
+    assert a["E"] == pytest.approx(b["E"], rel=1e-12)
+    np.testing.assert_allclose(a["F"], b["F"], rtol=1e-9, atol=1e-9 * np.abs(b["F"]).max())
+    np.testing.assert_allclose(a["dVdl"][0::2], b["dVdl"], rtol=1e-9)
+    assert np.abs(a["dVdl"][1::2]).max() < 1e-9 * np.abs(b["dVdl"]).max()
+
+
+def test_four_form_hamiltonian_forces_by_finite_differences():
+    s = _four_form_system(True)
+    lam = np.array([0.375, 0.8125, 0.625, 0.25])
+    out = _energy4(s, lam, True)
+    h = 1e-4
+    for i in np.nonzero(s["site"] >= 0)[0][:2]:
+        for a in range(3):
+            xp = s["x"].astype(np.float64).copy()
+            xm = xp.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            sp, sm = dict(s), dict(s)
+            sp["x"], sm["x"] = xp, xm
+            h_eff = (float(np.float32(xp[i, a])) - float(np.float32(xm[i, a]))) / 2
+            fd = -(_energy4(sp, lam, True)["E"] - _energy4(sm, lam, True)["E"]) / (2 * h_eff)
+            assert fd == pytest.approx(out["F"][i, a], rel=1e-5, abs=1e-6 * np.abs(out["F"]).max())

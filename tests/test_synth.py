@@ -50,3 +50,17 @@ def test_solvated_500k_shape():
     assert s["x"].shape == (500000, 3) and s["L"] == 17.0 and (s["p"], s["depth"]) == (10, 5)
     assert len(s["lam"]) == 200
     np.testing.assert_allclose(_site_changes(s), -1.0, atol=1e-5)
+
+
+def test_tautomer_sites_forms():
+    s = synth.tautomer_sites(synth.periodic_uniform(seed=5, n=500, L=2.0, n_sites=6, site_size=4), seed=2,
+                             tautomer_fraction=0.5)
+    K = 6
+    assert s["forms"] == 4 and s["lam"].shape == (2 * K,) and s["lam"].dtype == np.float32
+    assert np.array_equal(s["qC"], s["qD"])
+    for k in range(K):
+        g = s["site"] == k
+        assert abs(float(s["qA"][g].astype(np.float64).sum() - s["qB"][g].astype(np.float64).sum())) < 1e-5
+        assert abs(float(s["qC"][g].astype(np.float64).sum() - s["qA"][g].astype(np.float64).sum()) + 1.0) < 1e-5
+    out = ~(s["site"] >= 0)
+    assert np.array_equal(s["qA"][out], s["qB"][out])
