@@ -119,6 +119,23 @@ fmm_status fmm_set_charges(fmm_handle* h, int n_atoms, int n_sites, const float*
                            const float* qB, const int32_t* site, const float* lambda,
                            void* stream);
 
+/* Sites with two lambda coordinates over four charge forms (Sec. 2.1, Eq. 2:
+ * protonation lambda_p and tautomer lambda_t):
+ *   q_i = (1 - lp)[(1 - lt) qA_i + lt qB_i] + lp[(1 - lt) qC_i + lt qD_i]
+ * for atoms of a site; other atoms keep qA_i.  A site without tautomers has
+ * qB = qA and qD = qC (its lt derivative is then 0).
+ *   qA .. qD: [n_atoms] float (device), the four forms
+ *   site:     [n_atoms] int32, site index in [0, n_sites) or -1
+ *   lambda:   [2 n_sites] float (device): lp_0, lt_0, lp_1, lt_1, ...
+ * Otherwise as fmm_set_charges.  Until the next fmm_set_charges, every
+ * lambda and dV/dlambda array of this handle (fmm_set_lambda,
+ * fmm_bind_lambda, fmm_eval, fmm_eval_host, fmm_adjoint4, fmm_lambda_step)
+ * has 2 n_sites entries in this order; with Hamiltonian interpolation the
+ * intra-site correction uses the covariance of the forms' charges. */
+fmm_status fmm_set_charges4(fmm_handle* h, int n_atoms, int n_sites, const float* qA,
+                            const float* qB, const float* qC, const float* qD,
+                            const int32_t* site, const float* lambda, void* stream);
+
 /* Replace lambda ([n_sites] float, device), stream-ordered copy. */
 fmm_status fmm_set_lambda(fmm_handle* h, const float* lambda, void* stream);
 
@@ -172,6 +189,17 @@ void fmm_host_free(void* p);
 fmm_status fmm_adjoint(fmm_handle* h, const double* gbar, const float* F, const float* phi,
                        const float* dVdlambda, float* grad_x, float* grad_qA, float* grad_qB,
                        float* grad_lambda, void* stream);
+
+/* Adjoint for four-form sites (after fmm_set_charges4): dL/dq^X_i =
+ * (phi_i + k_e g_X,i) w_X(lp, lt) * gbar for form X of a site atom (w_X its
+ * bilinear weight; g_X,i the Hamiltonian-interpolation term, 0 otherwise),
+ * dL/dqA_i = phi_i * gbar outside sites; grad_lambda and dVdlambda have
+ * 2 n_sites entries.  Any output may be NULL.  FMM_ERR_STATE for two-form
+ * sites (use fmm_adjoint), and fmm_adjoint returns FMM_ERR_STATE for
+ * four-form sites. */
+fmm_status fmm_adjoint4(fmm_handle* h, const double* gbar, const float* F, const float* phi,
+                        const float* dVdlambda, float* grad_x, float* grad_qA, float* grad_qB,
+                        float* grad_qC, float* grad_qD, float* grad_lambda, void* stream);
 
 /* Copy the binning of the last fmm_eval into caller device buffers (any may
  * be NULL): key [n_atoms] uint32 Morton key of each atom's leaf (input

@@ -8,9 +8,9 @@ streams only.
 """
 from .binding import (FMM, Batch, FmmError, KE_DEFAULT, STAGES, host_operator, host_regular, lambda_step,
                       library_path, load, pinned_empty)
-from .autograd import FMMEnergy, fmm_energy
+from .autograd import FMMEnergy, FMMEnergy4, fmm_energy, fmm_energy4
 
 load()  # fail loudly at import when the native library is missing
 
-__all__ = ["FMM", "Batch", "lambda_step", "FmmError", "FMMEnergy", "fmm_energy", "KE_DEFAULT", "STAGES", "host_operator",
+__all__ = ["FMM", "Batch", "lambda_step", "FmmError", "FMMEnergy", "FMMEnergy4", "fmm_energy", "fmm_energy4", "KE_DEFAULT", "STAGES", "host_operator",
            "host_regular", "library_path", "load", "pinned_empty"]

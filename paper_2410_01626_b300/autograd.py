@@ -43,3 +43,36 @@ class FMMEnergy(torch.autograd.Function):
 def fmm_energy(x, qA, qB, site, lam, solver):
     """E as a differentiable function of positions, both charge forms and lambda."""
     return FMMEnergy.apply(x, qA, qB, site, lam, solver)
+
+
+class FMMEnergy4(torch.autograd.Function):
+    """The same for sites with two lambda coordinates over four charge forms (Sec. 2.1, Eq. 2):
+    dE/dq^X_i = k_e phi_i w_X with the bilinear weights w_X of the atom's site."""
+
+    @staticmethod
+    def forward(ctx, x, qA, qB, qC, qD, site, lam, solver):
+        key = tuple(t.data_ptr() for t in (qA, qB, qC, qD, site)) + tuple(t._version for t in (qA, qB, qC, qD, site))
+        if getattr(solver, "_charge_key", None) != key:
+            solver.set_charges4(*(t.detach().contiguous() for t in (qA, qB, qC, qD)), site.contiguous(),
+                                lam.detach().contiguous())
+            solver._charge_key = key
+        elif lam.numel():
+            solver.set_lambda(lam.detach().contiguous())
+        E, F, dV, phi = solver.eval(x.detach().contiguous(), phi=True)
+        ctx.solver = solver
+        ctx.save_for_backward(F, phi, dV)
+        ctx.needs = ctx.needs_input_grad
+        return E.reshape(())
+
+    @staticmethod
+    def backward(ctx, gE):
+        F, phi, dV = ctx.saved_tensors
+        g = gE.detach().reshape(1).to(torch.float64).contiguous()
+        nx, na, nb, nc, nd, _, nl, _ = ctx.needs
+        gx, gq, gl = ctx.solver.adjoint4(g, F, phi, dV, grad_x=nx, grad_q=(na, nb, nc, nd), grad_lam=nl)
+        return (gx, *gq, None, gl, None)
+
+
+def fmm_energy4(x, qA, qB, qC, qD, site, lam, solver):
+    """E of four-form sites as a differentiable function of positions, the four forms and lambda."""
+    return FMMEnergy4.apply(x, qA, qB, qC, qD, site, lam, solver)

@@ -41,11 +41,13 @@ class FmmOptions(ctypes.Structure):
 EXPORTS = {
     "fmm_create": (I, [ctypes.POINTER(FmmBox), I, I, I, ctypes.POINTER(FmmOptions), ctypes.POINTER(P)]),
     "fmm_set_charges": (I, [P, I, I, P, P, P, P, P]),
+    "fmm_set_charges4": (I, [P, I, I, P, P, P, P, P, P, P]),
     "fmm_set_lambda": (I, [P, P, P]),
     "fmm_bind_lambda": (I, [P, P]),
     "fmm_eval": (I, [P, P, P, P, P, P, P]),
     "fmm_eval_host": (I, [P, P, P, P, P, P]),
     "fmm_adjoint": (I, [P, P, P, P, P, P, P, P, P, P]),
+    "fmm_adjoint4": (I, [P, P, P, P, P, P, P, P, P, P, P, P]),
     "fmm_get_binning": (I, [P, P, P, P, P, P]),
     "fmm_status_word": (I, [P, ctypes.POINTER(I), P]),
     "fmm_stage_times": (I, [P, P, I]),
@@ -144,6 +146,8 @@ class FMM:
         self.ke = float(ke) if ke else KE_DEFAULT
         self.n = 0
         self.K = 0
+        self.nlam = 0  # lambda coordinates: K (two-form sites) or 2K (four-form sites)
+        self.forms = 2
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -160,7 +164,25 @@ class FMM:
             _dev(lam, torch.float32, "lambda")
         _check(self._lib.fmm_set_charges(self._h, n, K, _ptr(qA), _ptr(qB), _ptr(site), _ptr(lam) if K else None,
                                          _stream()), "fmm_set_charges")
-        self.n, self.K = n, K
+        self.n, self.K, self.nlam, self.forms = n, K, K, 2
+        self._site = site
+
+    def set_charges4(self, qA, qB, qC, qD, site, lam):
+        """Sites with two lambda coordinates over four charge forms (Sec. 2.1, Eq. 2):
+        q = (1 - lp)[(1 - lt) qA + lt qB] + lp[(1 - lt) qC + lt qD]; lam = [2K] = (lp, lt) per
+        site.  dV/dlambda then has 2K entries in the same order."""
+        n = qA.numel()
+        if lam.numel() % 2:
+            raise ValueError("lambda must hold (lambda_p, lambda_t) for every site")
+        K = lam.numel() // 2
+        for t, nm in ((qA, "qA"), (qB, "qB"), (qC, "qC"), (qD, "qD")):
+            _dev(t, torch.float32, nm)
+        _dev(site, torch.int32, "site")
+        if K:
+            _dev(lam, torch.float32, "lambda")
+        _check(self._lib.fmm_set_charges4(self._h, n, K, _ptr(qA), _ptr(qB), _ptr(qC), _ptr(qD), _ptr(site),
+                                          _ptr(lam) if K else None, _stream()), "fmm_set_charges4")
+        self.n, self.K, self.nlam, self.forms = n, K, 2 * K, 4
         self._site = site
 
     def set_lambda(self, lam):
@@ -177,7 +199,7 @@ class FMM:
         dev = device or torch.device("cuda")
         E = torch.empty(1, dtype=torch.float64, device=dev)
         F = torch.empty(self.n, 3, dtype=torch.float32, device=dev)
-        dV = torch.empty(self.K, dtype=torch.float32, device=dev)
+        dV = torch.empty(self.nlam, dtype=torch.float32, device=dev)
         ph = torch.empty(self.n, dtype=torch.float32, device=dev) if phi else None
         return E, F, dV, ph
 
@@ -209,11 +231,22 @@ class FMM:
         gx = torch.empty(self.n, 3, dtype=torch.float32, device=dev) if grad_x else None
         ga = torch.empty(self.n, dtype=torch.float32, device=dev) if grad_qA else None
         gb = torch.empty(self.n, dtype=torch.float32, device=dev) if grad_qB else None
-        gl = torch.empty(self.K, dtype=torch.float32, device=dev) if grad_lam else None
+        gl = torch.empty(self.nlam, dtype=torch.float32, device=dev) if grad_lam else None
         _check(self._lib.fmm_adjoint(self._h, _ptr(gbar), _ptr(F), _ptr(phi), _ptr(dVdl) if self.K else None,
                                      _ptr(gx), _ptr(ga), _ptr(gb), _ptr(gl) if self.K else None, _stream()),
                "fmm_adjoint")
         return gx, ga, gb, gl
+
+    def adjoint4(self, gbar, F, phi, dVdl, grad_x=True, grad_q=(True, True, True, True), grad_lam=True):
+        """Reverse mode for four-form sites: (dL/dx, (dL/dq^A .. dL/dq^D), dL/dlambda)."""
+        dev = F.device
+        gx = torch.empty(self.n, 3, dtype=torch.float32, device=dev) if grad_x else None
+        gq = [torch.empty(self.n, dtype=torch.float32, device=dev) if w else None for w in grad_q]
+        gl = torch.empty(self.nlam, dtype=torch.float32, device=dev) if grad_lam else None
+        _check(self._lib.fmm_adjoint4(self._h, _ptr(gbar), _ptr(F), _ptr(phi), _ptr(dVdl) if self.K else None,
+                                      _ptr(gx), *[_ptr(t) for t in gq], _ptr(gl) if self.K else None, _stream()),
+               "fmm_adjoint4")
+        return gx, gq, gl
 
     def binning(self):
         dev = torch.device("cuda")

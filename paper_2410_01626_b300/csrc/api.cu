@@ -64,6 +64,9 @@ void free_atoms(Handle& h) {
     dfree(h.dq);
     dfree(h.phis);
     dfree(h.near);
+    dfree(h.qC);
+    dfree(h.qD);
+    dfree(h.dqt);
     h.perm = nullptr;
     h.sorted_key = nullptr;
     h.cap = 0;
@@ -92,7 +95,7 @@ void free_all(Handle& h) {
     dfree(h.leafmom);
     dfree(h.hi_coef);
     dfree(h.hi_site);
-    dfree(h.hi_phi);
+    dfree(h.hi_g);
     dfree(h.root);
     dfree(h.status);
     dfree(h.work);
@@ -384,22 +387,28 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     return FMM_OK;
 }
 
-fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const float* qB, const int32_t* site,
-                           const float* lambda, void* stream) {
+// Shared by fmm_set_charges (two forms per site, one lambda) and fmm_set_charges4 (four forms,
+// two lambda coordinates per site, Sec. 2.1 Eq. 2).
+static fmm_status set_charges_impl(fmm_handle* H, int n, int K, int nforms, const float* const* q,
+                                   const int32_t* site, const float* lambda, void* stream) {
     if (!H || n < 0 || K < 0) return FMM_ERR_ARG;
-    if (n > 0 && (!qA || !qB || !site)) return FMM_ERR_ARG;
+    for (int f = 0; f < nforms; ++f)
+        if (n > 0 && !q[f]) return FMM_ERR_ARG;
+    if (n > 0 && !site) return FMM_ERR_ARG;
     if (K > 0 && !lambda) return FMM_ERR_ARG;
     Handle& h = H->h;
     cudaStream_t st = S(stream);
-    if (n > h.cap) {
+    const int ncoord = nforms == 4 ? 2 : 1;
+    h.charges_set = false;
+    if (n > h.cap || (nforms == 4 && !h.qC)) {
         free_atoms(h);
         fmm_status e;
         if ((e = dalloc(&h.qA, n)) || (e = dalloc(&h.qB, n)) || (e = dalloc(&h.site, n)) || (e = dalloc(&h.key, n)) ||
             (e = dalloc(&h.kA, n)) || (e = dalloc(&h.kB, n)) || (e = dalloc(&h.vA, n)) || (e = dalloc(&h.vB, n)) ||
             (e = dalloc(&h.inv, n)) || (e = dalloc(&h.pos, n)) || (e = dalloc(&h.dq, n)) ||
-            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.near, n))) {
+            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.near, n)) ||
+            (nforms == 4 && ((e = dalloc(&h.qC, n)) || (e = dalloc(&h.qD, n)) || (e = dalloc(&h.dqt, n))))) {
             free_atoms(h);
-            h.charges_set = false;
             return e;
         }
         h.cap = n;
@@ -410,27 +419,23 @@ fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const f
             dfree(h.epart);
             if (dalloc(&h.epart, nparts)) {
                 h.epart_cap = 0;
-                h.charges_set = false;
                 return FMM_ERR_OOM;
             }
             h.epart_cap = nparts;
         }
     }
     if (h.hamiltonian && (n > h.hi_cap || K > h.hi_kcap)) {
-        dfree(h.hi_phi);
+        dfree(h.hi_g);
         dfree(h.hi_site);
         h.hi_cap = h.hi_kcap = 0;
-        if (dalloc(&h.hi_phi, n > 0 ? n : 1) || dalloc(&h.hi_site, 2L * (K > 0 ? K : 1))) {
-            h.charges_set = false;
-            return FMM_ERR_OOM;
-        }
+        if (dalloc(&h.hi_g, n > 0 ? n : 1) || dalloc(&h.hi_site, 3L * (K > 0 ? K : 1))) return FMM_ERR_OOM;
         h.hi_cap = n;
         h.hi_kcap = K;
     }
-    if (K > h.lam_cap) {
+    if (ncoord * K > h.lam_cap) {
         dfree(h.lam);
-        if (dalloc(&h.lam, K)) return FMM_ERR_OOM;
-        h.lam_cap = K;
+        if (dalloc(&h.lam, ncoord * K)) return FMM_ERR_OOM;
+        h.lam_cap = ncoord * K;
     }
     // site map: validated and grouped on the host (ascending input index within a site)
     std::vector<int32_t> hs(n);
@@ -460,18 +465,33 @@ fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const f
     if ((e = cuda_ok(cudaMemcpy(h.site_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice))) ||
         (e = cuda_ok(cudaMemcpy(h.site_atoms, atoms.data(), sizeof(int) * atoms.size(), cudaMemcpyHostToDevice))))
         return e;
+    float* dst[4] = {h.qA, h.qB, h.qC, h.qD};
     if (n > 0) {
-        if ((e = cuda_ok(cudaMemcpyAsync(h.qA, qA, sizeof(float) * n, cudaMemcpyDeviceToDevice, st))) ||
-            (e = cuda_ok(cudaMemcpyAsync(h.qB, qB, sizeof(float) * n, cudaMemcpyDeviceToDevice, st))) ||
-            (e = cuda_ok(cudaMemcpyAsync(h.site, site, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st))))
-            return e;
+        for (int f = 0; f < nforms; ++f)
+            if ((e = cuda_ok(cudaMemcpyAsync(dst[f], q[f], sizeof(float) * n, cudaMemcpyDeviceToDevice, st)))) return e;
+        if ((e = cuda_ok(cudaMemcpyAsync(h.site, site, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st)))) return e;
     }
-    if (K > 0 && (e = cuda_ok(cudaMemcpyAsync(h.lam, lambda, sizeof(float) * K, cudaMemcpyDeviceToDevice, st))))
+    if (K > 0 &&
+        (e = cuda_ok(cudaMemcpyAsync(h.lam, lambda, sizeof(float) * ncoord * K, cudaMemcpyDeviceToDevice, st))))
         return e;
     h.n = n;
     h.K = K;
+    h.nforms = nforms;
+    h.ncoord = ncoord;
     h.charges_set = true;
     return FMM_OK;
+}
+
+fmm_status fmm_set_charges(fmm_handle* H, int n, int K, const float* qA, const float* qB, const int32_t* site,
+                           const float* lambda, void* stream) {
+    const float* q[2] = {qA, qB};
+    return set_charges_impl(H, n, K, 2, q, site, lambda, stream);
+}
+
+fmm_status fmm_set_charges4(fmm_handle* H, int n, int K, const float* qA, const float* qB, const float* qC,
+                            const float* qD, const int32_t* site, const float* lambda, void* stream) {
+    const float* q[4] = {qA, qB, qC, qD};
+    return set_charges_impl(H, n, K, 4, q, site, lambda, stream);
 }
 
 fmm_status fmm_set_lambda(fmm_handle* H, const float* lambda, void* stream) {
@@ -480,7 +500,7 @@ fmm_status fmm_set_lambda(fmm_handle* H, const float* lambda, void* stream) {
     if (!h.charges_set) return FMM_ERR_STATE;
     if (h.K == 0) return FMM_OK;
     if (!lambda) return FMM_ERR_ARG;
-    return cuda_ok(cudaMemcpyAsync(h.lam, lambda, sizeof(float) * h.K, cudaMemcpyDeviceToDevice, S(stream)));
+    return cuda_ok(cudaMemcpyAsync(h.lam, lambda, sizeof(float) * h.ncoord * h.K, cudaMemcpyDeviceToDevice, S(stream)));
 }
 
 fmm_status fmm_bind_lambda(fmm_handle* H, const float* lambda) {
@@ -516,8 +536,12 @@ fmm_status fmm_eval_host(fmm_handle* H, const float* x_host, double* E_host, flo
             return e;
         h.host_cap = n;
     }
-    if (h.K > 0 && !h.hdV_dev) {
-        if (dalloc(&h.hdV_dev, h.lam_cap)) return FMM_ERR_OOM;
+    const int nlam = h.ncoord * h.K;
+    if (nlam > h.hdV_cap) {  // dV/dlambda staging, one entry per site coordinate
+        dfree(h.hdV_dev);
+        h.hdV_cap = 0;
+        if (dalloc(&h.hdV_dev, nlam)) return FMM_ERR_OOM;
+        h.hdV_cap = nlam;
     }
     fmm_status e = FMM_OK;
     if (n > 0 && (e = cuda_ok(cudaMemcpyAsync(h.hx_dev, x_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st))))
@@ -530,8 +554,8 @@ fmm_status fmm_eval_host(fmm_handle* H, const float* x_host, double* E_host, flo
     if (F_host && n > 0 &&
         (e = cuda_ok(cudaMemcpyAsync(F_host, h.hF_dev, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st))))
         return e;
-    if (dV_host && h.K > 0 &&
-        (e = cuda_ok(cudaMemcpyAsync(dV_host, h.hdV_dev, sizeof(float) * h.K, cudaMemcpyDeviceToHost, st))))
+    if (dV_host && nlam > 0 &&
+        (e = cuda_ok(cudaMemcpyAsync(dV_host, h.hdV_dev, sizeof(float) * nlam, cudaMemcpyDeviceToHost, st))))
         return e;
     return cuda_ok(cudaStreamSynchronize(st));
 }
@@ -560,8 +584,25 @@ fmm_status fmm_adjoint(fmm_handle* H, const double* gbar, const float* F, const 
     if (gx && !F) return FMM_ERR_ARG;
     if ((gqA || gqB) && !phi) return FMM_ERR_ARG;
     if (glam && h.K > 0 && !dVdl) return FMM_ERR_ARG;
+    if (h.nforms != 2) return FMM_ERR_STATE;  // four-form sites: fmm_adjoint4
     cudaGetLastError();
-    launch_adjoint(&h, gbar, F, phi, dVdl, gx, gqA, gqB, glam, S(stream));
+    float* gq[4] = {gqA, gqB, nullptr, nullptr};
+    launch_adjoint(&h, gbar, F, phi, dVdl, gx, gq, glam, S(stream));
+    return cuda_ok(cudaGetLastError());
+}
+
+fmm_status fmm_adjoint4(fmm_handle* H, const double* gbar, const float* F, const float* phi, const float* dVdl,
+                        float* gx, float* gqA, float* gqB, float* gqC, float* gqD, float* glam, void* stream) {
+    if (!H || !gbar) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    if (!h.charges_set) return FMM_ERR_STATE;
+    if (h.nforms != 4) return FMM_ERR_STATE;  // two-form sites: fmm_adjoint
+    if (gx && !F) return FMM_ERR_ARG;
+    if ((gqA || gqB || gqC || gqD) && !phi) return FMM_ERR_ARG;
+    if (glam && h.K > 0 && !dVdl) return FMM_ERR_ARG;
+    cudaGetLastError();
+    float* gq[4] = {gqA, gqB, gqC, gqD};
+    launch_adjoint(&h, gbar, F, phi, dVdl, gx, gq, glam, S(stream));
     return cuda_ok(cudaGetLastError());
 }
 

@@ -61,6 +61,10 @@ struct Handle {
     // atoms
     int cap = 0, n = 0, K = 0;
     float *qA = nullptr, *qB = nullptr, *lam = nullptr;
+    float *qC = nullptr, *qD = nullptr;  // four-form sites (Eq. 2): forms C and D
+    int nforms = 2;                      // charge forms per site: 2 (Eq. 1) or 4 (Eq. 2)
+    int ncoord = 1;                      // lambda coordinates per site: 1 or 2 (lambda_p, lambda_t)
+    float* dqt = nullptr;                // four-form sites: dq/dlambda_t per sorted atom (dq holds dq/dlambda_p)
     const float* lam_bound = nullptr;
     int32_t* site = nullptr;
     int* site_ptr = nullptr;    // [K+1]
@@ -80,10 +84,10 @@ struct Handle {
     double* root = nullptr;     // [nc] FP64 root multipole, then [5] Q D T at root+nc
     // Hamiltonian interpolation: h of the periodic pair potential (normalised root local
     // expansion, [ncp]), per-site energy and dV/dlambda corrections ([K][2]), and per-atom
-    // phi_h = sum_{j in site, j != i} dq_j psi_ij + dq_i psi_0 (input order) for the adjoint
+    // per-form terms of the Hamiltonian correction's charge gradient (input order) for the adjoint
     float* hi_coef = nullptr;
-    double* hi_site = nullptr;
-    float* hi_phi = nullptr;
+    double* hi_site = nullptr;  // [K][3]: energy, dV/dlambda_p (or dV/dlambda), dV/dlambda_t corrections
+    float4* hi_g = nullptr;  // per atom (input order), per form X: sum_j (q^X_j - q_j) psi_ij
     int hi_cap = 0, hi_kcap = 0;
     int* status = nullptr;
     float* work = nullptr;  // split-K partial products (8 x the largest M2M output level)
@@ -102,6 +106,7 @@ struct Handle {
     float* hF_dev = nullptr;
     float* hdV_dev = nullptr;
     double* hE_dev = nullptr;
+    int hdV_cap = 0;
     int host_cap = 0;
     void* tc = nullptr;  // tensor-core M2L state (m2l_tc.cu)
 };
@@ -113,7 +118,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
                 cudaStream_t st);
 int launches_per_eval(const Handle* h);
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi,
-                    const float* dVdl, float* gx, float* gqA, float* gqB, float* glam,
+                    const float* dVdl, float* gx, float* const* gq /*[4] forms, may be null*/, float* glam,
                     cudaStream_t st);
 // translate_tc.cu
 TranslateOp translate_pack(const std::vector<float>& W, int Mtot, int K);  // W row-major [Mtot][K]

@@ -214,11 +214,20 @@ __global__ void k_bin_place(int n, const uint32_t* __restrict__ key, const uint3
     placed[start[key[i]] + slot[i]] = (uint32_t)i;
 }
 
+// The charge forms of the atoms and the site coordinates (Sec. 2.1, Eq. 1 and Eq. 2).
+struct ChargeForms {
+    const float* q[4];     // forms A, B (two-form sites), + C, D (four-form sites)
+    int nforms;            // 2: q = qA + lambda (qB - qA); 4: bilinear in (lambda_p, lambda_t)
+    const int32_t* site;
+    int K;
+    const float* lam;      // [K] or [2K] = (lambda_p, lambda_t) per site
+    float* dq;             // dq/dlambda (two forms) or dq/dlambda_p (four forms), sorted order
+    float* dqt;            // dq/dlambda_t (four forms), sorted order
+};
+
 // Position and charges of input atom i at sorted slot s (the gather of the binning step).
 __device__ __forceinline__ void gather_atom(int i, int s, const float* __restrict__ x, const BoxGeom& g,
-                                            const float* __restrict__ qA, const float* __restrict__ qB,
-                                            const int32_t* __restrict__ site, int K, const float* __restrict__ lam,
-                                            float4* __restrict__ pos, float* __restrict__ dq,
+                                            const ChargeForms& cf, float4* __restrict__ pos,
                                             uint32_t* __restrict__ inv, int* __restrict__ status) {
     float u[3];
     const double o[3] = {g.o0, g.o1, g.o2};
@@ -233,19 +242,30 @@ __device__ __forceinline__ void gather_atom(int i, int s, const float* __restric
         else
             u[a] = u32;
     }
-    const float a = qA[i], b = qB[i];
-    const int st = site[i];
-    float d = 0.f, q = a;
+    const float a = cf.q[0][i];
+    const int st = cf.site[i];
+    float d = 0.f, dt = 0.f, q = a;
     if (st >= 0) {
-        if (st < K) {
-            d = b - a;
-            q = fmaf(lam[st], d, a);
+        if (st < cf.K) {
+            if (cf.nforms == 4) {
+                const float lp = cf.lam[2 * st], lt = cf.lam[2 * st + 1];
+                const float b = cf.q[1][i], c = cf.q[2][i], e = cf.q[3][i];
+                const float ab = fmaf(lt, b - a, a), cd = fmaf(lt, e - c, c);
+                q = fmaf(lp, cd - ab, ab);
+                d = cd - ab;
+                dt = fmaf(lp, (e - c) - (b - a), b - a);
+            } else {
+                const float b = cf.q[1][i];
+                d = b - a;
+                q = fmaf(cf.lam[st], d, a);
+            }
         } else {
             atomicOr(status, FMM_DEV_SITE);
         }
     }
     pos[s] = make_float4(u[0], u[1], u[2], q);
-    dq[s] = d;
+    cf.dq[s] = d;
+    if (cf.nforms == 4) cf.dqt[s] = dt;
     inv[i] = (uint32_t)s;
 }
 
@@ -253,11 +273,8 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
                                                           const uint32_t* __restrict__ count,
                                                           const uint32_t* __restrict__ placed,
                                                           uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
-                                                          const float* __restrict__ x, BoxGeom g,
-                                                          const float* __restrict__ qA, const float* __restrict__ qB,
-                                                          const int32_t* __restrict__ site, int K,
-                                                          const float* __restrict__ lam, float4* __restrict__ pos,
-                                                          float* __restrict__ dq, uint32_t* __restrict__ inv,
+                                                          const float* __restrict__ x, BoxGeom g, ChargeForms cf,
+                                                          float4* __restrict__ pos, uint32_t* __restrict__ inv,
                                                           int* __restrict__ status) {
     const int leaf = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (leaf >= nleaf) return;
@@ -269,7 +286,7 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
         if (lane < c) {
             perm[st + r] = v;
             skey[st + r] = (uint32_t)leaf;
-            gather_atom((int)v, st + r, x, g, qA, qB, site, K, lam, pos, dq, inv, status);
+            gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
         }
         return;
     }
@@ -281,7 +298,7 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
         for (int k = 0; k < c; ++k) r += placed[st + k] < v ? 1 : 0;
         perm[st + r] = v;
         skey[st + r] = (uint32_t)leaf;
-        gather_atom((int)v, st + r, x, g, qA, qB, site, K, lam, pos, dq, inv, status);
+        gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
     }
 }
 
@@ -881,25 +898,29 @@ __global__ void __launch_bounds__(kOutThreads) k_far_out(int n, int use_far, Nea
 }
 
 // ---- Hamiltonian interpolation: the intra-site correction ----
-// For atoms i, j of one site k, interpolating the Hamiltonian instead of the charges changes
-// the pair term by lambda_k (1 - lambda_k) dq_i dq_j psi(r_ij) (Sec. 2.1, Eq. 1), including
-// i = j with the self-image term psi_0.  psi is the pair potential the FMM sums: 1/r open;
-// periodic, psi(r) = 1/|r| + sum over the 26 neighbouring images 1/|r - nL| + c2 |r|^2 + h(r),
-// with c2 = 2 pi / 3V and h the lattice remainder, evaluated as the root local expansion of a
-// unit charge at the root centre (the lattice operator's first column) at u = r / L.
+// With forms X of a site and their weights w_X (two forms: (1 - lambda, lambda); four forms:
+// the bilinear weights of (lambda_p, lambda_t), Sec. 2.1 Eq. 1 and Eq. 2), q_i = sum_X w_X q^X_i.
+// Interpolating the Hamiltonian instead of the charges changes the pair term of atoms i, j of
+// one site by C_ij = sum_X w_X q^X_i q^X_j - q_i q_j = sum_X w_X (q^X_i - q_i)(q^X_j - q_j)
+// (for two forms lambda (1 - lambda) dq_i dq_j), i = j with the self-image term psi_0, and
+// dC_ij/dl = sum_X (dw_X/dl)(q^X_i - q_i)(q^X_j - q_j).  psi is the pair potential the FMM
+// sums: 1/r open; periodic, psi(r) = 1/|r| + sum over the 26 neighbouring images 1/|r - nL|
+// + c2 |r|^2 + h(r), with c2 = 2 pi / 3V and h the lattice remainder, evaluated as the root
+// local expansion of a unit charge at the root centre (the lattice operator's first column)
+// at u = r / L.
 struct HiParams {
-    int K, periodic;
+    int K, periodic, nforms;
     float L, ke, c2;
     const float* coef;  // h, normalised root local expansion (periodic)
     const int* site_ptr;
     const int* site_atoms;
     const uint32_t* inv;
     const float4* pos;
-    const float* dq;
-    const float* lam;
+    const float* q[4];  // the forms, input order
+    const float* lam;   // [K] or [2K]
     float* F;           // input order, corrected in place (may be null)
-    double* site_out;   // [K][2]: energy and dV/dlambda corrections
-    float* phi_h;       // input order: sum_{j != i} dq_j psi_ij + dq_i psi_0
+    double* site_out;   // [K][3]: energy, dV/dlambda(_p), dV/dlambda_t corrections
+    float4* g_h;        // input order, per form X: sum_{j} (q^X_j - q_j) psi_ij (j = i: psi_0)
 };
 
 // psi(r) - [self ? 1/|r| : 0] and its gradient in r; r = 0 with self gives psi_0
@@ -943,6 +964,17 @@ __device__ void hi_pair(const HiParams& p, float rx, float ry, float rz, bool se
     gz += hz * iL * iL;
 }
 
+// the forms' deviations q^X - q of atom `ia` under weights w (unused forms: 0)
+__device__ __forceinline__ void hi_dev(const HiParams& p, int ia, const float* w, float* dev) {
+    float Q[4] = {0.f, 0.f, 0.f, 0.f}, q = 0.f;
+    for (int X = 0; X < p.nforms; ++X) {
+        Q[X] = p.q[X][ia];
+        q = fmaf(w[X], Q[X], q);
+    }
+#pragma unroll
+    for (int X = 0; X < 4; ++X) dev[X] = X < p.nforms ? Q[X] - q : 0.f;
+}
+
 // one warp per site, one lane per site atom: each lane sums over the other atoms of its site
 // (every pair is evaluated from both sides, so no atomics and a fixed order)
 template <int P>
@@ -951,22 +983,41 @@ __global__ void __launch_bounds__(128) k_hi(HiParams p) {
     const int k = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (k >= p.K) return;
     const int a0 = p.site_ptr[k], na = p.site_ptr[k + 1] - a0;
-    const float lam = p.lam[k];
-    const float w = lam * (1.f - lam);
+    float w[4] = {0.f, 0.f, 0.f, 0.f}, wp[4] = {0.f, 0.f, 0.f, 0.f}, wt[4] = {0.f, 0.f, 0.f, 0.f};
+    if (p.nforms == 4) {
+        const float lp = p.lam[2 * k], lt = p.lam[2 * k + 1];
+        w[0] = (1.f - lp) * (1.f - lt), w[1] = (1.f - lp) * lt, w[2] = lp * (1.f - lt), w[3] = lp * lt;
+        wp[0] = -(1.f - lt), wp[1] = -lt, wp[2] = 1.f - lt, wp[3] = lt;
+        wt[0] = -(1.f - lp), wt[1] = 1.f - lp, wt[2] = -lp, wt[3] = lp;
+    } else {
+        const float l = p.lam[k];
+        w[0] = 1.f - l, w[1] = l;
+        wp[0] = -1.f, wp[1] = 1.f;
+    }
     float psi0, t0, t1, t2;
     hi_pair<P>(p, 0.f, 0.f, 0.f, true, psi0, t0, t1, t2);
-    double e = 0.0;
+    double e = 0.0, ep = 0.0, et = 0.0;
     for (int a = lane; a < na; a += 32) {
         const int ia = p.site_atoms[a0 + a];
-        const uint32_t sa = p.inv[ia];
-        const float4 pa = p.pos[sa];
-        const float da = p.dq[sa];
-        float ph = da * psi0, gx = 0.f, gy = 0.f, gz = 0.f;
+        const float4 pa = p.pos[p.inv[ia]];
+        float da[4];
+        hi_dev(p, ia, w, da);
+        float c = 0.f, cp = 0.f, ct = 0.f, g[4];
+#pragma unroll
+        for (int X = 0; X < 4; ++X) {
+            c = fmaf(w[X], da[X] * da[X], c);
+            cp = fmaf(wp[X], da[X] * da[X], cp);
+            ct = fmaf(wt[X], da[X] * da[X], ct);
+            g[X] = da[X] * psi0;
+        }
+        float sc = c * psi0, scp = cp * psi0, sct = ct * psi0;  // 2 x (this atom's energy share)
+        float gx = 0.f, gy = 0.f, gz = 0.f;
         for (int b = 0; b < na; ++b) {
             if (b == a) continue;
-            const uint32_t sb = p.inv[p.site_atoms[a0 + b]];
-            const float4 pb = p.pos[sb];
-            const float db = p.dq[sb];
+            const int ib = p.site_atoms[a0 + b];
+            const float4 pb = p.pos[p.inv[ib]];
+            float db[4];
+            hi_dev(p, ib, w, db);
             float rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
             if (p.periodic) {  // minimum image: the truncated h is most accurate for small |r|
                 rx -= p.L * rintf(rx / p.L);
@@ -975,25 +1026,42 @@ __global__ void __launch_bounds__(128) k_hi(HiParams p) {
             }
             float psi, hx, hy, hz;
             hi_pair<P>(p, rx, ry, rz, false, psi, hx, hy, hz);
-            ph += db * psi;
-            gx += db * hx;
-            gy += db * hy;
-            gz += db * hz;
+            float cab = 0.f, cpab = 0.f, ctab = 0.f;
+#pragma unroll
+            for (int X = 0; X < 4; ++X) {
+                const float pr = da[X] * db[X];
+                cab = fmaf(w[X], pr, cab);
+                cpab = fmaf(wp[X], pr, cpab);
+                ctab = fmaf(wt[X], pr, ctab);
+                g[X] = fmaf(db[X], psi, g[X]);
+            }
+            sc = fmaf(cab, psi, sc);
+            scp = fmaf(cpab, psi, scp);
+            sct = fmaf(ctab, psi, sct);
+            gx = fmaf(cab, hx, gx);
+            gy = fmaf(cab, hy, gy);
+            gz = fmaf(cab, hz, gz);
         }
         if (p.F) {
-            const float c = p.ke * w * da;
-            p.F[3L * ia] -= c * gx;
-            p.F[3L * ia + 1] -= c * gy;
-            p.F[3L * ia + 2] -= c * gz;
+            p.F[3L * ia] -= p.ke * gx;
+            p.F[3L * ia + 1] -= p.ke * gy;
+            p.F[3L * ia + 2] -= p.ke * gz;
         }
-        p.phi_h[ia] = ph;
-        e += 0.5 * (double)da * (double)ph;
+        p.g_h[ia] = make_float4(g[0], g[1], g[2], g[3]);
+        e += 0.5 * (double)sc;
+        ep += 0.5 * (double)scp;
+        et += 0.5 * (double)sct;
     }
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
+    for (int d = 16; d >= 1; d >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, d);
+        ep += __shfl_xor_sync(0xffffffffu, ep, d);
+        et += __shfl_xor_sync(0xffffffffu, et, d);
+    }
     if (lane == 0) {
-        p.site_out[2 * k] = (double)p.ke * (double)w * e;
-        p.site_out[2 * k + 1] = (double)p.ke * (1.0 - 2.0 * (double)lam) * e;
+        p.site_out[3 * k] = (double)p.ke * e;
+        p.site_out[3 * k + 1] = (double)p.ke * ep;
+        p.site_out[3 * k + 2] = (double)p.ke * et;
     }
 }
 
@@ -1284,11 +1352,13 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, float4* __restrict__ 
 constexpr int kFinalBlocks = 32;
 static_assert(8 + 5 * kQdtBlocks + 4 + kFinalBlocks + 1 <= kRootDoubles, "root scratch layout");
 __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restrict__ epart, double ke,
-                                               double* __restrict__ E, int K, const int* __restrict__ site_ptr,
+                                               double* __restrict__ E, int K, int ncoord,
+                                               const int* __restrict__ site_ptr,
                                                const int* __restrict__ site_atoms, const uint32_t* __restrict__ inv,
-                                               const float* __restrict__ dq, const float* __restrict__ phis,
-                                               float* __restrict__ dVdl, double* __restrict__ blocksum,
-                                               unsigned int* __restrict__ ticket, const double* __restrict__ hi_site) {
+                                               const float* __restrict__ dq, const float* __restrict__ dqt,
+                                               const float* __restrict__ phis, float* __restrict__ dVdl,
+                                               double* __restrict__ blocksum, unsigned int* __restrict__ ticket,
+                                               const double* __restrict__ hi_site) {
     __shared__ double red[256];
     __shared__ bool last;
     const int per = (nparts + kFinalBlocks - 1) / kFinalBlocks;
@@ -1313,29 +1383,37 @@ __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restr
         for (int b = 0; b < kFinalBlocks; ++b) t += ((volatile double*)blocksum)[b];
         double hsum = 0.0;  // Hamiltonian interpolation: per-site corrections, in site order
         if (hi_site)
-            for (int k = 0; k < K; ++k) hsum += hi_site[2 * k];
+            for (int k = 0; k < K; ++k) hsum += hi_site[3 * k];
         if (E) E[0] = 0.5 * ke * t + hsum;
         *ticket = 0u;  // ready for the next call
     }
     if (dVdl)
         for (int k = blockIdx.x * 256 + threadIdx.x; k < K; k += kFinalBlocks * 256) {
-            double v = 0.0;
+            double v = 0.0, vt = 0.0;  // dE/dlambda(_p), dE/dlambda_t
             for (int a = site_ptr[k]; a < site_ptr[k + 1]; ++a) {
                 const uint32_t si = inv[site_atoms[a]];
                 v += (double)dq[si] * (double)phis[si];
+                if (ncoord == 2) vt += (double)dqt[si] * (double)phis[si];
             }
-            dVdl[k] = (float)(ke * v + (hi_site ? hi_site[2 * k + 1] : 0.0));
+            dVdl[ncoord * k] = (float)(ke * v + (hi_site ? hi_site[3 * k + 1] : 0.0));
+            if (ncoord == 2) dVdl[2 * k + 1] = (float)(ke * vt + (hi_site ? hi_site[3 * k + 2] : 0.0));
         }
 }
 
-__global__ void k_adjoint(int n, int K, const double* __restrict__ gbar, const float* __restrict__ F,
-                          const float* __restrict__ phi, const float* __restrict__ dVdl,
-                          const int32_t* __restrict__ site, const float* __restrict__ lam,
-                          float* __restrict__ gx, float* __restrict__ gqA, float* __restrict__ gqB,
-                          float* __restrict__ glam, float ke, const float* __restrict__ phi_h) {
+struct ChargeGrads {
+    float* q[4];  // dL/dq^X per form (any may be null)
+};
+
+// Reverse mode: gbar = dL/dE.  dE/dx = -F; dE/dlambda = dV/dlambda; dE/dq^X_i = k phi_i w_X
+// for a site atom (w_X the weight of form X in q_i), plus k w_X g_h[i][X] with Hamiltonian
+// interpolation; atoms outside every site have q_i = qA_i.
+__global__ void k_adjoint(int n, int K, int ncoord, int nforms, const double* __restrict__ gbar,
+                          const float* __restrict__ F, const float* __restrict__ phi, const float* __restrict__ dVdl,
+                          const int32_t* __restrict__ site, const float* __restrict__ lam, float* __restrict__ gx,
+                          ChargeGrads gq, float* __restrict__ glam, float ke, const float4* __restrict__ g_h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float g = (float)gbar[0];
-    if (i < K && glam) glam[i] = dVdl[i] * g;
+    if (i < ncoord * K && glam) glam[i] = dVdl[i] * g;
     if (i >= n) return;
     if (gx) {
         gx[3L * i] = -F[3L * i] * g;
@@ -1343,11 +1421,22 @@ __global__ void k_adjoint(int n, int K, const double* __restrict__ gbar, const f
         gx[3L * i + 2] = -F[3L * i + 2] * g;
     }
     const int s = site[i];
-    const float l = (s >= 0 && s < K) ? lam[s] : 0.f;
-    // Hamiltonian interpolation adds dE/d dq_i = ke lambda (1 - lambda) phi_h_i (dq = qB - qA)
-    const float hterm = (phi_h && s >= 0 && s < K) ? ke * l * (1.f - l) * phi_h[i] : 0.f;
-    if (gqA) gqA[i] = (phi[i] * (1.f - l) - hterm) * g;
-    if (gqB) gqB[i] = (phi[i] * l + hterm) * g;
+    float w[4] = {1.f, 0.f, 0.f, 0.f};
+    if (s >= 0 && s < K) {
+        if (nforms == 4) {
+            const float lp = lam[2 * s], lt = lam[2 * s + 1];
+            w[0] = (1.f - lp) * (1.f - lt), w[1] = (1.f - lp) * lt, w[2] = lp * (1.f - lt), w[3] = lp * lt;
+        } else {
+            w[0] = 1.f - lam[s], w[1] = lam[s];
+        }
+    }
+    float hg[4] = {0.f, 0.f, 0.f, 0.f};
+    if (g_h && s >= 0 && s < K) {
+        const float4 t = g_h[i];
+        hg[0] = t.x, hg[1] = t.y, hg[2] = t.z, hg[3] = t.w;
+    }
+    for (int X = 0; X < nforms; ++X)
+        if (gq.q[X]) gq.q[X][i] = w[X] * (phi[i] + ke * hg[X]) * g;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1426,9 +1515,9 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     h->sorted_key = h->kB;
     if (n > 0) {
         k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(n, h->key, h->vA, h->start, h->vB);
+        ChargeForms cf{{h->qA, h->qB, h->qC, h->qD}, h->nforms, h->site, h->K, lam, h->dq, h->dqt};
         k_bin_order_gather<<<(nleaf + 3) / 4, 128, 0, st>>>(nleaf, h->start, h->count, h->vB, h->perm,
-                                                            h->sorted_key, x, g, h->qA, h->qB, h->site, h->K, lam,
-                                                            h->pos, h->dq, h->inv, h->status);
+                                                            h->sorted_key, x, g, cf, h->pos, h->inv, h->status);
     }
     // --- near field on the caller's stream, concurrent with the multipole chain ---
     NearParams a{};
@@ -1521,6 +1610,11 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         HiParams hp{};
         hp.K = h->K;
         hp.periodic = h->periodic;
+        hp.nforms = h->nforms;
+        hp.q[0] = h->qA;
+        hp.q[1] = h->qB;
+        hp.q[2] = h->qC;
+        hp.q[3] = h->qD;
         hp.L = (float)h->box.edge;
         hp.ke = (float)h->ke;
         hp.c2 = (float)(2.0 * M_PI / (3.0 * h->box.edge * h->box.edge * h->box.edge));
@@ -1529,19 +1623,18 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         hp.site_atoms = h->site_atoms;
         hp.inv = h->inv;
         hp.pos = h->pos;
-        hp.dq = h->dq;
         hp.lam = lam;
         hp.F = F;
         hp.site_out = h->hi_site;
-        hp.phi_h = h->hi_phi;
+        hp.g_h = h->hi_g;
         FMM_DISPATCH_P(h->p, launch_hi, hp, st);
     }
     stage(h, 7, st);
     const int nparts = (n + kOutThreads - 1) / kOutThreads;  // one q phi partial per output block
     double* fin = h->root + h->nc + 8 + 5 * kQdtBlocks + 4;  // [kFinalBlocks] block totals, then the ticket
-    k_final<<<kFinalBlocks, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->site_ptr, h->site_atoms, h->inv, h->dq,
-                                          h->phis, dVdl, fin, reinterpret_cast<unsigned int*>(fin + kFinalBlocks),
-                                          hi ? h->hi_site : nullptr);
+    k_final<<<kFinalBlocks, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->ncoord, h->site_ptr, h->site_atoms,
+                                          h->inv, h->dq, h->dqt, h->phis, dVdl, fin,
+                                          reinterpret_cast<unsigned int*>(fin + kFinalBlocks), hi ? h->hi_site : nullptr);
     stage(h, 8, st);
     return 0;
 }
@@ -1627,12 +1720,13 @@ extern "C" fmm_status fmm_binning_noalloc(const fmm_box* box, int periodic, int 
 }
 
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi, const float* dVdl,
-                    float* gx, float* gqA, float* gqB, float* glam, cudaStream_t st) {
-    const int m = h->n > h->K ? h->n : h->K;
+                    float* gx, float* const* gq, float* glam, cudaStream_t st) {
+    const int m = h->n > h->ncoord * h->K ? h->n : h->ncoord * h->K;
     if (m == 0) return;
     const float* lam = h->lam_bound ? h->lam_bound : h->lam;
-    k_adjoint<<<(m + 255) / 256, 256, 0, st>>>(h->n, h->K, gbar, F, phi, dVdl, h->site, lam, gx, gqA, gqB, glam,
-                                               (float)h->ke, h->hamiltonian ? h->hi_phi : nullptr);
+    ChargeGrads g{{gq[0], gq[1], h->nforms == 4 ? gq[2] : nullptr, h->nforms == 4 ? gq[3] : nullptr}};
+    k_adjoint<<<(m + 255) / 256, 256, 0, st>>>(h->n, h->K, h->ncoord, h->nforms, gbar, F, phi, dVdl, h->site, lam, gx,
+                                               g, glam, (float)h->ke, h->hamiltonian ? h->hi_g : nullptr);
 }
 
 }  // namespace fmmcph
