@@ -1,0 +1,48 @@
+"""Lambda-side potentials (double well, pH potential, partition function correction): the
+oracle against closed forms, and the library's host-side correction against the oracle."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lambda_bias as lb
+
+
+def test_spline_values_and_slopes_at_the_knots():
+    a0, a1, h, d, kw = 0.0, 1.0, 7.5, -2.25, 900.0
+    for l, v in ((a0, 0.0), (0.5, h), (a1, d)):
+        V, dV = lb.potential(l, a0, a1, h, d, kw)
+        assert V == pytest.approx(v, abs=1e-14) and dV == pytest.approx(0.0, abs=1e-12)
+    # continuity across the knots and the walls, and the walls' slopes
+    for l in (a0, 0.5, a1):
+        for e in (1e-9,):
+            assert lb.potential(l - e, a0, a1, h, d, kw)[0] == pytest.approx(lb.potential(l + e, a0, a1, h, d, kw)[0],
+                                                                              abs=1e-6)
+    assert lb.potential(-0.1, a0, a1, h, d, kw)[1] == pytest.approx(-90.0)
+    assert lb.potential(1.1, a0, a1, h, d, kw)[0] == pytest.approx(d + 0.5 * 900.0 * 0.01)
+    # derivative by central differences inside the pieces
+    for l in (0.13, 0.37, 0.61, 0.94, -0.05, 1.07):
+        fd = (lb.potential(l + 1e-7, a0, a1, h, d, kw)[0] - lb.potential(l - 1e-7, a0, a1, h, d, kw)[0]) / 2e-7
+        assert fd == pytest.approx(lb.potential(l, a0, a1, h, d, kw)[1], rel=1e-6, abs=1e-6)
+
+
+def test_pfc_symmetric_case_is_zero():
+    assert lb.pfc_delta(pH=4.0, pKa=4.0, h=8.0, kT=2.494339) == pytest.approx(0.0, abs=1e-9)
+
+
+@pytest.mark.parametrize("dpH", [-1.5, -0.3, 0.7, 2.0])
+def test_pfc_reaches_the_henderson_hasselbalch_ratio(dpH):
+    """Independent check: the population ratio of the corrected potential by a plain
+    trapezoid rule on a fine grid."""
+    kT, h = 2.494339, 6.0
+    d = lb.pfc_delta(pH=4.0 + dpH, pKa=4.0, h=h, kT=kT)
+    l = np.linspace(-0.1, 1.1, 240001)
+    V = np.array([lb.potential(x, 0.0, 1.0, h, d, 1000.0)[0] for x in l])
+    w = np.exp(-V / kT)
+    mid = len(l) // 2
+    zp = np.trapezoid(w[: mid + 1], l[: mid + 1])
+    zd = np.trapezoid(w[mid:], l[mid:])
+    assert math.log10(zd / zp) == pytest.approx(dpH, abs=2e-6)
+    # deprotonated state favoured above the pKa: the lambda = 1 well is the lower one
+    assert (d < 0) == (dpH > 0)
