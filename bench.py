@@ -535,11 +535,13 @@ def run_batch(args):
 
 def run_loop(args):
     """lambda dynamics on the 500k system: per step one FMM evaluation (CUDA graph) and one
-    device Langevin step; lambda is bound to the solver so charges refresh every step."""
+    device Langevin step with the double-well / pH bias (Sec. 2.2-2.3; per-site pKa_ref drawn
+    around the pH, barrier 5 kJ/mol, partition function correction); lambda is bound to the
+    solver so charges refresh every step."""
     import numpy as np
     import torch
     import synth
-    from paper_2410_01626_b300 import FMM, lambda_step
+    from paper_2410_01626_b300 import FMM, lambda_bias, lambda_step
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -550,6 +552,9 @@ def run_loop(args):
     f.set_charges(t["qA"], t["qB"], t["site"], t["lam"])
     lam = t["lam"].clone()
     vel = torch.zeros_like(lam)
+    pH = 5.0
+    pka = np.random.default_rng(11).uniform(3.5, 6.5, len(s["lam"]))
+    bias = lambda_bias(pH, pka, 5.0, device=dev)
     f.bind_lambda(lam)
     E, F, dV, _ = f.outputs(dev)
     f.eval_into(t["x"], E, F, dV)
@@ -565,7 +570,7 @@ def run_loop(args):
 
     def one():
         g.replay()
-        lambda_step(lam, vel, dV, step[0], 5, first=(step[0] == 0))
+        lambda_step(lam, vel, dV, step[0], 5, first=(step[0] == 0), bias=bias)
         step[0] += 1
 
     for _ in range(max(args.warmup, 3)):
@@ -587,8 +592,11 @@ def run_loop(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
             "data": "synthetic",
             "config": {"workload": "loop1000: " + WORKLOAD, "langevin": "BAOAB m=60 u, dt=2 fs, gamma=1/ps, 300 K",
+                       "bias": "double well (barrier 5 kJ/mol) + pH 5 offset by partition function correction, "
+                               "pKa_ref U(3.5, 6.5) per site",
                        "l2": "working set > L2 per step"},
             "lambda_range": [float(lam_np.min()), float(lam_np.max())],
+            "deprotonated_fraction": float((lam_np > 0.5).mean()),
             "gpu_launches": (f.launches_per_eval() + 1) * n_steps, "clocks": clocks,
             "roofline": None, "cpu_baseline": None, "e2e": None}
     if rank == 0:

@@ -253,6 +253,29 @@ fmm_status fmm_lambda_step(int n_sites, float* lambda, float* velocity, const fl
                            double mass, double gamma, double kT, unsigned long long seed,
                            unsigned long long step, int first, double lo, double hi, void* stream);
 
+/* The lambda-side bias potential (Sec. 2.2) on one lambda coordinate: a double well of
+ * cubic Hermite pieces, wells at a0 < a1, the central barrier at b = (a0 + a1) / 2,
+ *   V(a0) = 0, V(b) = barrier, V(a1) = delta, zero slope at a0, b and a1,
+ * each piece V_a + (V_b - V_a)(3 s^2 - 2 s^3), and harmonic walls kwall (l - a)^2 / 2
+ * outside [a0, a1].  The pH potential (Eq. 4) enters through delta:
+ * fmm_lambda_pfc returns the delta (partition function correction, Sec. 2.3) for which
+ * the populations exp(-V / kT) implies on [lo, b] (protonated, lambda near 0) and
+ * [b, hi] (deprotonated) satisfy Z_deprot / Z_prot = 10^(pH - pKa_ref), the free energy
+ * of deprotonation ln(10) kT (pKa_ref - pH) of Eq. 4; [lo, hi] are the reflecting walls
+ * of fmm_lambda_step.  Host FP64 (Gauss-Legendre quadrature, bisection).  Returns
+ * FMM_ERR_ARG for kT <= 0, a0 >= a1, lo > a0 or hi < a1, or delta == NULL. */
+fmm_status fmm_lambda_pfc(double pH, double pKa_ref, double barrier, double kT, double a0, double a1,
+                          double kwall, double lo, double hi, double* delta);
+
+/* fmm_lambda_step with the bias potential: the force on coordinate k is
+ * -dV/dlambda_k - dV_dw/dlambda(lambda_k; bias[5k .. 5k+4] = a0, a1, barrier, delta,
+ * kwall), evaluated at the current lambda.  bias: [n][5] float (device); NULL is the
+ * unbiased step. */
+fmm_status fmm_lambda_step_bias(int n, float* lambda, float* velocity, const float* dVdlambda,
+                                const float* bias, double dt, double mass, double gamma, double kT,
+                                unsigned long long seed, unsigned long long step, int first, double lo,
+                                double hi, void* stream);
+
 /* Batches of independent replicas (different sizes, boxes, depths, precisions).
  * fmm_batch_create takes n existing handles (charges already set; the batch does not own
  * them).  fmm_batch_eval evaluates every replica; x, E, F, dVdlambda are HOST arrays of n

@@ -6,11 +6,11 @@ in an open or periodic cube, computed by hand-written sm_103a CUDA kernels
 behind a C ABI (``include/fmmcph.h``).  PyTorch supplies device memory and
 streams only.
 """
-from .binding import (FMM, Batch, FmmError, KE_DEFAULT, STAGES, host_operator, host_regular, lambda_step,
-                      library_path, load, pinned_empty)
+from .binding import (FMM, Batch, FmmError, KE_DEFAULT, STAGES, host_operator, host_regular, lambda_bias, lambda_pfc,
+                      lambda_step, library_path, load, pinned_empty)
 from .autograd import FMMEnergy, FMMEnergy4, fmm_energy, fmm_energy4
 
 load()  # fail loudly at import when the native library is missing
 
 __all__ = ["FMM", "Batch", "lambda_step", "FmmError", "FMMEnergy", "FMMEnergy4", "fmm_energy", "fmm_energy4", "KE_DEFAULT", "STAGES", "host_operator",
-           "host_regular", "library_path", "load", "pinned_empty"]
+           "host_regular", "library_path", "load", "pinned_empty", "lambda_pfc", "lambda_bias"]

@@ -58,6 +58,9 @@ EXPORTS = {
     "fmm_binning_noalloc": (I, [ctypes.POINTER(FmmBox), I, I, I, P, P, P, P, P, P]),
     "fmm_lambda_step": (I, [I, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                             ctypes.c_ulonglong, ctypes.c_ulonglong, I, ctypes.c_double, ctypes.c_double, P]),
+    "fmm_lambda_step_bias": (I, [I, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_ulonglong, ctypes.c_ulonglong, I, ctypes.c_double, ctypes.c_double, P]),
+    "fmm_lambda_pfc": (I, [ctypes.c_double] * 9 + [ctypes.POINTER(ctypes.c_double)]),
     "fmm_batch_create": (I, [I, P, ctypes.POINTER(P)]),
     "fmm_batch_eval": (I, [P, P, P, P, P, P]),
     "fmm_batch_destroy": (None, [P]),
@@ -314,11 +317,39 @@ def host_regular(p, u):
 
 
 def lambda_step(lam, vel, dVdl, step, seed, dt=0.002, mass=60.0, gamma=1.0, kT=2.494339, first=False,
-                lo=-0.1, hi=1.1):
-    """One device-side BAOAB step of the lambda particles (in place)."""
+                lo=-0.1, hi=1.1, bias=None):
+    """One device-side BAOAB step of the lambda particles (in place); ``bias`` ([n, 5] float:
+    a0, a1, barrier, delta, kwall per coordinate, see ``lambda_bias``) adds the double-well force."""
     _dev(lam, torch.float32, "lambda"), _dev(vel, torch.float32, "velocity"), _dev(dVdl, torch.float32, "dVdl")
-    _check(load().fmm_lambda_step(lam.numel(), _ptr(lam), _ptr(vel), _ptr(dVdl), dt, mass, gamma, kT, int(seed),
-                                  int(step), int(bool(first)), lo, hi, _stream()), "fmm_lambda_step")
+    if bias is None:
+        _check(load().fmm_lambda_step(lam.numel(), _ptr(lam), _ptr(vel), _ptr(dVdl), dt, mass, gamma, kT, int(seed),
+                                      int(step), int(bool(first)), lo, hi, _stream()), "fmm_lambda_step")
+        return
+    _dev(bias, torch.float32, "bias")
+    if bias.numel() != 5 * lam.numel():
+        raise ValueError("bias must hold 5 values per lambda coordinate")
+    _check(load().fmm_lambda_step_bias(lam.numel(), _ptr(lam), _ptr(vel), _ptr(dVdl), _ptr(bias), dt, mass, gamma,
+                                       kT, int(seed), int(step), int(bool(first)), lo, hi, _stream()),
+           "fmm_lambda_step_bias")
+
+
+def lambda_pfc(pH, pKa_ref, barrier, kT=2.494339, a0=0.0, a1=1.0, kwall=1000.0, lo=-0.1, hi=1.1):
+    """Well offset delta of the double well (partition function correction, host FP64)."""
+    d = ctypes.c_double()
+    _check(load().fmm_lambda_pfc(float(pH), float(pKa_ref), float(barrier), float(kT), float(a0), float(a1),
+                                 float(kwall), float(lo), float(hi), ctypes.byref(d)), "fmm_lambda_pfc")
+    return d.value
+
+
+def lambda_bias(pH, pKa_ref, barrier, kT=2.494339, a0=0.0, a1=1.0, kwall=1000.0, lo=-0.1, hi=1.1, device="cuda"):
+    """Bias parameters [n, 5] for ``lambda_step`` from per-coordinate pKa_ref and barrier
+    (sequences of equal length, or scalars): the double well with the pH offset from
+    ``lambda_pfc``."""
+    import numpy as np
+    pk = np.atleast_1d(np.asarray(pKa_ref, np.float64))
+    bh = np.broadcast_to(np.atleast_1d(np.asarray(barrier, np.float64)), pk.shape)
+    rows = [[a0, a1, b, lambda_pfc(pH, p, b, kT, a0, a1, kwall, lo, hi), kwall] for p, b in zip(pk, bh)]
+    return torch.tensor(rows, dtype=torch.float32, device=device)
 
 
 class Batch:

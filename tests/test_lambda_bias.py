@@ -46,3 +46,22 @@ def test_pfc_reaches_the_henderson_hasselbalch_ratio(dpH):
     assert math.log10(zd / zp) == pytest.approx(dpH, abs=2e-6)
     # deprotonated state favoured above the pKa: the lambda = 1 well is the lower one
     assert (d < 0) == (dpH > 0)
+
+
+@pytest.mark.parametrize("dpH,barrier", [(-1.5, 6.0), (0.0, 8.0), (0.7, 6.0), (2.0, 4.0)])
+def test_library_pfc_matches_oracle(dpH, barrier):
+    """The library's host-side correction (Gauss-Legendre, bisection) against the oracle's
+    (adaptive quadrature, Brent)."""
+    from paper_2410_01626_b300 import lambda_pfc
+    kT = 2.494339
+    want = lb.pfc_delta(pH=4.0 + dpH, pKa=4.0, h=barrier, kT=kT)
+    got = lambda_pfc(4.0 + dpH, 4.0, barrier, kT)
+    assert got == pytest.approx(want, abs=1e-9 * kT)
+
+
+def test_library_pfc_rejects_bad_arguments():
+    from paper_2410_01626_b300 import FmmError, lambda_pfc
+    with pytest.raises(FmmError):
+        lambda_pfc(7.0, 4.0, 5.0, kT=0.0)
+    with pytest.raises(FmmError):
+        lambda_pfc(7.0, 4.0, 5.0, a0=1.0, a1=0.0)
