@@ -118,9 +118,8 @@ class ClockSampler:
 # from an ncu capture of the tensor-core kernel built from the source with this sha1; reported
 # only while the source is unchanged.
 NCU_M2L_TRAFFIC = {
-    "sha1": "5dbe299fdce825d14655b666a20ed922f2bb65f0",
-    "3xtf32": 176_549_120 + 11_954_944,
-    "tf32": 50_770_176 + 2_946_816,
+    "sha1": "a6e7e50512cdfe1e03f8bf586087deac7d42cf09",
+    "3xbf16": 51_974_144 + 3_781_888,
 }
 
 
