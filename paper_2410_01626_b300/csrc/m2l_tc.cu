@@ -19,8 +19,9 @@
 //                      all deltas: the B descriptor just starts delta rows further in.
 // Operands are stored in 16-byte core-matrix rows ("cells": 4 TF32 or 8 BF16 coefficients),
 // so every mode has the same byte layout; one MMA consumes 32 bytes of K (8 TF32 or 16 BF16).
-// Warp 0 lane 0 streams slabs and operator chunks with cp.async.bulk into a 3-stage ring;
-// warp 1 lane 0 issues the MMAs; warps 2..9 drain TMEM into the Morton-ordered L.
+// Warp 0 streams slabs and operator chunks with cp.async.bulk into a ring of up to 16 stages
+// (several lanes issue copies per round); warp 1 issues the MMAs (one elected lane, the loop
+// warp-wide); warps 2..9 drain TMEM into the Morton-ordered L.
 // Every wait is bounded; on expiry the CTA flags FMM_DEV_TIMEOUT and returns cleanly.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -40,12 +41,12 @@ namespace {
 constexpr int kTcRows = 192;    // virtual rows (N) per CTA: 280 CTAs = two full waves at depth 5
 constexpr int kTcTmemCols = 512; // two accumulators, 256 columns apart
 constexpr int kTcAccStride = 256;
-constexpr int kTcStages = 3;    // operator-chunk ring depth
-constexpr uint32_t kTcTBytes = 16384;  // one ring stage: one operator chunk, hi (+ lo) parts
+constexpr int kTcMaxStages = 16;  // operator-chunk ring depth: as many stages as shared memory holds
 constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
-// Operand forms.  K chunk (input coefficients per slab / operator chunk): 32 for TF32, 16 for
-// the split 3xTF32 form (hi and lo parts), 32 for the split 3xBF16 form; in every form one ring
-// stage is 16 KB and one slab buffer about 86 KB, so two slab buffers fit next to a 3-stage ring.
+// Operand forms.  K chunk (input coefficients per slab / operator chunk): 16 for TF32, 8 for
+// the split 3xTF32 form (hi and lo parts), 16 for the split 3xBF16 form.  In every form a ring
+// stage is 8 KB (one operator chunk, both parts) and a slab buffer 64 bytes per row (about 43 KB
+// at depth 5), so two slab buffers leave room for a 16-stage ring.
 enum TcMode { kTf32 = 0, kTf32x3 = 1, kBf16x3 = 2 };
 template <int MODE>
 struct TcCfg {
@@ -53,12 +54,12 @@ struct TcCfg {
     static constexpr bool kBf16 = MODE == kBf16x3;
     static constexpr int kElem = kBf16 ? 2 : 4;             // bytes per operand element
     static constexpr int kPerCell = 16 / kElem;             // coefficients per 16-byte cell
-    static constexpr int kChunk = kBf16 ? 32 : (kSplit ? 16 : 32);
-    static constexpr int kKG = kChunk / kPerCell;           // cells per chunk row (8, 4, 4)
+    static constexpr int kChunk = kBf16 ? 16 : (kSplit ? 8 : 16);
+    static constexpr int kKG = kChunk / kPerCell;           // cells per chunk row (4, 2, 2)
     static constexpr int kKSteps = kChunk * kElem / 32;     // MMAs per chunk (32 bytes of K each)
     static constexpr int kParts = kSplit ? 2 : 1;
     static constexpr uint32_t kPartBytes = 128u * kChunk * kElem;  // one operator part (hi or lo)
-    static constexpr uint32_t kStageBytes = kParts * kPartBytes;   // 16 KB
+    static constexpr uint32_t kStageBytes = kParts * kPartBytes;   // 8 KB in every form
 };
 
 struct TcLevels {
@@ -146,8 +147,8 @@ struct TcTile {
     int level, cls, r0, pad;
 };
 
-// Warp roles (10 warps): warp 0 lane 0 = bulk-copy producer, warp 1 lane 0 = MMA issuer,
-// warps 2..9 = accumulator drains.  The tensor core aligns addends to the largest and
+// Warp roles (10 warps): warp 0 = bulk-copy producer, warp 1 = MMA issuer (one elected lane
+// issues), warps 2..9 = accumulator drains.  The tensor core aligns addends to the largest and
 // truncates, so a long chain of MMAs into one FP32 accumulator drifts; here each source
 // class pi and K chunk is accumulated into one of two TMEM accumulators (ping-pong)
 // and then added by the drain warps into FP32 registers (round to nearest), which bounds
@@ -160,11 +161,11 @@ template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const TcTile* __restrict__ tiles, TcLevels lv, const float* __restrict__ Mtc,
              const float* __restrict__ Mtc_lo, const float* __restrict__ Ttc, float* __restrict__ L, int ncp,
-             int NKC, int slab_rows, int* __restrict__ status) {
+             int NKC, int slab_rows, int nstages, int* __restrict__ status) {
     using Cfg = TcCfg<MODE>;
     constexpr bool SPLIT = Cfg::kSplit;
     constexpr int kTcKG = Cfg::kKG;
-    static_assert(Cfg::kStageBytes == kTcTBytes, "ring stage size");
+    constexpr uint32_t kTcTBytes = Cfg::kStageBytes;
     extern __shared__ __align__(1024) uint8_t smem[];
     // two slab buffers, each [part][kgroup][3 ranges][slab_rows][16 B]; range dx+1 holds the source
     // rows r0 + dx (n+2)^2 - (n+3) .. + slab_rows, i.e. every delta_y, delta_z shift of one delta_x
@@ -173,14 +174,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t slab_bytes = part_bytes * Cfg::kParts;
     uint8_t* slab0 = smem;
     uint8_t* tring = smem + 2 * (size_t)slab_bytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tring + (size_t)kTcStages * kTcTBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tring + (size_t)nstages * kTcTBytes);
     uint64_t* slab_full = bars + 0;    // [2]
     uint64_t* slab_empty = bars + 2;   // [2]
     uint64_t* acc_full = bars + 4;     // [2]
     uint64_t* acc_empty = bars + 6;    // [2]
-    uint64_t* t_full = bars + 8;                 // [kTcStages]
-    uint64_t* t_empty = bars + 8 + kTcStages;    // [kTcStages]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8 + 2 * kTcStages);
+    uint64_t* t_full = bars + 8;                 // [nstages]
+    uint64_t* t_empty = bars + 8 + nstages;      // [nstages]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8 + 2 * nstages);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     // copies issued (operator chunks, slabs) by the producer and consumed by the MMA issuer,
     // so that after an abort the outstanding copies are waited for before the CTA exits
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc::mbar_init(acc_full + q, 1);
             tc::mbar_init(acc_empty + q, kTcDrainWarps);
         }
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < nstages; ++s) {
             tc::mbar_init(t_full + s, 1);
             tc::mbar_init(t_empty + s, 1);
         }
@@ -229,62 +230,109 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const float* Mlev_lo = SPLIT ? Mtc_lo + lv.mtc_off[lev] : nullptr;
 
     if (warp == 0) {
-        if (lane == 0) {
-            // ---------------- producer ----------------
-            int t_issued = 0, slabs_issued = 0;
-            auto load_slab = [&](int g) {
-                ++slabs_issued;
-                const int pi = g / NKC, ch = g % NKC, buf = g & 1;
-                uint8_t* dst = slab0 + (size_t)buf * slab_bytes;
+        // ---------------- producer (the whole warp) ----------------
+        // One thread issuing one copy at a time cannot keep the MMAs fed: each turn of its loop
+        // (waits, barrier arithmetic, copy issue) is a chain of dependent single-thread
+        // instructions several hundred cycles long, longer than the MMAs of one operator chunk.
+        // So the lanes share the work: in each round, lane r issues the chunk of the r-th next
+        // valid offset of the group (up to min(8, ring depth - 1) chunks per round), and a slab load
+        // is spread over the lanes as one copy each.  Control flow is warp-uniform; a failed
+        // wait in any lane ends the round before anything of it is issued.
+        int* sel = const_cast<int*>(copy_count + 4);  // [32]: operator index by rank
+        // chunks issued per round: at most nstages - 1, because the MMA issuer waits for chunk
+        // j + 1 before it releases chunk j, and a round's last lane needs the stage that chunk
+        // nstages back released
+        const int per_round = min(8, nstages - 1);
+        int t_issued = 0, slabs_issued = 0;
+        auto load_slab = [&](int g) {
+            const int pi = g / NKC, ch = g % NKC, buf = g & 1;
+            uint8_t* dst = slab0 + (size_t)buf * slab_bytes;
+            if (lane == 0)
                 tc::mbar_arrive_expect_tx(slab_full + buf,
                                           (uint32_t)(rl[0] + rl[1] + rl[2]) * 16u * kTcKG * Cfg::kParts);
-                for (int kg = 0; kg < kTcKG; ++kg)
-                    for (int q = 0; q < 3; ++q) {
-                        const long e = (((long)pi * NKG + ch * kTcKG + kg) * R + rs[q]) * 4;
-                        uint8_t* dq = dst + (size_t)kg * kg_stride + (size_t)q * slab_rows * 16;
-                        tc::bulk_g2s(dq, Mlev + e, (uint32_t)rl[q] * 16u, slab_full + buf);
-                        if (SPLIT) tc::bulk_g2s(dq + part_bytes, Mlev_lo + e, (uint32_t)rl[q] * 16u, slab_full + buf);
-                    }
-            };
-            int stage = 0;
-            uint32_t ephase = 0;
-            bool first_round = true;
-            bool ok = true;
-            load_slab(0);
-            for (int g = 0; g < ngroups && ok; ++g) {
-                const int pi = g / NKC, ch = g % NKC;
-                const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
-                bool next_issued = false;
-#pragma unroll
-                for (int d = 0; d < 27; ++d) {
-                    const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                    const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
-                    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                    if (!first_round && !tc::mbar_wait(t_empty + stage, ephase, kWaitLimit)) {
-                        ok = false;
-                        break;
-                    }
-                    const int op = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
-                    tc::mbar_arrive_expect_tx(t_full + stage, kTcTBytes);
-                    tc::bulk_g2s(tring + (size_t)stage * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
-                                 kTcTBytes, t_full + stage);  // hi (+ lo) operator chunk
-                    ++t_issued;
-                    if (++stage == kTcStages) {
-                        stage = 0;
-                        if (!first_round) ephase ^= 1u;
-                        first_round = false;
-                    }
-                    if (!next_issued && g + 1 < ngroups) {  // prefetch the next group's slab
+            __syncwarp();
+            if (lane < 3 * kTcKG) {  // one (cell, delta_x range) per lane
+                const int kg = lane / 3, q = lane % 3;
+                const int rsq = r0 + (q - 1) * m2 * m2 - hal;
+                const int rlq = min(kTcRows + 2 * hal, R - rsq);
+                const long e = (((long)pi * NKG + ch * kTcKG + kg) * R + rsq) * 4;
+                uint8_t* dq = dst + (size_t)kg * kg_stride + (size_t)q * slab_rows * 16;
+                tc::bulk_g2s(dq, Mlev + e, (uint32_t)rlq * 16u, slab_full + buf);
+                if (SPLIT) tc::bulk_g2s(dq + part_bytes, Mlev_lo + e, (uint32_t)rlq * 16u, slab_full + buf);
+            }
+            ++slabs_issued;
+        };
+        int base_stage = 0, base_round = 0;  // ring position of chunk t_issued
+        bool ok = true;
+        load_slab(0);
+        for (int g = 0; g < ngroups && ok; ++g) {
+            const int pi = g / NKC, ch = g % NKC;
+            // the valid shifts of this (target class, source class), in ascending order
+            bool valid = false;
+            int op_d = 0;
+            if (lane < 27) {
+                const int ox = 2 * (lane / 9 - 1) + (pi & 1) - cx, oy = 2 * ((lane / 3) % 3 - 1) + ((pi >> 1) & 1) - cy,
+                          oz = 2 * (lane % 3 - 1) + ((pi >> 2) & 1) - cz;
+                valid = abs(ox) > 1 || abs(oy) > 1 || abs(oz) > 1;
+                op_d = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+            }
+            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+            const int cnt = __popc(vmask);
+            if (valid) sel[__popc(vmask & ((1u << lane) - 1u))] = op_d;
+            __syncwarp();
+            // The next group's slab goes into the buffer of group g - 1, free once that group's
+            // MMAs have completed: it is issued as soon as the buffer is free, tested (without
+            // blocking) between rounds, so that the ring keeps filling meanwhile.
+            bool next_issued = g + 1 >= ngroups;
+            const int gn = g + 1;
+            const uint32_t gn_parity = (uint32_t)(((gn >> 1) - 1) & 1);
+            for (int i0 = 0; i0 < cnt; i0 += per_round) {
+                if (!next_issued) {
+                    const bool freed =
+                        __shfl_sync(0xffffffffu, gn < 2 || (lane == 0 && tc::mbar_test_wait(slab_empty + (gn & 1), gn_parity)), 0);
+                    if (freed) {
                         next_issued = true;
-                        const int gn = g + 1;
-                        if (gn >= 2 && !tc::mbar_wait(slab_empty + (gn & 1), ((gn >> 1) - 1) & 1, kWaitLimit)) {
-                            ok = false;
-                            break;
-                        }
                         load_slab(gn);
                     }
                 }
+                const int nr = min(per_round, cnt - i0);
+                const bool mine = lane < nr;
+                int stage = base_stage + lane, round = base_round;
+                if (stage >= nstages) {
+                    stage -= nstages;
+                    ++round;
+                }
+                bool good = true;
+                if (mine && t_issued + lane >= nstages)  // the chunk nstages back has been consumed
+                    good = tc::mbar_wait(t_empty + stage, (uint32_t)((round - 1) & 1), kWaitLimit);
+                if (__ballot_sync(0xffffffffu, !good)) {
+                    ok = false;
+                    break;
+                }
+                if (mine) {
+                    const int op = sel[i0 + lane];
+                    tc::mbar_arrive_expect_tx(t_full + stage, kTcTBytes);
+                    tc::bulk_g2s(tring + (size_t)stage * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
+                                 kTcTBytes, t_full + stage);  // hi (+ lo) operator chunk
+                }
+                t_issued += nr;
+                base_stage += nr;
+                if (base_stage >= nstages) {
+                    base_stage -= nstages;
+                    ++base_round;
+                }
             }
+            __syncwarp();  // sel is rewritten by the next group
+            if (ok && !next_issued) {
+                const bool good = __shfl_sync(0xffffffffu, lane != 0 || tc::mbar_wait(slab_empty + (gn & 1), gn_parity, kWaitLimit), 0);
+                if (!good) {
+                    ok = false;
+                    break;
+                }
+                load_slab(gn);
+            }
+        }
+        if (lane == 0) {
             if (!ok) {
                 *abort_flag = 1;
                 atomicOr(status, FMM_DEV_TIMEOUT);
@@ -294,10 +342,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer ----------------
+        {
+            // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------
             // Lean loop: the 27 shifts are unrolled (constant delta), the ring position is a
-            // running counter, and the abort flag is only consulted when a wait expires.
+            // running counter, and the abort flag is only consulted when a wait expires.  Every
+            // lane runs the loop so that descriptors and counters stay warp-uniform.
             const uint32_t idesc = Cfg::kBf16 ? tc::idesc_bf16(128, kTcRows) : tc::idesc_tf32(128, kTcRows);
             // descriptors are built once and advanced by adding (byte offset >> 4) to the address field
             const uint64_t a_base = tc::smem_desc_kmajor(tc::smem_u32(tring), 2048u, 128u);
@@ -311,11 +360,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
                 const int ab = g & 1;
                 const uint32_t dacc = tmem + (uint32_t)(ab * kTcAccStride);
-                if (g >= 2 && !tc::mbar_wait(acc_empty + ab, ((g >> 1) - 1) & 1, kWaitLimit)) {
+                if (g >= 2 && !tc::mbar_wait_all(acc_empty + ab, ((g >> 1) - 1) & 1, kWaitLimit)) {
                     ok = false;
                     break;
                 }
-                if (!tc::mbar_wait(slab_full + buf, (g >> 1) & 1, kWaitLimit)) {
+                if (!tc::mbar_wait_all(slab_full + buf, (g >> 1) & 1, kWaitLimit)) {
                     ok = false;
                     break;
                 }
@@ -328,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
                     const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
                     if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                    if (!tc::mbar_wait(t_full + stage, tphase, kWaitLimit)) {
+                    if (!tc::mbar_wait_all(t_full + stage, tphase, kWaitLimit)) {
                         ok = false;
                         break;
                     }
@@ -340,34 +389,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const uint64_t ad = ad0 + (uint64_t)ks * (4096u >> 4);
                         const uint64_t bd = bd0 + (uint64_t)ks * ((2u * kg_stride) >> 4);
                         if (Cfg::kBf16) {  // 3xBF16: hi(T) hi(M) + hi(T) lo(M) + lo(T) hi(M)
-                            tc::mma_bf16(dacc, ad, bd, idesc, acc);
-                            tc::mma_bf16(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
-                            tc::mma_bf16(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
+                            tc::mma_bf16_w(dacc, ad, bd, idesc, acc);
+                            tc::mma_bf16_w(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
+                            tc::mma_bf16_w(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
                         } else {
-                            tc::mma_tf32(dacc, ad, bd, idesc, acc);
+                            tc::mma_tf32_w(dacc, ad, bd, idesc, acc);
                             if (SPLIT) {  // 3xTF32: + hi(T) lo(M) + lo(T) hi(M)
-                                tc::mma_tf32(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
-                                tc::mma_tf32(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
+                                tc::mma_tf32_w(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
+                                tc::mma_tf32_w(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
                             }
                         }
                         acc = 1;
                     }
-                    tc::mma_commit(t_empty + stage);
-                    if (++stage == kTcStages) {
+                    tc::mma_commit_w(t_empty + stage);
+                    if (++stage == nstages) {
                         stage = 0;
                         tphase ^= 1u;
                     }
                 }
-                tc::mma_commit(slab_empty + buf);
-                tc::mma_commit(acc_full + ab);  // this group's partial sum is complete
+                tc::mma_commit_w(slab_empty + buf);
+                tc::mma_commit_w(acc_full + ab);  // this group's partial sum is complete
             }
             if (!ok) {
-                *abort_flag = 1;
-                atomicOr(status, FMM_DEV_TIMEOUT);
-                for (int g2 = 0; g2 < 2; ++g2) tc::mma_commit(acc_full + g2);  // release the drains
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    atomicOr(status, FMM_DEV_TIMEOUT);
+                }
+                for (int g2 = 0; g2 < 2; ++g2) tc::mma_commit_w(acc_full + g2);  // release the drains
             }
-            copy_count[2] = t_taken;
-            copy_count[3] = slabs_taken;
+            if (lane == 0) {
+                copy_count[2] = t_taken;
+                copy_count[3] = slabs_taken;
+            }
         }
         __syncwarp();
     } else {
@@ -381,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bool ok = true;
         for (int grp = 0; grp < ngroups; ++grp) {
             const int ab = grp & 1;
-            if (!tc::mbar_wait(acc_full + ab, (grp >> 1) & 1, kWaitLimit) || *abort_flag) {
+            if (!tc::mbar_wait_backoff(acc_full + ab, (grp >> 1) & 1, kWaitLimit) || *abort_flag) {
                 ok = false;
                 break;
             }
@@ -419,9 +472,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     if (warp == 0 && lane == 0 && *abort_flag) {
         // copies issued but never consumed may still be landing in shared memory: wait for them
-        // (bounded) before the CTA exits; ring use j is stage j % 3 with phase parity (j / 3) & 1
+        // (bounded) before the CTA exits; ring use j is stage j % nstages with phase parity
+        // (j / nstages) & 1
         for (int j = copy_count[2]; j < copy_count[0]; ++j)
-            tc::mbar_wait(t_full + j % kTcStages, (uint32_t)((j / kTcStages) & 1), kWaitLimit);
+            tc::mbar_wait(t_full + j % nstages, (uint32_t)((j / nstages) & 1), kWaitLimit);
         for (int g = copy_count[3]; g < copy_count[1]; ++g)
             tc::mbar_wait(slab_full + (g & 1), (uint32_t)((g >> 1) & 1), kWaitLimit);
     }
@@ -442,6 +496,7 @@ struct TcState {
     int NKC = 0;
     int KG = 0;  // 16-byte cells per K chunk
     int slab_rows = 0;
+    int nstages = 0;  // operator ring depth
     size_t smem = 0;
     TcLevels lv{};
 };
@@ -511,20 +566,24 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     const int nc = h->nc, ncp = h->ncp, d = h->depth;
     st->mode = h->precision == FMM_MIXED_3XTF32 ? kTf32x3 : h->precision == FMM_MIXED_3XBF16 ? kBf16x3 : kTf32;
     int chunk = 0, nparts = 1;
+    uint32_t stage_bytes = 0;
     std::vector<uint8_t> T;
     switch (st->mode) {
         case kTf32x3:
             chunk = TcCfg<kTf32x3>::kChunk, st->KG = TcCfg<kTf32x3>::kKG, nparts = 2;
+            stage_bytes = TcCfg<kTf32x3>::kStageBytes;
             st->NKC = (ncp + chunk - 1) / chunk;
             pack_operators<kTf32x3>(T_rowmajor, nc, st->NKC, T);
             break;
         case kBf16x3:
             chunk = TcCfg<kBf16x3>::kChunk, st->KG = TcCfg<kBf16x3>::kKG, nparts = 2;
+            stage_bytes = TcCfg<kBf16x3>::kStageBytes;
             st->NKC = (ncp + chunk - 1) / chunk;
             pack_operators<kBf16x3>(T_rowmajor, nc, st->NKC, T);
             break;
         default:
             chunk = TcCfg<kTf32>::kChunk, st->KG = TcCfg<kTf32>::kKG, nparts = 1;
+            stage_bytes = TcCfg<kTf32>::kStageBytes;
             st->NKC = (ncp + chunk - 1) / chunk;
             pack_operators<kTf32>(T_rowmajor, nc, st->NKC, T);
     }
@@ -551,7 +610,12 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
             for (int r0 = S; r0 < R - S; r0 += kTcRows) tiles.push_back({l, c, r0, 0});
     }
     st->slab_rows = kTcRows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
-    st->smem = 2 * (size_t)3 * st->slab_rows * st->KG * 16 * nparts + (size_t)kTcStages * kTcTBytes + 256;
+    // two slab buffers, then as many ring stages as fit (at least 3), then barriers and flags
+    constexpr size_t kBarBytes = 1024;  // barriers, TMEM slot, flags, copy counts, rank table
+    const size_t slabs = 2 * (size_t)3 * st->slab_rows * st->KG * 16 * nparts;
+    const size_t room = 227 * 1024 > slabs + kBarBytes ? 227 * 1024 - slabs - kBarBytes : 0;
+    st->nstages = std::max(3, std::min(kTcMaxStages, (int)(room / stage_bytes)));
+    st->smem = slabs + (size_t)st->nstages * stage_bytes + kBarBytes;
     st->ntiles = (int)tiles.size();
     if (cudaMalloc(&st->Ttc, T.size()) != cudaSuccess ||
         cudaMalloc(&st->Mtc, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess ||
@@ -606,15 +670,15 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream) {
     switch (st->mode) {
         case kTf32x3:
             k_m2l_tc<kTf32x3><<<st->ntiles, kTcThreads, st->smem, stream>>>(
-                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, h->status);
+                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
             break;
         case kBf16x3:
             k_m2l_tc<kBf16x3><<<st->ntiles, kTcThreads, st->smem, stream>>>(
-                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, h->status);
+                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
             break;
         default:
             k_m2l_tc<kTf32><<<st->ntiles, kTcThreads, st->smem, stream>>>(
-                st->tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, h->status);
+                st->tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
     }
 }
 
