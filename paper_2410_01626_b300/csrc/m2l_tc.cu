@@ -384,24 +384,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     ++t_taken;
                     const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
                     const uint64_t bd0 = b_buf + (uint64_t)((dx + 1) * slab_rows + dy * m2 + dz);
+                    // the MMAs of this chunk, then the commit that releases its ring stage; one
+                    // elected lane issues each K step's products (hi(T) hi(M) + hi(T) lo(M) +
+                    // lo(T) hi(M) in the split forms)
 #pragma unroll
                     for (int ks = 0; ks < Cfg::kKSteps; ++ks) {  // 32 bytes of K = two cells per MMA
                         const uint64_t ad = ad0 + (uint64_t)ks * (4096u >> 4);
                         const uint64_t bd = bd0 + (uint64_t)ks * ((2u * kg_stride) >> 4);
-                        if (Cfg::kBf16) {  // 3xBF16: hi(T) hi(M) + hi(T) lo(M) + lo(T) hi(M)
-                            tc::mma_bf16_w(dacc, ad, bd, idesc, acc);
-                            tc::mma_bf16_w(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
-                            tc::mma_bf16_w(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
+                        const bool last_ks = ks == Cfg::kKSteps - 1;
+                        if (SPLIT) {
+                            if (last_ks)
+                                tc::mma3_w<Cfg::kBf16, true>(dacc, ad, bd, ad + (Cfg::kPartBytes >> 4),
+                                                             bd + (part_bytes >> 4), idesc, acc, t_empty + stage);
+                            else
+                                tc::mma3_w<Cfg::kBf16, false>(dacc, ad, bd, ad + (Cfg::kPartBytes >> 4),
+                                                              bd + (part_bytes >> 4), idesc, acc, nullptr);
                         } else {
-                            tc::mma_tf32_w(dacc, ad, bd, idesc, acc);
-                            if (SPLIT) {  // 3xTF32: + hi(T) lo(M) + lo(T) hi(M)
-                                tc::mma_tf32_w(dacc, ad, bd + (part_bytes >> 4), idesc, 1);
-                                tc::mma_tf32_w(dacc, ad + (Cfg::kPartBytes >> 4), bd, idesc, 1);
-                            }
+                            if (last_ks)
+                                tc::mma1_tf32_w<true>(dacc, ad, bd, idesc, acc, t_empty + stage);
+                            else
+                                tc::mma1_tf32_w<false>(dacc, ad, bd, idesc, acc, nullptr);
                         }
                         acc = 1;
                     }
-                    tc::mma_commit_w(t_empty + stage);
                     if (++stage == nstages) {
                         stage = 0;
                         tphase ^= 1u;

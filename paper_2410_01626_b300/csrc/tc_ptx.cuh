@@ -146,6 +146,69 @@ __device__ __forceinline__ void mma_commit_w(uint64_t* bar) {
         : "memory");
 }
 
+// One K step of a split product (hi*hi + hi*lo + lo*hi) into D, all three MMAs issued by one
+// elected lane of the warp, optionally followed by a commit to `bar`: one election per K step
+// keeps the issuing loop short enough for the tensor pipe never to wait on it (N = 192).
+template <bool BF16, bool COMMIT>
+__device__ __forceinline__ void mma3_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint64_t alo, uint64_t blo,
+                                       uint32_t idesc, uint32_t accumulate, uint64_t* bar) {
+    if (BF16) {
+        if (COMMIT)
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %5, p;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, 1;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %2, %5, 1;\n"
+                " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%7];\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "l"(alo), "l"(blo), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
+                : "memory");
+        else
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %5, p;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, 1;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %2, %5, 1;\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "l"(alo), "l"(blo), "r"(idesc), "r"(accumulate)
+                : "memory");
+    } else {
+        if (COMMIT)
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %5, p;\n"
+                " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %4, %5, 1;\n"
+                " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %3, %2, %5, 1;\n"
+                " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%7];\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "l"(alo), "l"(blo), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
+                : "memory");
+        else
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %5, p;\n"
+                " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %4, %5, 1;\n"
+                " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %3, %2, %5, 1;\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "l"(alo), "l"(blo), "r"(idesc), "r"(accumulate)
+                : "memory");
+    }
+}
+// One TF32 MMA by one elected lane, optionally followed by a commit to `bar`.
+template <bool COMMIT>
+__device__ __forceinline__ void mma1_tf32_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate,
+                                            uint64_t* bar) {
+    if (COMMIT)
+        asm volatile(
+            "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%5];\n}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+
 // 32 lanes x 32 bits, 16 consecutive columns per thread: thread t of warp w reads
 // TMEM lane (32 w + t), columns [col, col + 16).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
