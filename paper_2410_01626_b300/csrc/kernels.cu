@@ -160,19 +160,28 @@ __global__ void k_bin_count(int n, const float* __restrict__ x, BoxGeom g, uint3
 }
 
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 16;  // leaf counts per thread and pass: 16,384 per pass, all loads in flight
 __global__ void __launch_bounds__(kScanThreads) k_bin_scan(int nleaf, uint32_t* __restrict__ leafcnt,
                                                            uint32_t* __restrict__ start, uint32_t* __restrict__ count) {
     __shared__ uint32_t wsum[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t carry = 0;
-    for (int base = 0; base < nleaf; base += 4 * kScanThreads) {
-        uint32_t v[4], tot = 0;
+    for (int base = 0; base < nleaf; base += kScanPer * kScanThreads) {
+        const int l0 = base + kScanPer * t;
+        const bool whole = l0 + kScanPer <= nleaf;  // l0 is a multiple of 16: aligned vector access
+        uint32_t v[kScanPer], tot = 0;
+        if (whole) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int l = base + 4 * t + e;
-            v[e] = l < nleaf ? leafcnt[l] : 0u;
-            tot += v[e];
+            for (int e = 0; e < kScanPer; e += 4) {
+                const uint4 q = *reinterpret_cast<const uint4*>(leafcnt + l0 + e);
+                v[e] = q.x, v[e + 1] = q.y, v[e + 2] = q.z, v[e + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < kScanPer; ++e) v[e] = l0 + e < nleaf ? leafcnt[l0 + e] : 0u;
         }
+#pragma unroll
+        for (int e = 0; e < kScanPer; ++e) tot += v[e];
         uint32_t x = tot;  // inclusive scan of the thread totals
 #pragma unroll
         for (int k = 1; k < 32; k <<= 1) {
@@ -192,15 +201,28 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_scan(int nleaf, uint32_t* 
         }
         __syncthreads();
         uint32_t run = carry + x - tot + (w > 0 ? wsum[w - 1] : 0u);
+        uint32_t st[kScanPer];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int l = base + 4 * t + e;
-            if (l < nleaf) {
-                start[l] = run;
-                count[l] = v[e];
-                leafcnt[l] = 0u;
-            }
+        for (int e = 0; e < kScanPer; ++e) {
+            st[e] = run;
             run += v[e];
+        }
+        if (whole) {
+#pragma unroll
+            for (int e = 0; e < kScanPer; e += 4) {
+                *reinterpret_cast<uint4*>(start + l0 + e) = make_uint4(st[e], st[e + 1], st[e + 2], st[e + 3]);
+                *reinterpret_cast<uint4*>(count + l0 + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                *reinterpret_cast<uint4*>(leafcnt + l0 + e) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < kScanPer; ++e) {
+                if (l0 + e < nleaf) {
+                    start[l0 + e] = st[e];
+                    count[l0 + e] = v[e];
+                    leafcnt[l0 + e] = 0u;
+                }
+            }
         }
         carry += wsum[31];
         __syncthreads();
@@ -1481,6 +1503,14 @@ static void configure_p2m() {
 
 void configure_kernels(int p) { FMM_DISPATCH_P(p, configure_p2m); }
 
+// K slices for a split-K translation whose output is tree level l: the work buffer holds
+// 8^d ncp floats, so at most 8^(d-l) slices of that level's output fit; at most `want`.
+static inline int split_slices(int d, int l, int want) {
+    long cap = 1;
+    for (int i = l; i < d && cap < want; ++i) cap *= 8;
+    return (int)std::min<long>(cap, want);
+}
+
 int launches_per_eval(const Handle* h) {
     const int d = h->depth;
     int n = 4 /*count, scan, place, order+gather*/ + 1 /*p2m*/;
@@ -1488,7 +1518,10 @@ int launches_per_eval(const Handle* h) {
     if (d >= lmin) n += 2 * (d - lmin);  // M2M parent levels d-1 .. lmin (split-K product + sum)
     if (h->periodic) n += 3;       // Q/D/T partials + root + lattice
     if (d >= lmin) n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? m2l_tc_launches(h) : 1;  // M2L
-    if (d >= lmin) n += d - lmin + (h->periodic ? 1 : 0);  // L2L
+    if (d >= lmin) {  // L2L: coarse levels split over K (product + sum), the finest level in place
+        const int lfirst = h->periodic ? 1 : lmin + 1;
+        for (int l = lfirst; l <= d; ++l) n += (h->l2l_tc.dev && split_slices(d, l, 8) > 1) ? 2 : 1;
+    }
     n += 1 /*p2p*/ + 1 /*far field + outputs*/ + 1 /*final*/;
     if (h->hamiltonian && h->K > 0) n += 1;  // intra-site correction
     return n;
@@ -1557,9 +1590,9 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lmin = h->periodic ? 1 : 2;
     for (int l = d - 1; l >= lmin; --l) {
         const int np = 1 << (3 * l);
-        if (h->m2m_tc.dev)
+        if (h->m2m_tc.dev)  // split K by child octant; coarse levels into up to 32 slices (their latency)
             translate_tc(h->m2m_tc, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, np, h->M + h->lvl_off[l] * h->ncp,
-                         h->ncp, false, h->status, cs, 8, h->work);  // split K by child octant
+                         h->ncp, false, h->status, cs, split_slices(d, l, 32), h->work);
         else
             sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
                   h->M + h->lvl_off[l] * h->ncp, h->ncp, false, cs, 8, h->work);  // split K by child octant
@@ -1593,9 +1626,9 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lfirst = h->periodic ? 1 : lmin + 1;
     for (int l = lfirst; l <= d; ++l) {
         const int np = 1 << (3 * (l - 1));
-        if (h->l2l_tc.dev)
+        if (h->l2l_tc.dev)  // coarse levels split over K (one chunk per block), summed in a fixed order
             translate_tc(h->l2l_tc, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, np, h->L + h->lvl_off[l] * h->ncp,
-                         8 * h->ncp, true, h->status, cs);
+                         8 * h->ncp, true, h->status, cs, split_slices(d, l, 8), h->work);
         else
             sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
                   h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, cs);
