@@ -81,7 +81,16 @@ __device__ __forceinline__ uint32_t spread3_tc(uint32_t v) {
     return v;
 }
 
-// Pack one level's multipoles into [class][cell][(n+2)^3 rows][16 bytes].  TF32 forms: a cell
+// The levels packed by one launch: level i covers threads first[i] .. first[i + 1] - 1.
+struct PackLevels {
+    int nlev;
+    int n[kMaxDepth + 1], R[kMaxDepth + 1];
+    long first[kMaxDepth + 2];
+    long m_off[kMaxDepth + 1];  // float offset of the level in M
+    long t_off[kMaxDepth + 1];  // float offset of the level in the packed arrays
+};
+
+// Pack every level's multipoles into [class][cell][(n+2)^3 rows][16 bytes] (one launch).  TF32 forms: a cell
 // holds 4 coefficients rounded to TF32 (round to nearest: the tensor core itself would
 // truncate), and the lo part is the TF32 rounding of the remainder.  BF16 form: a cell holds
 // 8 coefficients rounded to BF16 (nearest even), lo = BF16 rounding of the remainder.
@@ -93,11 +102,17 @@ __device__ __forceinline__ float bf16_lo_of(uint32_t pair) { return __uint_as_fl
 __device__ __forceinline__ float bf16_hi_of(uint32_t pair) { return __uint_as_float(pair & 0xFFFF0000u); }
 
 template <bool BF16>
-__global__ void k_m2l_pack(int n, int R, int NKG, int ncp, int periodic, const float* __restrict__ Mlev,
-                           float* __restrict__ Mtc, float* __restrict__ Mtc_lo) {
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long total = 8L * NKG * R;
-    if (tid >= total) return;
+__global__ void k_m2l_pack(PackLevels pl, int NKG, int ncp, int periodic, const float* __restrict__ M,
+                           float* __restrict__ Mtc_all, float* __restrict__ Mtc_lo_all) {
+    const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= pl.first[pl.nlev]) return;
+    int lv = 0;
+    while (lv + 1 < pl.nlev && gt >= pl.first[lv + 1]) ++lv;
+    const long tid = gt - pl.first[lv];
+    const int n = pl.n[lv], R = pl.R[lv];
+    const float* Mlev = M + pl.m_off[lv];
+    float* Mtc = Mtc_all + pl.t_off[lv];
+    float* Mtc_lo = Mtc_lo_all ? Mtc_lo_all + pl.t_off[lv] : nullptr;
     const int row = (int)(tid % R);
     const int g = (int)((tid / R) % NKG);
     const int cls = (int)(tid / ((long)R * NKG));
@@ -653,23 +668,31 @@ void m2l_tc_free(Handle* h) {
 }
 
 int m2l_tc_launches(const Handle* h) {
-    return (h->depth - h->lmin + 1) + 1;  // one pack per level + the MMA kernel
+    return 2;  // the pack of every level + the MMA kernel
 }
 
 void launch_m2l_tc(Handle* h, cudaStream_t stream) {
     TcState* st = tc_state(h);
     const int NKG = st->NKC * st->KG;
     const bool bf16 = st->mode == kBf16x3;
+    PackLevels pl{};
+    long tot = 0;
     for (int l = h->lmin; l <= h->depth; ++l) {
-        const long total = 8L * NKG * st->lv.R[l];
-        const unsigned grid = (unsigned)((total + 255) / 256);
-        float* lo = st->Mtc_lo ? st->Mtc_lo + st->lv.mtc_off[l] : nullptr;
+        const int i = pl.nlev++;
+        pl.n[i] = st->lv.n[l];
+        pl.R[i] = st->lv.R[l];
+        pl.first[i] = tot;
+        pl.m_off[i] = h->lvl_off[l] * h->ncp;
+        pl.t_off[i] = st->lv.mtc_off[l];
+        tot += 8L * NKG * st->lv.R[l];
+    }
+    pl.first[pl.nlev] = tot;
+    if (tot > 0) {
+        const unsigned grid = (unsigned)((tot + 255) / 256);
         if (bf16)
-            k_m2l_pack<true><<<grid, 256, 0, stream>>>(st->lv.n[l], st->lv.R[l], NKG, h->ncp, h->periodic,
-                                                       h->M + h->lvl_off[l] * h->ncp, st->Mtc + st->lv.mtc_off[l], lo);
+            k_m2l_pack<true><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
         else
-            k_m2l_pack<false><<<grid, 256, 0, stream>>>(st->lv.n[l], st->lv.R[l], NKG, h->ncp, h->periodic,
-                                                        h->M + h->lvl_off[l] * h->ncp, st->Mtc + st->lv.mtc_off[l], lo);
+            k_m2l_pack<false><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
     }
     if (st->ntiles == 0) return;
     switch (st->mode) {
