@@ -100,6 +100,15 @@ struct Handle {
     // the multipole chain runs on `chain` (highest priority) while the near field runs on the
     // caller's stream; fork/join by events
     cudaStream_t chain = nullptr;
+    // one evaluation as a CUDA graph (fmm_eval, fmm_eval_host): captured on `gcap` the second time
+    // in a row the same buffers come, replayed on the caller's stream while they and the handle's
+    // launch state (generation `gen`, bumped by every call that changes it) stay the same
+    cudaStream_t gcap = nullptr;
+    cudaGraphExec_t g_exec = nullptr;
+    const void* g_key[5]{};
+    const void* g_last[5]{};
+    unsigned long long gen = 0, g_key_gen = 0, g_last_gen = ~0ull;
+    bool g_off = false;  // a capture failed once: evaluations stay eager launches
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // host staging for fmm_eval_host
     float* hx_dev = nullptr;
