@@ -153,12 +153,23 @@ fmm_status fmm_bind_lambda(fmm_handle* h, const float* lambda);
  *   phi:        [n_atoms] float, k_e * potential at each atom (kJ/mol/e),
  *               input order (may be NULL)
  * Stream-ordered; all outputs are complete when the stream reaches the end
- * of the call.  Returns FMM_ERR_STATE before fmm_set_charges. */
+ * of the call.  Returns FMM_ERR_STATE before fmm_set_charges.
+ * The second call in a row with the same five pointers captures the
+ * evaluation into a CUDA graph owned by the handle (on a private stream) and
+ * later calls with those pointers replay it on `stream`; the kernels and the
+ * results are those of launching them one by one.  The graph reads the
+ * buffers at replay, so positions and lambda written in place (or with
+ * fmm_set_lambda) are seen; fmm_set_charges*, fmm_bind_lambda and
+ * fmm_set_profiling discard it.  While profiling, or when `stream` is being
+ * captured by the caller, the kernels are launched one by one (and so join
+ * the caller's capture). */
 fmm_status fmm_eval(fmm_handle* h, const float* x, double* E, float* F, float* dVdlambda,
                     float* phi, void* stream);
 
 /* The same evaluation with HOST buffers: copies x_host to the device, runs
- * fmm_eval and copies E, F and dV/dlambda back, then synchronises `stream`.
+ * fmm_eval (on the handle's own device staging buffers, so from the second
+ * call on as a graph replay) and copies E, F and dV/dlambda back, then
+ * synchronises `stream`.
  * For page-locked host buffers the copies are asynchronous DMA.  Any output
  * pointer may be NULL. */
 fmm_status fmm_eval_host(fmm_handle* h, const float* x_host, double* E_host, float* F_host,
