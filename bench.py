@@ -118,8 +118,8 @@ class ClockSampler:
 # from an ncu capture of the tensor-core kernel built from the source with this sha1; reported
 # only while the source is unchanged.
 NCU_M2L_TRAFFIC = {
-    "sha1": "b7a2461489f7dd9af90dcbe45223250f81a79186",
-    "3xbf16": 51_291_392 + 3_089_152,
+    "sha1": "91d2733486dbb110376ad1c8b5787ee0f89fdbc1",
+    "3xbf16": 50_605_312 + 2_625_536,  # the launch of the two finest levels (256 tiles)
 }
 
 
@@ -380,7 +380,11 @@ def run_native(args):
     # roofline of the dominant kernel (M2L), live from the stage events
     peaks = load_peaks()
     nc = (s["p"] + 1) ** 2
-    boxes = sum(8 ** l for l in range(1, s["depth"] + 1))
+    # the M2L launch the "m2l" stage times: every level, or with the tensor-core M2L the two
+    # finest levels (the coarse levels then run on a side branch beside it)
+    split = stages.get("m2l_coarse", 0.0) > 0.0
+    lev = range(s["depth"] - 1, s["depth"] + 1) if split else range(1, s["depth"] + 1)
+    boxes = sum(8 ** l for l in lev)
     m2l_flop = boxes * 189 * 2 * nc * nc
     m2l_ms = stages.get("m2l", float("nan"))
     achieved = m2l_flop / (m2l_ms * 1e-3) / 1e12
@@ -405,7 +409,7 @@ def run_native(args):
         roof["pipe_flop_per_launch"] = executed
         roof["pipe_frac"] = executed / (m2l_ms * 1e-3) / 1e12 / peak
     roof["traffic"] = m2l_traffic(precision)
-    roof["kernel"] = "M2L"
+    roof["kernel"] = "M2L, levels %d..%d" % (lev[0], lev[-1])
     roof["flop_per_launch"] = m2l_flop
     roof["ms_per_launch"] = m2l_ms
 

@@ -224,13 +224,27 @@ fmm_status fmm_get_binning(fmm_handle* h, uint32_t* key, uint32_t* perm, uint32_
 fmm_status fmm_status_word(fmm_handle* h, int* device_status, void* stream);
 
 /* Per-stage device times of the last fmm_eval when profiling is enabled
- * (CUDA events between the stages): ms[0..n) = binning, P2M, M2M, lattice,
- * M2L, L2L, outputs (the wait for the near field, then L2P, F, phi and the
- * energy partials), final reduction -- consecutive intervals -- and, as
- * ms[8], the near field (P2P), which runs on the eval's stream concurrently
- * with P2M .. L2L (those run on an internal stream of the handle, forked from
- * and joined back to the eval's stream, so graph capture of fmm_eval works).
- * Synchronises.  Returns the number of stages written (at most 9). */
+ * (CUDA events; profiling mode launches kernel by kernel).  ms[0..n):
+ *   0 binning, 1 P2M, 2 M2M: consecutive, from the start of the evaluation;
+ *   3 root: the periodic root multipole, lattice operator and Q/D/T sums;
+ *   4 M2L: the M2L of the levels on the internal chain stream (pack + MMA
+ *     kernel; with the side branch below, the MMA kernel of the two finest
+ *     levels only, after their pack and the wait for the near field);
+ *   5 L2L: the L2L into the levels after the M2L of ms[4] (with the side
+ *     branch, the wait for it and the L2L into the two finest levels);
+ *   6 outputs: the wait for the chain, then L2P, F, phi, energy partials;
+ *   7 final: E and dV/dlambda;
+ *   8 near field (P2P): from the end of binning, on the eval's stream,
+ *     concurrently with P2M .. M2M;
+ *   9, 10: with the tensor-core M2L and tree levels below the two finest,
+ *     a side branch forked after the M2M runs the M2L of those coarse levels
+ *     (ms[9]: the MMA kernel, after their pack and the wait for the near
+ *     field), then the root (ms[3]) and the L2L into the coarse levels
+ *     (ms[10]), concurrently with ms[4]; 0 without it.
+ * The chain and the side branch run on internal streams of the handle,
+ * forked from and joined back to the eval's stream, so graph capture of
+ * fmm_eval works.  Synchronises.  Returns the number of stages written (at
+ * most 11). */
 int fmm_stage_times(fmm_handle* h, float* ms, int n);
 fmm_status fmm_set_profiling(fmm_handle* h, int enable);
 

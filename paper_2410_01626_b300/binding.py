@@ -24,9 +24,10 @@ PRECISIONS = {"fp32": FMM_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF
 INTERPOLATIONS = {"charge": 0, "hamiltonian": 1}
 DEV_DOMAIN, DEV_SITE, DEV_TIMEOUT = 1, 2, 4
 KE_DEFAULT = 138.935458
-# consecutive stages of one evaluation, then the near field, which runs on the caller's stream
-# concurrently with the chain p2m .. l2l ("outputs" includes the wait for it)
-STAGES = ("binning", "p2m", "m2m", "root", "m2l", "l2l", "outputs", "final", "p2p")
+# stage intervals of one evaluation (fmm_stage_times): the chain binning .. final, the near field
+# ("p2p", concurrent with p2m .. m2m), and the coarse levels' M2L and L2L, which run on a side
+# branch beside the finest levels' M2L (0 where an evaluation has no such branch)
+STAGES = ("binning", "p2m", "m2m", "root", "m2l", "l2l", "outputs", "final", "p2p", "m2l_coarse", "l2l_coarse")
 
 
 class FmmBox(ctypes.Structure):

@@ -105,14 +105,18 @@ void free_all(Handle& h) {
     dfree(h.hE_dev);
     if (h.ev_valid) {
         for (auto& e : h.ev) cudaEventDestroy(e);
-        for (auto& e : h.ev_p2p) cudaEventDestroy(e);
     }
     h.ev_valid = false;
     if (h.fork_ev) cudaEventDestroy(h.fork_ev);
     if (h.join_ev) cudaEventDestroy(h.join_ev);
+    for (cudaEvent_t* e : {&h.m2m_ev, &h.p2p_ev, &h.side_ev}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
     if (h.chain) cudaStreamDestroy(h.chain);
+    if (h.side) cudaStreamDestroy(h.side);
     h.fork_ev = h.join_ev = nullptr;
-    h.chain = nullptr;
+    h.chain = h.side = nullptr;
     if (h.g_exec) cudaGraphExecDestroy(h.g_exec);
     if (h.gcap) cudaStreamDestroy(h.gcap);
     h.g_exec = nullptr;
@@ -367,15 +371,18 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     cudaMemset(h.root, 0, sizeof(double) * (nc + kRootDoubles));
     cudaMemset(h.site_ptr, 0, sizeof(int));
     for (auto& e : h.ev) cudaEventCreate(&e);
-    for (auto& e : h.ev_p2p) cudaEventCreate(&e);
     h.ev_valid = true;
     {
         int least = 0, greatest = 0;
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (cudaStreamCreateWithPriority(&h.chain, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&h.side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaStreamCreateWithFlags(&h.gcap, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.m2m_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.p2p_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.side_ev, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             free_all(h);
             delete H;
@@ -697,16 +704,15 @@ fmm_status fmm_set_profiling(fmm_handle* H, int enable) {
 int fmm_stage_times(fmm_handle* H, float* ms, int n) {
     if (!H || !ms || !H->h.profiling) return 0;
     Handle& h = H->h;
-    if (cudaEventSynchronize(h.ev[kNumStages - 1]) != cudaSuccess) {
+    if (h.ev_used <= 0 || cudaEventSynchronize(h.ev[h.ev_used - 1]) != cudaSuccess) {  // the last one recorded
         cudaGetLastError();
         return 0;
     }
     int k = 0;
     for (; k < n && k < kNumStages; ++k) {
         float t = 0.f;
-        const cudaError_t r = k < kNumStages - 1 ? cudaEventElapsedTime(&t, h.ev[k], h.ev[k + 1])
-                                                 : cudaEventElapsedTime(&t, h.ev_p2p[0], h.ev_p2p[1]);
-        if (r != cudaSuccess) {
+        const int a = h.stage_ev[k][0], b = h.stage_ev[k][1];
+        if (a >= 0 && b >= 0 && cudaEventElapsedTime(&t, h.ev[a], h.ev[b]) != cudaSuccess) {
             cudaGetLastError();
             t = -1.f;
         }

@@ -13,7 +13,8 @@ constexpr int kMaxDepth = 7;
 constexpr int kLeafMomStride = 8;  // floats per leaf in Handle::leafmom
 constexpr int kRootDoubles = 8 + 5 * 64 + 4 + 40;  // Handle::root beyond nc: Q D T, k_qdt partials, FP32 copies, k_final totals + ticket
 constexpr int kNumOps = 343;  // M2L offsets o in {-3..3}^3 (the inner 27 slots unused)
-constexpr int kNumStages = 9;  // 8 consecutive stage intervals, then the near field on the side branch
+constexpr int kNumStages = 11;  // the stage intervals fmm_stage_times reports
+constexpr int kNumEvents = 24;  // profiling: timing events recorded per evaluation
 
 inline int ncoef(int p) { return (p + 1) * (p + 1); }
 inline int ncoef_padded(int p) { return (ncoef(p) + 15) / 16 * 16; }
@@ -94,12 +95,17 @@ struct Handle {
     bool charges_set = false;
     // profiling
     bool profiling = false;
-    cudaEvent_t ev[kNumStages + 1]{};  // ev[0..8]: boundaries of the 8 consecutive stages (ev[9] unused)
-    cudaEvent_t ev_p2p[2]{};           // the near field on the caller's stream, concurrent with the chain
+    cudaEvent_t ev[kNumEvents]{};  // a pool of timing events, taken in launch order
+    int ev_used = 0;
+    int stage_ev[kNumStages][2]{};  // per stage: the pool events that bracket it, -1 if not run
     bool ev_valid = false;
     // the multipole chain runs on `chain` (highest priority) while the near field runs on the
-    // caller's stream; fork/join by events
+    // caller's stream; fork/join by events.  With the tensor-core M2L and coarse levels below
+    // the two finest, `side` (also highest priority) takes the coarse levels' M2L, the periodic
+    // root and the coarse levels' L2L, concurrently with the finest levels' M2L on `chain`.
     cudaStream_t chain = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t m2m_ev = nullptr, p2p_ev = nullptr, side_ev = nullptr;
     // one evaluation as a CUDA graph (fmm_eval, fmm_eval_host): captured on `gcap` the second time
     // in a row the same buffers come, replayed on the caller's stream while they and the handle's
     // launch state (generation `gen`, bumped by every call that changes it) stay the same
@@ -140,6 +146,9 @@ bool m2l_tc_supported(const Handle* h);
 int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor);  // [343][nc][nc], output-major
 void m2l_tc_free(Handle* h);
 int m2l_tc_launches(const Handle* h);
-void launch_m2l_tc(Handle* h, cudaStream_t st);
+// the M2L of tree levels lo .. hi (clamped to the handle's levels): the pack of their
+// multipoles (kM2lPack), then the MMA kernel over their tiles (kM2lMma)
+constexpr int kM2lPack = 1, kM2lMma = 2;
+void launch_m2l_tc(Handle* h, cudaStream_t st, int lo, int hi, int parts = kM2lPack | kM2lMma);
 
 }  // namespace fmmcph

@@ -1511,13 +1511,45 @@ static inline int split_slices(int d, int l, int want) {
     return (int)std::min<long>(cap, want);
 }
 
+// profiling: record the next pool event on `st` and return its index (-1 when not profiling)
+static inline int mark(Handle* h, cudaStream_t st) {
+    if (!h->profiling || h->ev_used >= kNumEvents) return -1;
+    cudaEventRecord(h->ev[h->ev_used], st);
+    return h->ev_used++;
+}
+static inline void span(Handle* h, int k, int a, int b) {
+    h->stage_ev[k][0] = a;
+    h->stage_ev[k][1] = b;
+}
+
+// L2L into tree level l from level l - 1, added to the M2L result already there
+static void l2l_level(Handle* h, int l, cudaStream_t st) {
+    const int np = 1 << (3 * (l - 1));
+    if (h->l2l_tc.dev)  // coarse levels split over K (one chunk per block), summed in a fixed order
+        translate_tc(h->l2l_tc, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, np, h->L + h->lvl_off[l] * h->ncp,
+                     8 * h->ncp, true, h->status, st, split_slices(h->depth, l, 8), h->work);
+    else
+        sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
+              h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, st);
+}
+
+// The coarse levels (lmin .. depth - 2) get their own branch when the M2L runs on the tensor
+// cores: their M2L, the periodic root and their L2L run on `side` concurrently with the M2L of
+// the two finest levels, which dominates; only the L2L into the two finest levels follows it.
+static inline int coarse_top(const Handle* h) {
+    const int lmin = h->periodic ? 1 : 2;
+    const bool tc = h->precision != FMM_FP32 && m2l_tc_supported(h) && h->ntiles > 0;
+    return (tc && h->depth - 2 >= lmin) ? h->depth - 2 : -1;
+}
+
 int launches_per_eval(const Handle* h) {
     const int d = h->depth;
     int n = 4 /*count, scan, place, order+gather*/ + 1 /*p2m*/;
     const int lmin = h->periodic ? 1 : 2;
     if (d >= lmin) n += 2 * (d - lmin);  // M2M parent levels d-1 .. lmin (split-K product + sum)
     if (h->periodic) n += 3;       // Q/D/T partials + root + lattice
-    if (d >= lmin) n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? m2l_tc_launches(h) : 1;  // M2L
+    if (d >= lmin)  // M2L: the coarse and the finest levels in two launches when split
+        n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? (coarse_top(h) >= 0 ? 2 : 1) * m2l_tc_launches(h) : 1;
     if (d >= lmin) {  // L2L: coarse levels split over K (product + sum), the finest level in place
         const int lfirst = h->periodic ? 1 : lmin + 1;
         for (int l = lfirst; l <= d; ++l) n += (h->l2l_tc.dev && split_slices(d, l, 8) > 1) ? 2 : 1;
@@ -1530,17 +1562,15 @@ int launches_per_eval(const Handle* h) {
 // FP32 copies of c2 (Q, D, T) for the per-atom correction, after the FP64 totals and partials
 static inline float* qdt_float(Handle* h) { return reinterpret_cast<float*>(h->root + h->nc + 8 + 5 * kQdtBlocks); }
 
-static inline void stage(Handle* h, int i, cudaStream_t st) {
-    if (h->profiling) cudaEventRecord(h->ev[i], st);
-}
-
 int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, float* phi, cudaStream_t st) {
     const int n = h->n, d = h->depth, nb = 1 << d;
     const int nleaf = 1 << (3 * d);
     const float hleaf = (float)(h->box.edge / nb);
     BoxGeom g{h->box.origin[0], h->box.origin[1], h->box.origin[2], h->box.edge, h->s_bin, nb, d, h->periodic};
     const float* lam = h->lam_bound ? h->lam_bound : h->lam;
-    stage(h, 0, st);
+    h->ev_used = 0;
+    for (auto& se : h->stage_ev) se[0] = se[1] = -1;
+    const int e0 = mark(h, st);
     // --- binning: counting sort by leaf (see k_bin_count .. k_bin_order_gather) ---
     if (n > 0) k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(n, x, g, h->key, h->vA, h->leafcnt, h->status);
     k_bin_scan<<<1, kScanThreads, 0, st>>>(nleaf, h->leafcnt, h->start, h->count);
@@ -1572,19 +1602,22 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.phi_out = phi;
     a.phis = h->phis;
     a.epart = h->epart;
-    stage(h, 1, st);
+    const int e1 = mark(h, st);
+    span(h, 0, e0, e1);
     // fork: the chain P2M .. L2L on h->chain (highest priority), P2P here
     cudaStream_t cs = h->chain;
+    const int lc = coarse_top(h);  // top coarse level of the side branch, -1 without one
     cudaEventRecord(h->fork_ev, st);
     cudaStreamWaitEvent(cs, h->fork_ev, 0);
-    if (h->profiling) cudaEventRecord(h->ev_p2p[0], st);
     k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, h->near);
-    if (h->profiling) cudaEventRecord(h->ev_p2p[1], st);
+    span(h, 8, e1, mark(h, st));
+    if (lc >= 0) cudaEventRecord(h->p2p_ev, st);
         // --- P2M ---
     float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
     float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
     FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, h, Mleaf, h->periodic ? h->leafmom : nullptr, cs);
-    stage(h, 2, cs);
+    const int e2 = mark(h, cs);
+    span(h, 1, e1, e2);
     // --- M2M (FP32) for parent levels d-1 .. lmin: one GEMM per level,
     //     [parents x 8 ncp] (the 8 children are contiguous) x [8 ncp x ncp] ---
     const int lmin = h->periodic ? 1 : 2;
@@ -1597,43 +1630,72 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
             sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
                   h->M + h->lvl_off[l] * h->ncp, h->ncp, false, cs, 8, h->work);  // split K by child octant
     }
-    stage(h, 3, cs);
-    // --- periodic root (FP64) ---
-    if (h->periodic) {
+    const int e3 = mark(h, cs);
+    span(h, 2, e2, e3);
+    // --- periodic root (FP64): root multipole, lattice operator, Q/D/T for the background term ---
+    auto root = [&](cudaStream_t rs) {
+        if (!h->periodic) return;
         const int nrowblk = (h->nc + 3) / 4;
         const float* M1 = (d >= 1) ? h->M + h->lvl_off[1] * h->ncp : nullptr;
-        k_qdt<<<kQdtBlocks, 256, 0, cs>>>(nleaf, h->box.edge / nb, 0.5 * h->box.edge, h->leafmom, h->root + h->nc + 8);
-        k_root<<<nrowblk, 128, 0, cs>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, h->root);
-        k_lattice<<<(h->ncp + 3) / 4, 128, 0, cs>>>(h->nc, h->ncp, h->Lam, h->root, h->L,
+        k_qdt<<<kQdtBlocks, 256, 0, rs>>>(nleaf, h->box.edge / nb, 0.5 * h->box.edge, h->leafmom, h->root + h->nc + 8);
+        k_root<<<nrowblk, 128, 0, rs>>>(h->nc, h->ncp, d, h->Ad, M1, h->M, h->root);
+        k_lattice<<<(h->ncp + 3) / 4, 128, 0, rs>>>(h->nc, h->ncp, h->Lam, h->root, h->L,
                                                      2.0 * M_PI / (3.0 * h->box.edge * h->box.edge * h->box.edge),
                                                      qdt_float(h));
-    }
-    stage(h, 4, cs);
-    // --- M2L ---
-    if (d >= lmin && h->ntiles > 0) {
-        if (h->precision != FMM_FP32 && m2l_tc_supported(h)) {
-            launch_m2l_tc(h, cs);
-        } else {
-            LevelOffsets lo{};
-            for (int l = 0; l <= d; ++l) lo.off[l] = h->lvl_off[l];
-            k_m2l_fp32<<<h->ntiles, h->ncp, sizeof(float) * kM2LTB * h->ncp, cs>>>(
-                h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
-        }
-    }
-    stage(h, 5, cs);
-    // --- L2L: levels lmin+1 .. d (periodic: 1 .. d from the lattice-filled root): one GEMM per
-    //     level, [parents x ncp] x [ncp x 8 ncp] accumulated into the contiguous children ---
+    };
+    // L2L: levels lmin+1 .. d (periodic: 1 .. d from the lattice-filled root)
     const int lfirst = h->periodic ? 1 : lmin + 1;
-    for (int l = lfirst; l <= d; ++l) {
-        const int np = 1 << (3 * (l - 1));
-        if (h->l2l_tc.dev)  // coarse levels split over K (one chunk per block), summed in a fixed order
-            translate_tc(h->l2l_tc, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, np, h->L + h->lvl_off[l] * h->ncp,
-                         8 * h->ncp, true, h->status, cs, split_slices(d, l, 8), h->work);
-        else
-            sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
-                  h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, cs);
+    if (lc >= 0) {
+        // Side branch: the coarse levels' pack and M2L, the root, the coarse levels' L2L.  Their
+        // M2L writes only levels lmin .. lc of L, the root only level 0, and the split-K work
+        // buffer of their L2L is free: the M2M has finished and the chain's L2L waits for this.
+        // Both M2L launches wait for the near field: their CTAs take whole SMs, so one started
+        // earlier would only slow the near field down, and a near field left waiting behind
+        // them would finish last.  The coarse one is issued first, so that its few CTAs run in
+        // the first wave and the root and L2L after them fit beside the finest levels' tiles.
+        cudaStream_t ss = h->side;
+        cudaEventRecord(h->m2m_ev, cs);
+        cudaStreamWaitEvent(ss, h->m2m_ev, 0);
+        launch_m2l_tc(h, ss, lmin, lc, kM2lPack);
+        launch_m2l_tc(h, cs, lc + 1, d, kM2lPack);
+        const int s0 = mark(h, ss);
+        launch_m2l_tc(h, ss, lmin, lc, kM2lMma);
+        const int s1 = mark(h, ss);
+        span(h, 9, s0, s1);
+        root(ss);
+        const int s2 = mark(h, ss);
+        span(h, 3, s1, s2);
+        for (int l = lfirst; l <= lc; ++l) l2l_level(h, l, ss);
+        span(h, 10, s2, mark(h, ss));
+        cudaEventRecord(h->side_ev, ss);
+        // chain: the finest levels' M2L, then the L2L into them from the side branch's levels
+        const int e4 = mark(h, cs);
+        launch_m2l_tc(h, cs, lc + 1, d, kM2lMma);
+        const int e5 = mark(h, cs);
+        span(h, 4, e4, e5);
+        cudaStreamWaitEvent(cs, h->side_ev, 0);
+        for (int l = std::max(lfirst, lc + 1); l <= d; ++l) l2l_level(h, l, cs);
+        span(h, 5, e5, mark(h, cs));
+    } else {
+        root(cs);
+        const int e4 = mark(h, cs);
+        span(h, 3, e3, e4);
+        if (d >= lmin && h->ntiles > 0) {
+            if (h->precision != FMM_FP32 && m2l_tc_supported(h)) {
+                launch_m2l_tc(h, cs, lmin, d);
+            } else {
+                LevelOffsets lo{};
+                for (int l = 0; l <= d; ++l) lo.off[l] = h->lvl_off[l];
+                k_m2l_fp32<<<h->ntiles, h->ncp, sizeof(float) * kM2LTB * h->ncp, cs>>>(
+                    h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
+            }
+        }
+        const int e5 = mark(h, cs);
+        span(h, 4, e4, e5);
+        for (int l = lfirst; l <= d; ++l) l2l_level(h, l, cs);
+        span(h, 5, e5, mark(h, cs));
     }
-    stage(h, 6, cs);
+    const int e6 = h->stage_ev[5][1];
     // join, then the far field and the outputs per atom
     cudaEventRecord(h->join_ev, cs);
     cudaStreamWaitEvent(st, h->join_ev, 0);
@@ -1662,13 +1724,14 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         hp.g_h = h->hi_g;
         FMM_DISPATCH_P(h->p, launch_hi, hp, st);
     }
-    stage(h, 7, st);
+    const int e7 = mark(h, st);
+    span(h, 6, e6, e7);
     const int nparts = (n + kOutThreads - 1) / kOutThreads;  // one q phi partial per output block
     double* fin = h->root + h->nc + 8 + 5 * kQdtBlocks + 4;  // [kFinalBlocks] block totals, then the ticket
     k_final<<<kFinalBlocks, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->ncoord, h->site_ptr, h->site_atoms,
                                           h->inv, h->dq, h->dqt, h->phis, dVdl, fin,
                                           reinterpret_cast<unsigned int*>(fin + kFinalBlocks), hi ? h->hi_site : nullptr);
-    stage(h, 8, st);
+    span(h, 7, e7, mark(h, st));
     return 0;
 }
 

@@ -513,6 +513,7 @@ struct TcState {
     float* Ttc = nullptr;
     TcTile* tiles = nullptr;
     int ntiles = 0;
+    int tile_first[kMaxDepth + 2] = {};  // the tiles of level l are [tile_first[l], tile_first[l + 1])
     int NKC = 0;
     int KG = 0;  // 16-byte cells per K chunk
     int slab_rows = 0;
@@ -616,7 +617,9 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
         st->lv.l_off[l] = 0;
     }
     std::vector<TcTile> tiles;
+    for (int l = 0; l <= kMaxDepth + 1; ++l) st->tile_first[l] = 0;
     for (int l = h->lmin; l <= d; ++l) {
+        st->tile_first[l] = (int)tiles.size();
         const int n = 1 << (l - 1);
         const int R = (n + 2) * (n + 2) * (n + 2);
         const int S = dmax_shift(n);
@@ -629,6 +632,7 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
         for (int c = 0; c < 8; ++c)
             for (int r0 = S; r0 < R - S; r0 += kTcRows) tiles.push_back({l, c, r0, 0});
     }
+    for (int l = d + 1; l <= kMaxDepth + 1; ++l) st->tile_first[l] = (int)tiles.size();
     st->slab_rows = kTcRows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
     // two slab buffers, then as many ring stages as fit (at least 3), then barriers and flags
     constexpr size_t kBarBytes = 1024;  // barriers, TMEM slot, flags, copy counts, rank table
@@ -668,16 +672,19 @@ void m2l_tc_free(Handle* h) {
 }
 
 int m2l_tc_launches(const Handle* h) {
-    return 2;  // the pack of every level + the MMA kernel
+    return 2;  // per call of launch_m2l_tc: the pack of its levels + the MMA kernel
 }
 
-void launch_m2l_tc(Handle* h, cudaStream_t stream) {
+void launch_m2l_tc(Handle* h, cudaStream_t stream, int lo, int hi, int parts) {
     TcState* st = tc_state(h);
     const int NKG = st->NKC * st->KG;
     const bool bf16 = st->mode == kBf16x3;
+    lo = std::max(lo, h->lmin);
+    hi = std::min(hi, h->depth);
+    if (lo > hi) return;
     PackLevels pl{};
     long tot = 0;
-    for (int l = h->lmin; l <= h->depth; ++l) {
+    for (int l = lo; l <= hi; ++l) {
         const int i = pl.nlev++;
         pl.n[i] = st->lv.n[l];
         pl.R[i] = st->lv.R[l];
@@ -687,26 +694,28 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream) {
         tot += 8L * NKG * st->lv.R[l];
     }
     pl.first[pl.nlev] = tot;
-    if (tot > 0) {
+    if (tot > 0 && (parts & kM2lPack)) {
         const unsigned grid = (unsigned)((tot + 255) / 256);
         if (bf16)
             k_m2l_pack<true><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
         else
             k_m2l_pack<false><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
     }
-    if (st->ntiles == 0) return;
+    const int t0 = st->tile_first[lo], nt = st->tile_first[hi + 1] - t0;
+    if (nt <= 0 || !(parts & kM2lMma)) return;
+    const TcTile* tiles = st->tiles + t0;
     switch (st->mode) {
         case kTf32x3:
-            k_m2l_tc<kTf32x3><<<st->ntiles, kTcThreads, st->smem, stream>>>(
-                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
+            k_m2l_tc<kTf32x3><<<nt, kTcThreads, st->smem, stream>>>(
+                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
             break;
         case kBf16x3:
-            k_m2l_tc<kBf16x3><<<st->ntiles, kTcThreads, st->smem, stream>>>(
-                st->tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
+            k_m2l_tc<kBf16x3><<<nt, kTcThreads, st->smem, stream>>>(
+                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
             break;
         default:
-            k_m2l_tc<kTf32><<<st->ntiles, kTcThreads, st->smem, stream>>>(
-                st->tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
+            k_m2l_tc<kTf32><<<nt, kTcThreads, st->smem, stream>>>(
+                tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
     }
 }
 
