@@ -273,7 +273,6 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         return FMM_ERR_ARG;
     }
     upload_constants(p);
-    configure_kernels(p);
 
     const int nc = h.nc, ncp = h.ncp;
     fmm_status st = FMM_OK;
@@ -353,7 +352,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     const long nleaf = 1L << (3 * depth);
     if ((st = dalloc(&h.M, (size_t)acc * ncp)) || (st = dalloc(&h.L, (size_t)acc * ncp)) ||
         (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.start, nleaf)) ||
-        (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.leafcnt, nleaf)) || (st = dalloc(&h.epart, nleaf)) ||
+        (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.leafcnt, leafcnt_words(nleaf))) || (st = dalloc(&h.epart, nleaf)) ||
         (st = dalloc(&h.leafmom, (long)kLeafMomStride * nleaf)) || (st = dalloc(&h.root, nc + kRootDoubles)) || (st = dalloc(&h.status, 1)) ||
         (st = dalloc(&h.site_ptr, 1)) ||
         (st = dalloc(&h.work, 8L * (depth >= 1 ? (1L << (3 * (depth - 1))) : 1) * ncp))) {
@@ -367,7 +366,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     cudaMemset(h.M, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.L, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.status, 0, sizeof(int));
-    cudaMemset(h.leafcnt, 0, sizeof(uint32_t) * nleaf);
+    cudaMemset(h.leafcnt, 0, sizeof(uint32_t) * leafcnt_words(nleaf));
     cudaMemset(h.root, 0, sizeof(double) * (nc + kRootDoubles));
     cudaMemset(h.site_ptr, 0, sizeof(int));
     for (auto& e : h.ev) cudaEventCreate(&e);

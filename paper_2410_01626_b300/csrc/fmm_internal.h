@@ -74,7 +74,7 @@ struct Handle {
     uint32_t *key = nullptr, *kA = nullptr, *kB = nullptr, *vA = nullptr, *vB = nullptr;
     uint32_t *perm = nullptr, *inv = nullptr, *sorted_key = nullptr;
     uint32_t *start = nullptr, *count = nullptr;
-    uint32_t* leafcnt = nullptr;  // [nleaf] per-leaf counters of the binning step, zero between calls
+    uint32_t* leafcnt = nullptr;  // [leafcnt_words(nleaf)] per-leaf, then per-tile counters of the binning step, zero between calls
     float4* pos = nullptr;
     float* dq = nullptr;
     float* phis = nullptr;   // sorted-order potential (without k_e)
@@ -128,9 +128,9 @@ struct Handle {
 
 // kernels.cu
 void upload_constants(int p);
-void configure_kernels(int p);  // per-kernel launch attributes for expansion degree p
 int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, float* phi,
                 cudaStream_t st);
+int leafcnt_words(int nleaf);  // the binning's counters: one per leaf, one per scan tile
 int launches_per_eval(const Handle* h);
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi,
                     const float* dVdl, float* gx, float* const* gq /*[4] forms, may be null*/, float* glam,

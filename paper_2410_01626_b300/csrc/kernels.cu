@@ -1,14 +1,16 @@
 // CUDA kernels of one FMM evaluation (sm_103a).
 //
-// Stages (all on the caller's stream):
+// Stages (launch_eval at the end of this file places them on the caller's stream and on the
+// handle's chain and side streams):
 //   binning   k_bin_count -> k_bin_scan -> k_bin_place -> k_bin_order_gather (counting sort by leaf)
 //             (Morton keys of the leaf cells, stable on (key, index); the gather also forms
 //             q_i = qA_i + lambda_s (qB_i - qA_i), Sec. 2.1 Eq. 1 with charge-only forms)
-//   P2M       k_p2m<P>        one block per 8 sibling leaves: per-atom harmonics in shared memory, fixed-order leaf sums
-//   M2M       k_sgemm         per level, one dense GEMM over the 8 contiguous children
-//   root      k_root, k_lattice (periodic) FP64 root multipole and lattice operator
+//   P2M       k_p2m<P>        32 leaves per block, two column sets x two atom parities per leaf, sums in registers
+//   M2M       k_translate_tc  per level, one product over the 8 contiguous children (translate_tc.cu;
+//                             FP32 SGEMM in the FP32 mode)
+//   root      k_qdt, k_root, k_lattice (periodic) FP64 root multipole, lattice operator, Q/D/T
 //   M2L       k_m2l_fp32 (FP32 CUDA cores) or the tcgen05 kernel in m2l_tc.cu
-//   L2L       k_sgemm         per level, one dense GEMM into the 8 contiguous children
+//   L2L       k_translate_tc  per level, one product into the 8 contiguous children (as M2M)
 //   outputs   k_far_out<P>    far field per atom (L2P + periodic background term) + near field -> F, phi, E partials
 //             k_p2p           P2P over the 27 neighbour leaves + forces / potential / energy
 //   final     k_final         E (FP64, fixed-order reduction) and dV/dlambda per site
@@ -143,95 +145,120 @@ __global__ void k_keys(int n, const float* __restrict__ x, BoxGeom g, uint32_t* 
 
 // ---- binning as a counting sort by leaf ----
 // (1) k_bin_count: key of every atom and a claim on a slot of its leaf (atomic, so the slot
-//     order inside a leaf is arbitrary); (2) k_bin_scan: exclusive scan of the leaf counts ->
-//     start, count (and the counters are cleared for the next call); (3) k_bin_place: atom i
-//     goes to start[key] + slot; (4) k_bin_order_gather: one warp per leaf puts the leaf's
-//     atoms in ascending input index -- exactly the order of a stable sort on (key, index) --
-//     and gathers positions and charges in that order.
-__global__ void k_bin_count(int n, const float* __restrict__ x, BoxGeom g, uint32_t* __restrict__ key,
-                            uint32_t* __restrict__ slot, uint32_t* __restrict__ leafcnt, int* __restrict__ status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    bool bad = false;
-    const uint32_t k = leaf_key(x, i, g, bad);
-    key[i] = k;
-    slot[i] = atomicAdd(leafcnt + k, 1u);
-    if (bad) atomicOr(status, FMM_DEV_DOMAIN);
+//     order inside a leaf is arbitrary), and the atom counts of tiles of kScanTile leaves
+//     (a block histogram in shared memory, then one atomic per tile and block); (2) k_bin_scan,
+//     one block per tile: the tile's offset is the sum of the tile counts before it, then an
+//     exclusive scan of its leaf counts -> start, count (and the counters are cleared for the
+//     next call); (3) k_bin_place: atom i goes to start[key] + slot, and the tile counts are
+//     cleared; (4) k_bin_order_gather: one warp per leaf puts the leaf's atoms in ascending
+//     input index -- exactly the order of a stable sort on (key, index) -- and gathers positions
+//     and charges in that order.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 16;                          // leaf counts per thread, vector loads
+constexpr int kScanTile = kScanThreads * kScanPer;    // leaves per scan block
+constexpr int kMaxScanTiles = (1 << (3 * kMaxDepth)) / kScanTile;
+constexpr int kCountThreads = 256;
+
+inline int scan_tiles(int nleaf) { return (nleaf + kScanTile - 1) / kScanTile; }
+int leafcnt_words(int nleaf) { return nleaf + scan_tiles(nleaf); }
+
+__global__ void __launch_bounds__(kCountThreads) k_bin_count(int n, const float* __restrict__ x, BoxGeom g,
+                                                             uint32_t* __restrict__ key, uint32_t* __restrict__ slot,
+                                                             uint32_t* __restrict__ leafcnt, int ntiles,
+                                                             uint32_t* __restrict__ tilecnt,
+                                                             int* __restrict__ status) {
+    __shared__ uint32_t hist[kMaxScanTiles];
+    for (int t = threadIdx.x; t < ntiles; t += kCountThreads) hist[t] = 0u;
+    __syncthreads();
+    const int i = blockIdx.x * kCountThreads + threadIdx.x;
+    if (i < n) {
+        bool bad = false;
+        const uint32_t k = leaf_key(x, i, g, bad);
+        key[i] = k;
+        slot[i] = atomicAdd(leafcnt + k, 1u);
+        if (ntiles > 1) atomicAdd(hist + k / kScanTile, 1u);
+        if (bad) atomicOr(status, FMM_DEV_DOMAIN);
+    }
+    if (ntiles > 1) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < ntiles; t += kCountThreads)
+            if (hist[t]) atomicAdd(tilecnt + t, hist[t]);
+    }
 }
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 16;  // leaf counts per thread and pass: 16,384 per pass, all loads in flight
 __global__ void __launch_bounds__(kScanThreads) k_bin_scan(int nleaf, uint32_t* __restrict__ leafcnt,
+                                                           const uint32_t* __restrict__ tilecnt,
                                                            uint32_t* __restrict__ start, uint32_t* __restrict__ count) {
-    __shared__ uint32_t wsum[32];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    uint32_t carry = 0;
-    for (int base = 0; base < nleaf; base += kScanPer * kScanThreads) {
-        const int l0 = base + kScanPer * t;
-        const bool whole = l0 + kScanPer <= nleaf;  // l0 is a multiple of 16: aligned vector access
-        uint32_t v[kScanPer], tot = 0;
-        if (whole) {
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    __shared__ uint32_t wpre[kScanThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, b = blockIdx.x;
+    // the leaves before this tile: the sum of the tile counts before it (integers: any order)
+    uint32_t pre = 0;
+    for (int i = t; i < b; i += kScanThreads) pre += tilecnt[i];
 #pragma unroll
-            for (int e = 0; e < kScanPer; e += 4) {
-                const uint4 q = *reinterpret_cast<const uint4*>(leafcnt + l0 + e);
-                v[e] = q.x, v[e + 1] = q.y, v[e + 2] = q.z, v[e + 3] = q.w;
-            }
-        } else {
+    for (int k = 16; k >= 1; k >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, k);
+    if (lane == 0) wpre[w] = pre;
+    const int l0 = b * kScanTile + kScanPer * t;
+    const bool whole = l0 + kScanPer <= nleaf;  // l0 is a multiple of 16: aligned vector access
+    uint32_t v[kScanPer], tot = 0;
+    if (whole) {
 #pragma unroll
-            for (int e = 0; e < kScanPer; ++e) v[e] = l0 + e < nleaf ? leafcnt[l0 + e] : 0u;
+        for (int e = 0; e < kScanPer; e += 4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(leafcnt + l0 + e);
+            v[e] = q.x, v[e + 1] = q.y, v[e + 2] = q.z, v[e + 3] = q.w;
         }
+    } else {
 #pragma unroll
-        for (int e = 0; e < kScanPer; ++e) tot += v[e];
-        uint32_t x = tot;  // inclusive scan of the thread totals
+        for (int e = 0; e < kScanPer; ++e) v[e] = l0 + e < nleaf ? leafcnt[l0 + e] : 0u;
+    }
 #pragma unroll
-        for (int k = 1; k < 32; k <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, k);
-            if (lane >= k) x += y;
+    for (int e = 0; e < kScanPer; ++e) tot += v[e];
+    uint32_t x = tot;  // inclusive scan of the thread totals
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, k);
+        if (lane >= k) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t base = 0;
+#pragma unroll
+    for (int j = 0; j < kScanThreads / 32; ++j) {
+        base += wpre[j];
+        if (j < w) base += wsum[j];
+    }
+    uint32_t run = base + x - tot;
+    uint32_t st[kScanPer];
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e) {
+        st[e] = run;
+        run += v[e];
+    }
+    if (whole) {
+#pragma unroll
+        for (int e = 0; e < kScanPer; e += 4) {
+            *reinterpret_cast<uint4*>(start + l0 + e) = make_uint4(st[e], st[e + 1], st[e + 2], st[e + 3]);
+            *reinterpret_cast<uint4*>(count + l0 + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            *reinterpret_cast<uint4*>(leafcnt + l0 + e) = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t z = wsum[lane];
-#pragma unroll
-            for (int k = 1; k < 32; k <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, z, k);
-                if (lane >= k) z += y;
-            }
-            wsum[lane] = z;
-        }
-        __syncthreads();
-        uint32_t run = carry + x - tot + (w > 0 ? wsum[w - 1] : 0u);
-        uint32_t st[kScanPer];
+    } else {
 #pragma unroll
         for (int e = 0; e < kScanPer; ++e) {
-            st[e] = run;
-            run += v[e];
-        }
-        if (whole) {
-#pragma unroll
-            for (int e = 0; e < kScanPer; e += 4) {
-                *reinterpret_cast<uint4*>(start + l0 + e) = make_uint4(st[e], st[e + 1], st[e + 2], st[e + 3]);
-                *reinterpret_cast<uint4*>(count + l0 + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-                *reinterpret_cast<uint4*>(leafcnt + l0 + e) = make_uint4(0u, 0u, 0u, 0u);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < kScanPer; ++e) {
-                if (l0 + e < nleaf) {
-                    start[l0 + e] = st[e];
-                    count[l0 + e] = v[e];
-                    leafcnt[l0 + e] = 0u;
-                }
+            if (l0 + e < nleaf) {
+                start[l0 + e] = st[e];
+                count[l0 + e] = v[e];
+                leafcnt[l0 + e] = 0u;
             }
         }
-        carry += wsum[31];
-        __syncthreads();
     }
 }
 
 __global__ void k_bin_place(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
-                            const uint32_t* __restrict__ start, uint32_t* __restrict__ placed) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+                            const uint32_t* __restrict__ start, uint32_t* __restrict__ placed, int ntiles,
+                            uint32_t* __restrict__ tilecnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0)  // every k_bin_scan block has read them
+        for (int t = threadIdx.x; t < ntiles; t += blockDim.x) tilecnt[t] = 0u;
     if (i >= n) return;
     placed[start[key[i]] + slot[i]] = (uint32_t)i;
 }
@@ -516,29 +543,25 @@ __device__ __forceinline__ void regular_harmonics_cols(float x, float y, float z
     }
 }
 
-// P2M, one 256-thread block per 8 consecutive leaves (the children of one parent, whose atoms
-// are contiguous in leaf order).  Atoms are taken 128 at a time.  For atom t of the chunk,
-// thread t (warps 0-3) writes q R_hat_n^m(u) for the columns m < MS and thread 128 + t (warps
-// 4-7) the columns m >= MS plus the atom's moments, into shared memory (row stride NC rounded
-// up to odd, so the column writes are conflict free); the two halves cost about the same.
-// Then thread t sums "virtual coefficient" v = t % 128 (+ 128, ...) over the atoms of leaves
-// 4 (t / 128) .. +3 in order: v < NC is a multipole coefficient, v = NC + k (k < kMom) is
-// moment k of the leaf for the periodic correction, about the leaf centre: q_hi, q_lo
-// (q_hi = q rounded to a multiple of 2^-11, so the FP32 sum of q_hi is exact and
-// Q = sum q_hi + sum q_lo is good to FP64 level), q dx, q dy, q dz, q |d|^2.  k_qdt turns them
-// into Q, D, T about the box centre in FP64 with all lanes busy: this GPU's FP64 pipe is
-// narrow, so no FP64 instruction runs per atom or per leaf thread.  Every sum runs in a fixed
-// order, so the result is deterministic.
-constexpr int kP2mThreads = 256;
-constexpr int kP2mChunk = 128;
-constexpr int kP2mLeaves = 8;
+// P2M: M_b = sum over the leaf's atoms of q R_hat_n^m(u), u = (x - c_b) / h, with the
+// normalised regular harmonics of the recurrence above, every sum in registers.  A block takes
+// 32 leaves: warps 0-1 the columns m < MS and warps 2-3 the columns m >= MS of the recurrence
+// (warp-uniform, so the two column sets never diverge in a warp; MS balances their cost, the
+// diagonal chain to MS - 1 included).  Within a warp, lanes 2k and 2k+1 share leaf k of the
+// warp's 16: lane 2k sums over the leaf's even atoms and lane 2k+1 over its odd atoms, each in
+// order; one shuffle adds the two (a + b: the same value in both lanes), and the two lanes
+// write alternate coefficients.  With no shared memory, 20 warps per SM are resident at p = 10.
+// The warps of the columns m >= MS also sum the leaf's moments for the periodic correction,
+// about the leaf centre: q_hi, q_lo (q_hi = q rounded to a multiple of 2^-11, so the FP32 sum
+// of q_hi is exact and Q = sum q_hi + sum q_lo is good to FP64 level), q dx, q dy, q dz,
+// q |d|^2.  k_qdt turns them into Q, D, T about the box centre in FP64 with all lanes busy:
+// this GPU's FP64 pipe is narrow, so no FP64 instruction runs per atom or per leaf thread.
+// Every sum runs in a fixed order, so the result is deterministic.
 constexpr int kMom = 6;        // leaf moments for the periodic correction
 constexpr int kMomStride = kLeafMomStride;  // floats per leaf in the moment array
 template <int P>
 struct P2mCfg {
     static constexpr int NC = (P + 1) * (P + 1);
-    static constexpr int NCS = NC | 1;
-    static constexpr int kSlots = (NC + kMom + kP2mChunk - 1) / kP2mChunk;
     // column split: sum over m < MS of (P - m + 1), plus the chain to MS - 1, against the rest
     static constexpr int split() {
         int best = 1, bestd = 1 << 30;
@@ -554,106 +577,88 @@ struct P2mCfg {
         return best;
     }
     static constexpr int MS = P >= 1 ? split() : 1;
-    static constexpr size_t kSmem = sizeof(float) * kP2mChunk * (NCS + kMom);
 };
 
-template <int P>
-__global__ void __launch_bounds__(kP2mThreads) k_p2m(int nleaf, float h, const uint32_t* __restrict__ start,
-                                                     const uint32_t* __restrict__ count,
-                                                     const float4* __restrict__ pos, float* __restrict__ M,
-                                                     int ncp, float* __restrict__ leafmom) {
-    using Cfg = P2mCfg<P>;
-    constexpr int NC = Cfg::NC, NCS = Cfg::NCS, SL = Cfg::kSlots, MS = Cfg::MS;
-    constexpr int kLPT = kP2mLeaves / 2;  // leaves per reducing thread
-    extern __shared__ __align__(16) float p2m_smem[];
-    float* hsm = p2m_smem;                         // [chunk][NCS] harmonics
-    float* msm = p2m_smem + kP2mChunk * NCS;       // [kMom][chunk] moments
-    const int t = threadIdx.x;
-    const int L0 = blockIdx.x * kP2mLeaves;
-    const int nl = min(kP2mLeaves, nleaf - L0);
-    __shared__ int lo_s[kP2mLeaves], hi_s[kP2mLeaves];
-    if (t < kP2mLeaves) {
-        const int l = L0 + min(t, nl - 1);
-        lo_s[t] = t < nl ? (int)start[l] : 0;
-        hi_s[t] = t < nl ? (int)(start[l] + count[l]) : 0;
-    }
-    __syncthreads();
-    const int a0 = lo_s[0], a1 = hi_s[nl - 1];
-    const float ih = 1.0f / h;
-    const int role = t >> 7, ct = t & (kP2mChunk - 1);
-    const int jbase = role * kLPT;
-    float acc[SL][kLPT];
+constexpr int kP2mLeaves = 32;
+template <int P, int M0, int M1, class F>
+__device__ __forceinline__ void for_cols(F&& f) {  // the coefficient slots of columns M0 .. M1
 #pragma unroll
-    for (int j = 0; j < kLPT; ++j)
+    for (int m = M0; m <= M1; ++m)
 #pragma unroll
-        for (int c = 0; c < SL; ++c) acc[c][j] = 0.f;
-    for (int base = a0; base < a1; base += kP2mChunk) {
-        const int a = base + ct;
-        if (a < a1) {
-            const float4 p4 = pos[a];
-            int j = 0;  // the atom's leaf: the last k with lo_s[k] <= a (empty leaves share starts)
-#pragma unroll
-            for (int k = 1; k < kP2mLeaves; ++k)
-                if (k < nl && lo_s[k] <= a) j = k;
-            const uint32_t lf = (uint32_t)(L0 + j);
-            const float cx = (compact3(lf) + 0.5f) * h, cy = (compact3(lf >> 1) + 0.5f) * h,
-                        cz = (compact3(lf >> 2) + 0.5f) * h;
-            const float q = p4.w;
-            const float dx = p4.x - cx, dy = p4.y - cy, dz = p4.z - cz;
-            float* row = hsm + ct * NCS;
-            auto put = [&](int n, int m, float re, float im) {
-                if (m == 0) {
-                    row[n * n] = q * re;
-                } else {
-                    row[n * n + 2 * m - 1] = q * re;
-                    row[n * n + 2 * m] = -q * im;
-                }
-            };
-            if (role == 0) {
-                regular_harmonics_cols<P, 0, MS - 1>(dx * ih, dy * ih, dz * ih, put);
+        for (int n = m; n <= P; ++n) {
+            if (m == 0) {
+                f(n * n);
             } else {
-                regular_harmonics_cols<P, MS, P>(dx * ih, dy * ih, dz * ih, put);
-                const float qhi = rintf(q * 2048.f) * (1.f / 2048.f);
-                msm[0 * kP2mChunk + ct] = qhi;
-                msm[1 * kP2mChunk + ct] = q - qhi;
-                msm[2 * kP2mChunk + ct] = q * dx;
-                msm[3 * kP2mChunk + ct] = q * dy;
-                msm[4 * kP2mChunk + ct] = q * dz;
-                msm[5 * kP2mChunk + ct] = q * (dx * dx + dy * dy + dz * dz);
+                f(n * n + 2 * m - 1);
+                f(n * n + 2 * m);
             }
         }
-        __syncthreads();
-        const int top = min(a1, base + kP2mChunk);
-#pragma unroll
-        for (int c = 0; c < SL; ++c) {
-            const int v = ct + c * kP2mChunk;
-            if (v >= NC + (leafmom ? kMom : 0)) continue;
-            // coefficient v: column v of the harmonics rows; moment v - NC: its own row
-            const float* src = v < NC ? hsm + v : msm + (v - NC) * kP2mChunk;
-            const int stride = v < NC ? NCS : 1;
-#pragma unroll
-            for (int jj = 0; jj < kLPT; ++jj) {
-                const int j = jbase + jj;
-                const int s0 = max(lo_s[j], base), s1 = min(hi_s[j], top);
-                float sum = acc[c][jj];
-                for (int b = s0; b < s1; ++b) sum += src[(b - base) * stride];
-                acc[c][jj] = sum;
+}
+template <int P, int M0, int M1, bool MOM>
+__device__ __forceinline__ void p2m_leaf_cols(const float4* __restrict__ pos, int st, int cnt, int par, float cx,
+                                              float cy, float cz, float ih, float* acc, float* mom) {
+    for (int k = par; k < cnt; k += 2) {
+        const float4 p4 = pos[st + k];
+        const float q = p4.w, dx = p4.x - cx, dy = p4.y - cy, dz = p4.z - cz;
+        regular_harmonics_cols<P, M0, M1>(dx * ih, dy * ih, dz * ih, [&](int n, int m, float re, float im) {
+            if (m == 0) {
+                acc[n * n] = fmaf(q, re, acc[n * n]);
+            } else {
+                acc[n * n + 2 * m - 1] = fmaf(q, re, acc[n * n + 2 * m - 1]);
+                acc[n * n + 2 * m] = fmaf(-q, im, acc[n * n + 2 * m]);
             }
+        });
+        if (MOM) {
+            const float qhi = rintf(q * 2048.f) * (1.f / 2048.f);
+            mom[0] += qhi;
+            mom[1] += q - qhi;
+            mom[2] = fmaf(q, dx, mom[2]);
+            mom[3] = fmaf(q, dy, mom[3]);
+            mom[4] = fmaf(q, dz, mom[4]);
+            mom[5] = fmaf(q, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), mom[5]);
         }
-        __syncthreads();
     }
 #pragma unroll
-    for (int jj = 0; jj < kLPT; ++jj) {
-        const int j = jbase + jj;
-        if (j >= nl) break;
-        float* out = M + (long)(L0 + j) * ncp;
+    for (int i = 0; i < (MOM ? kMom : 0); ++i) mom[i] += __shfl_xor_sync(0xffffffffu, mom[i], 1);
+    for_cols<P, M0, M1>([&](int i) { acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 1); });
+}
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m(int nleaf, float h, const uint32_t* __restrict__ start,
+                                             const uint32_t* __restrict__ count, const float4* __restrict__ pos,
+                                             float* __restrict__ M, int ncp, float* __restrict__ leafmom) {
+    using Cfg = P2mCfg<P>;
+    constexpr int NC = Cfg::NC, MS = Cfg::MS;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int leaf = blockIdx.x * kP2mLeaves + (w & 1) * 16 + (lane >> 1);
+    const int par = lane & 1;
+    const bool valid = leaf < nleaf;
+    const int st = valid ? (int)start[leaf] : 0, cnt = valid ? (int)count[leaf] : 0;
+    const uint32_t lf = valid ? (uint32_t)leaf : 0u;
+    const float cx = (compact3(lf) + 0.5f) * h, cy = (compact3(lf >> 1) + 0.5f) * h,
+                cz = (compact3(lf >> 2) + 0.5f) * h;
+    const float ih = 1.0f / h;
+    float acc[NC];
 #pragma unroll
-        for (int c = 0; c < SL; ++c) {
-            const int v = ct + c * kP2mChunk;
-            if (v < NC) out[v] = acc[c][jj];
-            else if (leafmom && v < NC + kMom) leafmom[(long)(L0 + j) * kMomStride + (v - NC)] = acc[c][jj];
+    for (int i = 0; i < NC; ++i) acc[i] = 0.f;
+    float mom[kMom];
+#pragma unroll
+    for (int i = 0; i < kMom; ++i) mom[i] = 0.f;
+    float* out = M + (long)lf * ncp;
+    auto put = [&](int i) {  // the two lanes of a leaf write alternate slots
+        if (valid && (i & 1) == par) out[i] = acc[i];
+    };
+    if (w < 2) {
+        p2m_leaf_cols<P, 0, MS - 1, false>(pos, st, cnt, par, cx, cy, cz, ih, acc, mom);
+        for_cols<P, 0, MS - 1>(put);
+    } else {
+        p2m_leaf_cols<P, MS, P, true>(pos, st, cnt, par, cx, cy, cz, ih, acc, mom);
+        for_cols<P, MS, P>(put);
+        if (valid) {
+            for (int v = NC + par; v < ncp; v += 2) out[v] = 0.f;
+            if (leafmom && par == 0)
+#pragma unroll
+                for (int k = 0; k < kMom; ++k) leafmom[(long)lf * kMomStride + k] = mom[k];
         }
-        for (int v = NC + ct; v < ncp; v += kP2mChunk) out[v] = 0.f;
     }
 }
 
@@ -1465,8 +1470,8 @@ __global__ void k_adjoint(int n, int K, int ncoord, int nforms, const double* __
 template <int P>
 static void launch_p2m(int nleaf, float h, const Handle* hd, float* Mleaf, float* mom,
                        cudaStream_t st) {
-    k_p2m<P><<<(nleaf + kP2mLeaves - 1) / kP2mLeaves, kP2mThreads, P2mCfg<P>::kSmem, st>>>(
-        nleaf, h, hd->start, hd->count, hd->pos, Mleaf, hd->ncp, mom);
+    k_p2m<P><<<(nleaf + kP2mLeaves - 1) / kP2mLeaves, 128, 0, st>>>(nleaf, h, hd->start, hd->count, hd->pos,
+                                                                     Mleaf, hd->ncp, mom);
 }
 template <int P>
 static void launch_far_out(int n, int use_far, const NearParams& a, const uint32_t* skey, const float4* near,
@@ -1496,12 +1501,6 @@ static void launch_far_out(int n, int use_far, const NearParams& a, const uint32
 
 static inline int sort_passes(int depth) { return (3 * depth + 7) / 8; }
 
-template <int P>
-static void configure_p2m() {
-    cudaFuncSetAttribute(k_p2m<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P2mCfg<P>::kSmem);
-}
-
-void configure_kernels(int p) { FMM_DISPATCH_P(p, configure_p2m); }
 
 // K slices for a split-K translation whose output is tree level l: the work buffer holds
 // 8^d ncp floats, so at most 8^(d-l) slices of that level's output fit; at most `want`.
@@ -1572,12 +1571,16 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     for (auto& se : h->stage_ev) se[0] = se[1] = -1;
     const int e0 = mark(h, st);
     // --- binning: counting sort by leaf (see k_bin_count .. k_bin_order_gather) ---
-    if (n > 0) k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(n, x, g, h->key, h->vA, h->leafcnt, h->status);
-    k_bin_scan<<<1, kScanThreads, 0, st>>>(nleaf, h->leafcnt, h->start, h->count);
+    const int ntiles = scan_tiles(nleaf);
+    uint32_t* tilecnt = h->leafcnt + nleaf;  // [ntiles] atoms per tile of kScanTile leaves
+    if (n > 0)
+        k_bin_count<<<(n + kCountThreads - 1) / kCountThreads, kCountThreads, 0, st>>>(
+            n, x, g, h->key, h->vA, h->leafcnt, ntiles, tilecnt, h->status);
+    k_bin_scan<<<ntiles, kScanThreads, 0, st>>>(nleaf, h->leafcnt, tilecnt, h->start, h->count);
     h->perm = h->kA;
     h->sorted_key = h->kB;
     if (n > 0) {
-        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(n, h->key, h->vA, h->start, h->vB);
+        k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(n, h->key, h->vA, h->start, h->vB, ntiles, tilecnt);
         ChargeForms cf{{h->qA, h->qB, h->qC, h->qD}, h->nforms, h->site, h->K, lam, h->dq, h->dqt};
         k_bin_order_gather<<<(nleaf + 3) / 4, 128, 0, st>>>(nleaf, h->start, h->count, h->vB, h->perm,
                                                             h->sorted_key, x, g, cf, h->pos, h->inv, h->status);
