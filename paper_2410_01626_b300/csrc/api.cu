@@ -109,7 +109,7 @@ void free_all(Handle& h) {
     h.ev_valid = false;
     if (h.fork_ev) cudaEventDestroy(h.fork_ev);
     if (h.join_ev) cudaEventDestroy(h.join_ev);
-    for (cudaEvent_t* e : {&h.m2m_ev, &h.p2p_ev, &h.side_ev}) {
+    for (cudaEvent_t* e : {&h.m2m_ev, &h.side_ev}) {
         if (*e) cudaEventDestroy(*e);
         *e = nullptr;
     }
@@ -380,7 +380,6 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
             cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.m2m_ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h.p2p_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.side_ev, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             free_all(h);

@@ -105,7 +105,7 @@ struct Handle {
     // root and the coarse levels' L2L, concurrently with the finest levels' M2L on `chain`.
     cudaStream_t chain = nullptr;
     cudaStream_t side = nullptr;
-    cudaEvent_t m2m_ev = nullptr, p2p_ev = nullptr, side_ev = nullptr;
+    cudaEvent_t m2m_ev = nullptr, side_ev = nullptr;
     // one evaluation as a CUDA graph (fmm_eval, fmm_eval_host): captured on `gcap` the second time
     // in a row the same buffers come, replayed on the caller's stream while they and the handle's
     // launch state (generation `gen`, bumped by every call that changes it) stay the same

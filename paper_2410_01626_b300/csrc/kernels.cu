@@ -1614,7 +1614,6 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     cudaStreamWaitEvent(cs, h->fork_ev, 0);
     k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, h->near);
     span(h, 8, e1, mark(h, st));
-    if (lc >= 0) cudaEventRecord(h->p2p_ev, st);
         // --- P2M ---
     float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
     float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
@@ -1652,10 +1651,10 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         // Side branch: the coarse levels' pack and M2L, the root, the coarse levels' L2L.  Their
         // M2L writes only levels lmin .. lc of L, the root only level 0, and the split-K work
         // buffer of their L2L is free: the M2M has finished and the chain's L2L waits for this.
-        // Both M2L launches wait for the near field: their CTAs take whole SMs, so one started
-        // earlier would only slow the near field down, and a near field left waiting behind
-        // them would finish last.  The coarse one is issued first, so that its few CTAs run in
-        // the first wave and the root and L2L after them fit beside the finest levels' tiles.
+        // The coarse M2L is issued first, so that its few CTAs run in the first wave and the
+        // root and L2L after them fit beside the finest levels' tiles.  Neither M2L launch
+        // waits for the near field: their CTAs take the SMs the near field's blocks leave, and
+        // its remaining blocks run on the SMs the M2L's second wave leaves idle.
         cudaStream_t ss = h->side;
         cudaEventRecord(h->m2m_ev, cs);
         cudaStreamWaitEvent(ss, h->m2m_ev, 0);
