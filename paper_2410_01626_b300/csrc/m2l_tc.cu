@@ -473,16 +473,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (ok && !*abort_flag) {
             const int j = q * 32 + lane;  // output coefficient = TMEM lane
-            float* Ll = L + lv.l_off[lev] * (long)ncp;
+            float* Ll = L + lv.l_off[lev] * (long)ncp + j;
+            // grid position of this half's first row, then advanced row by row (an odometer)
+            const int rfirst = r0 + half * (kTcRows / 2);
+            int ip = rfirst / (m2 * m2), jp = (rfirst / m2) % m2, kp = rfirst % m2;
+            uint32_t mij = spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1);
 #pragma unroll
             for (int e = 0; e < kTcRows / 2; ++e) {
-                const int r = r0 + half * (kTcRows / 2) + e;
-                if (r >= R) continue;
-                const int ip = r / (m2 * m2), jp = (r / m2) % m2, kp = r % m2;
-                if (ip < 1 || ip > n || jp < 1 || jp > n || kp < 1 || kp > n) continue;
-                const uint32_t box =
-                    ((spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1) | (spread3_tc(kp - 1) << 2)) << 3) | (uint32_t)c;
-                if (j < ncp) Ll[(long)box * ncp + j] = sum[e];
+                if (rfirst + e < R && ip >= 1 && ip <= n && jp >= 1 && jp <= n && kp >= 1 && kp <= n && j < ncp) {
+                    const uint32_t box = ((mij | (spread3_tc(kp - 1) << 2)) << 3) | (uint32_t)c;
+                    Ll[(long)box * ncp] = sum[e];
+                }
+                if (++kp == m2) {
+                    kp = 0;
+                    if (++jp == m2) {
+                        jp = 0;
+                        ++ip;
+                    }
+                    mij = spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1);
+                }
             }
         } else if (lane == 0) {
             atomicOr(status, FMM_DEV_TIMEOUT);

@@ -83,6 +83,14 @@ def test_binning_large_stable():
     _binning_case(s, 5)
 
 
+@pytest.mark.parametrize("depth", [6, 7])
+def test_binning_bit_exact_deep_trees(depth):
+    """Deep trees: the leaf-count scan runs over many tiles (64 and 512 at depths 6 and 7),
+    most leaves empty; low p keeps the rest of the evaluation cheap."""
+    s = synth.open_uniform(seed=12, n=300000, L=4.0, n_sites=2, p=2, depth=depth)
+    _binning_case(s, depth)
+
+
 # ---------------------------------------------------------------- near field only
 @pytest.mark.parametrize("depth", [0, 1])
 def test_open_near_field_only_equals_direct_sum(depth):
