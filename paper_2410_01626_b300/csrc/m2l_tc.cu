@@ -472,25 +472,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lane == 0) tc::mbar_arrive(acc_empty + ab);
         }
         if (ok && !*abort_flag) {
+            // The 96 rows of this half go to their Morton boxes: first a table of the rows' box
+            // offsets in shared memory (the operator ring is idle: every MMA has completed), three
+            // rows per lane, then one store per row.  A fully unrolled loop doing the index
+            // arithmetic per row is long straight-line code that runs once per tile, mostly
+            // waiting for instruction fetch.
+            int* tab = reinterpret_cast<int*>(tring) + (warp - 2) * (kTcRows / 2);
+            const int rfirst = r0 + half * (kTcRows / 2);
+            for (int e = lane; e < kTcRows / 2; e += 32) {
+                const int r = rfirst + e;
+                const int ip = r / (m2 * m2), jp = (r / m2) % m2, kp = r % m2;
+                int off = -1;
+                if (r < R && ip >= 1 && ip <= n && jp >= 1 && jp <= n && kp >= 1 && kp <= n)
+                    off = (int)(((spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1) | (spread3_tc(kp - 1) << 2)) << 3) |
+                                (uint32_t)c) * ncp;
+                tab[e] = off;
+            }
+            __syncwarp();
             const int j = q * 32 + lane;  // output coefficient = TMEM lane
             float* Ll = L + lv.l_off[lev] * (long)ncp + j;
-            // grid position of this half's first row, then advanced row by row (an odometer)
-            const int rfirst = r0 + half * (kTcRows / 2);
-            int ip = rfirst / (m2 * m2), jp = (rfirst / m2) % m2, kp = rfirst % m2;
-            uint32_t mij = spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1);
+            if (j < ncp) {
 #pragma unroll
-            for (int e = 0; e < kTcRows / 2; ++e) {
-                if (rfirst + e < R && ip >= 1 && ip <= n && jp >= 1 && jp <= n && kp >= 1 && kp <= n && j < ncp) {
-                    const uint32_t box = ((mij | (spread3_tc(kp - 1) << 2)) << 3) | (uint32_t)c;
-                    Ll[(long)box * ncp] = sum[e];
-                }
-                if (++kp == m2) {
-                    kp = 0;
-                    if (++jp == m2) {
-                        jp = 0;
-                        ++ip;
-                    }
-                    mij = spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1);
+                for (int e = 0; e < kTcRows / 2; ++e) {
+                    const int off = tab[e];
+                    if (off >= 0) Ll[off] = sum[e];
                 }
             }
         } else if (lane == 0) {
