@@ -164,7 +164,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
         tc::fence_after_sync();
         const int m = mt * kGRows + warp * 32 + lane;
         const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
+        // a rolled loop: this epilogue runs once per CTA, and unrolled it is long straight-line
+        // code that mostly waits for instruction fetch
+#pragma unroll 1
         for (int cb = 0; cb < kGBoxes; cb += 16) {
             float v[16];
             tc::tmem_ld16(base + cb, v);
@@ -197,9 +199,18 @@ __global__ void k_translate_sum(int N, int ldc, int nz, const float* __restrict_
                                 float* __restrict__ C, int accumulate) {
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)N * ldc) return;
+    const float c0 = accumulate ? C[e] : 0.f;
     float s = 0.f;
-    for (int z = 0; z < nz; ++z) s += P[z * pstride + e];
-    C[e] = accumulate ? C[e] + s : s;
+    int z = 0;
+    for (; z + 8 <= nz; z += 8) {  // eight loads in flight, then the adds in slice order
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = P[(z + k) * pstride + e];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += v[k];
+    }
+    for (; z < nz; ++z) s += P[z * pstride + e];
+    C[e] = accumulate ? c0 + s : s;
 }
 
 float tf32_rna(float x) {  // nearest, ties away from zero (cvt.rna.tf32.f32); finite inputs
