@@ -416,6 +416,12 @@ def run_native(args):
     roof["traffic"] = m2l_traffic(precision)
     roof["kernel"] = "M2L, levels %d..%d" % (lev[0], lev[-1])
     roof["flop_per_launch"] = m2l_flop
+    # the same interactions counted as a rotation-based O(p^3) M2L would do them (rotate,
+    # translate along z, rotate back: about 6 (p + 1)^3 flop each), the minimal algorithmic
+    # count, so that the dense formulation's extra work does not flatter the rate
+    rot_flop = boxes * 189 * 6 * (s["p"] + 1) ** 3
+    roof["flop_per_launch_rotation_count"] = rot_flop
+    roof["achieved_rotation_count"] = rot_flop / (m2l_ms * 1e-3) / 1e12
     roof["ms_per_launch"] = m2l_ms
 
     cpu = None
