@@ -226,7 +226,8 @@ fmm_status fmm_status_word(fmm_handle* h, int* device_status, void* stream);
 /* Per-stage device times of the last fmm_eval when profiling is enabled
  * (CUDA events; profiling mode launches kernel by kernel).  ms[0..n):
  *   0 binning, 1 P2M, 2 M2M: consecutive, from the start of the evaluation;
- *   3 root: the periodic root multipole, lattice operator and Q/D/T sums;
+ *   3 root: the periodic root multipole, lattice operator and Q/D/T sums (0
+ *     in an open box);
  *   4 M2L: the M2L of the levels on the internal chain stream (pack + MMA
  *     kernel; with the side branch below, the MMA kernel of the two finest
  *     levels only, after their pack and the wait for the near field);

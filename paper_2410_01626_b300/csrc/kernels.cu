@@ -1666,7 +1666,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         span(h, 9, s0, s1);
         root(ss);
         const int s2 = mark(h, ss);
-        span(h, 3, s1, s2);
+        if (h->periodic) span(h, 3, s1, s2);
         for (int l = lfirst; l <= lc; ++l) l2l_level(h, l, ss);
         span(h, 10, s2, mark(h, ss));
         cudaEventRecord(h->side_ev, ss);
@@ -1681,7 +1681,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     } else {
         root(cs);
         const int e4 = mark(h, cs);
-        span(h, 3, e3, e4);
+        if (h->periodic) span(h, 3, e3, e4);
         if (d >= lmin && h->ntiles > 0) {
             if (h->precision != FMM_FP32 && m2l_tc_supported(h)) {
                 launch_m2l_tc(h, cs, lmin, d);

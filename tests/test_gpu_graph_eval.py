@@ -72,3 +72,26 @@ def test_host_buffer_evaluations_repeat_exactly():
     for o in outs:
         assert torch.equal(o[0], ref[0].cpu()) and torch.equal(o[1], ref[1].cpu()) and torch.equal(o[2], ref[2].cpu())
     f.close()
+
+
+@pytest.mark.parametrize("periodic,depth,side", [(True, 4, True), (False, 4, True), (False, 2, False)])
+def test_stage_times_cover_the_branches(periodic, depth, side):
+    """Profiling mode reports every stage of an evaluation; the coarse levels' side branch (M2L of
+    levels below the two finest, root, their L2L) appears exactly when the tree has such levels."""
+    from paper_2410_01626_b300 import STAGES
+    if periodic:
+        s = synth.periodic_uniform(seed=21, n=20000, L=4.0, n_sites=8, site_size=4, p=10, depth=depth)
+    else:
+        s = synth.open_uniform(seed=21, n=20000, L=4.0, n_sites=8, site_size=4, p=10, depth=depth)
+    f = FMM(s["L"], s["periodic"], s["p"], s["depth"], origin=s["origin"], precision="3xbf16")
+    t = {k: torch.from_numpy(np.ascontiguousarray(s[k])).cuda() for k in ("x", "qA", "qB", "site", "lam")}
+    f.set_charges(t["qA"], t["qB"], t["site"], t["lam"])
+    f.set_profiling(True)
+    f.eval(t["x"])
+    ms = f.stage_times()
+    f.close()
+    assert list(ms) == list(STAGES)
+    assert all(v >= 0.0 for v in ms.values()), ms
+    for k in ("binning", "p2m", "m2l", "outputs", "final", "p2p"):
+        assert ms[k] > 0.0, (k, ms)
+    assert (ms["m2l_coarse"] > 0.0) == side and (ms["root"] > 0.0) == periodic, ms
