@@ -180,7 +180,9 @@ def run_reference(args):
         return 0
     s = synth.solvated_30k() if args.small else synth.solvated_500k()
     n = len(s["qA"])
-    base = time_oracle(s, targets_small=8, targets_large=40)
+    # the per-atom cost is the difference of two samples that share the structure-factor cost:
+    # far enough apart (16 and 400 atoms) that the fixed part's jitter does not swamp it
+    base = time_oracle(s, targets_small=16, targets_large=400)
     per_target = base["per_target_s"]
     rng = np.random.default_rng(1)
     for _ in range(max(args.warmup - 2, 0)):
