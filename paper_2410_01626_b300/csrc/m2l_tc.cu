@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint8_t* tring = smem + 2 * (size_t)slab_bytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(tring + (size_t)nstages * kTcTBytes);
     uint64_t* slab_full = bars + 0;    // [2]
-    uint64_t* slab_empty = bars + 2;   // [2]
+    // (bars + 2 .. 3 unused: a slab buffer is free once its group's MMAs have completed, which is
+    // the accumulator's acc_full phase of that group, so the producer waits on that)
     uint64_t* acc_full = bars + 4;     // [2]
     uint64_t* acc_empty = bars + 6;    // [2]
     uint64_t* t_full = bars + 8;                 // [nstages]
@@ -214,7 +215,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (threadIdx.x == 0) {
         for (int q = 0; q < 2; ++q) {
             tc::mbar_init(slab_full + q, 1);
-            tc::mbar_init(slab_empty + q, 1);
             tc::mbar_init(acc_full + q, 1);
             tc::mbar_init(acc_empty + q, kTcDrainWarps);
         }
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int i0 = 0; i0 < cnt; i0 += per_round) {
                 if (!next_issued) {
                     const bool freed =
-                        __shfl_sync(0xffffffffu, gn < 2 || (lane == 0 && tc::mbar_test_wait(slab_empty + (gn & 1), gn_parity)), 0);
+                        __shfl_sync(0xffffffffu, gn < 2 || (lane == 0 && tc::mbar_test_wait(acc_full + (gn & 1), gn_parity)), 0);
                     if (freed) {
                         next_issued = true;
                         load_slab(gn);
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             __syncwarp();  // sel is rewritten by the next group
             if (ok && !next_issued) {
-                const bool good = __shfl_sync(0xffffffffu, lane != 0 || tc::mbar_wait(slab_empty + (gn & 1), gn_parity, kWaitLimit), 0);
+                const bool good = __shfl_sync(0xffffffffu, lane != 0 || tc::mbar_wait(acc_full + (gn & 1), gn_parity, kWaitLimit), 0);
                 if (!good) {
                     ok = false;
                     break;
@@ -427,8 +427,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         tphase ^= 1u;
                     }
                 }
-                tc::mma_commit_w(slab_empty + buf);
-                tc::mma_commit_w(acc_full + ab);  // this group's partial sum is complete
+                tc::mma_commit_w(acc_full + ab);  // this group's partial sum is complete, its slab free
             }
             if (!ok) {
                 if (lane == 0) {
