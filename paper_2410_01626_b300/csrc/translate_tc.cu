@@ -28,7 +28,7 @@ namespace fmmcph {
 
 namespace {
 
-constexpr int kGThreads = 128;
+constexpr int kGThreads = 256;  // two threads per box row: latency-bound code gets more issue slots
 constexpr int kGRows = 128;               // M per CTA (one MMA)
 constexpr int kGBoxes = 128;              // N per CTA
 constexpr int kGChunk = 16;               // K coefficients per stage
@@ -79,14 +79,17 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const uint32_t idesc = tc::idesc_tf32(kGRows, kGBoxes);
     const uint64_t wdesc0 = tc::smem_desc_kmajor(tc::smem_u32(wst), 2048u, 128u);
     const uint64_t xdesc0 = tc::smem_desc_kmajor(tc::smem_u32(xst), 2048u, 128u);
-    const int p = n0 + t;  // this thread's box row of X
+    const int row = t & (kGBoxes - 1), half = t / kGBoxes;  // this thread's box row of X, half of its cells
+    constexpr int kHalfCells = kGCells / 2;
+    const int p = n0 + row;
     const int nch = kc1 - kc0;
     auto load_x = [&](int kc, float4* xv) {
 #pragma unroll
-        for (int g = 0; g < kGCells; ++g) {
+        for (int gg = 0; gg < kHalfCells; ++gg) {
+            const int g = half * kHalfCells + gg;
             const int k = kc * kGChunk + g * 4;
-            xv[g] = (p < N && k < K) ? *reinterpret_cast<const float4*>(X + (long)p * ldx + k)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+            xv[gg] = (p < N && k < K) ? *reinterpret_cast<const float4*>(X + (long)p * ldx + k)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
     int w_issued = 0, w_taken = 0;  // W chunks copied / consumed (thread 0)
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         tc::mbar_arrive_expect_tx(w_full + s, kGStage);
         tc::bulk_g2s(wst + (size_t)s * kGStage, Wp + ((size_t)mt * nkc + kc0 + i) * kGStage, kGStage, w_full + s);
     };
-    float4 xv[kGCells], xn[kGCells];
+    float4 xv[kHalfCells], xn[kHalfCells];
     if (nch > 0) {
         load_x(kc0, xv);
         if (t == 0) issue_w(0);
@@ -113,14 +116,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
         // would truncate)
         uint8_t* xs = xst + (size_t)s * kGStage;
 #pragma unroll
-        for (int g = 0; g < kGCells; ++g) {
-            const float4 v = xv[g];
+        for (int gg = 0; gg < kHalfCells; ++gg) {
+            const int g = half * kHalfCells + gg;
+            const float4 v = xv[gg];
             const float4 hi = make_float4(tc::round_tf32(v.x), tc::round_tf32(v.y), tc::round_tf32(v.z),
                                           tc::round_tf32(v.w));
             const float4 lo = make_float4(tc::round_tf32(v.x - hi.x), tc::round_tf32(v.y - hi.y),
                                           tc::round_tf32(v.z - hi.z), tc::round_tf32(v.w - hi.w));
-            *reinterpret_cast<float4*>(xs + (size_t)g * 2048 + (size_t)t * 16) = hi;
-            *reinterpret_cast<float4*>(xs + kGPart + (size_t)g * 2048 + (size_t)t * 16) = lo;
+            *reinterpret_cast<float4*>(xs + (size_t)g * 2048 + (size_t)row * 16) = hi;
+            *reinterpret_cast<float4*>(xs + kGPart + (size_t)g * 2048 + (size_t)row * 16) = lo;
         }
         tc::fence_proxy_async();  // the generic-proxy stores above, for the tensor core
         __syncthreads();
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             }
         }
 #pragma unroll
-        for (int g = 0; g < kGCells; ++g) xv[g] = xn[g];
+        for (int gg = 0; gg < kHalfCells; ++gg) xv[gg] = xn[gg];
     }
     __syncthreads();
     const bool ok = *abort_flag == 0;
@@ -162,12 +166,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const bool done = tc::mbar_wait(acc_done, 0, kGWaitLimit);
     if (ok && done && kc1 > kc0) {
         tc::fence_after_sync();
-        const int m = mt * kGRows + warp * 32 + lane;
-        const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (the rows), warps 0-3 the first half of the
+        // columns (boxes) and warps 4-7 the second
+        const int q = warp & 3;
+        const int m = mt * kGRows + q * 32 + lane;
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16);
         // a rolled loop: this epilogue runs once per CTA, and unrolled it is long straight-line
         // code that mostly waits for instruction fetch
 #pragma unroll 1
-        for (int cb = 0; cb < kGBoxes; cb += 16) {
+        for (int cb = half * (kGBoxes / 2); cb < (half + 1) * (kGBoxes / 2); cb += 16) {
             float v[16];
             tc::tmem_ld16(base + cb, v);
             if (m < Mtot) {
