@@ -176,10 +176,13 @@ fmm_status fmm_eval_host(fmm_handle* h, const float* x_host, double* E_host, flo
                          float* dVdlambda_host, void* stream);
 
 /* Page-locked host memory for the buffers of fmm_eval_host (not part of the
- * method; a convenience for callers).  Copies from this memory run at full
- * PCIe rate in both directions; on the B300 hosts measured here, page-locked
- * memory obtained by other routes (e.g. a framework's pinned-tensor cache)
- * fed host-to-device copies several times slower.  fmm_host_alloc writes the
+ * method; a convenience for callers).  Copies between this memory and the
+ * device are asynchronous DMA.  They run at the PCIe rate (6 MB in 0.12 ms
+ * each way on the B300 hosts measured here) while the CPU caches hold none of
+ * the buffer's lines; a buffer the CPU has just written or read runs several
+ * times slower on those hosts (a 6 MB host-to-device copy from a buffer
+ * written by the CPU took 0.5-1.3 ms, and write-combined memory did no
+ * better there).  fmm_host_alloc writes the
  * address to *out (NULL on failure) and returns FMM_ERR_ARG for bytes == 0 or
  * out == NULL, FMM_ERR_OOM when the allocation fails.  Free with
  * fmm_host_free (NULL is ignored). */
