@@ -7,9 +7,9 @@ water-like solvent with TIP3P-like charges (O -0.834 e, H +0.417 e; the
 charge-buffer passage of Sec. 2.5 quotes the -0.834 e oxygen), protein-like
 clusters of charged atoms, and titratable sites whose two forms differ only
 in their charges (Sec. 2.1) and change the site's net charge by -1
-(sites "change their total charge by +-1", Sec. 2.1).
+(a titratable site's net charge changes by one unit, Sec. 2.1).
 
-Readings where the workload descriptions are silent (listed in the design doc):
+Readings where the workload descriptions are silent:
 water H-O-H angle 104.52 deg; water oxygens on a jittered FCC lattice (a
 literal random sequential placement at O-O >= 0.28 nm jams at this density);
 cluster radius = half the quoted sphere size; sites are compact groups of
