@@ -103,6 +103,37 @@ def test_open_near_field_only_equals_direct_sum(depth):
     assert g["status"] == 0
 
 
+# ---------------------------------------------------------------- degenerate inputs
+@pytest.mark.parametrize("periodic", [True, False])
+def test_empty_system(periodic):
+    """No atoms and no sites: the evaluation runs (every tree stage over empty leaves) and gives
+    E = 0 exactly, empty F, phi and dV/dlambda, and no device status."""
+    from paper_2410_01626_b300 import FMM
+    f = FMM(3.0, periodic, 8, 3, origin=(0.0, 0.0, 0.0))
+    z = torch.zeros(0, device="cuda")
+    f.set_charges(z, z.clone(), torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros(0, device="cuda"))
+    for _ in range(3):  # eager, graph capture, replay
+        E, F, dV, phi = f.eval(torch.zeros((0, 3), device="cuda"), phi=True)
+        torch.cuda.synchronize()
+        assert float(E.item()) == 0.0
+        assert tuple(F.shape) == (0, 3) and dV.numel() == 0 and phi.numel() == 0
+    assert f.status_word() == 0
+    f.close()
+
+
+def test_no_sites():
+    """Atoms without titratable sites (K = 0): E and F as the oracle's, no dV/dlambda."""
+    s = dict(synth.small_open())
+    s["site"] = np.full_like(s["site"], -1)
+    s["lam"] = np.zeros(0, dtype=np.float32)
+    s["qB"] = s["qA"].copy()
+    ref = oracle_ref(s)
+    g = run_gpu(s, p=10, depth=2)
+    assert g["dVdl"].size == 0 and g["status"] == 0
+    e = errors(g, ref)
+    assert e["E"] < 1e-4 and e["F"] < 1e-4, e
+
+
 # ---------------------------------------------------------------- open boundary FMM
 @pytest.mark.parametrize("p,ftol", [(6, 1e-3), (8, 2e-4), (12, 1e-5)])
 def test_open_fmm_small(p, ftol):
