@@ -1375,7 +1375,7 @@ __global__ void __launch_bounds__(128) k_p2p(NearParams a, float4* __restrict__ 
 // E = 1/2 k sum of the per-block partials of q phi, totalled in FP64: each of the
 // kFinalBlocks blocks sums a fixed slice, and the last block to finish (atomic ticket) adds the
 // block totals in block order, so the result is deterministic.  dV/dlambda_k = k sum over the
-// site's atoms of dq phi (FP64), one thread per site.
+// site's atoms of dq phi (FP64), one warp per site in a fixed order.
 constexpr int kFinalBlocks = 32;
 static_assert(8 + 5 * kQdtBlocks + 4 + kFinalBlocks + 1 <= kRootDoubles, "root scratch layout");
 __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restrict__ epart, double ke,
@@ -1414,16 +1414,25 @@ __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restr
         if (E) E[0] = 0.5 * ke * t + hsum;
         *ticket = 0u;  // ready for the next call
     }
+    // one warp per site: lane j sums the site's atoms j, j + 32, ... in order, then a fixed-order
+    // shuffle tree adds the lanes (the site's atoms are loaded in parallel, not one after another)
+    const int lane = threadIdx.x & 31;
     if (dVdl)
-        for (int k = blockIdx.x * 256 + threadIdx.x; k < K; k += kFinalBlocks * 256) {
+        for (int k = (blockIdx.x * 256 + threadIdx.x) >> 5; k < K; k += kFinalBlocks * 8) {
             double v = 0.0, vt = 0.0;  // dE/dlambda(_p), dE/dlambda_t
-            for (int a = site_ptr[k]; a < site_ptr[k + 1]; ++a) {
+            for (int a = site_ptr[k] + lane; a < site_ptr[k + 1]; a += 32) {
                 const uint32_t si = inv[site_atoms[a]];
                 v += (double)dq[si] * (double)phis[si];
                 if (ncoord == 2) vt += (double)dqt[si] * (double)phis[si];
             }
-            dVdl[ncoord * k] = (float)(ke * v + (hi_site ? hi_site[3 * k + 1] : 0.0));
-            if (ncoord == 2) dVdl[2 * k + 1] = (float)(ke * vt + (hi_site ? hi_site[3 * k + 2] : 0.0));
+            for (int off = 16; off > 0; off >>= 1) {
+                v += __shfl_down_sync(0xffffffffu, v, off);
+                vt += __shfl_down_sync(0xffffffffu, vt, off);
+            }
+            if (lane == 0) {
+                dVdl[ncoord * k] = (float)(ke * v + (hi_site ? hi_site[3 * k + 1] : 0.0));
+                if (ncoord == 2) dVdl[2 * k + 1] = (float)(ke * vt + (hi_site ? hi_site[3 * k + 2] : 0.0));
+            }
         }
 }
 
