@@ -150,7 +150,8 @@ __global__ void k_keys(int n, const float* __restrict__ x, BoxGeom g, uint32_t* 
 //     one block per tile: the tile's offset is the sum of the tile counts before it, then an
 //     exclusive scan of its leaf counts -> start, count (and the counters are cleared for the
 //     next call); (3) k_bin_place: atom i goes to start[key] + slot, and the tile counts are
-//     cleared; (4) k_bin_order_gather: one warp per leaf puts the leaf's atoms in ascending
+//     cleared; (4) k_bin_order_gather: a warp takes two leaves (a half-warp each when both hold at most
+//     16 atoms, else one after the other) and puts each leaf's atoms in ascending
 //     input index -- exactly the order of a stable sort on (key, index) -- and gathers positions
 //     and charges in that order.
 constexpr int kScanThreads = 256;
@@ -325,29 +326,48 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
                                                           const float* __restrict__ x, BoxGeom g, ChargeForms cf,
                                                           float4* __restrict__ pos, uint32_t* __restrict__ inv,
                                                           int* __restrict__ status) {
-    const int leaf = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (leaf >= nleaf) return;
-    const int st = (int)start[leaf], c = (int)count[leaf];
-    if (c <= 32) {  // the whole leaf in one register per lane: rank = number of smaller indices
-        const uint32_t v = lane < c ? placed[st + lane] : 0xFFFFFFFFu;
-        int r = 0;
-        for (int k = 0; k < c; ++k) r += __shfl_sync(0xffffffffu, v, k) < v ? 1 : 0;
-        if (lane < c) {
+    // a warp takes leaves l0 and l0 + 1
+    const int l0 = 2 * (blockIdx.x * 4 + (threadIdx.x >> 5)), lane = threadIdx.x & 31;
+    if (l0 >= nleaf) return;
+    const bool two = l0 + 1 < nleaf;
+    const int c0 = (int)count[l0], c1 = two ? (int)count[l0 + 1] : 0;
+    if (c0 <= 16 && c1 <= 16) {  // one leaf per half-warp, one atom per lane
+        const int half = lane >> 4, sub = lane & 15, c = half ? c1 : c0;
+        const int leaf = l0 + half;
+        const int st = c > 0 ? (int)start[leaf] : 0;
+        const uint32_t v = sub < c ? placed[st + sub] : 0xFFFFFFFFu;
+        int r = 0;  // rank = number of smaller indices in the leaf (padding is never smaller)
+        for (int k = 0; k < 16; ++k) r += __shfl_sync(0xffffffffu, v, k, 16) < v ? 1 : 0;
+        if (sub < c) {
             perm[st + r] = v;
             skey[st + r] = (uint32_t)leaf;
             gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
         }
         return;
     }
-    // larger leaves: the same ranks by a pass over the leaf per element (O(c^2 / 32) per warp,
-    // the order of the leaf's own near-field work)
-    for (int e = lane; e < c; e += 32) {
-        const uint32_t v = placed[st + e];
-        int r = 0;
-        for (int k = 0; k < c; ++k) r += placed[st + k] < v ? 1 : 0;
-        perm[st + r] = v;
-        skey[st + r] = (uint32_t)leaf;
-        gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
+    for (int leaf = l0; leaf < l0 + (two ? 2 : 1); ++leaf) {
+        const int st = (int)start[leaf], c = leaf == l0 ? c0 : c1;
+        if (c <= 32) {  // the whole leaf in one register per lane
+            const uint32_t v = lane < c ? placed[st + lane] : 0xFFFFFFFFu;
+            int r = 0;
+            for (int k = 0; k < c; ++k) r += __shfl_sync(0xffffffffu, v, k) < v ? 1 : 0;
+            if (lane < c) {
+                perm[st + r] = v;
+                skey[st + r] = (uint32_t)leaf;
+                gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
+            }
+            continue;
+        }
+        // larger leaves: the same ranks by a pass over the leaf per element (O(c^2 / 32) per warp,
+        // the order of the leaf's own near-field work)
+        for (int e = lane; e < c; e += 32) {
+            const uint32_t v = placed[st + e];
+            int r = 0;
+            for (int k = 0; k < c; ++k) r += placed[st + k] < v ? 1 : 0;
+            perm[st + r] = v;
+            skey[st + r] = (uint32_t)leaf;
+            gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
+        }
     }
 }
 
@@ -1591,7 +1611,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     if (n > 0) {
         k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(n, h->key, h->vA, h->start, h->vB, ntiles, tilecnt);
         ChargeForms cf{{h->qA, h->qB, h->qC, h->qD}, h->nforms, h->site, h->K, lam, h->dq, h->dqt};
-        k_bin_order_gather<<<(nleaf + 3) / 4, 128, 0, st>>>(nleaf, h->start, h->count, h->vB, h->perm,
+        k_bin_order_gather<<<((nleaf + 1) / 2 + 3) / 4, 128, 0, st>>>(nleaf, h->start, h->count, h->vB, h->perm,
                                                             h->sorted_key, x, g, cf, h->pos, h->inv, h->status);
     }
     // --- near field on the caller's stream, concurrent with the multipole chain ---
