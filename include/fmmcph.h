@@ -288,11 +288,14 @@ fmm_status fmm_lambda_step(int n_sites, float* lambda, float* velocity, const fl
  * each piece V_a + (V_b - V_a)(3 s^2 - 2 s^3), and harmonic walls kwall (l - a)^2 / 2
  * outside [a0, a1].  The pH potential (Eq. 4) enters through delta:
  * fmm_lambda_pfc returns the delta (partition function correction, Sec. 2.3) for which
- * the populations exp(-V / kT) implies on [lo, b] (protonated, lambda near 0) and
- * [b, hi] (deprotonated) satisfy Z_deprot / Z_prot = 10^(pH - pKa_ref), the free energy
- * of deprotonation ln(10) kT (pKa_ref - pH) of Eq. 4; [lo, hi] are the reflecting walls
- * of fmm_lambda_step.  Host FP64 (Gauss-Legendre quadrature, bisection).  Returns
- * FMM_ERR_ARG for kT <= 0, a0 >= a1, lo > a0 or hi < a1, or delta == NULL. */
+ * the partition functions Z_prot = int_lo^b exp(-V / kT) (protonated, lambda near 0) and
+ * Z_deprot = int_b^hi exp(-V / kT) satisfy Z_deprot / Z_prot = 10^(pH - pKa_ref), the free
+ * energy of deprotonation ln(10) kT (pKa_ref - pH) of Eq. 4.  Sec. 2.3 integrates over
+ * [0, 0.5] and [0.5, 1]: pass lo = 0, hi = 1 (with a0 = 0, a1 = 1).  Passing the reflecting
+ * walls of fmm_lambda_step instead (lo = -0.1, hi = 1.1) makes the condition hold for the
+ * population the dynamics samples, which the paper's integrals leave out.  Host FP64
+ * (Gauss-Legendre quadrature, bisection).  Returns FMM_ERR_ARG for kT <= 0, a0 >= a1,
+ * lo >= b, hi <= b, kwall < 0 or delta == NULL. */
 fmm_status fmm_lambda_pfc(double pH, double pKa_ref, double barrier, double kT, double a0, double a1,
                           double kwall, double lo, double hi, double* delta);
 

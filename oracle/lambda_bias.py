@@ -11,12 +11,17 @@ coordinate (arXiv 2410.01626, Sec. 2.2 "Calibration of Protonation Dynamics"):
   ln(10) kT (pKa_ref - pH);
 * the partition function correction (Sec. 2.3): the well offset delta is refined until the
   populations of the two states that V implies match that free energy, i.e.
-  Z_deprot / Z_prot = 10^(pH - pKa_ref) with Z_prot = int_lo^b exp(-V/kT) and
-  Z_deprot = int_b^hi exp(-V/kT) over the sampled interval [lo, hi] (the reflecting walls).
+  Z_deprot / Z_prot = 10^(pH - pKa_ref) with Z_prot = int_0^0.5 exp(-V/kT) and
+  Z_deprot = int_0.5^1 exp(-V/kT), the bounds Sec. 2.3 states (lo = 0, hi = 1, split at the
+  barrier b = 0.5 of the wells at 0 and 1).  Other bounds are an option: lo, hi = the
+  reflecting walls (-0.1, 1.1) make the condition hold for the population the dynamics
+  samples, a departure from the paper's integrals used only where a test needs that
+  population.
 
 Parity pins (tests/test_lambda_bias.py): the spline's values and slopes at the knots,
 continuity, the symmetric case (pH = pKa, symmetric wells: delta = 0), and the population
-ratio of the corrected potential by an independent quadrature.
+ratio of the corrected potential by an independent quadrature over [0, 0.5] and [0.5, 1]
+(and over the walls' interval for the optional bounds).
 """
 from __future__ import annotations
 
@@ -40,8 +45,9 @@ def potential(l, a0, a1, h, delta, kw):
     return va + (vb - va) * (3 * s * s - 2 * s ** 3), (vb - va) * (6 * s - 6 * s * s) / (lb - la)
 
 
-def population_ratio(a0, a1, h, delta, kw, kT, lo, hi):
-    """Z_deprot / Z_prot of exp(-V/kT) on [lo, hi] split at the barrier."""
+def population_ratio(a0, a1, h, delta, kw, kT, lo=0.0, hi=1.0):
+    """Z_deprot / Z_prot of exp(-V/kT) on [lo, hi] split at the barrier (Sec. 2.3: [0, 0.5]
+    and [0.5, 1] by default)."""
     b = 0.5 * (a0 + a1)
     f = lambda l: math.exp(-potential(l, a0, a1, h, delta, kw)[0] / kT)  # noqa: E731
     pts = [a0, a1]
@@ -50,8 +56,9 @@ def population_ratio(a0, a1, h, delta, kw, kT, lo, hi):
     return zd / zp
 
 
-def pfc_delta(pH, pKa, h, kT, a0=0.0, a1=1.0, kw=1000.0, lo=-0.1, hi=1.1):
-    """The well offset delta for which Z_deprot / Z_prot = 10^(pH - pKa)."""
+def pfc_delta(pH, pKa, h, kT, a0=0.0, a1=1.0, kw=1000.0, lo=0.0, hi=1.0):
+    """The well offset delta for which Z_deprot / Z_prot = 10^(pH - pKa), the partition
+    functions taken over [lo, b] and [b, hi] (Sec. 2.3: lo = 0, hi = 1)."""
     target = math.log(10.0) * (pH - pKa)
     g = lambda d: math.log(population_ratio(a0, a1, h, d, kw, kT, lo, hi)) - target  # noqa: E731
     lo_d, hi_d = -50 * kT - abs(target) * kT, 50 * kT + abs(target) * kT

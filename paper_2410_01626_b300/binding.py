@@ -334,22 +334,25 @@ def lambda_step(lam, vel, dVdl, step, seed, dt=0.002, mass=60.0, gamma=1.0, kT=2
            "fmm_lambda_step_bias")
 
 
-def lambda_pfc(pH, pKa_ref, barrier, kT=2.494339, a0=0.0, a1=1.0, kwall=1000.0, lo=-0.1, hi=1.1):
-    """Well offset delta of the double well (partition function correction, host FP64)."""
+def lambda_pfc(pH, pKa_ref, barrier, kT=2.494339, a0=0.0, a1=1.0, kwall=1000.0, lo=0.0, hi=1.0):
+    """Well offset delta of the double well (partition function correction, host FP64); the
+    partition functions run over [lo, b] and [b, hi], by default Sec. 2.3's [0, 0.5] and
+    [0.5, 1]."""
     d = ctypes.c_double()
     _check(load().fmm_lambda_pfc(float(pH), float(pKa_ref), float(barrier), float(kT), float(a0), float(a1),
                                  float(kwall), float(lo), float(hi), ctypes.byref(d)), "fmm_lambda_pfc")
     return d.value
 
 
-def lambda_bias(pH, pKa_ref, barrier, kT=2.494339, a0=0.0, a1=1.0, kwall=1000.0, lo=-0.1, hi=1.1, device="cuda"):
+def lambda_bias(pH, pKa_ref, barrier, kT=2.494339, a0=0.0, a1=1.0, kwall=1000.0, pfc_lo=0.0, pfc_hi=1.0,
+                device="cuda"):
     """Bias parameters [n, 5] for ``lambda_step`` from per-coordinate pKa_ref and barrier
     (sequences of equal length, or scalars): the double well with the pH offset from
-    ``lambda_pfc``."""
+    ``lambda_pfc`` over [pfc_lo, pfc_hi] (Sec. 2.3: [0, 1])."""
     import numpy as np
     pk = np.atleast_1d(np.asarray(pKa_ref, np.float64))
     bh = np.broadcast_to(np.atleast_1d(np.asarray(barrier, np.float64)), pk.shape)
-    rows = [[a0, a1, b, lambda_pfc(pH, p, b, kT, a0, a1, kwall, lo, hi), kwall] for p, b in zip(pk, bh)]
+    rows = [[a0, a1, b, lambda_pfc(pH, p, b, kT, a0, a1, kwall, pfc_lo, pfc_hi), kwall] for p, b in zip(pk, bh)]
     return torch.tensor(rows, dtype=torch.float32, device=device)
 
 

@@ -188,8 +188,8 @@ double boltzmann_integral(double u, double v, double a0, double a1, double h, do
 
 extern "C" fmm_status fmm_lambda_pfc(double pH, double pKa_ref, double barrier, double kT, double a0, double a1,
                                      double kwall, double lo, double hi, double* delta) {
-    if (!delta || !(kT > 0.0) || !(a0 < a1) || lo > a0 || hi < a1 || !(kwall >= 0.0)) return FMM_ERR_ARG;
     const double m = 0.5 * (a0 + a1);
+    if (!delta || !(kT > 0.0) || !(a0 < a1) || !(lo < m) || !(hi > m) || !(kwall >= 0.0)) return FMM_ERR_ARG;
     const double target = std::log(10.0) * (pH - pKa_ref);
     const double zp = boltzmann_integral(lo, m, a0, a1, barrier, 0.0, kwall, kT);  // independent of delta
     // ln(Z_deprot / Z_prot) decreases monotonically in delta: bisect

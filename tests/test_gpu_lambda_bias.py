@@ -36,17 +36,21 @@ def test_double_well_force_matches_oracle():
     assert np.abs(f - want).max() < 1e-4 * scale + 2 * m * 1.2e-7 / dt ** 2
 
 
-def test_sampled_protonation_matches_henderson_hasselbalch():
+def test_sampled_protonation_matches_the_corrected_populations():
     """8192 independent lambda particles in the corrected double well at four pH - pKa
-    values: the fraction with lambda > 0.5 approaches r / (1 + r), r = 10^(pH - pKa).
+    values.  The correction (Sec. 2.3) sets the offset from the partition functions over
+    [0, 0.5] and [0.5, 1]; the dynamics samples the whole interval between its reflecting
+    walls (-0.1, 1.1), harmonic walls included.  So the fraction with lambda > 0.5
+    approaches r / (1 + r), r = Z_deprot / Z_prot of the corrected potential over the walls'
+    interval (oracle quadrature); r is 10^(pH - pKa) only up to the walls' tails.
     A light particle (5 u), gamma = 2 / ps and a 2 kJ/mol barrier keep the well-to-well
     transition time (Kramers) near 3 ps, so 60 ps gives ~20 transitions per particle."""
     groups = [-1.0, 0.0, 0.5, 1.5]
     per = 2048
     n = per * len(groups)
-    pH = 5.0
+    pH, barrier = 5.0, 2.0
     pk = np.repeat([pH - g for g in groups], per)
-    bias = lambda_bias(pH, pk, 2.0, KT)
+    bias = lambda_bias(pH, pk, barrier, KT)
     lam = torch.full((n,), 0.5, device="cuda")
     vel = torch.zeros(n, device="cuda")
     zero = torch.zeros(n, device="cuda")
@@ -60,5 +64,6 @@ def test_sampled_protonation_matches_henderson_hasselbalch():
             samples += 1
     frac = (frac / samples).cpu().numpy()
     for g, fr in zip(groups, frac):
-        r = 10.0 ** g
-        assert fr == pytest.approx(r / (1 + r), abs=0.015), (g, fr)
+        d = lb.pfc_delta(pH=pH, pKa=pH - g, h=barrier, kT=KT)
+        r = lb.population_ratio(0.0, 1.0, barrier, d, 1000.0, KT, lo=-0.1, hi=1.1)
+        assert fr == pytest.approx(r / (1 + r), abs=0.015), (g, fr, r / (1 + r))
