@@ -321,26 +321,31 @@ fmm_status fmm_batch_eval(fmm_batch* b, const float* const* x, double* const* E,
                           float* const* dVdlambda, void* stream);
 void fmm_batch_destroy(fmm_batch* b);
 
-/* Binning with no device allocation, for callers that cannot call cudaMalloc: code running
- * while a CUDA stream is being captured into a graph, processes whose device memory comes from
- * a fixed budget or a foreign allocator, and real-time loops that must not allocate.  The paper
- * has no counterpart; it is the binning step of fmm_eval (Morton keys, stable sort, leaf
- * ranges) on its own.
+/* Binning with no device allocation.  Some callers cannot call cudaMalloc: a host program
+ * (an MD engine, for instance) that owns all of the GPU's memory through its own pool or a
+ * fixed budget, or a loop that must not stall, since cudaMalloc may synchronise the device.
+ * For them this call runs the binning step of fmm_eval (Morton keys, stable sort, leaf
+ * ranges) without allocating: its sort scratch is a static device array inside the library.
+ * The paper has no counterpart.
  *   box, periodic, depth: as for fmm_create (0 <= depth <= 7)
- *   n_atoms:  0 <= n_atoms <= FMM_NOALLOC_MAX_ATOMS, else FMM_ERR_ARG
- *   x:        [n_atoms][3] float positions
- *   key, perm:[n_atoms] uint32 outputs, start, count: [8^depth] uint32 outputs -- the same
+ *   n_atoms:  0 <= n_atoms <= FMM_NOALLOC_MAX_ATOMS, else FMM_ERR_ARG (nothing launched)
+ *   x:        [n_atoms][3] float positions (device)
+ *   key, perm:[n_atoms] uint32 outputs, start, count: [8^depth] uint32 outputs (device) -- the
  *             values fmm_get_binning returns after fmm_eval on the same positions
- * The sort scratch is a static device array inside the library, sized for
- * FMM_NOALLOC_MAX_ATOMS atoms (about 6.5 MB per GPU that loads the library, held until the
- * process exits).  The first call on a device looks up that array's device address; make that
- * first call before any stream capture.  Every call shares the array and keeps the last call's
- * contents, so calls that overlap on the GPU (unordered streams) race; calls on one stream are
- * ordered.  No device memory is allocated or freed.  Atoms outside an open box are clamped into
- * the boundary leaves (use fmm_status_word after fmm_eval to detect them). */
+ *   status:   one device int or NULL; when given, FMM_DEV_DOMAIN is OR-ed into it if an atom
+ *             lies outside an open box (such atoms are clamped into the boundary leaves).  The
+ *             call only sets bits: the caller clears the word.
+ * The scratch holds FMM_NOALLOC_MAX_ATOMS atoms (about 6.5 MB on every GPU that loads the
+ * library, kept until the process exits).  The first call on a device looks up the array's
+ * device address (with that device current) and caches it; make that first call before any
+ * stream capture.  Every call uses the same array, and the array keeps the last call's
+ * contents (nothing in it needs to start at zero), so calls that overlap on the GPU -- on
+ * streams with no ordering between them -- race; calls on one stream are ordered.  No
+ * device memory is allocated or freed. */
 #define FMM_NOALLOC_MAX_ATOMS 524288
 fmm_status fmm_binning_noalloc(const fmm_box* box, int periodic, int depth, int n_atoms, const float* x,
-                               uint32_t* key, uint32_t* perm, uint32_t* start, uint32_t* count, void* stream);
+                               uint32_t* key, uint32_t* perm, uint32_t* start, uint32_t* count, int* status,
+                               void* stream);
 
 void fmm_destroy(fmm_handle* h);
 const char* fmm_error_string(fmm_status s);

@@ -56,7 +56,7 @@ EXPORTS = {
     "fmm_launches_per_eval": (I, [P]),
     "fmm_host_operator": (I, [I, I, P, P]),
     "fmm_host_regular": (I, [I, P, P]),
-    "fmm_binning_noalloc": (I, [ctypes.POINTER(FmmBox), I, I, I, P, P, P, P, P, P]),
+    "fmm_binning_noalloc": (I, [ctypes.POINTER(FmmBox), I, I, I, P, P, P, P, P, P, P]),
     "fmm_lambda_step": (I, [I, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                             ctypes.c_ulonglong, ctypes.c_ulonglong, I, ctypes.c_double, ctypes.c_double, P]),
     "fmm_lambda_step_bias": (I, [I, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,

@@ -140,7 +140,7 @@ __global__ void k_keys(int n, const float* __restrict__ x, BoxGeom g, uint32_t* 
     bool bad = false;
     key[i] = leaf_key(x, i, g, bad);
     val[i] = (uint32_t)i;
-    if (bad) atomicOr(status, FMM_DEV_DOMAIN);
+    if (bad && status) atomicOr(status, FMM_DEV_DOMAIN);
 }
 
 // ---- binning as a counting sort by leaf ----
@@ -1773,7 +1773,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
 // library holds it until the process exits.  Calls share it, so calls that overlap on the GPU
 // (different streams, no ordering between them) race; calls on one stream are ordered.
 constexpr int kNoAllocSortBlocks = (FMM_NOALLOC_MAX_ATOMS + kSortTile - 1) / kSortTile;
-constexpr size_t kNoAllocWords = 3ull * FMM_NOALLOC_MAX_ATOMS + 256ull * kNoAllocSortBlocks + 64;
+constexpr size_t kNoAllocWords = 3ull * FMM_NOALLOC_MAX_ATOMS + 256ull * kNoAllocSortBlocks;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
 
 // Device address of the scratch array on the current device.  Host code may not use the
@@ -1803,7 +1803,7 @@ static fmm_status noalloc_scratch(uint32_t** out) {
 
 extern "C" fmm_status fmm_binning_noalloc(const fmm_box* box, int periodic, int depth, int n, const float* x,
                                           uint32_t* key, uint32_t* perm, uint32_t* start, uint32_t* count,
-                                          void* stream) {
+                                          int* status, void* stream) {
     if (!box || !(box->edge > 0.0) || !std::isfinite(box->edge)) return FMM_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(box->origin[a])) return FMM_ERR_ARG;
@@ -1817,7 +1817,6 @@ extern "C" fmm_status fmm_binning_noalloc(const fmm_box* box, int periodic, int 
     uint32_t* kC = scr + FMM_NOALLOC_MAX_ATOMS;
     uint32_t* vS = scr + 2L * FMM_NOALLOC_MAX_ATOMS;
     uint32_t* table = scr + 3L * FMM_NOALLOC_MAX_ATOMS;
-    int* status = reinterpret_cast<int*>(table + 256L * kNoAllocSortBlocks);
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = 1 << depth, nleaf = 1 << (3 * depth);
     BoxGeom g{box->origin[0], box->origin[1], box->origin[2], box->edge, std::ldexp(1.0, depth) / box->edge,
