@@ -142,37 +142,66 @@ def load_peaks():
 
 
 # ------------------------------------------------------------------ oracle timing
-def time_oracle(sys_, targets_small=100, targets_large=400, tol=1e-8):
-    """Time the FP64 Ewald oracle on a bounded sample (phi and forces at a few
-    hundred target atoms, with the full structure factors), and extrapolate
-    the cost of one full evaluation (all N atoms) linearly in the targets."""
+def oracle_sample_cost(sys_, targets, tol=1e-8, seed=0):
+    """One FP64 Ewald oracle call on `targets` random atoms of the system.  Returns the wall
+    seconds of its two phases from the oracle's own clock: the structure factors (the fixed
+    cost of any evaluation, every atom's charge) and the per-target sums divided by `targets`."""
     import numpy as np
     import oracle
     n = len(sys_["qA"])
-    rng = np.random.default_rng(0)
-    t1 = rng.choice(n, targets_small, replace=False)
-    t2 = rng.choice(n, targets_large, replace=False)
-    a = time.perf_counter()
-    oracle.evaluate(sys_, targets=t1, tol=tol, site_atoms=False)
-    b = time.perf_counter()
-    oracle.evaluate(sys_, targets=t2, tol=tol, site_atoms=False)
-    c = time.perf_counter()
-    per_target = max((c - b) - (b - a), 1e-9) / (targets_large - targets_small)
-    fixed = max((b - a) - targets_small * per_target, 0.0)
-    full = fixed + n * per_target
-    return {"value": 1.0 / full, "unit": "evals/s", "cores": oracle.nthreads(), "kind": "oracle",
-            "sample": (f"FP64 Ewald (tol {tol:g}) phi and forces at {targets_small} and {targets_large} random atoms of "
-                       f"the {n}-atom system; one full evaluation extrapolated as fixed + N x per-atom cost "
-                       f"({fixed:.2f} s + {n} x {per_target * 1e3:.3f} ms = {full:.0f} s)"),
-            "seconds_measured": c - a, "per_target_s": per_target}
+    t = np.random.default_rng(seed).choice(n, targets, replace=False)
+    oracle.evaluate(sys_, targets=t, tol=tol, site_atoms=False)
+    sf, tg = oracle.ewald_phase_seconds()
+    return sf, tg / targets
+
+
+def oracle_targets():
+    """Targets per oracle sample: a multiple of the oracle's dynamic chunk (8) times its threads,
+    so that every thread gets the same number of chunks."""
+    import oracle
+    return 64 * oracle.nthreads()
+
+
+def time_oracle(sys_, tol=1e-8, repeats=2, check_full=None):
+    """The cost of one full FP64 Ewald evaluation of all N atoms on the host cores, by the
+    model fixed + N x per-target with both terms measured by the oracle's phase clock on a
+    bounded sample (median of `repeats` samples of oracle_targets() random atoms).  With
+    `check_full` (a smaller system), that system is also evaluated in full and its measured
+    time is reported beside the model's prediction, as a check of the model."""
+    import statistics
+    import oracle
+    n = len(sys_["qA"])
+    T = oracle_targets()
+    runs = [oracle_sample_cost(sys_, T, tol, seed=r) for r in range(repeats)]
+    sf = statistics.median(r[0] for r in runs)
+    per = statistics.median(r[1] for r in runs)
+    full = sf + n * per
+    out = {"value": 1.0 / full, "unit": "evals/s", "cores": oracle.nthreads(), "kind": "oracle",
+           "extrapolated": True,
+           "sample": (f"FP64 Ewald oracle (tol {tol:g}) on {T} random target atoms of the {n}-atom system, "
+                      f"median of {repeats}; one full evaluation = structure factors {sf:.2f} s + "
+                      f"{n} x {per * 1e3:.4f} ms per target = {full:.0f} s (extrapolated from the sample)"),
+           "structure_factor_s": sf, "per_target_s": per, "full_eval_s_model": full}
+    if check_full is not None:
+        import time as _t
+        m = len(check_full["qA"])
+        sf_c, per_c = oracle_sample_cost(check_full, T, tol, seed=99)
+        a = _t.perf_counter()
+        oracle.evaluate(check_full, tol=tol)  # every atom: a real full evaluation
+        measured = _t.perf_counter() - a
+        model = sf_c + m * per_c
+        out["check_full"] = {"atoms": m, "measured_s": measured, "model_s": model, "model_over_measured": model / measured,
+                             "note": "one full FP64 Ewald evaluation of every atom, timed, against the sample model"}
+    return out
 
 
 def run_reference(args):
-    """The FP64 CPU oracle as the reference arm.  Warm-up samples fix the
-    per-atom cost; each timed step then evaluates a bounded sample (phi and
-    forces at 16 atoms with the full structure factors) and is extrapolated
-    to one full evaluation of all N atoms."""
-    import numpy as np
+    """The FP64 CPU oracle as the reference arm, on the same workload.  Each timed step is one
+    bounded sample (oracle_targets() random target atoms with the full structure factors); its
+    phase clock gives the step's estimate of one full evaluation of all N atoms (structure
+    factors + N x per-target cost).  `value` is that extrapolated rate; `ms_per_step` is the
+    sample's own measured wall time."""
+    import statistics
     import oracle
     import synth
     ws, rank, _ = dist_env()
@@ -180,28 +209,25 @@ def run_reference(args):
         return 0
     s = synth.solvated_30k() if args.small else synth.solvated_500k()
     n = len(s["qA"])
-    # the per-atom cost is the difference of two samples that share the structure-factor cost:
-    # far enough apart (16 and 400 atoms) that the fixed part's jitter does not swamp it
-    base = time_oracle(s, targets_small=16, targets_large=400)
-    per_target = base["per_target_s"]
-    rng = np.random.default_rng(1)
-    for _ in range(max(args.warmup - 2, 0)):
-        oracle.evaluate(s, targets=rng.choice(n, 16, replace=False), tol=1e-8, site_atoms=False)
-    full = []
-    for _ in range(args.steps):
-        tg = rng.choice(n, 16, replace=False)
+    T = oracle_targets()
+    for w in range(args.warmup):
+        oracle_sample_cost(s, T, seed=1000 + w)
+    full, wall = [], []
+    for i in range(args.steps):
         a = time.perf_counter()
-        oracle.evaluate(s, targets=tg, tol=1e-8, site_atoms=False)
-        dt = time.perf_counter() - a
-        full.append(dt + (n - 16) * per_target)
-    mean = sum(full) / len(full)
-    val = 1.0 / mean
-    cpu = {"value": val, "unit": "evals/s", "cores": oracle.nthreads(), "kind": "oracle",
-           "sample": (f"each step: FP64 Ewald (tol 1e-8) phi and forces at 16 random atoms of the {n}-atom "
-                      f"system with full structure factors, plus (N - 16) x {per_target * 1e3:.3f} ms per-atom "
-                      f"cost measured in warm-up")}
+        sf, per = oracle_sample_cost(s, T, seed=i)
+        wall.append(time.perf_counter() - a)
+        full.append(sf + n * per)
+    est = statistics.median(full)
+    val = 1.0 / est
+    cpu = {"value": val, "unit": "evals/s", "cores": oracle.nthreads(), "kind": "oracle", "extrapolated": True,
+           "sample": (f"each step: FP64 Ewald oracle (tol 1e-8) on {T} random target atoms of the {n}-atom system "
+                      f"with the full structure factors; the step's phase clock gives one full evaluation as "
+                      f"structure factors + N x per-target cost (median over steps {est:.0f} s, extrapolated)"),
+           "full_eval_s_model": est}
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(wall) / len(wall),
+            "value_is_extrapolated": True, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if not args.small else "solvated_30k", "precision": "fp64"},
             "cpu_baseline": cpu,
@@ -428,7 +454,7 @@ def run_native(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = time_oracle(s)
+        cpu = time_oracle(s, check_full=synth.solvated_30k() if not args.small else None)
         # accuracy of every mode against the FP64 oracle on sampled atoms (plus all site atoms,
         # so dV/dlambda is complete); E needs every atom and is compared between modes instead
         import oracle

@@ -87,6 +87,7 @@ def _load():
         _lib.orc_bin.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                  P, P, P, P, P]
         _lib.orc_nthreads.restype = ctypes.c_int
+        _lib.orc_ewald_phase_seconds.argtypes = [P]
         _lib.orc_ewald_pair.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, P, P]
     return _lib
@@ -98,6 +99,14 @@ def _p(a):
 
 def nthreads() -> int:
     return int(_load().orc_nthreads())
+
+
+def ewald_phase_seconds():
+    """Wall-clock seconds of the last Ewald call's two phases: (structure factors, per-target
+    sums).  Timing only, for the CPU baseline."""
+    out = np.zeros(2)
+    _load().orc_ewald_phase_seconds(_p(out))
+    return float(out[0]), float(out[1])
 
 
 def charges(qA, qB, site, lam):

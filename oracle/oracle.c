@@ -6,7 +6,8 @@
  *
  *   q_i      = qA_i + lambda_{s(i)} (qB_i - qA_i)            (Sec. 2.1, Eq. 1:
  *              the Hamiltonian is linear in lambda and the forms differ only
- *              in their charges; charge-interpolated reading, see DESIGN)
+ *              in their charges; read as charge interpolation, the Hamiltonian
+ *              form's intra-site difference being computed separately)
  *   phi_i    = sum_{j != i} q_j / |x_i - x_j|                 (open boundary)
  *   phi_i    = dE_Ewald/dq_i                                   (periodic cube,
  *              tinfoil boundary, uniform neutralising background)
@@ -93,9 +94,20 @@ static int half_space(int mx, int my, int mz) {
     return mz > 0;
 }
 
+/* Wall-clock seconds of the two phases of the last orc_ewald call (structure factors; the
+ * per-target sums), for timing the oracle as a CPU baseline.  Timing only: it changes nothing
+ * that is computed. */
+static double g_ewald_phase_s[2];
+extern double omp_get_wtime(void);
+void orc_ewald_phase_seconds(double* out) {
+    out[0] = g_ewald_phase_s[0];
+    out[1] = g_ewald_phase_s[1];
+}
+
 void orc_ewald(int n, const double* x, const double* q, double L, double alpha,
                double rc, int mmax, int nt, const int32_t* tgt, double* phi,
                double* grad) {
+    const double t_start = omp_get_wtime();
     const double V = L * L * L;
     const int side = 2 * mmax + 1;
     /* enumerate k vectors */
@@ -136,6 +148,7 @@ void orc_ewald(int n, const double* x, const double* q, double L, double alpha,
     }
     double Q = 0.0;
     for (int j = 0; j < n; ++j) Q += q[j];
+    const double t_sf = omp_get_wtime();
     const double rc2 = rc * rc;
     const double two_a_sqrtpi = 2.0 * alpha / sqrt(M_PI);
 #pragma omp parallel for schedule(dynamic, 8)
@@ -191,6 +204,8 @@ void orc_ewald(int n, const double* x, const double* q, double L, double alpha,
         grad[3 * t + 1] = gy;
         grad[3 * t + 2] = gz;
     }
+    g_ewald_phase_s[0] = t_sf - t_start;
+    g_ewald_phase_s[1] = omp_get_wtime() - t_sf;
     free(km);
     free(kw);
     free(Sre);
