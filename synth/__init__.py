@@ -195,7 +195,9 @@ def water_cluster(seed, L, n_waters, clusters, sites_per_cluster, site_size=5, n
     x = np.concatenate(cl_pts + [wat]) if cl_pts else wat
     qA = np.concatenate(cl_q + [wq]) if cl_q else wq
     x = np.mod(x, L)
-    return _finish(name, x, qA, groups, rng, L, True, p, depth)
+    out = _finish(name, x, qA, groups, rng, L, True, p, depth)
+    out["n_solute"] = off  # cluster atoms come first, then the waters as (O, H, H)
+    return out
 
 
 def oxygen_min_distance(sys_):
@@ -207,6 +209,51 @@ def oxygen_min_distance(sys_):
     t = cKDTree(np.mod(O, L), boxsize=L)
     d, _ = t.query(np.mod(O, L), k=2)
     return float(d[:, 1].min())
+
+
+BUFFER_QA = -0.834  # a water oxygen ...
+BUFFER_QB = 0.166   # ... whose charge changes by +1 (Sec. 2.5, charge buffers)
+
+
+def charge_buffers(s, distance=3.0, exclusion=2.0):
+    """The charge-buffer variant of a water_cluster system (Sec. 2.5): every site k is paired
+    with one water oxygen that joins the site and changes from -0.834 e (qA) to +0.166 e (qB)
+    with lambda_k, so that the pair's net charge, and the box's, does not depend on lambda.
+    The buffer of site k is the not yet used oxygen whose distance from the site's centroid is
+    nearest to `distance` (3 nm), among the oxygens at least `exclusion` (2 nm) from every
+    cluster atom (minimum image).  Returns a new system dict (name + "_buf")."""
+    from scipy.spatial import cKDTree
+    L = s["L"]
+    ns = s["n_solute"]
+    x = s["x"].astype(np.float64)
+    ox = np.arange(ns, len(x), 3)  # the water oxygens
+    assert np.allclose(s["qA"][ox], O_CHARGE)
+    tree = cKDTree(np.mod(x[:ns], L), boxsize=L)
+    dmin, _ = tree.query(np.mod(x[ox], L), k=1)
+    cand = ox[dmin >= exclusion]
+    site = s["site"].copy()
+    qB = s["qB"].copy()
+    used = np.zeros(len(cand), bool)
+    for k in range(len(s["lam"])):
+        g = np.nonzero(site == k)[0]
+        ref = x[g[0]]
+        d = x[g] - ref
+        d -= L * np.round(d / L)
+        c = ref + d.mean(0)
+        r = x[cand] - c
+        r -= L * np.round(r / L)
+        dist = np.sqrt((r * r).sum(1))
+        score = np.abs(dist - distance)
+        score[used] = np.inf
+        j = int(np.argmin(score))
+        used[j] = True
+        site[cand[j]] = k
+        qB[cand[j]] = BUFFER_QB
+    t = dict(s)
+    t["site"] = site
+    t["qB"] = np.ascontiguousarray(qB, np.float32)
+    t["name"] = s["name"] + "_buf"
+    return t
 
 
 # ---- the workloads ----
@@ -221,6 +268,11 @@ def solvated_30k(seed=1, p=8):
     L = 6.5
     return water_cluster(seed, L, 9000, [((L / 2,) * 3, 2000, 1.5)], [20], n_cell=14, p=p,
                          depth=4, name="solvated_30k")
+
+
+def solvated_30k_buf(seed=1, p=8):
+    """The 30k system with one charge buffer per site (Sec. 2.5): neutral at every lambda."""
+    return charge_buffers(solvated_30k(seed, p))
 
 
 def solvated_500k(seed=5, p=10):

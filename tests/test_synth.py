@@ -64,3 +64,35 @@ def test_tautomer_sites_forms():
         assert abs(float(s["qC"][g].astype(np.float64).sum() - s["qA"][g].astype(np.float64).sum()) + 1.0) < 1e-5
     out = ~(s["site"] >= 0)
     assert np.array_equal(s["qA"][out], s["qB"][out])
+
+
+def test_charge_buffer_variant():
+    """Sec. 2.5's charge buffers: every site owns one water oxygen whose charge goes from
+    -0.834 to +0.166 e with the site's lambda, so each site's net change is 0 and the box is
+    neutral at every lambda; the buffer is 2 nm or more from every cluster atom and about 3 nm
+    from its site (minimum image)."""
+    s = synth.solvated_30k_buf()
+    base = synth.solvated_30k()
+    assert s["x"].shape == base["x"].shape and np.array_equal(s["x"], base["x"])
+    np.testing.assert_allclose(_site_changes(s), 0.0, atol=1e-5)
+    K = len(s["lam"])
+    for lam in (np.zeros(K), np.ones(K), np.random.default_rng(3).uniform(-0.1, 1.1, K)):
+        w = np.where(s["site"] >= 0, lam[np.maximum(s["site"], 0)], 0.0)
+        q = s["qA"].astype(np.float64) + w * (s["qB"].astype(np.float64) - s["qA"].astype(np.float64))
+        assert abs(q.sum()) < 1e-4
+    L, ns = s["L"], s["n_solute"]
+    x = s["x"].astype(np.float64)
+    new = np.nonzero((s["site"] >= 0) & (base["site"] < 0))[0]
+    assert len(new) == K and len(np.unique(s["site"][new])) == K
+    assert (new >= ns).all() and ((new - ns) % 3 == 0).all()  # water oxygens
+    assert np.allclose(s["qA"][new], synth.BUFFER_QA) and np.allclose(s["qB"][new], synth.BUFFER_QB)
+    for i in new:
+        d = x[:ns] - x[i]
+        d -= L * np.round(d / L)
+        assert np.sqrt((d * d).sum(1)).min() >= 2.0
+        g = np.nonzero(base["site"] == s["site"][i])[0]
+        r = x[g] - x[g[0]]
+        r -= L * np.round(r / L)
+        c = x[g[0]] + r.mean(0) - x[i]
+        c -= L * np.round(c / L)
+        assert abs(np.linalg.norm(c) - 3.0) < 0.2
