@@ -63,9 +63,15 @@ typedef enum {
     FMM_FP32 = 0,        /* every stage in FP32 on CUDA cores (root/lattice FP64) */
     FMM_MIXED_TF32 = 1,  /* M2L on tcgen05 tensor cores in TF32, FP32 accumulate  */
     FMM_MIXED_3XTF32 = 2, /* M2L as three TF32 products (split operands)          */
-    FMM_MIXED_3XBF16 = 3  /* M2L as three BF16 products hi*hi + hi*lo + lo*hi of
+    FMM_MIXED_3XBF16 = 3, /* M2L as three BF16 products hi*hi + hi*lo + lo*hi of
                              split operands (about 16 significant bits, twice the
                              tensor rate of TF32), FP32 accumulate                  */
+    FMM_MIXED_FP16 = 4    /* M2L in FP16 on the tensor cores, FP32 accumulate: the
+                             input coefficients of degrees 0..3 as three products of
+                             split hi/lo operands (about 22 bits), all higher degrees
+                             as one product (11 bits) -- the far field's monopole and
+                             dipole parts keep full accuracy at about 0.4 of the
+                             3xBF16 tensor work                                      */
 } fmm_precision;
 
 typedef struct {
@@ -250,7 +256,26 @@ fmm_status fmm_status_word(fmm_handle* h, int* device_status, void* stream);
  * fmm_eval works.  Synchronises.  Returns the number of stages written (at
  * most 11). */
 int fmm_stage_times(fmm_handle* h, float* ms, int n);
+/* enable: 0 off, 1 per-stage events (the stages overlap as in an ordinary evaluation), 2 the
+ * same with every stage run on the eval's stream one after the other, so that each stage's
+ * time is that of its kernels alone; FMM_ERR_ARG otherwise. */
 fmm_status fmm_set_profiling(fmm_handle* h, int enable);
+
+/* Bounded device waits.  The tensor-core M2L kernel runs as a pipeline of warps (bulk-copy
+ * producer, MMA issuer, accumulator drains) that wait on one another through shared-memory
+ * barriers; every such wait gives up after a limit of `cycles` GPU clock cycles (<= 0 selects
+ * the default, about 2 s).  A CTA whose wait expires stops issuing work, lets its other warps
+ * stop, waits (with the default limit) for the copies and MMAs it already issued, frees its
+ * tensor memory and returns; the evaluation then sets FMM_DEV_TIMEOUT in the status word (its
+ * results are not valid) and the handle stays usable.  A small limit is a test of that path;
+ * no evaluation should need more than the default.  Discards the handle's evaluation graph. */
+fmm_status fmm_set_wait_limit(fmm_handle* h, long long cycles);
+
+/* Allocation-failure injection, for tests of the out-of-memory paths: with n >= 1 the n-th
+ * device allocation the library makes from now on (in any handle or thread) fails as if the
+ * device were out of memory, and the call that made it returns FMM_ERR_OOM after releasing
+ * what it had allocated; n = 0 switches the injection off.  Returns FMM_ERR_ARG for n < 0. */
+fmm_status fmm_inject_alloc_failure(int n);
 
 /* Number of kernel launches one fmm_eval issues with the current settings. */
 int fmm_launches_per_eval(const fmm_handle* h);

@@ -18,8 +18,9 @@ from . import build as _build
 P = ctypes.c_void_p
 I = ctypes.c_int
 
-FMM_FP32, FMM_MIXED_TF32, FMM_MIXED_3XTF32, FMM_MIXED_3XBF16 = 0, 1, 2, 3
-PRECISIONS = {"fp32": FMM_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF32, "3xbf16": FMM_MIXED_3XBF16}
+FMM_FP32, FMM_MIXED_TF32, FMM_MIXED_3XTF32, FMM_MIXED_3XBF16, FMM_MIXED_FP16 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": FMM_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF32, "3xbf16": FMM_MIXED_3XBF16,
+              "fp16": FMM_MIXED_FP16}
 # lambda dependence within a site (Sec. 2.1, Eq. 1): interpolated charges, or interpolated Hamiltonian
 INTERPOLATIONS = {"charge": 0, "hamiltonian": 1}
 DEV_DOMAIN, DEV_SITE, DEV_TIMEOUT = 1, 2, 4
@@ -56,6 +57,8 @@ EXPORTS = {
     "fmm_launches_per_eval": (I, [P]),
     "fmm_host_operator": (I, [I, I, P, P]),
     "fmm_host_regular": (I, [I, P, P]),
+    "fmm_set_wait_limit": (I, [P, ctypes.c_longlong]),
+    "fmm_inject_alloc_failure": (I, [I]),
     "fmm_binning_noalloc": (I, [ctypes.POINTER(FmmBox), I, I, I, P, P, P, P, P, P, P]),
     "fmm_lambda_step": (I, [I, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                             ctypes.c_ulonglong, ctypes.c_ulonglong, I, ctypes.c_double, ctypes.c_double, P]),
@@ -268,8 +271,13 @@ class FMM:
         _check(self._lib.fmm_status_word(self._h, ctypes.byref(s), _stream()), "fmm_status_word")
         return s.value
 
-    def set_profiling(self, on=True):
-        _check(self._lib.fmm_set_profiling(self._h, int(bool(on))), "fmm_set_profiling")
+    def set_wait_limit(self, cycles=0):
+        """Limit (GPU clock cycles) of the tensor-core M2L's pipeline waits; 0 = the default."""
+        _check(self._lib.fmm_set_wait_limit(self._h, int(cycles)), "fmm_set_wait_limit")
+
+    def set_profiling(self, on=True, serial=False):
+        """Per-stage event timing (stage_times); with ``serial`` every stage runs alone."""
+        _check(self._lib.fmm_set_profiling(self._h, (2 if serial else 1) if on else 0), "fmm_set_profiling")
 
     def stage_times(self):
         ms = (ctypes.c_float * len(STAGES))()

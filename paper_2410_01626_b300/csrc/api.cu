@@ -11,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <atomic>
 
 #include "fmm_internal.h"
 #include "operators.h"
@@ -20,6 +21,21 @@ using namespace fmmcph;
 struct fmm_handle {
     Handle h;
 };
+
+// Allocation-failure injection: > 0 counts down the library's device allocations; the one that
+// brings it to zero fails as if the device were out of memory (no cudaMalloc is attempted).
+static std::atomic<int> g_fail_alloc_in{0};
+
+cudaError_t fmmcph::device_alloc(void** p, size_t bytes) {
+    int k = g_fail_alloc_in.load();
+    while (k > 0 && !g_fail_alloc_in.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 namespace {
 
@@ -36,7 +52,7 @@ template <class T>
 fmm_status dalloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    if (device_alloc((void**)p, sizeof(T) * count) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return FMM_ERR_OOM;
@@ -246,7 +262,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     if (opt) {
         for (int r : opt->reserved)
             if (r != 0) return FMM_ERR_ARG;
-        if (opt->precision < FMM_FP32 || opt->precision > FMM_MIXED_3XBF16) return FMM_ERR_ARG;
+        if (opt->precision < FMM_FP32 || opt->precision > FMM_MIXED_FP16) return FMM_ERR_ARG;
         if (opt->interpolation != FMM_INTERP_CHARGE && opt->interpolation != FMM_INTERP_HAMILTONIAN)
             return FMM_ERR_ARG;
         precision = opt->precision;
@@ -692,9 +708,23 @@ fmm_status fmm_status_word(fmm_handle* H, int* device_status, void* stream) {
     return cuda_ok(cudaMemset(h.status, 0, sizeof(int)));
 }
 
+fmm_status fmm_inject_alloc_failure(int n) {
+    if (n < 0) return FMM_ERR_ARG;
+    g_fail_alloc_in.store(n);
+    return FMM_OK;
+}
+
+fmm_status fmm_set_wait_limit(fmm_handle* H, long long cycles) {
+    if (!H) return FMM_ERR_ARG;
+    H->h.wait_limit = cycles > 0 ? cycles : 0;
+    ++H->h.gen;  // a kernel argument: the captured evaluation graph no longer applies
+    return FMM_OK;
+}
+
 fmm_status fmm_set_profiling(fmm_handle* H, int enable) {
     if (!H) return FMM_ERR_ARG;
-    H->h.profiling = enable != 0;
+    if (enable < 0 || enable > 2) return FMM_ERR_ARG;
+    H->h.profiling = enable;
     ++H->h.gen;
     return FMM_OK;
 }

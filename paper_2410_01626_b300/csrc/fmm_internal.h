@@ -8,6 +8,10 @@
 
 namespace fmmcph {
 
+// Every device allocation of the library goes through here, so that a test can make one fail
+// (fmm_inject_alloc_failure) and check the FMM_ERR_OOM paths.
+cudaError_t device_alloc(void** p, size_t bytes);
+
 constexpr int kMaxP = FMM_MAX_P;
 constexpr int kMaxDepth = 7;
 constexpr int kLeafMomStride = 8;  // floats per leaf in Handle::leafmom
@@ -93,8 +97,11 @@ struct Handle {
     int* status = nullptr;
     float* work = nullptr;  // split-K partial products (8 x the largest M2M output level)
     bool charges_set = false;
+    // limit (clock cycles) of the pipeline waits of the tensor-core M2L; 0 = the default
+    // (about 2 s), a small value lets a test make the waits expire (fmm_set_wait_limit)
+    long long wait_limit = 0;
     // profiling
-    bool profiling = false;
+    int profiling = 0;  // 0 off, 1 per-stage events, 2 the same with every stage serialised
     cudaEvent_t ev[kNumEvents]{};  // a pool of timing events, taken in launch order
     int ev_used = 0;
     int stage_ev[kNumStages][2]{};  // per stage: the pool events that bracket it, -1 if not run

@@ -1636,19 +1636,24 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.epart = h->epart;
     const int e1 = mark(h, st);
     span(h, 0, e0, e1);
-    // fork: the chain P2M .. L2L on h->chain (highest priority), P2P here
-    cudaStream_t cs = h->chain;
+    // fork: the chain P2M .. L2L on h->chain (highest priority), P2P here.  Serialised
+    // profiling runs every stage on the eval's stream, one after the other, so that each
+    // stage's events time its kernels alone.
+    const bool serial = h->profiling == 2;
+    cudaStream_t cs = serial ? st : h->chain;
     const int lc = coarse_top(h);  // top coarse level of the side branch, -1 without one
     cudaEventRecord(h->fork_ev, st);
     cudaStreamWaitEvent(cs, h->fork_ev, 0);
     k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, h->near);
-    span(h, 8, e1, mark(h, st));
-        // --- P2M ---
+    const int e1n = mark(h, st);
+    span(h, 8, e1, e1n);
+    const int e1c = serial ? e1n : e1;  // start of the chain's first stage
+    // --- P2M ---
     float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
     float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
     FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, h, Mleaf, h->periodic ? h->leafmom : nullptr, cs);
     const int e2 = mark(h, cs);
-    span(h, 1, e1, e2);
+    span(h, 1, e1c, e2);
     // --- M2M (FP32) for parent levels d-1 .. lmin: one GEMM per level,
     //     [parents x 8 ncp] (the 8 children are contiguous) x [8 ncp x ncp] ---
     const int lmin = h->periodic ? 1 : 2;
@@ -1684,7 +1689,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         // root and L2L after them fit beside the finest levels' tiles.  Neither M2L launch
         // waits for the near field: their CTAs take the SMs the near field's blocks leave, and
         // its remaining blocks run on the SMs the M2L's second wave leaves idle.
-        cudaStream_t ss = h->side;
+        cudaStream_t ss = serial ? st : h->side;
         cudaEventRecord(h->m2m_ev, cs);
         cudaStreamWaitEvent(ss, h->m2m_ev, 0);
         launch_m2l_tc(h, ss, lmin, lc, kM2lPack);

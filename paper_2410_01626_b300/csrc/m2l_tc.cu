@@ -1,6 +1,6 @@
 // M2L on the 5th-generation tensor cores: tcgen05.mma kind::tf32 (one TF32 product, or three
-// products of hi/lo TF32 parts) or kind::f16 (three products of hi/lo BF16 parts), FP32
-// accumulation in TMEM.
+// products of hi/lo TF32 parts) or kind::f16 (three products of hi/lo BF16 parts, or FP16 with
+// hi/lo parts for the input degrees 0..3 only), FP32 accumulation in TMEM.
 //
 // The multipole-to-local translation of one level is, for every target box b,
 //     L_b = sum_{o in IL(b)} T_o M_{b+o}
@@ -24,6 +24,7 @@
 // warp-wide); warps 2..9 drain TMEM into the Morton-ordered L.
 // Every wait is bounded; on expiry the CTA flags FMM_DEV_TIMEOUT and returns cleanly.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,23 +45,37 @@ constexpr int kTcAccStride = 256;
 constexpr int kTcMaxStages = 16;  // operator-chunk ring depth: as many stages as shared memory holds
 constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
 // Operand forms.  K chunk (input coefficients per slab / operator chunk): 16 for TF32, 8 for
-// the split 3xTF32 form (hi and lo parts), 16 for the split 3xBF16 form.  In every form a ring
-// stage is 8 KB (one operator chunk, both parts) and a slab buffer 64 bytes per row (about 43 KB
-// at depth 5), so two slab buffers leave room for a 16-stage ring.
-enum TcMode { kTf32 = 0, kTf32x3 = 1, kBf16x3 = 2 };
+// the split 3xTF32 form (hi and lo parts), 16 for the split 3xBF16 form.  The FP16 form
+// (kF16mix) has chunks of two kinds in the same 4-cell layout as TF32: chunk 0 holds the
+// input coefficients 0..15 (degrees 0..3) as hi cells 0-1 and lo cells 2-3 (three products,
+// hi hi + hi lo + lo hi, about 22 bits), every later chunk 32 coefficients as hi cells 0-3
+// (one product per K step, 11 bits).  The low degrees carry the large monopole and dipole
+// parts of the far field, whose rounding the potential and dV/dlambda feel most; a single
+// product for every degree gives TF32-like errors (4e-4 in dV/dlambda at 500k atoms), the
+// split of degrees 0..3 alone the errors of the full split (5e-6).  In every form a ring stage
+// is 8 KB (one operator chunk, all parts) and a slab buffer 64 bytes per row (about 43 KB at
+// depth 5), so two slab buffers leave room for a 16-stage ring.
+enum TcMode { kTf32 = 0, kTf32x3 = 1, kBf16x3 = 2, kF16mix = 3 };
 template <int MODE>
 struct TcCfg {
-    static constexpr bool kSplit = MODE != kTf32;
+    static constexpr bool kSplit = MODE == kTf32x3 || MODE == kBf16x3;  // separate lo parts
     static constexpr bool kBf16 = MODE == kBf16x3;
-    static constexpr int kElem = kBf16 ? 2 : 4;             // bytes per operand element
+    static constexpr bool kMix = MODE == kF16mix;
+    static constexpr bool k16 = kBf16 || kMix;              // 16-bit elements, kind::f16
+    static constexpr int kElem = k16 ? 2 : 4;               // bytes per operand element
     static constexpr int kPerCell = 16 / kElem;             // coefficients per 16-byte cell
-    static constexpr int kChunk = kBf16 ? 16 : (kSplit ? 8 : 16);
-    static constexpr int kKG = kChunk / kPerCell;           // cells per chunk row (4, 2, 2)
+    static constexpr int kChunk = kMix ? 32 : kBf16 ? 16 : (kSplit ? 8 : 16);
+    static constexpr int kKG = kChunk / kPerCell;           // cells per chunk row (4, 2, 2, 4)
     static constexpr int kKSteps = kChunk * kElem / 32;     // MMAs per chunk (32 bytes of K each)
     static constexpr int kParts = kSplit ? 2 : 1;
     static constexpr uint32_t kPartBytes = 128u * kChunk * kElem;  // one operator part (hi or lo)
     static constexpr uint32_t kStageBytes = kParts * kPartBytes;   // 8 KB in every form
 };
+// FP16 form: first input coefficient and part (false = hi, true = lo) of cell j (0..3) of
+// chunk ch.
+__host__ __device__ inline int f16mix_base(int ch, int j) { return ch == 0 ? 8 * (j & 1) : 16 + 32 * (ch - 1) + 8 * j; }
+__host__ __device__ inline bool f16mix_lo(int ch, int j) { return ch == 0 && j >= 2; }
+inline int f16mix_chunks(int ncp) { return 1 + (ncp - 16 + 31) / 32; }
 
 struct TcLevels {
     int n[kMaxDepth + 1];
@@ -158,6 +173,49 @@ __global__ void k_m2l_pack(PackLevels pl, int NKG, int ncp, int periodic, const 
     if (Mtc_lo) reinterpret_cast<float4*>(Mtc_lo)[tid] = lo;
 }
 
+// FP16 form: cells of 8 coefficients rounded to FP16 (nearest even); the lo cells of chunk 0
+// hold the FP16 rounding of the remainder.  Coefficients at or beyond ncp are zero.
+__device__ __forceinline__ uint32_t f16_pair(float a, float b) {  // a in the low half (first in memory)
+    return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+}
+__global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int periodic, const float* __restrict__ M,
+                                  float* __restrict__ Mtc_all) {
+    const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= pl.first[pl.nlev]) return;
+    int lv = 0;
+    while (lv + 1 < pl.nlev && gt >= pl.first[lv + 1]) ++lv;
+    const long tid = gt - pl.first[lv];
+    const int n = pl.n[lv], R = pl.R[lv];
+    const float* Mlev = M + pl.m_off[lv];
+    const int row = (int)(tid % R);
+    const int gc = (int)((tid / R) % NKG);
+    const int cls = (int)(tid / ((long)R * NKG));
+    const int m2 = n + 2;
+    int i = row / (m2 * m2) - 1, j = (row / m2) % m2 - 1, k = row % m2 - 1;
+    const int ch = gc >> 2, cell = gc & 3;
+    const int base = f16mix_base(ch, cell);
+    bool ok = base < ncp;  // ncp is a multiple of 16: the cell's 8 coefficients all exist
+    if (periodic) {
+        i = (i + n) % n;
+        j = (j + n) % n;
+        k = (k + n) % n;
+    } else {
+        ok = ok && i >= 0 && i < n && j >= 0 && j < n && k >= 0 && k < n;
+    }
+    uint4 out = make_uint4(0u, 0u, 0u, 0u);
+    if (ok) {
+        const uint32_t box = ((spread3_tc(i) | (spread3_tc(j) << 1) | (spread3_tc(k) << 2)) << 3) | (uint32_t)cls;
+        const float4 x0 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + base);
+        const float4 x1 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + base + 4);
+        float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        if (f16mix_lo(ch, cell))
+#pragma unroll
+            for (int e = 0; e < 8; ++e) xs[e] -= __half2float(__float2half_rn(xs[e]));
+        out = make_uint4(f16_pair(xs[0], xs[1]), f16_pair(xs[2], xs[3]), f16_pair(xs[4], xs[5]), f16_pair(xs[6], xs[7]));
+    }
+    reinterpret_cast<uint4*>(Mtc_all + pl.t_off[lv])[tid] = out;
+}
+
 struct TcTile {
     int level, cls, r0, pad;
 };
@@ -176,7 +234,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const TcTile* __restrict__ tiles, TcLevels lv, const float* __restrict__ Mtc,
              const float* __restrict__ Mtc_lo, const float* __restrict__ Ttc, float* __restrict__ L, int ncp,
-             int NKC, int slab_rows, int nstages, int* __restrict__ status) {
+             int NKC, int slab_rows, int nstages, int* __restrict__ status, int last_half, long long wlim) {
     using Cfg = TcCfg<MODE>;
     constexpr bool SPLIT = Cfg::kSplit;
     constexpr int kTcKG = Cfg::kKG;
@@ -191,8 +249,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint8_t* tring = smem + 2 * (size_t)slab_bytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(tring + (size_t)nstages * kTcTBytes);
     uint64_t* slab_full = bars + 0;    // [2]
-    // (bars + 2 .. 3 unused: a slab buffer is free once its group's MMAs have completed, which is
-    // the accumulator's acc_full phase of that group, so the producer waits on that)
+    // (a slab buffer is free once its group's MMAs have completed, which is the accumulator's
+    // acc_full phase of that group, so the producer waits on that; bars + 3 is unused)
+    uint64_t* mma_done = bars + 2;     // after an abort: every MMA the issuer issued has completed
     uint64_t* acc_full = bars + 4;     // [2]
     uint64_t* acc_empty = bars + 6;    // [2]
     uint64_t* t_full = bars + 8;                 // [nstages]
@@ -222,6 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc::mbar_init(t_full + s, 1);
             tc::mbar_init(t_empty + s, 1);
         }
+        tc::mbar_init(mma_done, 1);
         *abort_flag = 0;
         for (int q = 0; q < 4; ++q) copy_count[q] = 0;
         tc::fence_mbar_init();
@@ -302,6 +362,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int gn = g + 1;
             const uint32_t gn_parity = (uint32_t)(((gn >> 1) - 1) & 1);
             for (int i0 = 0; i0 < cnt; i0 += per_round) {
+                if (__shfl_sync(0xffffffffu, *abort_flag, 0)) {  // another role gave up: issue nothing more
+                    ok = false;
+                    break;
+                }
                 if (!next_issued) {
                     const bool freed =
                         __shfl_sync(0xffffffffu, gn < 2 || (lane == 0 && tc::mbar_test_wait(acc_full + (gn & 1), gn_parity)), 0);
@@ -319,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 bool good = true;
                 if (mine && t_issued + lane >= nstages)  // the chunk nstages back has been consumed
-                    good = tc::mbar_wait(t_empty + stage, (uint32_t)((round - 1) & 1), kWaitLimit);
+                    good = tc::mbar_wait_abort(t_empty + stage, (uint32_t)((round - 1) & 1), wlim, abort_flag);
                 if (__ballot_sync(0xffffffffu, !good)) {
                     ok = false;
                     break;
@@ -339,8 +403,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             __syncwarp();  // sel is rewritten by the next group
             if (ok && !next_issued) {
-                const bool good = __shfl_sync(0xffffffffu, lane != 0 || tc::mbar_wait(acc_full + (gn & 1), gn_parity, kWaitLimit), 0);
-                if (!good) {
+                const bool good = __shfl_sync(
+                    0xffffffffu, lane != 0 || tc::mbar_wait_abort(acc_full + (gn & 1), gn_parity, wlim, abort_flag), 0);
+                if (!good || __shfl_sync(0xffffffffu, *abort_flag, 0)) {
                     ok = false;
                     break;
                 }
@@ -362,7 +427,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // Lean loop: the 27 shifts are unrolled (constant delta), the ring position is a
             // running counter, and the abort flag is only consulted when a wait expires.  Every
             // lane runs the loop so that descriptors and counters stay warp-uniform.
-            const uint32_t idesc = Cfg::kBf16 ? tc::idesc_bf16(128, kTcRows) : tc::idesc_tf32(128, kTcRows);
+            const uint32_t idesc = Cfg::kMix ? tc::idesc_f16(128, kTcRows)
+                                   : Cfg::kBf16 ? tc::idesc_bf16(128, kTcRows) : tc::idesc_tf32(128, kTcRows);
             // descriptors are built once and advanced by adding (byte offset >> 4) to the address field
             const uint64_t a_base = tc::smem_desc_kmajor(tc::smem_u32(tring), 2048u, 128u);
             const uint64_t b_base = tc::smem_desc_kmajor(tc::smem_u32(slab0), kg_stride, 128u);
@@ -372,14 +438,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int t_taken = 0, slabs_taken = 0;
             for (int g = 0; g < ngroups && ok; ++g) {
                 const int pi = g / NKC, buf = g & 1;
+                // FP16 form: the products of this group's chunk -- 0: split (three products),
+                // 1: two K steps of one product, 2: one K step (a half chunk at the end of K)
+                const int ch = g % NKC;
+                const int mix_kind = !Cfg::kMix ? 0 : ch == 0 ? 0 : (ch == NKC - 1 && last_half) ? 2 : 1;
                 const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
                 const int ab = g & 1;
                 const uint32_t dacc = tmem + (uint32_t)(ab * kTcAccStride);
-                if (g >= 2 && !tc::mbar_wait_all(acc_empty + ab, ((g >> 1) - 1) & 1, kWaitLimit)) {
+                if (g >= 2 && !tc::mbar_wait_all_abort(acc_empty + ab, ((g >> 1) - 1) & 1, wlim, abort_flag)) {
                     ok = false;
                     break;
                 }
-                if (!tc::mbar_wait_all(slab_full + buf, (g >> 1) & 1, kWaitLimit)) {
+                if (!tc::mbar_wait_all_abort(slab_full + buf, (g >> 1) & 1, wlim, abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -392,7 +462,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
                     const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
                     if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                    if (!tc::mbar_wait_all(t_full + stage, tphase, kWaitLimit)) {
+                    if (!tc::mbar_wait_all_abort(t_full + stage, tphase, wlim, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -402,6 +472,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     // the MMAs of this chunk, then the commit that releases its ring stage; one
                     // elected lane issues each K step's products (hi(T) hi(M) + hi(T) lo(M) +
                     // lo(T) hi(M) in the split forms)
+                    if (Cfg::kMix) {
+                        // A: cells of 2048 bytes (128 rows), a K step = two cells = 4096 bytes;
+                        // B: cells kg_stride apart.  Split chunk: hi in K-step slot 0, lo in slot 1.
+                        const uint64_t ad1 = ad0 + (4096u >> 4), bd1 = bd0 + ((2u * kg_stride) >> 4);
+                        if (mix_kind == 0)
+                            tc::mma3_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                        else if (mix_kind == 1)
+                            tc::mma_f16_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                        else
+                            tc::mma_f16_w<false, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                        acc = 1;
+                    } else
 #pragma unroll
                     for (int ks = 0; ks < Cfg::kKSteps; ++ks) {  // 32 bytes of K = two cells per MMA
                         const uint64_t ad = ad0 + (uint64_t)ks * (4096u >> 4);
@@ -429,13 +511,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 tc::mma_commit_w(acc_full + ab);  // this group's partial sum is complete, its slab free
             }
-            if (!ok) {
-                if (lane == 0) {
-                    *abort_flag = 1;
-                    atomicOr(status, FMM_DEV_TIMEOUT);
-                }
-                for (int g2 = 0; g2 < 2; ++g2) tc::mma_commit_w(acc_full + g2);  // release the drains
+            if (!ok && lane == 0) {
+                // Give up: no more MMAs.  The other roles see the flag in their waits (nothing
+                // completes a barrier phase without the work behind it, so the producer never
+                // reuses a buffer whose copy has not been consumed).
+                *abort_flag = 1;
+                atomicOr(status, FMM_DEV_TIMEOUT);
             }
+            // Every path: wait (with the full bound) until every MMA issued has completed, so
+            // that none is still reading shared memory or writing TMEM when the CTA frees them --
+            // also when a drain warp gave up after the last group was issued.  Normally this
+            // completes with the last group's accumulator, which the drains wait for anyway.
+            tc::mma_commit_w(mma_done);
+            tc::mbar_wait_all(mma_done, 0, kWaitLimit);
             if (lane == 0) {
                 copy_count[2] = t_taken;
                 copy_count[3] = slabs_taken;
@@ -453,7 +541,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bool ok = true;
         for (int grp = 0; grp < ngroups; ++grp) {
             const int ab = grp & 1;
-            if (!tc::mbar_wait_backoff(acc_full + ab, (grp >> 1) & 1, kWaitLimit) || *abort_flag) {
+            if (!tc::mbar_wait_backoff_abort(acc_full + ab, (grp >> 1) & 1, wlim, abort_flag) || *abort_flag) {
                 ok = false;
                 break;
             }
@@ -498,6 +586,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
         } else if (lane == 0) {
+            *abort_flag = 1;
             atomicOr(status, FMM_DEV_TIMEOUT);
         }
     }
@@ -528,6 +617,7 @@ struct TcState {
     int ntiles = 0;
     int tile_first[kMaxDepth + 2] = {};  // the tiles of level l are [tile_first[l], tile_first[l + 1])
     int NKC = 0;
+    int last_half = 0;  // FP16 form: the last chunk holds 16 coefficients (one K step)
     int KG = 0;  // 16-byte cells per K chunk
     int slab_rows = 0;
     int nstages = 0;  // operator ring depth
@@ -538,7 +628,7 @@ struct TcState {
 bool m2l_tc_supported(const Handle* h) {
     // M = 128 output coefficients per MMA; the slab of the deepest level fits in shared memory
     const bool mixed = h->precision == FMM_MIXED_TF32 || h->precision == FMM_MIXED_3XTF32 ||
-                       h->precision == FMM_MIXED_3XBF16;
+                       h->precision == FMM_MIXED_3XBF16 || h->precision == FMM_MIXED_FP16;
     return mixed && h->ncp <= 128 && h->depth <= 5;
 }
 
@@ -592,13 +682,35 @@ void pack_operators(const std::vector<float>& Trm, int nc, int NKC, std::vector<
                 }
             }
 }
+// FP16 form: [op][chunk][cell j (4)][128 rows][16 bytes], cell j of chunk ch holding the
+// coefficients f16mix_base(ch, j) .. + 7 (hi part, or for the lo cells of chunk 0 the FP16
+// rounding of the remainder), zero at or beyond nc.
+void pack_operators_f16mix(const std::vector<float>& Trm, int nc, int NKC, std::vector<uint8_t>& out) {
+    out.assign((size_t)kNumOps * NKC * 8192, 0);
+    for (int op = 0; op < kNumOps; ++op)
+        for (int ch = 0; ch < NKC; ++ch)
+            for (int j = 0; j < 4; ++j) {
+                const int base = f16mix_base(ch, j);
+                for (int jj = 0; jj < nc; ++jj)
+                    for (int e = 0; e < 8 && base + e < nc; ++e) {
+                        const float v = Trm[((size_t)op * nc + jj) * nc + base + e];
+                        const __half hi = __float2half_rn(v);
+                        const __half w = f16mix_lo(ch, j) ? __float2half_rn(v - __half2float(hi)) : hi;
+                        const size_t cell = (((size_t)op * NKC + ch) * 4 + j) * 128 + jj;
+                        std::memcpy(out.data() + cell * 16 + (size_t)e * 2, &w, 2);
+                    }
+            }
+}
 }  // namespace
 
 int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc] j-major*/) {
     TcState* st = new TcState();
     h->tc = st;
     const int nc = h->nc, ncp = h->ncp, d = h->depth;
-    st->mode = h->precision == FMM_MIXED_3XTF32 ? kTf32x3 : h->precision == FMM_MIXED_3XBF16 ? kBf16x3 : kTf32;
+    st->mode = h->precision == FMM_MIXED_3XTF32 ? kTf32x3
+               : h->precision == FMM_MIXED_3XBF16 ? kBf16x3
+               : h->precision == FMM_MIXED_FP16   ? kF16mix
+                                                  : kTf32;
     int chunk = 0, nparts = 1;
     uint32_t stage_bytes = 0;
     std::vector<uint8_t> T;
@@ -614,6 +726,13 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
             stage_bytes = TcCfg<kBf16x3>::kStageBytes;
             st->NKC = (ncp + chunk - 1) / chunk;
             pack_operators<kBf16x3>(T_rowmajor, nc, st->NKC, T);
+            break;
+        case kF16mix:
+            st->KG = TcCfg<kF16mix>::kKG, nparts = 1;
+            stage_bytes = TcCfg<kF16mix>::kStageBytes;
+            st->NKC = f16mix_chunks(ncp);
+            st->last_half = (ncp - 16) % 32 == 16;
+            pack_operators_f16mix(T_rowmajor, nc, st->NKC, T);
             break;
         default:
             chunk = TcCfg<kTf32>::kChunk, st->KG = TcCfg<kTf32>::kKG, nparts = 1;
@@ -654,10 +773,10 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     st->nstages = std::max(3, std::min(kTcMaxStages, (int)(room / stage_bytes)));
     st->smem = slabs + (size_t)st->nstages * stage_bytes + kBarBytes;
     st->ntiles = (int)tiles.size();
-    if (cudaMalloc(&st->Ttc, T.size()) != cudaSuccess ||
-        cudaMalloc(&st->Mtc, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess ||
-        (nparts == 2 && cudaMalloc(&st->Mtc_lo, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess) ||
-        cudaMalloc(&st->tiles, sizeof(TcTile) * (tiles.empty() ? 1 : tiles.size())) != cudaSuccess) {
+    if (device_alloc((void**)&st->Ttc, T.size()) != cudaSuccess ||
+        device_alloc((void**)&st->Mtc, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess ||
+        (nparts == 2 && device_alloc((void**)&st->Mtc_lo, sizeof(float) * (off > 0 ? off : 4)) != cudaSuccess) ||
+        device_alloc((void**)&st->tiles, sizeof(TcTile) * (tiles.empty() ? 1 : tiles.size())) != cudaSuccess) {
         cudaGetLastError();
         return FMM_ERR_OOM;
     }
@@ -670,6 +789,7 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     cudaFuncSetAttribute(k_m2l_tc<kTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_m2l_tc<kTf32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     cudaFuncSetAttribute(k_m2l_tc<kBf16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaFuncSetAttribute(k_m2l_tc<kF16mix>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     return FMM_OK;
 }
 
@@ -709,26 +829,37 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream, int lo, int hi, int parts) {
     pl.first[pl.nlev] = tot;
     if (tot > 0 && (parts & kM2lPack)) {
         const unsigned grid = (unsigned)((tot + 255) / 256);
-        if (bf16)
+        if (st->mode == kF16mix)
+            k_m2l_pack_f16mix<<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc);
+        else if (bf16)
             k_m2l_pack<true><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
         else
             k_m2l_pack<false><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
     }
     const int t0 = st->tile_first[lo], nt = st->tile_first[hi + 1] - t0;
     if (nt <= 0 || !(parts & kM2lMma)) return;
+    const long long wlim = h->wait_limit > 0 ? h->wait_limit : kWaitLimit;
     const TcTile* tiles = st->tiles + t0;
     switch (st->mode) {
         case kTf32x3:
             k_m2l_tc<kTf32x3><<<nt, kTcThreads, st->smem, stream>>>(
-                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
+                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
+                0, wlim);
             break;
         case kBf16x3:
             k_m2l_tc<kBf16x3><<<nt, kTcThreads, st->smem, stream>>>(
-                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
+                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
+                0, wlim);
+            break;
+        case kF16mix:
+            k_m2l_tc<kF16mix><<<nt, kTcThreads, st->smem, stream>>>(
+                tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
+                st->last_half, wlim);
             break;
         default:
             k_m2l_tc<kTf32><<<nt, kTcThreads, st->smem, stream>>>(
-                tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status);
+                tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
+                0, wlim);
     }
 }
 

@@ -71,6 +71,35 @@ __device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// Bounded waits that also give up when another role of the CTA has set the shared abort flag
+// (read only while the barrier is not yet complete, so the fast path is unchanged).  They
+// return true only when the phase has completed.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, long long limit,
+                                                const volatile int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort || clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ bool mbar_wait_all_abort(uint64_t* bar, uint32_t parity, long long limit,
+                                                    const volatile int* abort) {
+    return __all_sync(0xffffffffu, mbar_wait_abort(bar, parity, limit, abort));
+}
+__device__ __forceinline__ bool mbar_wait_backoff_abort(uint64_t* bar, uint32_t parity, long long limit,
+                                                        const volatile int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort || clock64() - t0 > limit) return false;
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+    }
+    return true;
+}
+
 // ---- bulk asynchronous copy global -> shared (16-byte aligned, size multiple of 16) ----
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -190,6 +219,45 @@ __device__ __forceinline__ void mma3_w(uint32_t d_tmem, uint64_t a, uint64_t b, 
                 : "memory");
     }
 }
+// The products of one 32-byte K step pair of a kind::f16 chunk by one elected lane: with TWO,
+// (a, b) + (a2, b2) (two consecutive K steps), else (a, b) alone; optionally followed by a
+// commit to `bar`.  The operand type (FP16 or BF16) comes from the instruction descriptor.
+template <bool TWO, bool COMMIT>
+__device__ __forceinline__ void mma_f16_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint64_t a2, uint64_t b2,
+                                          uint32_t idesc, uint32_t accumulate, uint64_t* bar) {
+    if (TWO) {
+        if (COMMIT)
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %5, p;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %5, 1;\n"
+                " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%7];\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "l"(a2), "l"(b2), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
+                : "memory");
+        else
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %5, p;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %5, 1;\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "l"(a2), "l"(b2), "r"(idesc), "r"(accumulate)
+                : "memory");
+    } else {
+        if (COMMIT)
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%5];\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
+                : "memory");
+        else
+            asm volatile(
+                "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+                : "memory");
+    }
+}
+
 // One TF32 MMA by one elected lane, optionally followed by a commit to `bar`.
 template <bool COMMIT>
 __device__ __forceinline__ void mma1_tf32_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate,
@@ -240,6 +308,11 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 // Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, dense.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor: kind::f16, D = F32, A = B = FP16, both K-major, dense.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ float round_tf32(float x) {

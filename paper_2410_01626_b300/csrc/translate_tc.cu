@@ -249,7 +249,7 @@ TranslateOp translate_pack(const std::vector<float>& W, int Mtot, int K) {
             P[(cell + (size_t)kGCells * kGRows) * 4 + e] = lo;  // part 1: kGCells cells further
         }
     op.bytes = P.size() * 4;
-    if (cudaMalloc(&op.dev, op.bytes) != cudaSuccess) {
+    if (device_alloc((void**)&op.dev, op.bytes) != cudaSuccess) {
         cudaGetLastError();
         op.dev = nullptr;
         return op;
