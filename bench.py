@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32", "3xtf32", "3xbf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "tf32", "3xtf32", "3xbf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="30k-atom system (for profiling runs)")
@@ -261,10 +261,10 @@ def run_native(args):
 
     from paper_2410_01626_b300.binding import load as _load
     precision = args.precision
-    if precision == "auto":  # the split-BF16 tensor-core mode when the library offers it for this p
+    if precision == "auto":  # the FP16 tensor-core mode (split low degrees) when the library offers it for this p
         try:
-            FMM(s["L"], True, s["p"], 0, precision="3xbf16").close()
-            precision = "3xbf16"
+            FMM(s["L"], True, s["p"], 0, precision="fp16").close()
+            precision = "fp16"
         except Exception:
             precision = "fp32"
 
@@ -294,6 +294,16 @@ def run_native(args):
         stage_runs.append(f.stage_times())
     f.set_profiling(False)
     stages = {k: statistics.median(r[k] for r in stage_runs) for k in stage_runs[0]}
+    # the same with every stage run alone, one after the other: each kernel's own duration,
+    # which its roofline needs (in the ordinary evaluation the stages share the SMs)
+    f.set_profiling(True, serial=True)
+    alone_runs = []
+    for _ in range(3):
+        flush.zero_()
+        one_step()
+        alone_runs.append(f.stage_times())
+    f.set_profiling(False)
+    stages_alone = {k: statistics.median(r[k] for r in alone_runs) for k in alone_runs[0]}
     # leaving profiling mode drops the handle's evaluation graph: warm up again, so that its
     # capture (host work while the GPU waits) stays outside the timed region
     for _ in range(max(args.warmup, 3)):
@@ -345,7 +355,7 @@ def run_native(args):
         return ws * 1000.0 / (sum(tms) / len(tms)), (Eg, Fg, dVg)
 
     modes = {precision: {"evals_per_s": value, "out": (E, F, dV)}}
-    for prec in ("fp32", "tf32", "3xtf32", "3xbf16"):
+    for prec in ("fp32", "tf32", "3xtf32", "3xbf16", "fp16"):
         if prec not in modes:
             try:
                 v, o = time_mode(prec, min(args.steps, 10))
@@ -419,7 +429,7 @@ def run_native(args):
     lev = range(s["depth"] - 1, s["depth"] + 1) if split else range(1, s["depth"] + 1)
     boxes = sum(8 ** l for l in lev)
     m2l_flop = boxes * 189 * 2 * nc * nc
-    m2l_ms = stages.get("m2l", float("nan"))
+    m2l_ms = stages_alone.get("m2l", float("nan"))  # the kernel alone (L2 flushed before the step)
     achieved = m2l_flop / (m2l_ms * 1e-3) / 1e12
     sm_mhz = clocks.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1177.0)
     if precision == "fp32":
@@ -428,17 +438,23 @@ def run_native(args):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"FP32 FMA: 148 SM x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled median)"}
     else:
-        bf16 = peaks.get("bf16_tflops_sustained", 1379.9)
-        if precision == "3xbf16":
-            peak = bf16
-            src = "measured sustained bf16 cuBLAS, of measured"
-        else:
-            peak = bf16 * 0.5
-            src = "measured sustained bf16 cuBLAS x 0.5 (nominal tf32/bf16 ratio), of measured"
+        # the M2L launch is a sub-millisecond kernel, so the burst figure applies; the sustained
+        # one (a seconds-long GEMM loop under the power cap) is reported beside it
+        bf16 = peaks.get("bf16_tflops", 1738.8)
+        bf16_sus = peaks.get("bf16_tflops_sustained", 1348.1)
+        ratio = 1.0 if precision in ("3xbf16", "fp16") else 0.5  # 16-bit forms: the bf16 rate; TF32: half
+        peak = bf16 * ratio
+        src = ("measured burst bf16 cuBLAS, of measured" if ratio == 1.0 else
+               "measured burst bf16 cuBLAS x 0.5 (nominal tf32/bf16 ratio), of measured")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": src}
-        # what the tensor pipe executes: 128 x 128 padded operators, 3 products per term when split
-        executed = m2l_flop * (128.0 / nc) ** 2 * (3 if precision in ("3xtf32", "3xbf16") else 1)
+                "peak_source": src, "peak_sustained": bf16_sus * ratio,
+                "frac_of_sustained": achieved / (bf16_sus * ratio)}
+        # what the tensor pipe executes: 128 output rows x the K it multiplies -- ncp (padded
+        # coefficients) once, three times in the split forms, and in the FP16 form the first
+        # 16 coefficients three times and the rest once
+        ncp = 16 * ((nc + 15) // 16)
+        keff = {"tf32": ncp, "3xtf32": 3 * ncp, "3xbf16": 3 * ncp, "fp16": ncp + 32}[precision]
+        executed = boxes * 189 * 2.0 * 128 * keff
         roof["pipe_flop_per_launch"] = executed
         roof["pipe_frac"] = executed / (m2l_ms * 1e-3) / 1e12 / peak
     roof["traffic"] = m2l_traffic(precision)
@@ -451,6 +467,31 @@ def run_native(args):
     roof["flop_per_launch_rotation_count"] = rot_flop
     roof["achieved_rotation_count"] = rot_flop / (m2l_ms * 1e-3) / 1e12
     roof["ms_per_launch"] = m2l_ms
+    roof["ms_in_step"] = stages.get("m2l")  # the same launch inside an ordinary step, sharing SMs
+
+    # roofline of the near field (P2P), the kernel alone: 20 flop per ordered pair (3 sub, r^2
+    # 3, q/r 1, potential 1, q/r^3 2, gradient 3 FMA = 13 FP32 operations, counted as the usual
+    # 20 flop with the FMAs as two) against the FP32 pipe: 148 SMs x 128 lanes x 2 flop x clock
+    counts = f.binning()[3].cpu().numpy().astype(np.int64)
+    nb = 1 << s["depth"]
+    grid = np.zeros((nb, nb, nb), np.int64)
+    leaves = np.arange(len(counts))
+    def compact(v):
+        out = np.zeros_like(v)
+        for b in range(s["depth"]):
+            out |= ((v >> (3 * b)) & 1) << b
+        return out
+    grid[compact(leaves), compact(leaves >> 1), compact(leaves >> 2)] = counts
+    nbsum = sum(np.roll(grid, (dx, dy, dz), (0, 1, 2)) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1))
+    pairs = int((grid * nbsum).sum()) - n  # ordered pairs i != j over the 27 neighbour leaves
+    p2p_ms = stages_alone.get("p2p", float("nan"))
+    p2p_flop = 20.0 * pairs
+    p2p_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    p2p_ach = p2p_flop / (p2p_ms * 1e-3) / 1e12
+    roof_p2p = {"bound": "alu", "achieved": p2p_ach, "peak": p2p_peak, "unit": "TFLOP/s", "frac": p2p_ach / p2p_peak,
+                "peak_source": f"FP32 FMA: 148 SM x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (sampled median), derived",
+                "kernel": "P2P near field (k_p2p), alone", "pairs": pairs, "flop_per_launch": p2p_flop,
+                "ms_per_launch": p2p_ms, "ms_in_step": stages.get("p2p")}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -493,13 +534,14 @@ def run_native(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "3xtf32": "tf32x3", "3xbf16": "bf16x3"}[precision],
+                "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "3xtf32": "tf32x3", "3xbf16": "bf16x3", "fp16": "f16"}[precision],
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD if not args.small else "solvated_30k, p=10, depth 4",
                            "precision": precision, "atoms": n, "sites": K, "p": s["p"], "depth": s["depth"],
                            "l2": "flushed between steps (256 MiB write outside each step's event pair)",
                            "parallelism": f"replicas x{ws}"},
-                "stages_ms": stages, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "stages_ms": stages, "stages_alone_ms": stages_alone, "roofline": roof, "roofline_p2p": roof_p2p,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "wall_s_timed": wall1 - wall0}
         line["modes"] = modes
         print(json.dumps(line), flush=True)

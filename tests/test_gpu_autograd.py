@@ -108,7 +108,7 @@ def test_finite_differences_in_x_and_lambda(sys30k):
 def test_cuda_graph_replay_is_bitwise_equal():
     s = synth.periodic_uniform(seed=4, n=20000, L=5.0, p=8, depth=4)
     d = to_dev(s)
-    for prec in ("fp32", "3xtf32", "3xbf16"):
+    for prec in ("fp32", "3xtf32", "3xbf16", "fp16"):
         f = FMM(s["L"], True, s["p"], s["depth"], precision=prec)
         f.set_charges(d["qA"], d["qB"], d["site"], d["lam"])
         E, F, dV, _ = f.outputs()

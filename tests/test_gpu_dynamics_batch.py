@@ -81,7 +81,7 @@ def test_batch_equals_standalone_bitwise():
     systems = [synth.replica(100 + i) for i in (0, 3, 7, 12)]
     systems += [synth.periodic_uniform(seed=21, n=3000, L=3.0, p=8, depth=3),
                 synth.open_uniform(seed=22, n=2500, L=4.0, n_sites=3, site_size=4, p=6, depth=3)]
-    precisions = ["3xtf32", "tf32", "fp32", "3xbf16", "fp32", "3xbf16"]
+    precisions = ["3xtf32", "tf32", "fp32", "3xbf16", "fp16", "3xbf16"]
     solvers, devs, refs = [], [], []
     for s, prec in zip(systems, precisions):
         f, d = make_solver(s, precision=prec)

@@ -1,8 +1,8 @@
 """Parity at the full benchmark size: the solvated periodic system of 500,000
 atoms (17 nm cube, 160,000 waters and four 5,000-atom clusters, 200 sites;
-p = 10, depth 5), in the launch configuration the benchmark times (split-BF16
-M2L; the second call with the same buffers captures a CUDA graph and later
-calls replay it).
+p = 10, depth 5), in the launch configuration the benchmark times (FP16 M2L with
+split low degrees; the second call with the same buffers captures a CUDA graph
+and later calls replay it), and in the split-BF16 and FP32 forms.
 
 The FP64 oracle cannot evaluate all 500,000 atoms in seconds, so it computes
 Ewald potentials and forces one target at a time for 400 random atoms plus
@@ -10,7 +10,7 @@ every site atom (which makes dV/dlambda complete).  Bars: relative RMS force
 error <= 1e-4 for the mixed form at this size and dV/dlambda within 1e-4
 relative; the FP32 CUDA-core path meets the same bars.  E needs every atom, so
 it is checked through properties that hold at any size: E = 1/2 sum_i q_i phi_i
-with the returned phi (k_e times the potential), and agreement of the split-BF16
+with the returned phi (k_e times the potential), and agreement of the tensor-core
 and FP32 paths.
 """
 import numpy as np
@@ -61,13 +61,14 @@ def _evals(s, precision, calls):
 @pytest.fixture(scope="module")
 def runs(system):
     s, _ = system
-    bf, st_bf = _evals(s, "3xbf16", 3)
+    h, st_h = _evals(s, "fp16", 3)
+    bf, st_bf = _evals(s, "3xbf16", 1)
     fp, st_fp = _evals(s, "fp32", 1)
-    assert st_bf == 0 and st_fp == 0
-    return {"3xbf16": bf, "fp32": fp}
+    assert st_h == 0 and st_bf == 0 and st_fp == 0
+    return {"fp16": h, "3xbf16": bf, "fp32": fp}
 
 
-@pytest.mark.parametrize("precision", ["3xbf16", "fp32"])
+@pytest.mark.parametrize("precision", ["fp16", "3xbf16", "fp32"])
 def test_full_size_sampled_atoms_vs_oracle(system, runs, precision):
     s, ref = system
     g = runs[precision][-1]
@@ -84,7 +85,7 @@ def test_full_size_sampled_atoms_vs_oracle(system, runs, precision):
 
 
 def test_full_size_graph_replay_repeats_the_eager_evaluation(runs):
-    eager, captured, replayed = runs["3xbf16"]
+    eager, captured, replayed = runs["fp16"]
     for k in ("F", "dVdl", "phi"):
         np.testing.assert_array_equal(captured[k], eager[k])
         np.testing.assert_array_equal(replayed[k], eager[k])
@@ -94,9 +95,11 @@ def test_full_size_graph_replay_repeats_the_eager_evaluation(runs):
 def test_full_size_energy_properties(system, runs):
     s, _ = system
     q, _ = oracle.charges(s["qA"], s["qB"], s["site"], s["lam"])
-    for prec in ("3xbf16", "fp32"):
+    for prec in ("fp16", "3xbf16", "fp32"):
         g = runs[prec][-1]
         e_phi = 0.5 * float(np.dot(q, g["phi"]))  # phi carries k_e
         assert abs(g["E"] - e_phi) < 1e-6 * abs(g["E"]), (prec, g["E"], e_phi)
-    Eb, Ef = runs["3xbf16"][-1]["E"], runs["fp32"][0]["E"]
-    assert abs(Eb - Ef) < 1e-5 * abs(Ef), (Eb, Ef)
+    Ef = runs["fp32"][0]["E"]
+    for prec in ("fp16", "3xbf16"):
+        Eb = runs[prec][-1]["E"]
+        assert abs(Eb - Ef) < 1e-5 * abs(Ef), (prec, Eb, Ef)

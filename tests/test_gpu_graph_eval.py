@@ -30,7 +30,7 @@ def _eager(s, x, lam, precision="3xbf16"):
     return out
 
 
-@pytest.mark.parametrize("precision", ["3xbf16", "fp32"])
+@pytest.mark.parametrize("precision", ["3xbf16", "fp16", "fp32"])
 def test_replayed_evaluations_equal_eager_launches(precision):
     s = synth.solvated_30k()
     f, t = _solver(s, precision)

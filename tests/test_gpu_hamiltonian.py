@@ -27,7 +27,8 @@ def _systems():
 
 
 @pytest.mark.parametrize("which,precision", [(0, "fp32"), (1, "fp32"), (2, "fp32"), (0, "3xtf32"), (1, "3xtf32"),
-                                             (2, "3xtf32"), (0, "3xbf16"), (2, "3xbf16")])
+                                             (2, "3xtf32"), (0, "3xbf16"), (2, "3xbf16"), (0, "fp16"),
+                                             (1, "fp16"), (2, "fp16")])
 def test_hamiltonian_parity_with_oracle(which, precision):
     s = _systems()[which]
     tg = None if which < 2 else np.arange(0, len(s["x"]), 97)

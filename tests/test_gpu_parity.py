@@ -209,6 +209,35 @@ def test_periodic_solvated_30k():
     assert g["status"] == 0
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_periodic_solvated_30k_charge_buffers(precision):
+    """The 30k system with a charge buffer per site (Sec. 2.5): neutral at every lambda, so
+    the background term vanishes and the periodic FMM alone must match Ewald, at the same
+    bars as the non-neutral base system (where the background term carries the net charge)."""
+    s = synth.solvated_30k_buf()
+    ref = oracle_ref(s, tol=1e-9)
+    g = run_gpu(s, precision=precision)
+    e = errors(g, ref)
+    assert e["F"] < 2e-4 and e["dVdl"] < 1e-4 and e["E"] < 1e-4, e
+    assert g["status"] == 0
+
+
+@pytest.mark.slow
+def test_periodic_p12_force_accuracy():
+    """p = 12 in a periodic box: the relative RMS force error against Ewald at most 1e-5
+    (the p = 12 bar), on the 30k solvated system at depth 4 (1,000 sampled atoms plus the
+    site atoms)."""
+    s = synth.solvated_30k(p=12)
+    tg = np.random.default_rng(12).choice(len(s["x"]), 1000, replace=False)
+    ref = oracle_ref(s, targets=tg, tol=1e-10)
+    g = run_gpu(s)
+    e = errors(g, ref, idx=ref["idx"])
+    print(f"periodic p=12: {e}")
+    assert e["F"] < 1e-5 and e["dVdl"] < 1e-4, e
+    assert g["status"] == 0
+
+
 # ---------------------------------------------------------------- API behaviour
 def test_deterministic_bitwise():
     s = synth.periodic_uniform(seed=3, n=4000, L=3.0, p=8, depth=3)
@@ -354,4 +383,57 @@ def test_3xbf16_close_to_fp32_path():
     dE = abs(a["E"] - b["E"]) / abs(a["E"])
     dV = np.linalg.norm(a["dVdl"] - b["dVdl"]) / np.linalg.norm(a["dVdl"])
     print(f"3xbf16 vs fp32: dF {dF:.2e} dE {dE:.2e} dVdl {dV:.2e}")
+    assert dF < 2e-6 and dE < 1e-5 and dV < 1e-4, (dF, dE, dV)
+
+
+# ---------------------------------------------------------------- tensor-core M2L (FP16, split low degrees)
+@pytest.mark.parametrize("periodic,p,depth", [(True, 8, 3), (True, 10, 3), (False, 8, 2), (False, 10, 4), (True, 10, 1)])
+def test_fp16_m2l_parity(periodic, p, depth):
+    """FP16 M2L: the input coefficients of degrees 0..3 as split hi/lo operands (three
+    products, about 22 bits), every higher degree as one FP16 product (11 bits).  E, F and
+    dV/dlambda within 1e-4 of the oracle, like the FP32 path."""
+    if periodic:
+        s = synth.periodic_uniform(seed=3, n=3000, L=3.0, n_sites=8, site_size=4, p=p, depth=depth)
+    else:
+        s = synth.open_uniform(seed=5, n=3000, L=5.0, n_sites=8, site_size=4, p=p, depth=depth)
+    ref = oracle_ref(s)
+    g = run_gpu(s, precision="fp16")
+    e = errors(g, ref)
+    print(f"fp16 periodic={periodic} p={p} depth={depth}: {e}")
+    assert g["status"] == 0
+    assert e["F"] < 1e-4 and e["E"] < 1e-4 and e["dVdl"] < 1e-4, e
+
+
+@pytest.mark.parametrize("periodic,p,depth", [(True, 4, 3), (True, 5, 3), (False, 6, 3), (True, 6, 3)])
+def test_fp16_m2l_low_orders_add_nothing_to_truncation(periodic, p, depth):
+    """At p = 4..6 the expansion's truncation error (1e-3 and above) dominates: the FP16 form
+    must add nothing to it -- its errors against the oracle equal the FP32 path's.  These
+    orders cover the other shapes of the K chunks (ncp = 32, 48, 64: a last chunk of one or
+    two K steps)."""
+    if periodic:
+        s = synth.periodic_uniform(seed=3, n=3000, L=3.0, n_sites=8, site_size=4, p=p, depth=depth)
+    else:
+        s = synth.open_uniform(seed=5, n=3000, L=5.0, n_sites=8, site_size=4, p=p, depth=depth)
+    ref = oracle_ref(s)
+    g = run_gpu(s, precision="fp16")
+    a = run_gpu(s, precision="fp32")
+    e, e32 = errors(g, ref), errors(a, ref)
+    print(f"fp16 p={p}: {e}; fp32: {e32}")
+    assert g["status"] == 0
+    for k in ("E", "F", "dVdl"):
+        assert e[k] < 1.05 * e32[k] + 1e-6, (k, e, e32)
+
+
+def test_fp16_close_to_fp32_path():
+    """The FP16 form against the FP32 CUDA-core path on the same input: the degrees 0..3 of
+    every multipole carry about 2^-22 relative rounding, the higher degrees 2^-12 of terms
+    that are themselves small.  Measured bars as for the split BF16 form; a wrong cell
+    layout, chunk kind or descriptor shows as an O(1) difference."""
+    s = synth.periodic_uniform(seed=11, n=6000, L=3.5, n_sites=8, site_size=4, p=10, depth=3)
+    a = run_gpu(s, precision="fp32")
+    b = run_gpu(s, precision="fp16")
+    dF = np.sqrt(((a["F"] - b["F"]) ** 2).sum() / (a["F"] ** 2).sum())
+    dE = abs(a["E"] - b["E"]) / abs(a["E"])
+    dV = np.linalg.norm(a["dVdl"] - b["dVdl"]) / np.linalg.norm(a["dVdl"])
+    print(f"fp16 vs fp32: dF {dF:.2e} dE {dE:.2e} dVdl {dV:.2e}")
     assert dF < 2e-6 and dE < 1e-5 and dV < 1e-4, (dF, dE, dV)
