@@ -95,7 +95,15 @@ typedef struct {
     int precision;      /* fmm_precision                           */
     double coulomb_k;   /* k_e; <= 0 selects 138.935458             */
     int interpolation;  /* fmm_interpolation                       */
-    int reserved[7];    /* must be zero                             */
+    /* Kernel tiles (results are the same for every choice; the autotuner picks them by timing).
+     * m2l_tile_rows: rows of the tensor-core M2L's per-CTA tile (the MMA's N): 128, 192 or 256;
+     *   0 selects 192.
+     * p2p_leaves_per_block: target leaves (one warp each) per near-field block: 2 or 4; 0
+     *   selects 4.
+     * Other values return FMM_ERR_ARG. */
+    int m2l_tile_rows;
+    int p2p_leaves_per_block;
+    int reserved[5];    /* must be zero                             */
 } fmm_options;
 
 typedef struct fmm_handle fmm_handle;
@@ -160,15 +168,17 @@ fmm_status fmm_bind_lambda(fmm_handle* h, const float* lambda);
  *               input order (may be NULL)
  * Stream-ordered; all outputs are complete when the stream reaches the end
  * of the call.  Returns FMM_ERR_STATE before fmm_set_charges.
- * The second call in a row with the same five pointers captures the
- * evaluation into a CUDA graph owned by the handle (on a private stream) and
- * later calls with those pointers replay it on `stream`; the kernels and the
- * results are those of launching them one by one.  The graph reads the
- * buffers at replay, so positions and lambda written in place (or with
- * fmm_set_lambda) are seen; fmm_set_charges*, fmm_bind_lambda and
- * fmm_set_profiling discard it.  While profiling, or when `stream` is being
- * captured by the caller, the kernels are launched one by one (and so join
- * the caller's capture). */
+ * When the same five pointers come again within the handle's last two eager
+ * evaluations, the evaluation is captured into a CUDA graph owned by the
+ * handle (on a private stream), and later calls with those pointers replay
+ * it on `stream`; the handle keeps the graphs of the two most recent pointer
+ * sets (so two sets used in turn both replay).  The kernels and the results
+ * are those of launching them one by one.  A graph reads the buffers at
+ * replay, so positions and lambda written in place (or with fmm_set_lambda)
+ * are seen; fmm_set_charges*, fmm_bind_lambda, fmm_set_profiling and
+ * fmm_set_wait_limit discard the graphs.  While profiling, or when `stream`
+ * is being captured by the caller, the kernels are launched one by one (and
+ * so join the caller's capture). */
 fmm_status fmm_eval(fmm_handle* h, const float* x, double* E, float* F, float* dVdlambda,
                     float* phi, void* stream);
 
@@ -180,6 +190,18 @@ fmm_status fmm_eval(fmm_handle* h, const float* x, double* E, float* F, float* d
  * pointer may be NULL. */
 fmm_status fmm_eval_host(fmm_handle* h, const float* x_host, double* E_host, float* F_host,
                          float* dVdlambda_host, void* stream);
+
+/* fmm_eval_host without the final synchronisation, for callers that keep several
+ * evaluations in flight: enqueues the copy of x_host to the device, the evaluation and the
+ * copies of E, F and dV/dlambda back, and returns.  The results are in the host buffers once
+ * `stream` has reached the end of the call (cudaStreamSynchronize, or an event recorded
+ * after it); until then the caller must keep the buffers and leave x_host unchanged.
+ * Consecutive calls use two device staging sets in turn: a call's position copy runs on the
+ * handle's own copy stream as soon as its set's previous use has finished, so with
+ * page-locked buffers it overlaps the previous call's evaluation.  When `stream` is being
+ * captured the copy runs on `stream` itself. */
+fmm_status fmm_eval_host_async(fmm_handle* h, const float* x_host, double* E_host, float* F_host,
+                               float* dVdlambda_host, void* stream);
 
 /* Page-locked host memory for the buffers of fmm_eval_host (not part of the
  * method; a convenience for callers).  Copies between this memory and the

@@ -37,7 +37,7 @@ class FmmBox(ctypes.Structure):
 
 class FmmOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coulomb_k", ctypes.c_double), ("interpolation", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("m2l_tile_rows", ctypes.c_int), ("p2p_leaves_per_block", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 EXPORTS = {
@@ -48,6 +48,7 @@ EXPORTS = {
     "fmm_bind_lambda": (I, [P, P]),
     "fmm_eval": (I, [P, P, P, P, P, P, P]),
     "fmm_eval_host": (I, [P, P, P, P, P, P]),
+    "fmm_eval_host_async": (I, [P, P, P, P, P, P]),
     "fmm_adjoint": (I, [P, P, P, P, P, P, P, P, P, P]),
     "fmm_adjoint4": (I, [P, P, P, P, P, P, P, P, P, P, P, P]),
     "fmm_get_binning": (I, [P, P, P, P, P, P]),
@@ -136,11 +137,12 @@ class FMM:
     """One solver handle: a cubic box, boundary, multipole order p and tree depth."""
 
     def __init__(self, edge, periodic, p, depth, origin=(0.0, 0.0, 0.0), precision="fp32", ke=None,
-                 interpolation="charge"):
+                 interpolation="charge", m2l_rows=0, p2p_warps=0):
         lib = load()
         box = FmmBox((ctypes.c_double * 3)(*[float(o) for o in origin]), float(edge))
         opt = FmmOptions(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                         float(ke) if ke else 0.0, INTERPOLATIONS[interpolation], (ctypes.c_int * 7)())
+                         float(ke) if ke else 0.0, INTERPOLATIONS[interpolation], int(m2l_rows), int(p2p_warps),
+                         (ctypes.c_int * 5)())
         h = ctypes.c_void_p()
         _check(lib.fmm_create(ctypes.byref(box), int(bool(periodic)), int(p), int(depth), ctypes.byref(opt),
                               ctypes.byref(h)), "fmm_create")
@@ -232,6 +234,20 @@ class FMM:
             return a.ctypes.data_as(ctypes.c_void_p)
         _check(self._lib.fmm_eval_host(self._h, hp(x_host), hp(E_host), hp(F_host), hp(dV_host), _stream()),
                "fmm_eval_host")
+
+    def eval_host_async(self, x_host, E_host, F_host, dV_host):
+        """As eval_host without waiting: the results are in the host buffers once the current
+        stream has reached the end of the call (page-locked buffers; keep them and x_host
+        unchanged until then).  Consecutive calls overlap one call's position copy with the
+        previous call's evaluation."""
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                return ctypes.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(ctypes.c_void_p)
+        _check(self._lib.fmm_eval_host_async(self._h, hp(x_host), hp(E_host), hp(F_host), hp(dV_host), _stream()),
+               "fmm_eval_host_async")
 
     def adjoint(self, gbar, F, phi, dVdl, grad_x=True, grad_qA=True, grad_qB=True, grad_lam=True):
         dev = F.device

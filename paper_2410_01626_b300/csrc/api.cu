@@ -89,6 +89,7 @@ void free_atoms(Handle& h) {
 }
 
 void free_all(Handle& h) {
+    m2l_tc_free(&h);  // every error path of fmm_create after m2l_tc_setup releases its state too
     free_atoms(h);
     dfree(h.T);
     dfree(h.A);
@@ -99,6 +100,8 @@ void free_all(Handle& h) {
     translate_free(h.m2m_tc);
     translate_free(h.l2l_tc);
     dfree(h.tiles);
+    dfree(h.bricks);
+    dfree(h.m2l_part);
     dfree(h.M);
     dfree(h.L);
     dfree(h.lam);
@@ -115,10 +118,12 @@ void free_all(Handle& h) {
     dfree(h.root);
     dfree(h.status);
     dfree(h.work);
-    dfree(h.hx_dev);
-    dfree(h.hF_dev);
-    dfree(h.hdV_dev);
-    dfree(h.hE_dev);
+    for (int i = 0; i < 2; ++i) {
+        dfree(h.hx_dev[i]);
+        dfree(h.hF_dev[i]);
+        dfree(h.hdV_dev[i]);
+        dfree(h.hE_dev[i]);
+    }
     if (h.ev_valid) {
         for (auto& e : h.ev) cudaEventDestroy(e);
     }
@@ -133,10 +138,19 @@ void free_all(Handle& h) {
     if (h.side) cudaStreamDestroy(h.side);
     h.fork_ev = h.join_ev = nullptr;
     h.chain = h.side = nullptr;
-    if (h.g_exec) cudaGraphExecDestroy(h.g_exec);
+    for (auto& g : h.g_slot) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
     if (h.gcap) cudaStreamDestroy(h.gcap);
-    h.g_exec = nullptr;
     h.gcap = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (h.hx_ev[i]) cudaEventDestroy(h.hx_ev[i]);
+        if (h.hfree_ev[i]) cudaEventDestroy(h.hfree_ev[i]);
+        h.hx_ev[i] = h.hfree_ev[i] = nullptr;
+    }
+    if (h.h2d) cudaStreamDestroy(h.h2d);
+    h.h2d = nullptr;
 }
 
 inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
@@ -258,6 +272,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     if (periodic != 0 && periodic != 1) return FMM_ERR_ARG;
     if (p < 1 || p > FMM_MAX_P || depth < 0 || depth > kMaxDepth) return FMM_ERR_ARG;
     int precision = FMM_FP32, interpolation = FMM_INTERP_CHARGE;
+    int m2l_rows = 0, p2p_warps = 0;
     double ke = 138.935458;
     if (opt) {
         for (int r : opt->reserved)
@@ -265,8 +280,13 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         if (opt->precision < FMM_FP32 || opt->precision > FMM_MIXED_FP16) return FMM_ERR_ARG;
         if (opt->interpolation != FMM_INTERP_CHARGE && opt->interpolation != FMM_INTERP_HAMILTONIAN)
             return FMM_ERR_ARG;
+        if (!m2l_tile_rows_ok(opt->m2l_tile_rows)) return FMM_ERR_ARG;
+        if (opt->p2p_leaves_per_block != 0 && opt->p2p_leaves_per_block != 2 && opt->p2p_leaves_per_block != 4)
+            return FMM_ERR_ARG;
         precision = opt->precision;
         interpolation = opt->interpolation;
+        m2l_rows = opt->m2l_tile_rows;
+        p2p_warps = opt->p2p_leaves_per_block;
         if (opt->coulomb_k > 0.0) ke = opt->coulomb_k;
     }
     fmm_handle* H = new (std::nothrow) fmm_handle();
@@ -280,6 +300,8 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     h.nc = ncoef(p);
     h.ncp = ncoef_padded(p);
     h.precision = precision;
+    h.m2l_rows = m2l_rows;
+    h.p2p_warps = p2p_warps > 0 ? p2p_warps : 4;
     h.hamiltonian = interpolation == FMM_INTERP_HAMILTONIAN;
     h.ke = ke;
     h.s_bin = std::ldexp(1.0, depth) / box->edge;
@@ -365,9 +387,13 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
             for (int p0 = 0; p0 < np; p0 += 16) tiles.push_back({l, c, p0, std::min(16, np - p0)});
     }
     h.ntiles = (int)tiles.size();
+    std::vector<F32Brick> bricks;
+    if (precision == FMM_FP32 && ncp <= 128) f32_bricks(h.lmin, depth, bricks);
+    h.nbricks = (int)bricks.size();
     const long nleaf = 1L << (3 * depth);
     if ((st = dalloc(&h.M, (size_t)acc * ncp)) || (st = dalloc(&h.L, (size_t)acc * ncp)) ||
-        (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.start, nleaf)) ||
+        (st = dalloc(&h.tiles, tiles.size())) || (st = dalloc(&h.bricks, bricks.size())) ||
+        (!bricks.empty() && (st = dalloc(&h.m2l_part, 8L * acc * ncp))) || (st = dalloc(&h.start, nleaf)) ||
         (st = dalloc(&h.count, nleaf)) || (st = dalloc(&h.leafcnt, leafcnt_words(nleaf))) || (st = dalloc(&h.epart, nleaf)) ||
         (st = dalloc(&h.leafmom, (long)kLeafMomStride * nleaf)) || (st = dalloc(&h.root, nc + kRootDoubles)) || (st = dalloc(&h.status, 1)) ||
         (st = dalloc(&h.site_ptr, 1)) ||
@@ -379,6 +405,8 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     h.epart_cap = (int)nleaf;
     if (!tiles.empty())
         cudaMemcpy(h.tiles, tiles.data(), sizeof(M2LTile) * tiles.size(), cudaMemcpyHostToDevice);
+    if (!bricks.empty())
+        cudaMemcpy(h.bricks, bricks.data(), sizeof(F32Brick) * bricks.size(), cudaMemcpyHostToDevice);
     cudaMemset(h.M, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.L, 0, sizeof(float) * acc * ncp);
     cudaMemset(h.status, 0, sizeof(int));
@@ -393,6 +421,11 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         if (cudaStreamCreateWithPriority(&h.chain, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaStreamCreateWithPriority(&h.side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaStreamCreateWithFlags(&h.gcap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h.h2d, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.hx_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.hx_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.hfree_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.hfree_ev[1], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.m2m_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -537,10 +570,12 @@ fmm_status fmm_bind_lambda(fmm_handle* H, const float* lambda) {
     return FMM_OK;
 }
 
-// One evaluation on `st`: a replay of the handle's cached graph when the buffers and the launch
-// state are those it was captured with; captured (on the handle's own stream) the second time in
-// a row the same buffers come; otherwise, while profiling, or while `st` is itself being
-// captured by the caller, the kernels are launched one by one.  Both paths run the same kernels.
+// One evaluation on `st`: a replay of one of the handle's two cached graphs when the buffers and
+// the launch state are those it was captured with; captured (on the handle's own stream, into
+// the least recently used slot) when the same buffers come again within the last two eager
+// evaluations (so two buffer sets used in turn both get graphs); otherwise, while profiling, or
+// while `st` is itself being captured by the caller, the kernels are launched one by one.  Both
+// paths run the same kernels.
 static fmm_status eval_dispatch(Handle& h, const float* x, double* E, float* F, float* dVdl, float* phi,
                                 cudaStream_t st) {
     cudaGetLastError();
@@ -555,32 +590,44 @@ static fmm_status eval_dispatch(Handle& h, const float* x, double* E, float* F, 
                 if (k[i] != key[i]) return false;
             return true;
         };
-        if (h.g_exec && h.g_key_gen == h.gen && same(h.g_key)) return cuda_ok(cudaGraphLaunch(h.g_exec, st));
-        if (h.g_last_gen == h.gen && same(h.g_last)) {
-            if (h.g_exec) cudaGraphExecDestroy(h.g_exec);
-            h.g_exec = nullptr;
-            cudaGraph_t g = nullptr;
+        for (auto& g : h.g_slot)
+            if (g.exec && g.gen == h.gen && same(g.key)) {
+                g.used = ++h.g_tick;
+                return cuda_ok(cudaGraphLaunch(g.exec, st));
+            }
+        bool seen = false;
+        for (int i = 0; i < 2; ++i) seen = seen || (h.g_hist_gen[i] == h.gen && same(h.g_hist[i]));
+        if (seen) {
+            Handle::EvalGraph& g = (!h.g_slot[0].exec || (h.g_slot[1].exec && h.g_slot[0].used <= h.g_slot[1].used))
+                                       ? h.g_slot[0] : h.g_slot[1];
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            cudaGraph_t gr = nullptr;
             bool ok = cudaStreamBeginCapture(h.gcap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
                 launch_eval(&h, x, E, F, dVdl, phi, h.gcap);
-                ok = cudaStreamEndCapture(h.gcap, &g) == cudaSuccess && g != nullptr;
+                ok = cudaStreamEndCapture(h.gcap, &gr) == cudaSuccess && gr != nullptr;
                 // per-node priorities: the chain keeps the precedence its stream gives it eagerly
-                ok = ok && cudaGraphInstantiateWithFlags(&h.g_exec, g, cudaGraphInstantiateFlagUseNodePriority) ==
+                ok = ok && cudaGraphInstantiateWithFlags(&g.exec, gr, cudaGraphInstantiateFlagUseNodePriority) ==
                                cudaSuccess;
-                if (g) cudaGraphDestroy(g);
+                if (gr) cudaGraphDestroy(gr);
             }
             if (ok) {
-                for (int i = 0; i < 5; ++i) h.g_key[i] = key[i];
-                h.g_key_gen = h.gen;
-                return cuda_ok(cudaGraphLaunch(h.g_exec, st));
+                for (int i = 0; i < 5; ++i) g.key[i] = key[i];
+                g.gen = h.gen;
+                g.used = ++h.g_tick;
+                return cuda_ok(cudaGraphLaunch(g.exec, st));
             }
             cudaGetLastError();  // capture is not available here: stay with eager launches
-            if (h.g_exec) cudaGraphExecDestroy(h.g_exec);
-            h.g_exec = nullptr;
+            for (auto& s2 : h.g_slot) {
+                if (s2.exec) cudaGraphExecDestroy(s2.exec);
+                s2.exec = nullptr;
+            }
             h.g_off = true;
         } else {
-            for (int i = 0; i < 5; ++i) h.g_last[i] = key[i];
-            h.g_last_gen = h.gen;
+            for (int i = 0; i < 5; ++i) h.g_hist[h.g_hist_next][i] = key[i];
+            h.g_hist_gen[h.g_hist_next] = h.gen;
+            h.g_hist_next ^= 1;
         }
     }
     launch_eval(&h, x, E, F, dVdl, phi, st);
@@ -595,45 +642,72 @@ fmm_status fmm_eval(fmm_handle* H, const float* x, double* E, float* F, float* d
     return eval_dispatch(h, x, E, F, dVdl, phi, S(stream));
 }
 
-fmm_status fmm_eval_host(fmm_handle* H, const float* x_host, double* E_host, float* F_host, float* dV_host,
-                         void* stream) {
+fmm_status fmm_eval_host_async(fmm_handle* H, const float* x_host, double* E_host, float* F_host, float* dV_host,
+                               void* stream) {
     if (!H) return FMM_ERR_ARG;
     Handle& h = H->h;
     if (!h.charges_set) return FMM_ERR_STATE;
     if (h.n > 0 && !x_host) return FMM_ERR_ARG;
     cudaStream_t st = S(stream);
     const int n = h.n;
-    if (n > h.host_cap || !h.hE_dev) {
-        dfree(h.hx_dev);
-        dfree(h.hF_dev);
-        dfree(h.hE_dev);
-        fmm_status e;
-        if ((e = dalloc(&h.hx_dev, 3L * n)) || (e = dalloc(&h.hF_dev, 3L * n)) || (e = dalloc(&h.hE_dev, 1)))
-            return e;
-        h.host_cap = n;
-    }
     const int nlam = h.ncoord * h.K;
-    if (nlam > h.hdV_cap) {  // dV/dlambda staging, one entry per site coordinate
-        dfree(h.hdV_dev);
-        h.hdV_cap = 0;
-        if (dalloc(&h.hdV_dev, nlam)) return FMM_ERR_OOM;
+    if (n > h.host_cap || !h.hE_dev[0] || nlam > h.hdV_cap) {
+        // (re)allocate both staging sets; wait for any call still using them
+        if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail("fmm_eval_host: synchronize", cudaGetLastError());
+        h.host_cap = h.hdV_cap = 0;
+        fmm_status e = FMM_OK;
+        for (int i = 0; i < 2 && e == FMM_OK; ++i) {
+            dfree(h.hx_dev[i]);
+            dfree(h.hF_dev[i]);
+            dfree(h.hE_dev[i]);
+            dfree(h.hdV_dev[i]);
+            if ((e = dalloc(&h.hx_dev[i], 3L * n)) || (e = dalloc(&h.hF_dev[i], 3L * n)) ||
+                (e = dalloc(&h.hE_dev[i], 1)) || (e = dalloc(&h.hdV_dev[i], nlam)))
+                break;
+        }
+        if (e != FMM_OK) return e;
+        h.host_cap = n;
         h.hdV_cap = nlam;
     }
+    const int s = h.h_next;
+    h.h_next ^= 1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    cudaGetLastError();
     fmm_status e = FMM_OK;
-    if (n > 0 && (e = cuda_ok(cudaMemcpyAsync(h.hx_dev, x_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st))))
+    if (n > 0) {
+        const size_t bytes = sizeof(float) * 3 * n;
+        if (!capturing) {
+            // the copy runs on the handle's copy stream once this staging set's previous use has
+            // finished, beside whatever `st` is still doing; `st` waits for it
+            if ((e = cuda_ok(cudaStreamWaitEvent(h.h2d, h.hfree_ev[s], 0))) ||
+                (e = cuda_ok(cudaMemcpyAsync(h.hx_dev[s], x_host, bytes, cudaMemcpyHostToDevice, h.h2d))) ||
+                (e = cuda_ok(cudaEventRecord(h.hx_ev[s], h.h2d))) || (e = cuda_ok(cudaStreamWaitEvent(st, h.hx_ev[s], 0))))
+                return e;
+        } else if ((e = cuda_ok(cudaMemcpyAsync(h.hx_dev[s], x_host, bytes, cudaMemcpyHostToDevice, st)))) {
+            return e;
+        }
+    }
+    if ((e = eval_dispatch(h, h.hx_dev[s], h.hE_dev[s], F_host ? h.hF_dev[s] : nullptr, dV_host ? h.hdV_dev[s] : nullptr,
+                           nullptr, st)))
         return e;
-    if ((e = eval_dispatch(h, h.hx_dev, h.hE_dev, F_host ? h.hF_dev : nullptr, dV_host ? h.hdV_dev : nullptr, nullptr,
-                           st)))
-        return e;
-    if (E_host && (e = cuda_ok(cudaMemcpyAsync(E_host, h.hE_dev, sizeof(double), cudaMemcpyDeviceToHost, st))))
+    if (E_host && (e = cuda_ok(cudaMemcpyAsync(E_host, h.hE_dev[s], sizeof(double), cudaMemcpyDeviceToHost, st))))
         return e;
     if (F_host && n > 0 &&
-        (e = cuda_ok(cudaMemcpyAsync(F_host, h.hF_dev, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st))))
+        (e = cuda_ok(cudaMemcpyAsync(F_host, h.hF_dev[s], sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st))))
         return e;
     if (dV_host && nlam > 0 &&
-        (e = cuda_ok(cudaMemcpyAsync(dV_host, h.hdV_dev, sizeof(float) * nlam, cudaMemcpyDeviceToHost, st))))
+        (e = cuda_ok(cudaMemcpyAsync(dV_host, h.hdV_dev[s], sizeof(float) * nlam, cudaMemcpyDeviceToHost, st))))
         return e;
-    return cuda_ok(cudaStreamSynchronize(st));
+    if (!capturing) e = cuda_ok(cudaEventRecord(h.hfree_ev[s], st));
+    return e;
+}
+
+fmm_status fmm_eval_host(fmm_handle* H, const float* x_host, double* E_host, float* F_host, float* dV_host,
+                         void* stream) {
+    const fmm_status e = fmm_eval_host_async(H, x_host, E_host, F_host, dV_host, stream);
+    if (e != FMM_OK) return e;
+    return cuda_ok(cudaStreamSynchronize(S(stream)));
 }
 
 fmm_status fmm_host_alloc(size_t bytes, void** out) {

@@ -24,6 +24,13 @@ inline int ncoef(int p) { return (p + 1) * (p + 1); }
 inline int ncoef_padded(int p) { return (ncoef(p) + 15) / 16 * 16; }
 inline int op_index(int ox, int oy, int oz) { return (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3); }
 
+// A brick of target boxes of one level and octant class for the FP32 CUDA-core M2L: the boxes
+// (i0 + i, j0 + j, k0 + k), 0 <= i < bx, j < by, k < bz, of the class sub-grid (n = 2^(level-1)
+// boxes per axis).
+struct F32Brick {
+    int level, cls, i0, j0, k0, bx, by, bz;
+};
+
 struct M2LTile {
     int level;
     int cls;          // child octant class of the target boxes (0..7)
@@ -58,6 +65,10 @@ struct Handle {
     TranslateOp m2m_tc, l2l_tc;  // mixed precisions: M2M and L2L on the tensor cores
     M2LTile* tiles = nullptr;  // M2L work list
     int ntiles = 0;
+    // FP32 CUDA-core M2L (ncp <= 128): bricks of target boxes of one level and octant class
+    F32Brick* bricks = nullptr;
+    int nbricks = 0;
+    float* m2l_part = nullptr;  // [8][nbox_total][ncp] partials per source class
     // tree storage
     std::vector<long> lvl_off;  // box offset of each level
     long nbox_total = 0;
@@ -100,6 +111,10 @@ struct Handle {
     // limit (clock cycles) of the pipeline waits of the tensor-core M2L; 0 = the default
     // (about 2 s), a small value lets a test make the waits expire (fmm_set_wait_limit)
     long long wait_limit = 0;
+    // kernel tiles (fmm_options): the tensor-core M2L's rows per CTA (0 = 192) and the near
+    // field's leaves (warps) per block (2, 4 or 8)
+    int m2l_rows = 0;
+    int p2p_warps = 4;
     // profiling
     int profiling = 0;  // 0 off, 1 per-stage events, 2 the same with every stage serialised
     cudaEvent_t ev[kNumEvents]{};  // a pool of timing events, taken in launch order
@@ -117,19 +132,29 @@ struct Handle {
     // in a row the same buffers come, replayed on the caller's stream while they and the handle's
     // launch state (generation `gen`, bumped by every call that changes it) stay the same
     cudaStream_t gcap = nullptr;
-    cudaGraphExec_t g_exec = nullptr;
-    const void* g_key[5]{};
-    const void* g_last[5]{};
-    unsigned long long gen = 0, g_key_gen = 0, g_last_gen = ~0ull;
+    struct EvalGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* key[5]{};
+        unsigned long long gen = 0, used = 0;
+    };
+    EvalGraph g_slot[2];           // the graphs of the two most recent buffer sets
+    const void* g_hist[2][5]{};    // the buffer sets of the last two eager evaluations
+    unsigned long long g_hist_gen[2] = {~0ull, ~0ull};
+    int g_hist_next = 0;
+    unsigned long long gen = 0, g_tick = 0;
     bool g_off = false;  // a capture failed once: evaluations stay eager launches
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    // host staging for fmm_eval_host
-    float* hx_dev = nullptr;
-    float* hF_dev = nullptr;
-    float* hdV_dev = nullptr;
-    double* hE_dev = nullptr;
+    // host staging for fmm_eval_host(_async): two device sets used in turn, so that the copy
+    // of one call's positions (on h2d) overlaps the previous call's evaluation
+    float* hx_dev[2] = {nullptr, nullptr};
+    float* hF_dev[2] = {nullptr, nullptr};
+    float* hdV_dev[2] = {nullptr, nullptr};
+    double* hE_dev[2] = {nullptr, nullptr};
     int hdV_cap = 0;
     int host_cap = 0;
+    int h_next = 0;
+    cudaStream_t h2d = nullptr;
+    cudaEvent_t hx_ev[2] = {nullptr, nullptr}, hfree_ev[2] = {nullptr, nullptr};
     void* tc = nullptr;  // tensor-core M2L state (m2l_tc.cu)
 };
 
@@ -139,6 +164,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
                 cudaStream_t st);
 int leafcnt_words(int nleaf);  // the binning's counters: one per leaf, one per scan tile
 int launches_per_eval(const Handle* h);
+void f32_bricks(int lmin, int depth, std::vector<F32Brick>& out);  // the FP32 M2L's work list
 void launch_adjoint(Handle* h, const double* gbar, const float* F, const float* phi,
                     const float* dVdl, float* gx, float* const* gq /*[4] forms, may be null*/, float* glam,
                     cudaStream_t st);
@@ -150,6 +176,7 @@ void translate_tc(const TranslateOp& op, const float* X, int ldx, int N, float* 
                   int* status, cudaStream_t st, int ksplit = 1, float* work = nullptr);
 // m2l_tc.cu
 bool m2l_tc_supported(const Handle* h);
+bool m2l_tile_rows_ok(int rows);  // 0 (the default) or a width the kernel is instantiated for
 int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor);  // [343][nc][nc], output-major
 void m2l_tc_free(Handle* h);
 int m2l_tc_launches(const Handle* h);

@@ -815,6 +815,162 @@ __global__ void k_m2l_fp32(const M2LTile* __restrict__ tiles, int nc, int ncp, c
     }
 }
 
+// ---- M2L, FP32 CUDA cores, register-blocked: a brick of target boxes of one level and class ----
+// The target boxes of octant class c form an n^3 sub-grid (n = 2^(level-1)); a source at offset
+// o of a target lies in class pi = (c + o) mod 2 at sub-grid displacement delta = (c + o - pi) / 2
+// in {-1, 0, 1}^3, so for fixed (c, pi) every delta maps the brick onto the brick shifted by
+// delta in the pi sub-grid.  A CTA owns a brick of up to 4 x 4 x 8 = 128 target boxes and all
+// output coefficients (ncp <= 128).  Per (source class pi, chunk of kF32KC input coefficients) it
+// stages the brick's source halo ((bx + 2)(by + 2)(bz + 2) boxes, periodic images or zeros) in
+// shared memory; per valid delta it stages the operator chunk T_o[k][j] and every thread adds
+// T x M for its 8 output coefficients x 8 boxes (64 FP32 accumulators, 64 FMAs per k).  Target
+// boxes outside the interaction list's near field only: no ghost-row work.  T is the bank
+// [op][k][j] (j = output coefficient, fastest).  A CTA takes one (brick, source class pi) pair
+// -- eight times as many CTAs as bricks, so that the waves on the SMs are nearly full -- and
+// writes its partial local expansions to part[pi]; k_sum8 adds the eight partials in a fixed
+// order into L.
+constexpr int kF32KC = 16;
+constexpr int kF32Halo = 6 * 6 * 10;
+
+void f32_bricks(int lmin, int depth, std::vector<F32Brick>& out) {
+    out.clear();
+    for (int l = lmin; l <= depth; ++l) {
+        const int n = 1 << (l - 1);
+        const int bx = std::min(n, 4), by = std::min(n, 4), bz = std::min(n, 8);
+        for (int c = 0; c < 8; ++c)
+            for (int i0 = 0; i0 < n; i0 += bx)
+                for (int j0 = 0; j0 < n; j0 += by)
+                    for (int k0 = 0; k0 < n; k0 += bz) out.push_back({l, c, i0, j0, k0, bx, by, bz});
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__ bricks, int ncp,
+                                                    const float* __restrict__ T, const float* __restrict__ M,
+                                                    float* __restrict__ part, long part_stride, LevelOffsets lo,
+                                                    int periodic) {
+    __shared__ float hs[kF32KC][kF32Halo];
+    __shared__ __align__(16) float ts[kF32KC][128];
+    const F32Brick br = bricks[blockIdx.x];
+    const int n = 1 << (br.level - 1);
+    const int cx = br.cls & 1, cy = (br.cls >> 1) & 1, cz = (br.cls >> 2) & 1;
+    const int hy = br.by + 2, hz = br.bz + 2, nh = (br.bx + 2) * hy * hz;
+    const int nbox = br.bx * br.by * br.bz;
+    const float* Ml = M + lo.off[br.level] * ncp;
+    const int tid = threadIdx.x;
+    // coefficients 8 tc .. +7, boxes 8 tb .. +7 of the brick.  A warp holds 4 coefficient groups x
+    // 8 box groups: its operator loads (two 16-byte reads per k) then fall in one 128-byte
+    // wavefront, and its 8 box pencils ((i * 6 + j) * 10 floats apart in the halo) in 8 distinct
+    // banks, so shared-memory traffic per k stays below the FMA time.
+    const int w = tid >> 5, lane = tid & 31;
+    const int tc = 4 * (w & 3) + (lane & 3), tb = 8 * (w >> 2) + (lane >> 2);
+    const bool cact = 8 * tc < ncp;
+    int hb[8];  // halo index of each of the thread's boxes at delta = (-1, -1, -1)
+    {
+        // the 8 boxes of a thread are consecutive in k when bz = 8 (n >= 8); smaller bricks
+        // take the general decomposition
+        const int b0 = 8 * tb;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int b = b0 + e;
+            const int k = b % br.bz, r = b / br.bz;
+            const int j = r % br.by, i = r / br.by;
+            hb[e] = b < nbox ? (i * hy + j) * hz + k : 0;
+        }
+    }
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[a][e] = 0.f;
+    const int nkc = ncp / kF32KC;
+    const int pi = blockIdx.y;
+    {
+        const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
+        for (int kc = 0; kc < nkc; ++kc) {
+            __syncthreads();  // the previous chunk's readers are done with hs and ts
+            // source halo of this (pi, kc): kF32KC consecutive coefficients per box
+            for (int h = tid; h < nh * kF32KC; h += 256) {
+                const int kk = h % kF32KC, hbx = h / kF32KC;
+                const int hk = hbx % hz, hj = (hbx / hz) % hy, hi = hbx / (hz * hy);
+                int si = br.i0 + hi - 1, sj = br.j0 + hj - 1, sk = br.k0 + hk - 1;
+                bool ok = true;
+                if (periodic) {
+                    si = (si + n) & (n - 1);
+                    sj = (sj + n) & (n - 1);
+                    sk = (sk + n) & (n - 1);
+                } else {
+                    ok = si >= 0 && si < n && sj >= 0 && sj < n && sk >= 0 && sk < n;
+                }
+                float v = 0.f;
+                if (ok) v = Ml[(long)morton3(2 * si + px, 2 * sj + py, 2 * sk + pz) * ncp + kc * kF32KC + kk];
+                hs[kk][hbx] = v;
+            }
+            for (int d = 0; d < 27; ++d) {
+                const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+                const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
+                if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;  // near field
+                const float* Tc = T + ((long)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * ncp + kc * kF32KC) * ncp;
+                __syncthreads();  // ts is free (and, for the first shift, hs is complete)
+                for (int q = tid; q < kF32KC * ncp / 4; q += 256) {
+                    const int k = q / (ncp / 4), j4 = q % (ncp / 4);
+                    reinterpret_cast<float4*>(&ts[k][0])[j4] = reinterpret_cast<const float4*>(Tc + (long)k * ncp)[j4];
+                }
+                __syncthreads();
+                const int so = ((dx + 1) * hy + (dy + 1)) * hz + (dz + 1);
+                if (cact) {
+#pragma unroll 4
+                    for (int k = 0; k < kF32KC; ++k) {
+                        const float4 a0 = *reinterpret_cast<const float4*>(&ts[k][8 * tc]);
+                        const float4 a1 = *reinterpret_cast<const float4*>(&ts[k][8 * tc + 4]);
+                        float bv[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) bv[e] = hs[k][hb[e] + so];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            acc[0][e] = fmaf(a0.x, bv[e], acc[0][e]);
+                            acc[1][e] = fmaf(a0.y, bv[e], acc[1][e]);
+                            acc[2][e] = fmaf(a0.z, bv[e], acc[2][e]);
+                            acc[3][e] = fmaf(a0.w, bv[e], acc[3][e]);
+                            acc[4][e] = fmaf(a1.x, bv[e], acc[4][e]);
+                            acc[5][e] = fmaf(a1.y, bv[e], acc[5][e]);
+                            acc[6][e] = fmaf(a1.z, bv[e], acc[6][e]);
+                            acc[7][e] = fmaf(a1.w, bv[e], acc[7][e]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (!cact) return;
+    float* Ll = part + (long)pi * part_stride + lo.off[br.level] * ncp;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int b = 8 * tb + e;
+        if (b >= nbox) continue;
+        const int k = b % br.bz, j = (b / br.bz) % br.by, i = b / (br.bz * br.by);
+        const uint32_t box = morton3(2 * (br.i0 + i) + cx, 2 * (br.j0 + j) + cy, 2 * (br.k0 + k) + cz);
+        float4* dst = reinterpret_cast<float4*>(Ll + (long)box * ncp + 8 * tc);
+        dst[0] = make_float4(acc[0][e], acc[1][e], acc[2][e], acc[3][e]);
+        dst[1] = make_float4(acc[4][e], acc[5][e], acc[6][e], acc[7][e]);
+    }
+}
+
+// L[i] = sum_{pi = 0..7} part[pi][i] in this order, over n floats (float4 vectors)
+__global__ void k_sum8(long n4, const float4* __restrict__ part, long stride4, float4* __restrict__ L) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+        float4 s = part[i];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+            const float4 v = part[q * stride4 + i];
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+        L[i] = s;
+    }
+}
+
 // ---- L2P: potential and gradient of the leaf local expansion at u (units of h) ----
 template <int P>
 __device__ __forceinline__ void l2p_eval(const float* __restrict__ Lb, float x, float y, float z, float& phi,
@@ -1176,14 +1332,17 @@ __device__ __forceinline__ void near_output(float4* __restrict__ near, int s, fl
     near[s] = make_float4(pot, gx, gy, gz);
 }
 
-__global__ void __launch_bounds__(128) k_p2p(NearParams a, float4* __restrict__ near) {
-    __shared__ float4 src_sm[4][kNearCap];  // packed pairs: [2j] = (x x y y), [2j+1] = (z z q q)
-    __shared__ int nb_off[4][28];
-    __shared__ int nb_s0[4][27];
-    __shared__ int nb_sc[4][27];
-    __shared__ float nb_sh[4][27][3];
+// W warps (target leaves) per block: 2 or 4 (the near-field block shape the autotuner picks; the
+// static shared memory of 4 warps is 43.5 KB, under the 48 KB a static allocation may use).
+template <int W>
+__global__ void __launch_bounds__(32 * W) k_p2p(NearParams a, float4* __restrict__ near) {
+    __shared__ float4 src_sm[W][kNearCap];  // packed pairs: [2j] = (x x y y), [2j+1] = (z z q q)
+    __shared__ int nb_off[W][28];
+    __shared__ int nb_s0[W][27];
+    __shared__ int nb_sc[W][27];
+    __shared__ float nb_sh[W][27][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int leaf = blockIdx.x * 4 + w;
+    const int leaf = blockIdx.x * W + w;
     if (leaf < a.nleaf) {
         const int nb = 1 << a.depth;
         const int ix = (int)compact3(leaf), iy = (int)compact3(leaf >> 1), iz = (int)compact3(leaf >> 2);
@@ -1577,7 +1736,8 @@ int launches_per_eval(const Handle* h) {
     if (d >= lmin) n += 2 * (d - lmin);  // M2M parent levels d-1 .. lmin (split-K product + sum)
     if (h->periodic) n += 3;       // Q/D/T partials + root + lattice
     if (d >= lmin)  // M2L: the coarse and the finest levels in two launches when split
-        n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? (coarse_top(h) >= 0 ? 2 : 1) * m2l_tc_launches(h) : 1;
+        n += (h->precision != FMM_FP32 && m2l_tc_supported(h)) ? (coarse_top(h) >= 0 ? 2 : 1) * m2l_tc_launches(h)
+             : (h->nbricks > 0 ? 2 : 1);  // FP32: the brick kernel and the sum of its partials
     if (d >= lmin) {  // L2L: coarse levels split over K (product + sum), the finest level in place
         const int lfirst = h->periodic ? 1 : lmin + 1;
         for (int l = lfirst; l <= d; ++l) n += (h->l2l_tc.dev && split_slices(d, l, 8) > 1) ? 2 : 1;
@@ -1644,7 +1804,8 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lc = coarse_top(h);  // top coarse level of the side branch, -1 without one
     cudaEventRecord(h->fork_ev, st);
     cudaStreamWaitEvent(cs, h->fork_ev, 0);
-    k_p2p<<<(nleaf + 3) / 4, 128, 0, st>>>(a, h->near);
+    if (h->p2p_warps == 2) k_p2p<2><<<(nleaf + 1) / 2, 64, 0, st>>>(a, h->near);
+    else k_p2p<4><<<(nleaf + 3) / 4, 128, 0, st>>>(a, h->near);
     const int e1n = mark(h, st);
     span(h, 8, e1, e1n);
     const int e1c = serial ? e1n : e1;  // start of the chain's first stage
@@ -1722,8 +1883,18 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
             } else {
                 LevelOffsets lo{};
                 for (int l = 0; l <= d; ++l) lo.off[l] = h->lvl_off[l];
-                k_m2l_fp32<<<h->ntiles, h->ncp, sizeof(float) * kM2LTB * h->ncp, cs>>>(
-                    h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
+                if (h->nbricks > 0) {
+                    // partials of every level lmin .. d (the part of the level arrays from lmin on)
+                    const long a0 = h->lvl_off[lmin] * h->ncp, n = (h->lvl_off[d + 1] - h->lvl_off[lmin]) * h->ncp;
+                    const long stride = h->nbox_total * h->ncp;
+                    k_m2l_f32<<<dim3(h->nbricks, 8), 256, 0, cs>>>(h->bricks, h->ncp, h->T, h->M, h->m2l_part, stride,
+                                                                   lo, h->periodic);
+                    k_sum8<<<std::min<long>((n / 4 + 255) / 256, 148L * 16), 256, 0, cs>>>(
+                        n / 4, reinterpret_cast<const float4*>(h->m2l_part + a0), stride / 4,
+                        reinterpret_cast<float4*>(h->L + a0));
+                } else
+                    k_m2l_fp32<<<h->ntiles, h->ncp, sizeof(float) * kM2LTB * h->ncp, cs>>>(
+                        h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
             }
         }
         const int e5 = mark(h, cs);

@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -39,7 +40,7 @@ namespace fmmcph {
 
 namespace {
 
-constexpr int kTcRows = 192;    // virtual rows (N) per CTA: 280 CTAs = two full waves at depth 5
+constexpr int kTcRows = 192;    // default virtual rows (N) per CTA: 280 CTAs = two full waves at depth 5
 constexpr int kTcTmemCols = 512; // two accumulators, 256 columns apart
 constexpr int kTcAccStride = 256;
 constexpr int kTcMaxStages = 16;  // operator-chunk ring depth: as many stages as shared memory holds
@@ -230,7 +231,7 @@ struct TcTile {
 constexpr int kTcThreads = 320;
 constexpr int kTcDrainWarps = 8;
 
-template <int MODE>
+template <int MODE, int ROWS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const TcTile* __restrict__ tiles, TcLevels lv, const float* __restrict__ Mtc,
              const float* __restrict__ Mtc_lo, const float* __restrict__ Ttc, float* __restrict__ L, int ncp,
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int rs[3], rl[3];
     for (int q = 0; q < 3; ++q) {
         rs[q] = r0 + (q - 1) * m2 * m2 - hal;          // >= 0: r0 >= S = m2^2 + hal
-        rl[q] = min(kTcRows + 2 * hal, R - rs[q]);     // > 0:  r0 < R - S
+        rl[q] = min(ROWS + 2 * hal, R - rs[q]);     // > 0:  r0 < R - S
     }
     const float* Mlev = Mtc + lv.mtc_off[lev];
     const float* Mlev_lo = SPLIT ? Mtc_lo + lv.mtc_off[lev] : nullptr;
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lane < 3 * kTcKG) {  // one (cell, delta_x range) per lane
                 const int kg = lane / 3, q = lane % 3;
                 const int rsq = r0 + (q - 1) * m2 * m2 - hal;
-                const int rlq = min(kTcRows + 2 * hal, R - rsq);
+                const int rlq = min(ROWS + 2 * hal, R - rsq);
                 const long e = (((long)pi * NKG + ch * kTcKG + kg) * R + rsq) * 4;
                 uint8_t* dq = dst + (size_t)kg * kg_stride + (size_t)q * slab_rows * 16;
                 tc::bulk_g2s(dq, Mlev + e, (uint32_t)rlq * 16u, slab_full + buf);
@@ -427,8 +428,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // Lean loop: the 27 shifts are unrolled (constant delta), the ring position is a
             // running counter, and the abort flag is only consulted when a wait expires.  Every
             // lane runs the loop so that descriptors and counters stay warp-uniform.
-            const uint32_t idesc = Cfg::kMix ? tc::idesc_f16(128, kTcRows)
-                                   : Cfg::kBf16 ? tc::idesc_bf16(128, kTcRows) : tc::idesc_tf32(128, kTcRows);
+            const uint32_t idesc = Cfg::kMix ? tc::idesc_f16(128, ROWS)
+                                   : Cfg::kBf16 ? tc::idesc_bf16(128, ROWS) : tc::idesc_tf32(128, ROWS);
             // descriptors are built once and advanced by adding (byte offset >> 4) to the address field
             const uint64_t a_base = tc::smem_desc_kmajor(tc::smem_u32(tring), 2048u, 128u);
             const uint64_t b_base = tc::smem_desc_kmajor(tc::smem_u32(slab0), kg_stride, 128u);
@@ -457,58 +458,65 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc::fence_after_sync();
                 const uint64_t b_buf = b_base + (((uint64_t)buf * slab_bytes) >> 4) + (uint64_t)hal;
                 uint32_t acc = 0;
+                // The unrolled loop over the 27 shifts, specialised per chunk kind so that the
+                // issue path of each chunk has no branch on it (the kind is fixed per group).
+                auto shifts = [&](auto kind_tag) {
+                    constexpr int kKind = decltype(kind_tag)::value;
 #pragma unroll
-                for (int d = 0; d < 27; ++d) {
-                    const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                    const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
-                    if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
-                    if (!tc::mbar_wait_all_abort(t_full + stage, tphase, wlim, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    ++t_taken;
-                    const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
-                    const uint64_t bd0 = b_buf + (uint64_t)((dx + 1) * slab_rows + dy * m2 + dz);
-                    // the MMAs of this chunk, then the commit that releases its ring stage; one
-                    // elected lane issues each K step's products (hi(T) hi(M) + hi(T) lo(M) +
-                    // lo(T) hi(M) in the split forms)
-                    if (Cfg::kMix) {
-                        // A: cells of 2048 bytes (128 rows), a K step = two cells = 4096 bytes;
-                        // B: cells kg_stride apart.  Split chunk: hi in K-step slot 0, lo in slot 1.
-                        const uint64_t ad1 = ad0 + (4096u >> 4), bd1 = bd0 + ((2u * kg_stride) >> 4);
-                        if (mix_kind == 0)
-                            tc::mma3_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
-                        else if (mix_kind == 1)
-                            tc::mma_f16_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
-                        else
-                            tc::mma_f16_w<false, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
-                        acc = 1;
-                    } else
+                    for (int d = 0; d < 27; ++d) {
+                        const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
+                        const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
+                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+                        if (!tc::mbar_wait_all_abort(t_full + stage, tphase, wlim, abort_flag)) return false;
+                        ++t_taken;
+                        const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
+                        const uint64_t bd0 = b_buf + (uint64_t)((dx + 1) * slab_rows + dy * m2 + dz);
+                        // the MMAs of this chunk, then the commit that releases its ring stage; one
+                        // elected lane issues each K step's products (hi(T) hi(M) + hi(T) lo(M) +
+                        // lo(T) hi(M) in the split forms)
+                        if (Cfg::kMix) {
+                            // A: cells of 2048 bytes (128 rows), a K step = two cells = 4096 bytes;
+                            // B: cells kg_stride apart.  Split chunk: hi in K-step slot 0, lo in slot 1.
+                            const uint64_t ad1 = ad0 + (4096u >> 4), bd1 = bd0 + ((2u * kg_stride) >> 4);
+                            if (kKind == 0)
+                                tc::mma3_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                            else if (kKind == 1)
+                                tc::mma_f16_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                            else
+                                tc::mma_f16_w<false, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                            acc = 1;
+                        } else
 #pragma unroll
-                    for (int ks = 0; ks < Cfg::kKSteps; ++ks) {  // 32 bytes of K = two cells per MMA
-                        const uint64_t ad = ad0 + (uint64_t)ks * (4096u >> 4);
-                        const uint64_t bd = bd0 + (uint64_t)ks * ((2u * kg_stride) >> 4);
-                        const bool last_ks = ks == Cfg::kKSteps - 1;
-                        if (SPLIT) {
-                            if (last_ks)
-                                tc::mma3_w<Cfg::kBf16, true>(dacc, ad, bd, ad + (Cfg::kPartBytes >> 4),
-                                                             bd + (part_bytes >> 4), idesc, acc, t_empty + stage);
-                            else
-                                tc::mma3_w<Cfg::kBf16, false>(dacc, ad, bd, ad + (Cfg::kPartBytes >> 4),
-                                                              bd + (part_bytes >> 4), idesc, acc, nullptr);
-                        } else {
-                            if (last_ks)
-                                tc::mma1_tf32_w<true>(dacc, ad, bd, idesc, acc, t_empty + stage);
-                            else
-                                tc::mma1_tf32_w<false>(dacc, ad, bd, idesc, acc, nullptr);
+                        for (int ks = 0; ks < Cfg::kKSteps; ++ks) {  // 32 bytes of K = two cells per MMA
+                            const uint64_t ad = ad0 + (uint64_t)ks * (4096u >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)ks * ((2u * kg_stride) >> 4);
+                            const bool last_ks = ks == Cfg::kKSteps - 1;
+                            if (SPLIT) {
+                                if (last_ks)
+                                    tc::mma3_w<Cfg::kBf16, true>(dacc, ad, bd, ad + (Cfg::kPartBytes >> 4),
+                                                                 bd + (part_bytes >> 4), idesc, acc, t_empty + stage);
+                                else
+                                    tc::mma3_w<Cfg::kBf16, false>(dacc, ad, bd, ad + (Cfg::kPartBytes >> 4),
+                                                                  bd + (part_bytes >> 4), idesc, acc, nullptr);
+                            } else {
+                                if (last_ks)
+                                    tc::mma1_tf32_w<true>(dacc, ad, bd, idesc, acc, t_empty + stage);
+                                else
+                                    tc::mma1_tf32_w<false>(dacc, ad, bd, idesc, acc, nullptr);
+                            }
+                            acc = 1;
                         }
-                        acc = 1;
+                        if (++stage == nstages) {
+                            stage = 0;
+                            tphase ^= 1u;
+                        }
                     }
-                    if (++stage == nstages) {
-                        stage = 0;
-                        tphase ^= 1u;
-                    }
-                }
+                    return true;
+                };
+                if (!Cfg::kMix || mix_kind == 0) ok = shifts(std::integral_constant<int, 0>{});
+                else if (mix_kind == 1) ok = shifts(std::integral_constant<int, 1>{});
+                else ok = shifts(std::integral_constant<int, 2>{});
+                if (!ok) break;
                 tc::mma_commit_w(acc_full + ab);  // this group's partial sum is complete, its slab free
             }
             if (!ok && lane == 0) {
@@ -535,9 +543,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int q = warp & 3;                    // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2;          // column half of the tile
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        float sum[kTcRows / 2];
+        float sum[ROWS / 2];
 #pragma unroll
-        for (int i = 0; i < kTcRows / 2; ++i) sum[i] = 0.f;
+        for (int i = 0; i < ROWS / 2; ++i) sum[i] = 0.f;
         bool ok = true;
         for (int grp = 0; grp < ngroups; ++grp) {
             const int ab = grp & 1;
@@ -546,9 +554,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc::fence_after_sync();
-            const uint32_t base = tmem + lane_base + (uint32_t)(ab * kTcAccStride + half * (kTcRows / 2));
+            const uint32_t base = tmem + lane_base + (uint32_t)(ab * kTcAccStride + half * (ROWS / 2));
 #pragma unroll
-            for (int cb = 0; cb < kTcRows / 2; cb += 16) {
+            for (int cb = 0; cb < ROWS / 2; cb += 16) {
                 float v[16];
                 tc::tmem_ld16(base + cb, v);
 #pragma unroll
@@ -564,9 +572,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // rows per lane, then one store per row.  A fully unrolled loop doing the index
             // arithmetic per row is long straight-line code that runs once per tile, mostly
             // waiting for instruction fetch.
-            int* tab = reinterpret_cast<int*>(tring) + (warp - 2) * (kTcRows / 2);
-            const int rfirst = r0 + half * (kTcRows / 2);
-            for (int e = lane; e < kTcRows / 2; e += 32) {
+            int* tab = reinterpret_cast<int*>(tring) + (warp - 2) * (ROWS / 2);
+            const int rfirst = r0 + half * (ROWS / 2);
+            for (int e = lane; e < ROWS / 2; e += 32) {
                 const int r = rfirst + e;
                 const int ip = r / (m2 * m2), jp = (r / m2) % m2, kp = r % m2;
                 int off = -1;
@@ -580,7 +588,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float* Ll = L + lv.l_off[lev] * (long)ncp + j;
             if (j < ncp) {
 #pragma unroll
-                for (int e = 0; e < kTcRows / 2; ++e) {
+                for (int e = 0; e < ROWS / 2; ++e) {
                     const int off = tab[e];
                     if (off >= 0) Ll[off] = sum[e];
                 }
@@ -607,6 +615,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 }  // namespace
 
+// The tile widths (virtual rows per CTA, the MMA N) the kernel is instantiated for.
+template <class F>
+void for_tile_rows(F&& f) {
+    f(std::integral_constant<int, 128>{});
+    f(std::integral_constant<int, 192>{});
+    f(std::integral_constant<int, 256>{});
+}
+bool m2l_tile_rows_ok(int rows) { return rows == 0 || rows == 128 || rows == 192 || rows == 256; }
+
 // ------------------------------------------------------------------------------------------
 struct TcState {
     int mode = kTf32;
@@ -620,6 +637,7 @@ struct TcState {
     int last_half = 0;  // FP16 form: the last chunk holds 16 coefficients (one K step)
     int KG = 0;  // 16-byte cells per K chunk
     int slab_rows = 0;
+    int rows = kTcRows;  // virtual rows (MMA N) per CTA: 128, 192 or 256
     int nstages = 0;  // operator ring depth
     size_t smem = 0;
     TcLevels lv{};
@@ -707,6 +725,7 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     TcState* st = new TcState();
     h->tc = st;
     const int nc = h->nc, ncp = h->ncp, d = h->depth;
+    st->rows = h->m2l_rows > 0 ? h->m2l_rows : kTcRows;
     st->mode = h->precision == FMM_MIXED_3XTF32 ? kTf32x3
                : h->precision == FMM_MIXED_3XBF16 ? kBf16x3
                : h->precision == FMM_MIXED_FP16   ? kF16mix
@@ -762,10 +781,10 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
         st->lv.l_off[l] = h->lvl_off[l];
         off += 8L * NKG * R * 4;  // 16-byte cells, counted in floats
         for (int c = 0; c < 8; ++c)
-            for (int r0 = S; r0 < R - S; r0 += kTcRows) tiles.push_back({l, c, r0, 0});
+            for (int r0 = S; r0 < R - S; r0 += st->rows) tiles.push_back({l, c, r0, 0});
     }
     for (int l = d + 1; l <= kMaxDepth + 1; ++l) st->tile_first[l] = (int)tiles.size();
-    st->slab_rows = kTcRows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
+    st->slab_rows = st->rows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
     // two slab buffers, then as many ring stages as fit (at least 3), then barriers and flags
     constexpr size_t kBarBytes = 1024;  // barriers, TMEM slot, flags, copy counts, rank table
     const size_t slabs = 2 * (size_t)3 * st->slab_rows * st->KG * 16 * nparts;
@@ -786,10 +805,13 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     // The attribute is process wide per kernel: set it to the per-block maximum once, so that
     // handles of different depths (different slab sizes) never lower each other's limit.
     constexpr int kMaxDynSmem = 227 * 1024;
-    cudaFuncSetAttribute(k_m2l_tc<kTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    cudaFuncSetAttribute(k_m2l_tc<kTf32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    cudaFuncSetAttribute(k_m2l_tc<kBf16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    cudaFuncSetAttribute(k_m2l_tc<kF16mix>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    for_tile_rows([&](auto rows_tag) {
+        constexpr int R = decltype(rows_tag)::value;
+        cudaFuncSetAttribute(k_m2l_tc<kTf32, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        cudaFuncSetAttribute(k_m2l_tc<kTf32x3, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        cudaFuncSetAttribute(k_m2l_tc<kBf16x3, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        cudaFuncSetAttribute(k_m2l_tc<kF16mix, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    });
     return FMM_OK;
 }
 
@@ -840,27 +862,32 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream, int lo, int hi, int parts) {
     if (nt <= 0 || !(parts & kM2lMma)) return;
     const long long wlim = h->wait_limit > 0 ? h->wait_limit : kWaitLimit;
     const TcTile* tiles = st->tiles + t0;
-    switch (st->mode) {
-        case kTf32x3:
-            k_m2l_tc<kTf32x3><<<nt, kTcThreads, st->smem, stream>>>(
-                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
-                0, wlim);
-            break;
-        case kBf16x3:
-            k_m2l_tc<kBf16x3><<<nt, kTcThreads, st->smem, stream>>>(
-                tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
-                0, wlim);
-            break;
-        case kF16mix:
-            k_m2l_tc<kF16mix><<<nt, kTcThreads, st->smem, stream>>>(
-                tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
-                st->last_half, wlim);
-            break;
-        default:
-            k_m2l_tc<kTf32><<<nt, kTcThreads, st->smem, stream>>>(
-                tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages, h->status,
-                0, wlim);
-    }
+    auto launch = [&](auto rows_tag) {
+        constexpr int R = decltype(rows_tag)::value;
+        if (R != st->rows) return;
+        switch (st->mode) {
+            case kTf32x3:
+                k_m2l_tc<kTf32x3, R><<<nt, kTcThreads, st->smem, stream>>>(
+                    tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages,
+                    h->status, 0, wlim);
+                break;
+            case kBf16x3:
+                k_m2l_tc<kBf16x3, R><<<nt, kTcThreads, st->smem, stream>>>(
+                    tiles, st->lv, st->Mtc, st->Mtc_lo, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages,
+                    h->status, 0, wlim);
+                break;
+            case kF16mix:
+                k_m2l_tc<kF16mix, R><<<nt, kTcThreads, st->smem, stream>>>(
+                    tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages,
+                    h->status, st->last_half, wlim);
+                break;
+            default:
+                k_m2l_tc<kTf32, R><<<nt, kTcThreads, st->smem, stream>>>(
+                    tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages,
+                    h->status, 0, wlim);
+        }
+    };
+    for_tile_rows(launch);
 }
 
 }  // namespace fmmcph

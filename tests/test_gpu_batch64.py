@@ -1,8 +1,10 @@
 """The batched workload against the oracle: 64 independent replicas of uneven size (N
 log-uniform in 5k..50k atoms at 100 atoms/nm^3, water plus one cluster, 5..40 sites of 5
-atoms; seeds 100..163; periodic, p = 8), each at the depth the autotuner picks, evaluated
-together through one Batch (parallel branches of one CUDA graph) in the mixed precision the
-batched benchmark runs (FP16 M2L with split low degrees).
+atoms; seeds 100..163; periodic, p = 8), each at the depth and kernel tiles the autotuner picks
+(the fastest depth whose force and dV/dlambda errors, estimated against an order p + 2
+evaluation, are within 0.7 x 1e-4), evaluated together through one Batch (parallel branches of
+one CUDA graph) in the mixed precision the batched benchmark runs (FP16 M2L with split low
+degrees).
 
 Every replica is compared with the FP64 Ewald oracle on 160 random atoms plus every site atom
 (so dV/dlambda is complete): relative RMS force error and dV/dlambda within 1e-4.  The TF32 form
@@ -15,7 +17,7 @@ import torch
 import synth
 from fmm_check import errors, oracle_ref, to_dev
 from paper_2410_01626_b300 import FMM, Batch
-from paper_2410_01626_b300.autotune import tune_depth
+from paper_2410_01626_b300.autotune import TILES, tune
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -25,10 +27,12 @@ def _batch(reps, precision, depths=None):
     for i, s in enumerate(reps):
         d = to_dev(s)
         if depths is None:
-            dep, _ = tune_depth(s["L"], True, s["p"], precision, d["x"], d["qA"], d["qB"], d["site"], d["lam"], reps=2)
+            cfg, _ = tune(s["L"], True, s["p"], precision, d["x"], d["qA"], d["qB"], d["site"], d["lam"], reps=2,
+                          tiles=TILES)
         else:
-            dep = depths[i]
-        f = FMM(s["L"], True, s["p"], dep, precision=precision)
+            cfg = {"depth": depths[i], "m2l_rows": 0, "p2p_warps": 0}
+        dep = cfg["depth"]
+        f = FMM(s["L"], True, s["p"], dep, precision=precision, m2l_rows=cfg["m2l_rows"], p2p_warps=cfg["p2p_warps"])
         f.set_charges(d["qA"], d["qB"], d["site"], d["lam"])
         solvers.append(f)
         xs.append(d["x"])

@@ -274,6 +274,40 @@ def test_eval_host_matches_device():
     f.close()
 
 
+def test_eval_host_async_calls_in_flight_match_device():
+    """Several fmm_eval_host_async calls in flight on one stream (different positions each, so
+    consecutive calls use the two staging sets in turn and overlap a copy with the previous
+    evaluation), then one synchronisation: every call's results equal fmm_eval's on the device
+    with its positions, bit for bit -- also with a synchronous fmm_eval_host in between and once
+    the staging sets' graphs are captured and replayed."""
+    s = synth.periodic_uniform(seed=6, n=3000, L=3.0, p=8, depth=3)
+    f, d = make_solver(s, precision="fp16")
+    rng = np.random.default_rng(3)
+    xs = [np.ascontiguousarray((s["x"] + rng.uniform(-0.01, 0.01, s["x"].shape)).astype(np.float32))
+          for _ in range(6)]
+    refs = []
+    for x in xs:
+        E, F, dV, _ = f.eval(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        refs.append((E.item(), F.cpu(), dV.cpu()))
+    n, K = len(s["x"]), len(s["lam"])
+    bufs = [(torch.from_numpy(x).pin_memory(), torch.empty(1, dtype=torch.float64).pin_memory(),
+             torch.empty(n, 3).pin_memory(), torch.empty(K).pin_memory()) for x in xs]
+    for rnd in range(3):  # eager, then capture of both staging sets' graphs, then replays
+        for i, (xh, Eh, Fh, dVh) in enumerate(bufs):
+            if rnd == 1 and i == 3:
+                f.eval_host(xh, Eh, Fh, dVh)  # a synchronous call between asynchronous ones
+            else:
+                f.eval_host_async(xh, Eh, Fh, dVh)
+        torch.cuda.synchronize()
+        for (xh, Eh, Fh, dVh), (E, F, dV) in zip(bufs, refs):
+            assert Eh.item() == E
+            assert torch.equal(Fh, F) and torch.equal(dVh, dV)
+            Eh.zero_(); Fh.zero_(); dVh.zero_()
+    assert f.status_word() == 0
+    f.close()
+
+
 def test_open_domain_error_is_reported():
     s = synth.small_open()
     s["x"][5] = [4.5, 1.0, 1.0]
@@ -437,3 +471,32 @@ def test_fp16_close_to_fp32_path():
     dV = np.linalg.norm(a["dVdl"] - b["dVdl"]) / np.linalg.norm(a["dVdl"])
     print(f"fp16 vs fp32: dF {dF:.2e} dE {dE:.2e} dVdl {dV:.2e}")
     assert dF < 2e-6 and dE < 1e-5 and dV < 1e-4, (dF, dE, dV)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "3xbf16"])
+def test_kernel_tiles_give_identical_results(precision):
+    """The M2L tile width (128, 192, 256 rows per CTA) and the near-field block shape (2 or 4
+    leaves per block) only change how the work is split: every choice gives bit for bit the
+    result of the default, at depths 3 and 5."""
+    from paper_2410_01626_b300 import FMM
+    for s in (synth.periodic_uniform(seed=17, n=40000, L=5.0, n_sites=8, site_size=4, p=10, depth=3),
+              synth.periodic_uniform(seed=18, n=150000, L=10.0, n_sites=8, site_size=4, p=10, depth=5)):
+        d = to_dev(s)
+        outs = []
+        for rows, warps in ((0, 0), (128, 0), (256, 0), (0, 2), (128, 2)):
+            f = FMM(s["L"], True, s["p"], s["depth"], precision=precision, m2l_rows=rows, p2p_warps=warps)
+            f.set_charges(d["qA"], d["qB"], d["site"], d["lam"])
+            E, F, dV, phi = f.eval(d["x"], phi=True)
+            torch.cuda.synchronize()
+            assert f.status_word() == 0
+            outs.append((E.item(), F.cpu(), dV.cpu(), phi.cpu()))
+            f.close()
+        for o in outs[1:]:
+            assert o[0] == outs[0][0]
+            for a, b in zip(o[1:], outs[0][1:]):
+                assert torch.equal(a, b)
+    from paper_2410_01626_b300 import FmmError
+    with pytest.raises(FmmError):
+        FMM(3.0, True, 8, 3, precision=precision, m2l_rows=100)
+    with pytest.raises(FmmError):
+        FMM(3.0, True, 8, 3, precision=precision, p2p_warps=8)
