@@ -836,7 +836,9 @@ void f32_bricks(int lmin, int depth, std::vector<F32Brick>& out) {
     out.clear();
     for (int l = lmin; l <= depth; ++l) {
         const int n = 1 << (l - 1);
-        const int bx = std::min(n, 4), by = std::min(n, 4), bz = std::min(n, 8);
+        // every brick is 4 x 4 x 8 boxes (those beyond n, on coarse levels, are computed and
+        // dropped), so that a thread's 8 boxes are 8 consecutive halo entries
+        const int bx = 4, by = 4, bz = 8;
         for (int c = 0; c < 8; ++c)
             for (int i0 = 0; i0 < n; i0 += bx)
                 for (int j0 = 0; j0 < n; j0 += by)
@@ -849,12 +851,11 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
                                                     float* __restrict__ part, long part_stride, LevelOffsets lo,
                                                     int periodic) {
     __shared__ float hs[kF32KC][kF32Halo];
-    __shared__ __align__(16) float ts[kF32KC][128];
+    __shared__ __align__(16) float ts[2][kF32KC][128];
     const F32Brick br = bricks[blockIdx.x];
     const int n = 1 << (br.level - 1);
     const int cx = br.cls & 1, cy = (br.cls >> 1) & 1, cz = (br.cls >> 2) & 1;
-    const int hy = br.by + 2, hz = br.bz + 2, nh = (br.bx + 2) * hy * hz;
-    const int nbox = br.bx * br.by * br.bz;
+    constexpr int hy = 6, hz = 10, nh = 6 * 6 * 10;  // halo of a 4 x 4 x 8 brick
     const float* Ml = M + lo.off[br.level] * ncp;
     const int tid = threadIdx.x;
     // coefficients 8 tc .. +7, boxes 8 tb .. +7 of the brick.  A warp holds 4 coefficient groups x
@@ -864,19 +865,9 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
     const int w = tid >> 5, lane = tid & 31;
     const int tc = 4 * (w & 3) + (lane & 3), tb = 8 * (w >> 2) + (lane >> 2);
     const bool cact = 8 * tc < ncp;
-    int hb[8];  // halo index of each of the thread's boxes at delta = (-1, -1, -1)
-    {
-        // the 8 boxes of a thread are consecutive in k when bz = 8 (n >= 8); smaller bricks
-        // take the general decomposition
-        const int b0 = 8 * tb;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int b = b0 + e;
-            const int k = b % br.bz, r = b / br.bz;
-            const int j = r % br.by, i = r / br.by;
-            hb[e] = b < nbox ? (i * hy + j) * hz + k : 0;
-        }
-    }
+    // the thread's 8 boxes are the pencil (i, j) = (tb / 4, tb % 4), k = 0..7: halo entries
+    // hb0 + e at delta = (-1, -1, -1)
+    const int hb0 = ((tb >> 2) * hy + (tb & 3)) * hz;
     float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -905,26 +896,57 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
                 if (ok) v = Ml[(long)morton3(2 * si + px, 2 * sj + py, 2 * sk + pz) * ncp + kc * kF32KC + kk];
                 hs[kk][hbx] = v;
             }
+            // the valid shifts of (c, pi): a bit per delta; operator chunks double-buffered --
+            // the next shift's chunk is read into registers while the current one is used
+            unsigned vmask = 0;
             for (int d = 0; d < 27; ++d) {
-                const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                const int ox = 2 * dx + px - cx, oy = 2 * dy + py - cy, oz = 2 * dz + pz - cz;
-                if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;  // near field
-                const float* Tc = T + ((long)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * ncp + kc * kF32KC) * ncp;
-                __syncthreads();  // ts is free (and, for the first shift, hs is complete)
-                for (int q = tid; q < kF32KC * ncp / 4; q += 256) {
-                    const int k = q / (ncp / 4), j4 = q % (ncp / 4);
-                    reinterpret_cast<float4*>(&ts[k][0])[j4] = reinterpret_cast<const float4*>(Tc + (long)k * ncp)[j4];
+                const int ox = 2 * (d / 9 - 1) + px - cx, oy = 2 * ((d / 3) % 3 - 1) + py - cy, oz = 2 * (d % 3 - 1) + pz - cz;
+                if (abs(ox) > 1 || abs(oy) > 1 || abs(oz) > 1) vmask |= 1u << d;
+            }
+            const int nq = kF32KC * ncp / 4;  // float4 of one operator chunk
+            auto chunk_src = [&](int d) {
+                const int ox = 2 * (d / 9 - 1) + px - cx, oy = 2 * ((d / 3) % 3 - 1) + py - cy, oz = 2 * (d % 3 - 1) + pz - cz;
+                return reinterpret_cast<const float4*>(
+                    T + ((long)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * ncp + kc * kF32KC) * ncp);
+            };
+            float4 pre[2];
+            auto fetch = [&](int d) {
+                const float4* src = chunk_src(d);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = tid + 256 * r;
+                    pre[r] = q < nq ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                __syncthreads();
+            };
+            auto stash = [&](int buf) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = tid + 256 * r;
+                    if (q < nq) reinterpret_cast<float4*>(&ts[buf][q / (ncp / 4)][0])[q % (ncp / 4)] = pre[r];
+                }
+            };
+            unsigned m = vmask;
+            int d = __ffs(m) - 1;
+            m &= m - 1;
+            fetch(d);
+            stash(0);
+            __syncthreads();  // the halo and the first operator chunk are in place
+            int cur = 0;
+            while (d >= 0) {
+                const int dn = m ? __ffs(m) - 1 : -1;
+                m &= m - 1;
+                if (dn >= 0) fetch(dn);
+                const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
                 const int so = ((dx + 1) * hy + (dy + 1)) * hz + (dz + 1);
                 if (cact) {
 #pragma unroll 4
                     for (int k = 0; k < kF32KC; ++k) {
-                        const float4 a0 = *reinterpret_cast<const float4*>(&ts[k][8 * tc]);
-                        const float4 a1 = *reinterpret_cast<const float4*>(&ts[k][8 * tc + 4]);
+                        const float4 a0 = *reinterpret_cast<const float4*>(&ts[cur][k][8 * tc]);
+                        const float4 a1 = *reinterpret_cast<const float4*>(&ts[cur][k][8 * tc + 4]);
                         float bv[8];
+                        const float* hrow = &hs[k][hb0 + so];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) bv[e] = hs[k][hb[e] + so];
+                        for (int e = 0; e < 8; ++e) bv[e] = hrow[e];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             acc[0][e] = fmaf(a0.x, bv[e], acc[0][e]);
@@ -938,17 +960,21 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
                         }
                     }
                 }
+                if (dn >= 0) stash(cur ^ 1);
+                __syncthreads();  // the next chunk is in place; nobody reads this one any more
+                cur ^= 1;
+                d = dn;
             }
         }
     }
     if (!cact) return;
     float* Ll = part + (long)pi * part_stride + lo.off[br.level] * ncp;
+    const int ti = br.i0 + (tb >> 2), tj = br.j0 + (tb & 3);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const int b = 8 * tb + e;
-        if (b >= nbox) continue;
-        const int k = b % br.bz, j = (b / br.bz) % br.by, i = b / (br.bz * br.by);
-        const uint32_t box = morton3(2 * (br.i0 + i) + cx, 2 * (br.j0 + j) + cy, 2 * (br.k0 + k) + cz);
+        const int tk = br.k0 + e;
+        if (ti >= n || tj >= n || tk >= n) continue;  // padding of a coarse level's brick
+        const uint32_t box = morton3(2 * ti + cx, 2 * tj + cy, 2 * tk + cz);
         float4* dst = reinterpret_cast<float4*>(Ll + (long)box * ncp + 8 * tc);
         dst[0] = make_float4(acc[0][e], acc[1][e], acc[2][e], acc[3][e]);
         dst[1] = make_float4(acc[4][e], acc[5][e], acc[6][e], acc[7][e]);
@@ -1320,6 +1346,7 @@ __device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsign
 //     atoms), since equal positions always share a leaf.  Slice sums are combined by a
 //     fixed-order shuffle tree; k_far_out adds the far field and writes the outputs.
 constexpr int kNearCap = 640;
+constexpr int kNT = 2;  // target atoms per lane in the near field's pair loop (4 measured slower)
 __device__ __forceinline__ float rsqrt_approx(float x) {  // MUFU reciprocal square root
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -1458,11 +1485,11 @@ __global__ void __launch_bounds__(32 * W) k_p2p(NearParams a, float4* __restrict
                 if (valid) near_output(near, st + ti, pot, gx, gy, gz);
             }
         } else if (cnt > 0) {
-            // (3) mapping: passes x TPG lanes (2 targets each) x G slices
-            int TPG = 32, G = 1, passes = (cnt + 63) / 64, best = 1 << 30;
+            // (3) mapping: passes x TPG lanes (kNT targets each) x G slices
+            int TPG = 32, G = 1, passes = (cnt + 32 * kNT - 1) / (32 * kNT), best = 1 << 30;
             const int p0 = passes;
             for (int ps = p0; ps < p0 + 4; ++ps) {
-                const int tpg = (cnt + 2 * ps - 1) / (2 * ps);
+                const int tpg = (cnt + kNT * ps - 1) / (kNT * ps);
                 const int g = 32 / tpg;
                 const int cost = ps * ((npairs + g - 1) / g + 4 * g + 16);
                 if (cost < best) {
@@ -1476,20 +1503,23 @@ __global__ void __launch_bounds__(32 * W) k_p2p(NearParams a, float4* __restrict
             const bool active = slice < G;
             const float4* sp4 = src_sm[w];
             for (int ps = 0; ps < passes; ++ps) {
-                const int ti0 = ps * 2 * TPG + tl, ti1 = ti0 + TPG;
-                const bool v0 = active && ti0 < cnt, v1 = active && ti1 < cnt;
-                const float4 far_pt = make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
-                const float4 me0 = v0 ? a.pos[st + ti0] : far_pt, me1 = v1 ? a.pos[st + ti1] : far_pt;
-                const unsigned long long mx0 = f2pack(me0.x, me0.x), my0 = f2pack(me0.y, me0.y),
-                                         mz0 = f2pack(me0.z, me0.z), mx1 = f2pack(me1.x, me1.x),
-                                         my1 = f2pack(me1.y, me1.y), mz1 = f2pack(me1.z, me1.z);
-                unsigned long long P0 = 0ull, X0 = 0ull, Y0 = 0ull, Z0 = 0ull, P1 = 0ull, X1 = 0ull, Y1 = 0ull, Z1 = 0ull;
+                int ti[kNT];
+                bool tv[kNT];
+                unsigned long long mx[kNT], my[kNT], mz[kNT], P[kNT], X[kNT], Y[kNT], Z[kNT];
+#pragma unroll
+                for (int r = 0; r < kNT; ++r) {
+                    ti[r] = ps * kNT * TPG + r * TPG + tl;
+                    tv[r] = active && ti[r] < cnt;
+                    const float4 me = tv[r] ? a.pos[st + ti[r]] : make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
+                    mx[r] = f2pack(me.x, me.x);
+                    my[r] = f2pack(me.y, me.y);
+                    mz[r] = f2pack(me.z, me.z);
+                    P[r] = X[r] = Y[r] = Z[r] = 0ull;
+                }
                 // sources minus target: the gradient of q/r at the target is q (s - x) / r^3
                 auto apply = [&](const unsigned long long sx, const unsigned long long sy, const unsigned long long sz,
-                                 const unsigned long long sq, const unsigned long long mx, const unsigned long long my,
-                                 const unsigned long long mz, unsigned long long& P, unsigned long long& GX,
-                                 unsigned long long& GY, unsigned long long& GZ, const bool check) {
-                    const unsigned long long dx = f2sub(sx, mx), dy = f2sub(sy, my), dz = f2sub(sz, mz);
+                                 const unsigned long long sq, const int r, const bool check) {
+                    const unsigned long long dx = f2sub(sx, mx[r]), dy = f2sub(sy, my[r]), dz = f2sub(sz, mz[r]);
                     const float2 r2 = f2unpack(f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx))));
                     float r0 = rsqrt_approx(r2.x), r1 = rsqrt_approx(r2.y);
                     if (check) {
@@ -1498,18 +1528,18 @@ __global__ void __launch_bounds__(32 * W) k_p2p(NearParams a, float4* __restrict
                     }
                     const unsigned long long ri = f2pack(r0, r1);
                     const unsigned long long qri = f2mul(sq, ri);
-                    P = f2add(P, qri);
+                    P[r] = f2add(P[r], qri);
                     const unsigned long long qri3 = f2mul(qri, f2mul(ri, ri));
-                    GX = f2fma(qri3, dx, GX);
-                    GY = f2fma(qri3, dy, GY);
-                    GZ = f2fma(qri3, dz, GZ);
+                    X[r] = f2fma(qri3, dx, X[r]);
+                    Y[r] = f2fma(qri3, dy, Y[r]);
+                    Z[r] = f2fma(qri3, dz, Z[r]);
                 };
                 auto step = [&](int t, const bool check) {
                     const float4 A = sp4[2 * t], B = sp4[2 * t + 1];
                     const unsigned long long sx = f2pack(A.x, A.y), sy = f2pack(A.z, A.w), sz = f2pack(B.x, B.y),
                                              sq = f2pack(B.z, B.w);
-                    apply(sx, sy, sz, sq, mx0, my0, mz0, P0, X0, Y0, Z0, check);
-                    apply(sx, sy, sz, sq, mx1, my1, mz1, P1, X1, Y1, Z1, check);
+#pragma unroll
+                    for (int r = 0; r < kNT; ++r) apply(sx, sy, sz, sq, r, check);
                 };
                 if (active) {
                     int t = slice;
@@ -1520,31 +1550,28 @@ __global__ void __launch_bounds__(32 * W) k_p2p(NearParams a, float4* __restrict
                     }
                     for (; t < npairs; t += G) step(t, false);
                 }
-                float v[8];
-                {
-                    const float2 p0v = f2unpack(P0), x0v = f2unpack(X0), y0v = f2unpack(Y0), z0v = f2unpack(Z0);
-                    const float2 p1v = f2unpack(P1), x1v = f2unpack(X1), y1v = f2unpack(Y1), z1v = f2unpack(Z1);
-                    v[0] = p0v.x + p0v.y;
-                    v[1] = x0v.x + x0v.y;
-                    v[2] = y0v.x + y0v.y;
-                    v[3] = z0v.x + z0v.y;
-                    v[4] = p1v.x + p1v.y;
-                    v[5] = x1v.x + x1v.y;
-                    v[6] = y1v.x + y1v.y;
-                    v[7] = z1v.x + z1v.y;
+                float v[4 * kNT];
+#pragma unroll
+                for (int r = 0; r < kNT; ++r) {
+                    const float2 pv = f2unpack(P[r]), xv = f2unpack(X[r]), yv = f2unpack(Y[r]), zv = f2unpack(Z[r]);
+                    v[4 * r] = pv.x + pv.y;
+                    v[4 * r + 1] = xv.x + xv.y;
+                    v[4 * r + 2] = yv.x + yv.y;
+                    v[4 * r + 3] = zv.x + zv.y;
                 }
                 // slice sums: fixed-order tree over the slices (slice 0 ends with the total)
                 for (int off = 1; off < G; off <<= 1) {
                     const bool take = (slice % (2 * off)) == 0 && slice + off < G;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
+                    for (int e = 0; e < 4 * kNT; ++e) {
                         const float o = __shfl_down_sync(0xffffffffu, v[e], off * TPG);
                         if (take) v[e] += o;
                     }
                 }
                 if (slice == 0) {
-                    if (v0) near_output(near, st + ti0, v[0], v[1], v[2], v[3]);
-                    if (v1) near_output(near, st + ti1, v[4], v[5], v[6], v[7]);
+#pragma unroll
+                    for (int r = 0; r < kNT; ++r)
+                        if (tv[r]) near_output(near, st + ti[r], v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
                 }
             }
         }
