@@ -96,8 +96,8 @@ typedef struct {
     double coulomb_k;   /* k_e; <= 0 selects 138.935458             */
     int interpolation;  /* fmm_interpolation                       */
     /* Kernel tiles (results are the same for every choice; the autotuner picks them by timing).
-     * m2l_tile_rows: rows of the tensor-core M2L's per-CTA tile (the MMA's N): 128, 192 or 256;
-     *   0 selects 192.
+     * m2l_tile_rows: rows of the tensor-core M2L's per-CTA tile (the MMA's N): 128, 160, 192,
+     *   224 or 256; 0 selects 192.
      * p2p_leaves_per_block: target leaves (one warp each) per near-field block: 2 or 4; 0
      *   selects 4.
      * Other values return FMM_ERR_ARG. */

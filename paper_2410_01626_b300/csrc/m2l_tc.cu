@@ -46,16 +46,20 @@ constexpr int kTcAccStride = 256;
 constexpr int kTcMaxStages = 16;  // operator-chunk ring depth: as many stages as shared memory holds
 constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
 // Operand forms.  K chunk (input coefficients per slab / operator chunk): 16 for TF32, 8 for
-// the split 3xTF32 form (hi and lo parts), 16 for the split 3xBF16 form.  The FP16 form
-// (kF16mix) has chunks of two kinds in the same 4-cell layout as TF32: chunk 0 holds the
-// input coefficients 0..15 (degrees 0..3) as hi cells 0-1 and lo cells 2-3 (three products,
-// hi hi + hi lo + lo hi, about 22 bits), every later chunk 32 coefficients as hi cells 0-3
-// (one product per K step, 11 bits).  The low degrees carry the large monopole and dipole
-// parts of the far field, whose rounding the potential and dV/dlambda feel most; a single
-// product for every degree gives TF32-like errors (4e-4 in dV/dlambda at 500k atoms), the
-// split of degrees 0..3 alone the errors of the full split (5e-6).  In every form a ring stage
+// the split 3xTF32 form (hi and lo parts), 16 for the split 3xBF16 form; there a ring stage
 // is 8 KB (one operator chunk, all parts) and a slab buffer 64 bytes per row (about 43 KB at
 // depth 5), so two slab buffers leave room for a 16-stage ring.
+// The FP16 form (kF16mix) has wider chunks of 6 cells (three K steps, 12 KB stages) of three
+// kinds: chunk 0 holds the input coefficients 0..15 (degrees 0..3) as hi cells 0-1 and lo
+// cells 2-3 (three products, hi hi + hi lo + lo hi, about 22 bits) and, when the plain K
+// steps leave one over, the last 16 coefficients as hi cells 4-5 (one product); every later
+// chunk holds 48 coefficients (three K steps of one product, 11 bits), or 32 in a last chunk
+// of two steps.  The low degrees carry the large monopole and dipole parts of the far field,
+// whose rounding the potential and dV/dlambda feel most; a single product for every degree
+// gives TF32-like errors (4e-4 in dV/dlambda at 500k atoms), the split of degrees 0..3 alone
+// the errors of the full split (5e-6).  Each ring stage costs the issuer one wait and one
+// commit, so wide chunks (3-4 MMAs each) keep the tensor pipe ahead of that per-stage work,
+// and at p = 10 an (operator, shift) takes 3 stages instead of 5.
 enum TcMode { kTf32 = 0, kTf32x3 = 1, kBf16x3 = 2, kF16mix = 3 };
 template <int MODE>
 struct TcCfg {
@@ -65,18 +69,32 @@ struct TcCfg {
     static constexpr bool k16 = kBf16 || kMix;              // 16-bit elements, kind::f16
     static constexpr int kElem = k16 ? 2 : 4;               // bytes per operand element
     static constexpr int kPerCell = 16 / kElem;             // coefficients per 16-byte cell
-    static constexpr int kChunk = kMix ? 32 : kBf16 ? 16 : (kSplit ? 8 : 16);
-    static constexpr int kKG = kChunk / kPerCell;           // cells per chunk row (4, 2, 2, 4)
+    static constexpr int kChunk = kMix ? 48 : kBf16 ? 16 : (kSplit ? 8 : 16);
+    static constexpr int kKG = kChunk / kPerCell;           // cells per chunk row (4, 2, 2, 6)
     static constexpr int kKSteps = kChunk * kElem / 32;     // MMAs per chunk (32 bytes of K each)
     static constexpr int kParts = kSplit ? 2 : 1;
     static constexpr uint32_t kPartBytes = 128u * kChunk * kElem;  // one operator part (hi or lo)
-    static constexpr uint32_t kStageBytes = kParts * kPartBytes;   // 8 KB in every form
+    static constexpr uint32_t kStageBytes = kParts * kPartBytes;   // 8 KB (12 KB in the FP16 form)
 };
-// FP16 form: first input coefficient and part (false = hi, true = lo) of cell j (0..3) of
-// chunk ch.
-__host__ __device__ inline int f16mix_base(int ch, int j) { return ch == 0 ? 8 * (j & 1) : 16 + 32 * (ch - 1) + 8 * j; }
-__host__ __device__ inline bool f16mix_lo(int ch, int j) { return ch == 0 && j >= 2; }
-inline int f16mix_chunks(int ncp) { return 1 + (ncp - 16 + 31) / 32; }
+// FP16 form.  The ncp - 16 coefficients above the split ones are m = (ncp - 16) / 16 plain K
+// steps: m / 3 chunks of three steps, and the remainder either as the tail of chunk 0 (one
+// step, layout bit 0) or as a last chunk of two steps (layout bit 1).
+inline int f16mix_layout(int ncp) {
+    const int m = (ncp - 16) / 16;
+    return m % 3 == 1 ? 1 : m % 3 == 2 ? 2 : 0;
+}
+inline int f16mix_chunks(int ncp) {
+    const int m = (ncp - 16) / 16;
+    return 1 + m / 3 + (m % 3 == 2 ? 1 : 0);
+}
+// First input coefficient of cell j (0..5) of chunk ch; ncp (no coefficient) for the tail
+// cells of a chunk 0 without a tail.  Cells at or beyond ncp hold zeros.
+__host__ __device__ inline int f16mix_base(int ch, int j, int ncp, int layout) {
+    if (ch == 0) return j < 4 ? 8 * (j & 1) : (layout & 1) ? ncp - 16 + 8 * (j - 4) : ncp;
+    return 16 + 48 * (ch - 1) + 8 * j;
+}
+// whether cell j of chunk ch holds the lo part (the FP16 rounding of the remainder)
+__host__ __device__ inline bool f16mix_lo(int ch, int j) { return ch == 0 && (j == 2 || j == 3); }
 
 struct TcLevels {
     int n[kMaxDepth + 1];
@@ -179,7 +197,7 @@ __global__ void k_m2l_pack(PackLevels pl, int NKG, int ncp, int periodic, const 
 __device__ __forceinline__ uint32_t f16_pair(float a, float b) {  // a in the low half (first in memory)
     return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
 }
-__global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int periodic, const float* __restrict__ M,
+__global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int layout, int periodic, const float* __restrict__ M,
                                   float* __restrict__ Mtc_all) {
     const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gt >= pl.first[pl.nlev]) return;
@@ -193,8 +211,8 @@ __global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int periodic,
     const int cls = (int)(tid / ((long)R * NKG));
     const int m2 = n + 2;
     int i = row / (m2 * m2) - 1, j = (row / m2) % m2 - 1, k = row % m2 - 1;
-    const int ch = gc >> 2, cell = gc & 3;
-    const int base = f16mix_base(ch, cell);
+    const int ch = gc / 6, cell = gc % 6;
+    const int base = f16mix_base(ch, cell, ncp, layout);
     bool ok = base < ncp;  // ncp is a multiple of 16: the cell's 8 coefficients all exist
     if (periodic) {
         i = (i + n) % n;
@@ -235,7 +253,7 @@ template <int MODE, int ROWS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const TcTile* __restrict__ tiles, TcLevels lv, const float* __restrict__ Mtc,
              const float* __restrict__ Mtc_lo, const float* __restrict__ Ttc, float* __restrict__ L, int ncp,
-             int NKC, int slab_rows, int nstages, int* __restrict__ status, int last_half, long long wlim) {
+             int NKC, int slab_rows, int nstages, int* __restrict__ status, int mix_layout, long long wlim) {
     using Cfg = TcCfg<MODE>;
     constexpr bool SPLIT = Cfg::kSplit;
     constexpr int kTcKG = Cfg::kKG;
@@ -315,10 +333,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // is spread over the lanes as one copy each.  Control flow is warp-uniform; a failed
         // wait in any lane ends the round before anything of it is issued.
         int* sel = const_cast<int*>(copy_count + 4);  // [32]: operator index by rank
-        // chunks issued per round: at most nstages - 1, because the MMA issuer waits for chunk
-        // j + 1 before it releases chunk j, and a round's last lane needs the stage that chunk
-        // nstages back released
-        const int per_round = min(8, nstages - 1);
+        // chunks issued per round: at most half the ring, so that a round is issued while the
+        // other half still holds chunks for the MMA issuer (a round waits for the stage of its
+        // last chunk, the one nstages back from it)
+        const int per_round = max(1, min(8, nstages / 2));
         int t_issued = 0, slabs_issued = 0;
         auto load_slab = [&](int g) {
             const int pi = g / NKC, ch = g % NKC, buf = g & 1;
@@ -437,12 +455,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t tphase = 0;
             bool ok = true;
             int t_taken = 0, slabs_taken = 0;
+            int* shift_tab = const_cast<int*>(copy_count) + 36;  // [27], after the producer's rank table
             for (int g = 0; g < ngroups && ok; ++g) {
                 const int pi = g / NKC, buf = g & 1;
                 // FP16 form: the products of this group's chunk -- 0: split (three products),
-                // 1: two K steps of one product, 2: one K step (a half chunk at the end of K)
+                // 3: split and the tail K step, 1: three K steps of one product, 2: two K steps
                 const int ch = g % NKC;
-                const int mix_kind = !Cfg::kMix ? 0 : ch == 0 ? 0 : (ch == NKC - 1 && last_half) ? 2 : 1;
+                const int mix_kind = !Cfg::kMix ? 0
+                                     : ch == 0  ? ((mix_layout & 1) ? 3 : 0)
+                                                : (ch == NKC - 1 && (mix_layout & 2)) ? 2 : 1;
                 const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
                 const int ab = g & 1;
                 const uint32_t dacc = tmem + (uint32_t)(ab * kTcAccStride);
@@ -458,32 +479,52 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc::fence_after_sync();
                 const uint64_t b_buf = b_base + (((uint64_t)buf * slab_bytes) >> 4) + (uint64_t)hal;
                 uint32_t acc = 0;
-                // The unrolled loop over the 27 shifts, specialised per chunk kind so that the
-                // issue path of each chunk has no branch on it (the kind is fixed per group).
+                // the slab row offsets of this (target class, source class)'s valid shifts, in
+                // ascending shift order (the order of the producer's copies)
+                int nshift = 0;
+                {
+                    bool valid = false;
+                    int off = 0;
+                    if (lane < 27) {
+                        const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+                        valid = abs(2 * dx + qx) > 1 || abs(2 * dy + qy) > 1 || abs(2 * dz + qz) > 1;
+                        off = (dx + 1) * slab_rows + dy * m2 + dz;
+                    }
+                    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+                    nshift = __popc(vmask);
+                    __syncwarp();  // the previous group's reads of the table are done
+                    if (valid) shift_tab[__popc(vmask & ((1u << lane) - 1u))] = off;
+                    __syncwarp();
+                }
+                // The loop over the valid shifts, kept rolled (a short loop body stays in the
+                // instruction cache beside the other roles' code) and specialised per chunk kind
+                // so that the issue path of each chunk has no branch on it (the kind is fixed
+                // per group).
                 auto shifts = [&](auto kind_tag) {
                     constexpr int kKind = decltype(kind_tag)::value;
-#pragma unroll
-                    for (int d = 0; d < 27; ++d) {
-                        const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                        const int ox = 2 * dx + qx, oy = 2 * dy + qy, oz = 2 * dz + qz;
-                        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) continue;
+#pragma unroll 1
+                    for (int i = 0; i < nshift; ++i) {
+                        const uint64_t bd0 = b_buf + (uint64_t)shift_tab[i];
                         if (!tc::mbar_wait_all_abort(t_full + stage, tphase, wlim, abort_flag)) return false;
                         ++t_taken;
                         const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
-                        const uint64_t bd0 = b_buf + (uint64_t)((dx + 1) * slab_rows + dy * m2 + dz);
                         // the MMAs of this chunk, then the commit that releases its ring stage; one
                         // elected lane issues each K step's products (hi(T) hi(M) + hi(T) lo(M) +
                         // lo(T) hi(M) in the split forms)
                         if (Cfg::kMix) {
                             // A: cells of 2048 bytes (128 rows), a K step = two cells = 4096 bytes;
-                            // B: cells kg_stride apart.  Split chunk: hi in K-step slot 0, lo in slot 1.
+                            // B: cells kg_stride apart.  Chunk 0: hi in K-step slot 0, lo in slot 1,
+                            // the tail in slot 2.
                             const uint64_t ad1 = ad0 + (4096u >> 4), bd1 = bd0 + ((2u * kg_stride) >> 4);
+                            const uint64_t ad2 = ad0 + (8192u >> 4), bd2 = bd0 + ((4u * kg_stride) >> 4);
                             if (kKind == 0)
-                                tc::mma3_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                                tc::mma_f16_n_w<3>(dacc, ad0, bd0, ad0, bd1, ad1, bd0, 0, 0, idesc, acc, t_empty + stage);
+                            else if (kKind == 3)
+                                tc::mma_f16_n_w<4>(dacc, ad0, bd0, ad0, bd1, ad1, bd0, ad2, bd2, idesc, acc, t_empty + stage);
                             else if (kKind == 1)
-                                tc::mma_f16_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                                tc::mma_f16_n_w<3>(dacc, ad0, bd0, ad1, bd1, ad2, bd2, 0, 0, idesc, acc, t_empty + stage);
                             else
-                                tc::mma_f16_w<false, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                                tc::mma_f16_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
                             acc = 1;
                         } else
 #pragma unroll
@@ -515,7 +556,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 };
                 if (!Cfg::kMix || mix_kind == 0) ok = shifts(std::integral_constant<int, 0>{});
                 else if (mix_kind == 1) ok = shifts(std::integral_constant<int, 1>{});
-                else ok = shifts(std::integral_constant<int, 2>{});
+                else if (mix_kind == 2) ok = shifts(std::integral_constant<int, 2>{});
+                else ok = shifts(std::integral_constant<int, 3>{});
                 if (!ok) break;
                 tc::mma_commit_w(acc_full + ab);  // this group's partial sum is complete, its slab free
             }
@@ -619,10 +661,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 template <class F>
 void for_tile_rows(F&& f) {
     f(std::integral_constant<int, 128>{});
+    f(std::integral_constant<int, 160>{});
     f(std::integral_constant<int, 192>{});
+    f(std::integral_constant<int, 224>{});
     f(std::integral_constant<int, 256>{});
 }
-bool m2l_tile_rows_ok(int rows) { return rows == 0 || rows == 128 || rows == 192 || rows == 256; }
+bool m2l_tile_rows_ok(int rows) {
+    return rows == 0 || rows == 128 || rows == 160 || rows == 192 || rows == 224 || rows == 256;
+}
 
 // ------------------------------------------------------------------------------------------
 struct TcState {
@@ -634,10 +680,10 @@ struct TcState {
     int ntiles = 0;
     int tile_first[kMaxDepth + 2] = {};  // the tiles of level l are [tile_first[l], tile_first[l + 1])
     int NKC = 0;
-    int last_half = 0;  // FP16 form: the last chunk holds 16 coefficients (one K step)
+    int mix_layout = 0;  // FP16 form: bit 0 = chunk 0 carries a tail K step, bit 1 = the last chunk has two
     int KG = 0;  // 16-byte cells per K chunk
     int slab_rows = 0;
-    int rows = kTcRows;  // virtual rows (MMA N) per CTA: 128, 192 or 256
+    int rows = kTcRows;  // virtual rows (MMA N) per CTA: 128, 160, 192, 224 or 256
     int nstages = 0;  // operator ring depth
     size_t smem = 0;
     TcLevels lv{};
@@ -700,21 +746,22 @@ void pack_operators(const std::vector<float>& Trm, int nc, int NKC, std::vector<
                 }
             }
 }
-// FP16 form: [op][chunk][cell j (4)][128 rows][16 bytes], cell j of chunk ch holding the
+// FP16 form: [op][chunk][cell j (6)][128 rows][16 bytes], cell j of chunk ch holding the
 // coefficients f16mix_base(ch, j) .. + 7 (hi part, or for the lo cells of chunk 0 the FP16
 // rounding of the remainder), zero at or beyond nc.
-void pack_operators_f16mix(const std::vector<float>& Trm, int nc, int NKC, std::vector<uint8_t>& out) {
-    out.assign((size_t)kNumOps * NKC * 8192, 0);
+void pack_operators_f16mix(const std::vector<float>& Trm, int nc, int ncp, int NKC, std::vector<uint8_t>& out) {
+    const int layout = f16mix_layout(ncp);
+    out.assign((size_t)kNumOps * NKC * TcCfg<kF16mix>::kStageBytes, 0);
     for (int op = 0; op < kNumOps; ++op)
         for (int ch = 0; ch < NKC; ++ch)
-            for (int j = 0; j < 4; ++j) {
-                const int base = f16mix_base(ch, j);
+            for (int j = 0; j < 6; ++j) {
+                const int base = f16mix_base(ch, j, ncp, layout);
                 for (int jj = 0; jj < nc; ++jj)
                     for (int e = 0; e < 8 && base + e < nc; ++e) {
                         const float v = Trm[((size_t)op * nc + jj) * nc + base + e];
                         const __half hi = __float2half_rn(v);
                         const __half w = f16mix_lo(ch, j) ? __float2half_rn(v - __half2float(hi)) : hi;
-                        const size_t cell = (((size_t)op * NKC + ch) * 4 + j) * 128 + jj;
+                        const size_t cell = (((size_t)op * NKC + ch) * 6 + j) * 128 + jj;
                         std::memcpy(out.data() + cell * 16 + (size_t)e * 2, &w, 2);
                     }
             }
@@ -750,8 +797,8 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
             st->KG = TcCfg<kF16mix>::kKG, nparts = 1;
             stage_bytes = TcCfg<kF16mix>::kStageBytes;
             st->NKC = f16mix_chunks(ncp);
-            st->last_half = (ncp - 16) % 32 == 16;
-            pack_operators_f16mix(T_rowmajor, nc, st->NKC, T);
+            st->mix_layout = f16mix_layout(ncp);
+            pack_operators_f16mix(T_rowmajor, nc, ncp, st->NKC, T);
             break;
         default:
             chunk = TcCfg<kTf32>::kChunk, st->KG = TcCfg<kTf32>::kKG, nparts = 1;
@@ -786,7 +833,7 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
     for (int l = d + 1; l <= kMaxDepth + 1; ++l) st->tile_first[l] = (int)tiles.size();
     st->slab_rows = st->rows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
     // two slab buffers, then as many ring stages as fit (at least 3), then barriers and flags
-    constexpr size_t kBarBytes = 1024;  // barriers, TMEM slot, flags, copy counts, rank table
+    constexpr size_t kBarBytes = 1024;  // barriers, TMEM slot, flags, copy counts, rank and shift tables
     const size_t slabs = 2 * (size_t)3 * st->slab_rows * st->KG * 16 * nparts;
     const size_t room = 227 * 1024 > slabs + kBarBytes ? 227 * 1024 - slabs - kBarBytes : 0;
     st->nstages = std::max(3, std::min(kTcMaxStages, (int)(room / stage_bytes)));
@@ -852,7 +899,7 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream, int lo, int hi, int parts) {
     if (tot > 0 && (parts & kM2lPack)) {
         const unsigned grid = (unsigned)((tot + 255) / 256);
         if (st->mode == kF16mix)
-            k_m2l_pack_f16mix<<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc);
+            k_m2l_pack_f16mix<<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, st->mix_layout, h->periodic, h->M, st->Mtc);
         else if (bf16)
             k_m2l_pack<true><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
         else
@@ -879,7 +926,7 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream, int lo, int hi, int parts) {
             case kF16mix:
                 k_m2l_tc<kF16mix, R><<<nt, kTcThreads, st->smem, stream>>>(
                     tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages,
-                    h->status, st->last_half, wlim);
+                    h->status, st->mix_layout, wlim);
                 break;
             default:
                 k_m2l_tc<kTf32, R><<<nt, kTcThreads, st->smem, stream>>>(

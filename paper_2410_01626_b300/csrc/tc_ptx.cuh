@@ -258,6 +258,35 @@ __device__ __forceinline__ void mma_f16_w(uint32_t d_tmem, uint64_t a, uint64_t 
     }
 }
 
+// N (3 or 4) kind::f16 products (a0, b0) .. (a{N-1}, b{N-1}) into D by one elected lane, then a
+// commit to `bar`; the first accumulates when `accumulate` is nonzero, the others always.
+template <int N>
+__device__ __forceinline__ void mma_f16_n_w(uint32_t d_tmem, uint64_t a0, uint64_t b0, uint64_t a1, uint64_t b1,
+                                            uint64_t a2, uint64_t b2, uint64_t a3, uint64_t b3, uint32_t idesc,
+                                            uint32_t accumulate, uint64_t* bar) {
+    static_assert(N == 3 || N == 4, "3 or 4 products");
+    if (N == 3)
+        asm volatile(
+            "{\n .reg .pred p, e;\n setp.ne.b32 p, %8, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %7, p;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %7, 1;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %7, 1;\n"
+            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%9];\n}" ::"r"(d_tmem),
+            "l"(a0), "l"(b0), "l"(a1), "l"(b1), "l"(a2), "l"(b2), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p, e;\n setp.ne.b32 p, %10, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %9, p;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %9, 1;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %9, 1;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %9, 1;\n"
+            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%11];\n}" ::"r"(d_tmem),
+            "l"(a0), "l"(b0), "l"(a1), "l"(b1), "l"(a2), "l"(b2), "l"(a3), "l"(b3), "r"(idesc), "r"(accumulate),
+            "r"(smem_u32(bar))
+            : "memory");
+}
+
 // One TF32 MMA by one elected lane, optionally followed by a commit to `bar`.
 template <bool COMMIT>
 __device__ __forceinline__ void mma1_tf32_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate,
