@@ -470,10 +470,10 @@ def run_native(args):
                 "peak_source": src, "peak_sustained": bf16_sus * ratio,
                 "frac_of_sustained": achieved / (bf16_sus * ratio)}
         # what the tensor pipe executes: 128 output rows x the K it multiplies -- ncp (padded
-        # coefficients) once, three times in the split forms, and in the FP16 form the first
-        # 16 coefficients three times and the rest once
+        # coefficients) once, three times in the split forms, and in the FP16 form once plus
+        # one K step of 16 for the cross terms of the lowest coefficients
         ncp = 16 * ((nc + 15) // 16)
-        keff = {"tf32": ncp, "3xtf32": 3 * ncp, "3xbf16": 3 * ncp, "fp16": ncp + 32}[precision]
+        keff = {"tf32": ncp, "3xtf32": 3 * ncp, "3xbf16": 3 * ncp, "fp16": ncp + 16}[precision]
         executed = boxes * 189 * 2.0 * 128 * keff
         roof["pipe_flop_per_launch"] = executed
         roof["pipe_frac"] = executed / (m2l_ms * 1e-3) / 1e12 / peak

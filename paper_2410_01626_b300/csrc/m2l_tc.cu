@@ -49,17 +49,18 @@ constexpr long long kWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
 // the split 3xTF32 form (hi and lo parts), 16 for the split 3xBF16 form; there a ring stage
 // is 8 KB (one operator chunk, all parts) and a slab buffer 64 bytes per row (about 43 KB at
 // depth 5), so two slab buffers leave room for a 16-stage ring.
-// The FP16 form (kF16mix) has wider chunks of 6 cells (three K steps, 12 KB stages) of three
-// kinds: chunk 0 holds the input coefficients 0..15 (degrees 0..3) as hi cells 0-1 and lo
-// cells 2-3 (three products, hi hi + hi lo + lo hi, about 22 bits) and, when the plain K
-// steps leave one over, the last 16 coefficients as hi cells 4-5 (one product); every later
-// chunk holds 48 coefficients (three K steps of one product, 11 bits), or 32 in a last chunk
-// of two steps.  The low degrees carry the large monopole and dipole parts of the far field,
-// whose rounding the potential and dV/dlambda feel most; a single product for every degree
-// gives TF32-like errors (4e-4 in dV/dlambda at 500k atoms), the split of degrees 0..3 alone
-// the errors of the full split (5e-6).  Each ring stage costs the issuer one wait and one
-// commit, so wide chunks (3-4 MMAs each) keep the tensor pipe ahead of that per-stage work,
-// and at p = 10 an (operator, shift) takes 3 stages instead of 5.
+// The FP16 form (kF16mix) works in K steps of 16 coefficients, one product each (11 bits):
+// step 0 holds the cross terms of the 8 lowest input coefficients (degrees 0 and 1 and four of
+// degree 2) -- A = lo(T) then hi(T), B = hi(M) then lo(M), so that one MMA adds
+// lo(T) hi(M) + hi(T) lo(M) -- and steps 1.. the hi parts of all coefficients, 16 per step.
+// With the hi hi products of step 1 the lowest coefficients are then carried to about 22 bits.
+// The low degrees carry the large monopole and dipole parts of the far field, whose rounding
+// the potential and dV/dlambda feel most; a single product for every degree gives TF32-like
+// errors (4e-4 in dV/dlambda at 500k atoms), the cross terms of degrees 0 and 1 alone the
+// errors of the full three-product split (5e-6).  The steps are grouped three to a chunk (6
+// cells, 12 KB stages; the last chunk may hold fewer), so at p = 10 an (operator, shift) is
+// 9 MMAs in 3 ring stages: each stage costs the issuer one wait and one commit, and three
+// MMAs per stage keep the tensor pipe ahead of that per-stage work.
 enum TcMode { kTf32 = 0, kTf32x3 = 1, kBf16x3 = 2, kF16mix = 3 };
 template <int MODE>
 struct TcCfg {
@@ -76,25 +77,20 @@ struct TcCfg {
     static constexpr uint32_t kPartBytes = 128u * kChunk * kElem;  // one operator part (hi or lo)
     static constexpr uint32_t kStageBytes = kParts * kPartBytes;   // 8 KB (12 KB in the FP16 form)
 };
-// FP16 form.  The ncp - 16 coefficients above the split ones are m = (ncp - 16) / 16 plain K
-// steps: m / 3 chunks of three steps, and the remainder either as the tail of chunk 0 (one
-// step, layout bit 0) or as a last chunk of two steps (layout bit 1).
-inline int f16mix_layout(int ncp) {
-    const int m = (ncp - 16) / 16;
-    return m % 3 == 1 ? 1 : m % 3 == 2 ? 2 : 0;
+// FP16 form: ncp / 16 + 1 K steps (the cross step and the hi steps), three to a chunk.
+inline int f16mix_steps(int ncp) { return ncp / 16 + 1; }
+inline int f16mix_chunks(int ncp) { return (f16mix_steps(ncp) + 2) / 3; }
+inline int f16mix_last_steps(int ncp) { return f16mix_steps(ncp) - 3 * (f16mix_chunks(ncp) - 1); }  // 1, 2 or 3
+// First input coefficient of cell j (0..5) of chunk ch: K step s = 3 ch + j / 2, half j % 2;
+// at or beyond ncp (steps past the last) the cell holds zeros.
+__host__ __device__ inline int f16mix_base(int ch, int j) {
+    const int s = 3 * ch + j / 2;
+    return s == 0 ? 0 : 16 * (s - 1) + 8 * (j & 1);
 }
-inline int f16mix_chunks(int ncp) {
-    const int m = (ncp - 16) / 16;
-    return 1 + m / 3 + (m % 3 == 2 ? 1 : 0);
-}
-// First input coefficient of cell j (0..5) of chunk ch; ncp (no coefficient) for the tail
-// cells of a chunk 0 without a tail.  Cells at or beyond ncp hold zeros.
-__host__ __device__ inline int f16mix_base(int ch, int j, int ncp, int layout) {
-    if (ch == 0) return j < 4 ? 8 * (j & 1) : (layout & 1) ? ncp - 16 + 8 * (j - 4) : ncp;
-    return 16 + 48 * (ch - 1) + 8 * j;
-}
-// whether cell j of chunk ch holds the lo part (the FP16 rounding of the remainder)
-__host__ __device__ inline bool f16mix_lo(int ch, int j) { return ch == 0 && (j == 2 || j == 3); }
+// which cells hold lo parts (the FP16 rounding of the remainder): in the cross step, the
+// first half of the operator (A) and the second half of the multipoles (B)
+__host__ __device__ inline bool f16mix_lo_T(int ch, int j) { return ch == 0 && j == 0; }
+__host__ __device__ inline bool f16mix_lo_M(int ch, int j) { return ch == 0 && j == 1; }
 
 struct TcLevels {
     int n[kMaxDepth + 1];
@@ -197,7 +193,7 @@ __global__ void k_m2l_pack(PackLevels pl, int NKG, int ncp, int periodic, const 
 __device__ __forceinline__ uint32_t f16_pair(float a, float b) {  // a in the low half (first in memory)
     return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
 }
-__global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int layout, int periodic, const float* __restrict__ M,
+__global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int periodic, const float* __restrict__ M,
                                   float* __restrict__ Mtc_all) {
     const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gt >= pl.first[pl.nlev]) return;
@@ -212,7 +208,7 @@ __global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int layout, i
     const int m2 = n + 2;
     int i = row / (m2 * m2) - 1, j = (row / m2) % m2 - 1, k = row % m2 - 1;
     const int ch = gc / 6, cell = gc % 6;
-    const int base = f16mix_base(ch, cell, ncp, layout);
+    const int base = f16mix_base(ch, cell);
     bool ok = base < ncp;  // ncp is a multiple of 16: the cell's 8 coefficients all exist
     if (periodic) {
         i = (i + n) % n;
@@ -227,7 +223,7 @@ __global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int layout, i
         const float4 x0 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + base);
         const float4 x1 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + base + 4);
         float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        if (f16mix_lo(ch, cell))
+        if (f16mix_lo_M(ch, cell))
 #pragma unroll
             for (int e = 0; e < 8; ++e) xs[e] -= __half2float(__float2half_rn(xs[e]));
         out = make_uint4(f16_pair(xs[0], xs[1]), f16_pair(xs[2], xs[3]), f16_pair(xs[4], xs[5]), f16_pair(xs[6], xs[7]));
@@ -236,7 +232,7 @@ __global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int layout, i
 }
 
 struct TcTile {
-    int level, cls, r0, pad;
+    int level, cls, r0, rows;  // rows: the tile's virtual rows (MMA N), a multiple of 16
 };
 
 // Warp roles (10 warps): warp 0 = bulk-copy producer, warp 1 = MMA issuer (one elected lane
@@ -253,7 +249,7 @@ template <int MODE, int ROWS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const TcTile* __restrict__ tiles, TcLevels lv, const float* __restrict__ Mtc,
              const float* __restrict__ Mtc_lo, const float* __restrict__ Ttc, float* __restrict__ L, int ncp,
-             int NKC, int slab_rows, int nstages, int* __restrict__ status, int mix_layout, long long wlim) {
+             int NKC, int slab_rows, int nstages, int* __restrict__ status, int last_steps, long long wlim) {
     using Cfg = TcCfg<MODE>;
     constexpr bool SPLIT = Cfg::kSplit;
     constexpr int kTcKG = Cfg::kKG;
@@ -283,6 +279,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     const TcTile tile = tiles[blockIdx.x];
     const int lev = tile.level, c = tile.cls, r0 = tile.r0;
+    const int nr = tile.rows;  // this tile's virtual rows (the MMA N): a multiple of 16, at most ROWS
+    const int nh = nr >> 1;    // columns per drain half (a multiple of 8)
     const int n = lv.n[lev], R = lv.R[lev];
     const int m2 = n + 2;
     const int NKG = NKC * kTcKG;
@@ -318,7 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int rs[3], rl[3];
     for (int q = 0; q < 3; ++q) {
         rs[q] = r0 + (q - 1) * m2 * m2 - hal;          // >= 0: r0 >= S = m2^2 + hal
-        rl[q] = min(ROWS + 2 * hal, R - rs[q]);     // > 0:  r0 < R - S
+        rl[q] = min(nr + 2 * hal, R - rs[q]);       // > 0:  r0 < R - S
     }
     const float* Mlev = Mtc + lv.mtc_off[lev];
     const float* Mlev_lo = SPLIT ? Mtc_lo + lv.mtc_off[lev] : nullptr;
@@ -348,7 +346,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lane < 3 * kTcKG) {  // one (cell, delta_x range) per lane
                 const int kg = lane / 3, q = lane % 3;
                 const int rsq = r0 + (q - 1) * m2 * m2 - hal;
-                const int rlq = min(ROWS + 2 * hal, R - rsq);
+                const int rlq = min(nr + 2 * hal, R - rsq);
                 const long e = (((long)pi * NKG + ch * kTcKG + kg) * R + rsq) * 4;
                 uint8_t* dq = dst + (size_t)kg * kg_stride + (size_t)q * slab_rows * 16;
                 tc::bulk_g2s(dq, Mlev + e, (uint32_t)rlq * 16u, slab_full + buf);
@@ -446,8 +444,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // Lean loop: the 27 shifts are unrolled (constant delta), the ring position is a
             // running counter, and the abort flag is only consulted when a wait expires.  Every
             // lane runs the loop so that descriptors and counters stay warp-uniform.
-            const uint32_t idesc = Cfg::kMix ? tc::idesc_f16(128, ROWS)
-                                   : Cfg::kBf16 ? tc::idesc_bf16(128, ROWS) : tc::idesc_tf32(128, ROWS);
+            const uint32_t idesc = Cfg::kMix ? tc::idesc_f16(128, nr)
+                                   : Cfg::kBf16 ? tc::idesc_bf16(128, nr) : tc::idesc_tf32(128, nr);
             // descriptors are built once and advanced by adding (byte offset >> 4) to the address field
             const uint64_t a_base = tc::smem_desc_kmajor(tc::smem_u32(tring), 2048u, 128u);
             const uint64_t b_base = tc::smem_desc_kmajor(tc::smem_u32(slab0), kg_stride, 128u);
@@ -456,14 +454,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bool ok = true;
             int t_taken = 0, slabs_taken = 0;
             int* shift_tab = const_cast<int*>(copy_count) + 36;  // [27], after the producer's rank table
+            int nshift = 0;
             for (int g = 0; g < ngroups && ok; ++g) {
                 const int pi = g / NKC, buf = g & 1;
-                // FP16 form: the products of this group's chunk -- 0: split (three products),
-                // 3: split and the tail K step, 1: three K steps of one product, 2: two K steps
+                // FP16 form: the K steps (one product each) of this group's chunk, 3 but in the last
                 const int ch = g % NKC;
-                const int mix_kind = !Cfg::kMix ? 0
-                                     : ch == 0  ? ((mix_layout & 1) ? 3 : 0)
-                                                : (ch == NKC - 1 && (mix_layout & 2)) ? 2 : 1;
+                const int mix_kind = !Cfg::kMix ? 0 : ch == NKC - 1 ? last_steps : 3;
                 const int qx = (pi & 1) - cx, qy = ((pi >> 1) & 1) - cy, qz = ((pi >> 2) & 1) - cz;
                 const int ab = g & 1;
                 const uint32_t dacc = tmem + (uint32_t)(ab * kTcAccStride);
@@ -480,9 +476,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const uint64_t b_buf = b_base + (((uint64_t)buf * slab_bytes) >> 4) + (uint64_t)hal;
                 uint32_t acc = 0;
                 // the slab row offsets of this (target class, source class)'s valid shifts, in
-                // ascending shift order (the order of the producer's copies)
-                int nshift = 0;
-                {
+                // ascending shift order (the order of the producer's copies): built at the first
+                // chunk of each source class
+                if (ch == 0) {
                     bool valid = false;
                     int off = 0;
                     if (lane < 27) {
@@ -502,30 +498,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // per group).
                 auto shifts = [&](auto kind_tag) {
                     constexpr int kKind = decltype(kind_tag)::value;
+                    // FP16 form: whether the chunk's stage was seen complete by the probe that
+                    // issued with the previous chunk's MMAs (then no wait is needed)
+                    bool ready = false;
 #pragma unroll 1
                     for (int i = 0; i < nshift; ++i) {
                         const uint64_t bd0 = b_buf + (uint64_t)shift_tab[i];
-                        if (!tc::mbar_wait_all_abort(t_full + stage, tphase, wlim, abort_flag)) return false;
+                        if (!ready && !tc::mbar_wait_all_abort(t_full + stage, tphase, wlim, abort_flag)) return false;
                         ++t_taken;
                         const uint64_t ad0 = a_base + (uint64_t)stage * (kTcTBytes >> 4);
+                        int nstage = stage + 1;
+                        uint32_t nphase = tphase;
+                        if (nstage == nstages) {
+                            nstage = 0;
+                            nphase ^= 1u;
+                        }
                         // the MMAs of this chunk, then the commit that releases its ring stage; one
                         // elected lane issues each K step's products (hi(T) hi(M) + hi(T) lo(M) +
                         // lo(T) hi(M) in the split forms)
                         if (Cfg::kMix) {
                             // A: cells of 2048 bytes (128 rows), a K step = two cells = 4096 bytes;
-                            // B: cells kg_stride apart.  Chunk 0: hi in K-step slot 0, lo in slot 1,
-                            // the tail in slot 2.
+                            // B: cells kg_stride apart
                             const uint64_t ad1 = ad0 + (4096u >> 4), bd1 = bd0 + ((2u * kg_stride) >> 4);
                             const uint64_t ad2 = ad0 + (8192u >> 4), bd2 = bd0 + ((4u * kg_stride) >> 4);
-                            if (kKind == 0)
-                                tc::mma_f16_n_w<3>(dacc, ad0, bd0, ad0, bd1, ad1, bd0, 0, 0, idesc, acc, t_empty + stage);
-                            else if (kKind == 3)
-                                tc::mma_f16_n_w<4>(dacc, ad0, bd0, ad0, bd1, ad1, bd0, ad2, bd2, idesc, acc, t_empty + stage);
-                            else if (kKind == 1)
-                                tc::mma_f16_n_w<3>(dacc, ad0, bd0, ad1, bd1, ad2, bd2, 0, 0, idesc, acc, t_empty + stage);
-                            else
-                                tc::mma_f16_w<true, true>(dacc, ad0, bd0, ad1, bd1, idesc, acc, t_empty + stage);
+                            const uint32_t probe = tc::mma_f16_n_probe_w<kKind>(dacc, ad0, bd0, ad1, bd1, ad2, bd2, idesc,
+                                                                               acc, t_empty + stage, t_full + nstage, nphase);
                             acc = 1;
+                            ready = __all_sync(0xffffffffu, probe != 0u);
                         } else
 #pragma unroll
                         for (int ks = 0; ks < Cfg::kKSteps; ++ks) {  // 32 bytes of K = two cells per MMA
@@ -547,17 +546,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             }
                             acc = 1;
                         }
-                        if (++stage == nstages) {
-                            stage = 0;
-                            tphase ^= 1u;
-                        }
+                        stage = nstage;
+                        tphase = nphase;
                     }
                     return true;
                 };
-                if (!Cfg::kMix || mix_kind == 0) ok = shifts(std::integral_constant<int, 0>{});
-                else if (mix_kind == 1) ok = shifts(std::integral_constant<int, 1>{});
+                if (!Cfg::kMix || mix_kind == 3) ok = shifts(std::integral_constant<int, 3>{});
                 else if (mix_kind == 2) ok = shifts(std::integral_constant<int, 2>{});
-                else ok = shifts(std::integral_constant<int, 3>{});
+                else ok = shifts(std::integral_constant<int, 1>{});
                 if (!ok) break;
                 tc::mma_commit_w(acc_full + ab);  // this group's partial sum is complete, its slab free
             }
@@ -596,27 +592,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc::fence_after_sync();
-            const uint32_t base = tmem + lane_base + (uint32_t)(ab * kTcAccStride + half * (ROWS / 2));
+            const uint32_t base = tmem + lane_base + (uint32_t)(ab * kTcAccStride + half * nh);
 #pragma unroll
-            for (int cb = 0; cb < ROWS / 2; cb += 16) {
-                float v[16];
-                tc::tmem_ld16(base + cb, v);
+            for (int cb = 0; cb < ROWS / 2; cb += 16) {  // nh is warp-uniform: the loads stay aligned
+                if (cb + 16 <= nh) {
+                    float v[16];
+                    tc::tmem_ld16(base + cb, v);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) sum[cb + e] += v[e];
+                    for (int e = 0; e < 16; ++e) sum[cb + e] += v[e];
+                } else if (cb + 8 <= nh) {
+                    float v[8];
+                    tc::tmem_ld8(base + cb, v);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) sum[cb + e] += v[e];
+                }
             }
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(acc_empty + ab);
         }
         if (ok && !*abort_flag) {
-            // The 96 rows of this half go to their Morton boxes: first a table of the rows' box
+            // The nh rows of this half go to their Morton boxes: first a table of the rows' box
             // offsets in shared memory (the operator ring is idle: every MMA has completed), three
             // rows per lane, then one store per row.  A fully unrolled loop doing the index
             // arithmetic per row is long straight-line code that runs once per tile, mostly
             // waiting for instruction fetch.
             int* tab = reinterpret_cast<int*>(tring) + (warp - 2) * (ROWS / 2);
-            const int rfirst = r0 + half * (ROWS / 2);
-            for (int e = lane; e < ROWS / 2; e += 32) {
+            const int rfirst = r0 + half * nh;
+            for (int e = lane; e < nh; e += 32) {
                 const int r = rfirst + e;
                 const int ip = r / (m2 * m2), jp = (r / m2) % m2, kp = r % m2;
                 int off = -1;
@@ -631,7 +634,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (j < ncp) {
 #pragma unroll
                 for (int e = 0; e < ROWS / 2; ++e) {
-                    const int off = tab[e];
+                    const int off = e < nh ? tab[e] : -1;
                     if (off >= 0) Ll[off] = sum[e];
                 }
             }
@@ -662,12 +665,13 @@ template <class F>
 void for_tile_rows(F&& f) {
     f(std::integral_constant<int, 128>{});
     f(std::integral_constant<int, 160>{});
+    f(std::integral_constant<int, 176>{});
     f(std::integral_constant<int, 192>{});
     f(std::integral_constant<int, 224>{});
     f(std::integral_constant<int, 256>{});
 }
 bool m2l_tile_rows_ok(int rows) {
-    return rows == 0 || rows == 128 || rows == 160 || rows == 192 || rows == 224 || rows == 256;
+    return rows == 0 || rows == 128 || rows == 160 || rows == 176 || rows == 192 || rows == 224 || rows == 256;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -680,10 +684,10 @@ struct TcState {
     int ntiles = 0;
     int tile_first[kMaxDepth + 2] = {};  // the tiles of level l are [tile_first[l], tile_first[l + 1])
     int NKC = 0;
-    int mix_layout = 0;  // FP16 form: bit 0 = chunk 0 carries a tail K step, bit 1 = the last chunk has two
+    int last_steps = 3;  // FP16 form: K steps in the last chunk (1..3)
     int KG = 0;  // 16-byte cells per K chunk
     int slab_rows = 0;
-    int rows = kTcRows;  // virtual rows (MMA N) per CTA: 128, 160, 192, 224 or 256
+    int rows = kTcRows;  // widest tile (MMA N) per CTA: 128, 160, 176, 192, 224 or 256
     int nstages = 0;  // operator ring depth
     size_t smem = 0;
     TcLevels lv{};
@@ -747,20 +751,19 @@ void pack_operators(const std::vector<float>& Trm, int nc, int NKC, std::vector<
             }
 }
 // FP16 form: [op][chunk][cell j (6)][128 rows][16 bytes], cell j of chunk ch holding the
-// coefficients f16mix_base(ch, j) .. + 7 (hi part, or for the lo cells of chunk 0 the FP16
-// rounding of the remainder), zero at or beyond nc.
-void pack_operators_f16mix(const std::vector<float>& Trm, int nc, int ncp, int NKC, std::vector<uint8_t>& out) {
-    const int layout = f16mix_layout(ncp);
+// coefficients f16mix_base(ch, j) .. + 7 (hi part, or for the lo cell of the cross step the
+// FP16 rounding of the remainder), zero at or beyond nc.
+void pack_operators_f16mix(const std::vector<float>& Trm, int nc, int NKC, std::vector<uint8_t>& out) {
     out.assign((size_t)kNumOps * NKC * TcCfg<kF16mix>::kStageBytes, 0);
     for (int op = 0; op < kNumOps; ++op)
         for (int ch = 0; ch < NKC; ++ch)
             for (int j = 0; j < 6; ++j) {
-                const int base = f16mix_base(ch, j, ncp, layout);
+                const int base = f16mix_base(ch, j);
                 for (int jj = 0; jj < nc; ++jj)
                     for (int e = 0; e < 8 && base + e < nc; ++e) {
                         const float v = Trm[((size_t)op * nc + jj) * nc + base + e];
                         const __half hi = __float2half_rn(v);
-                        const __half w = f16mix_lo(ch, j) ? __float2half_rn(v - __half2float(hi)) : hi;
+                        const __half w = f16mix_lo_T(ch, j) ? __float2half_rn(v - __half2float(hi)) : hi;
                         const size_t cell = (((size_t)op * NKC + ch) * 6 + j) * 128 + jj;
                         std::memcpy(out.data() + cell * 16 + (size_t)e * 2, &w, 2);
                     }
@@ -797,8 +800,8 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
             st->KG = TcCfg<kF16mix>::kKG, nparts = 1;
             stage_bytes = TcCfg<kF16mix>::kStageBytes;
             st->NKC = f16mix_chunks(ncp);
-            st->mix_layout = f16mix_layout(ncp);
-            pack_operators_f16mix(T_rowmajor, nc, ncp, st->NKC, T);
+            st->last_steps = f16mix_last_steps(ncp);
+            pack_operators_f16mix(T_rowmajor, nc, st->NKC, T);
             break;
         default:
             chunk = TcCfg<kTf32>::kChunk, st->KG = TcCfg<kTf32>::kKG, nparts = 1;
@@ -827,8 +830,13 @@ int m2l_tc_setup(Handle* h, const std::vector<float>& T_rowmajor /*[343][nc][nc]
         st->lv.mtc_off[l] = off;
         st->lv.l_off[l] = h->lvl_off[l];
         off += 8L * NKG * R * 4;  // 16-byte cells, counted in floats
+        // target rows S .. R - S - 1 in k tiles of equal width (a multiple of 16, at most the
+        // launch's width): at the coarse levels a tile is only as wide as its level needs
+        const int range = R - 2 * S;
+        const int k = (range + st->rows - 1) / st->rows;
+        const int w = std::min(st->rows, 16 * (((range + k - 1) / k + 15) / 16));
         for (int c = 0; c < 8; ++c)
-            for (int r0 = S; r0 < R - S; r0 += st->rows) tiles.push_back({l, c, r0, 0});
+            for (int r0 = S; r0 < R - S; r0 += w) tiles.push_back({l, c, r0, w});
     }
     for (int l = d + 1; l <= kMaxDepth + 1; ++l) st->tile_first[l] = (int)tiles.size();
     st->slab_rows = st->rows + 2 * ((1 << (d - 1)) + 3);  // one delta_x range at the deepest level
@@ -899,7 +907,7 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream, int lo, int hi, int parts) {
     if (tot > 0 && (parts & kM2lPack)) {
         const unsigned grid = (unsigned)((tot + 255) / 256);
         if (st->mode == kF16mix)
-            k_m2l_pack_f16mix<<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, st->mix_layout, h->periodic, h->M, st->Mtc);
+            k_m2l_pack_f16mix<<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc);
         else if (bf16)
             k_m2l_pack<true><<<grid, 256, 0, stream>>>(pl, NKG, h->ncp, h->periodic, h->M, st->Mtc, st->Mtc_lo);
         else
@@ -926,7 +934,7 @@ void launch_m2l_tc(Handle* h, cudaStream_t stream, int lo, int hi, int parts) {
             case kF16mix:
                 k_m2l_tc<kF16mix, R><<<nt, kTcThreads, st->smem, stream>>>(
                     tiles, st->lv, st->Mtc, nullptr, st->Ttc, h->L, h->ncp, st->NKC, st->slab_rows, st->nstages,
-                    h->status, st->mix_layout, wlim);
+                    h->status, st->last_steps, wlim);
                 break;
             default:
                 k_m2l_tc<kTf32, R><<<nt, kTcThreads, st->smem, stream>>>(

@@ -219,72 +219,54 @@ __device__ __forceinline__ void mma3_w(uint32_t d_tmem, uint64_t a, uint64_t b, 
                 : "memory");
     }
 }
-// The products of one 32-byte K step pair of a kind::f16 chunk by one elected lane: with TWO,
-// (a, b) + (a2, b2) (two consecutive K steps), else (a, b) alone; optionally followed by a
-// commit to `bar`.  The operand type (FP16 or BF16) comes from the instruction descriptor.
-template <bool TWO, bool COMMIT>
-__device__ __forceinline__ void mma_f16_w(uint32_t d_tmem, uint64_t a, uint64_t b, uint64_t a2, uint64_t b2,
-                                          uint32_t idesc, uint32_t accumulate, uint64_t* bar) {
-    if (TWO) {
-        if (COMMIT)
-            asm volatile(
-                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
-                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %5, p;\n"
-                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %5, 1;\n"
-                " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%7];\n}" ::"r"(d_tmem),
-                "l"(a), "l"(b), "l"(a2), "l"(b2), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
-                : "memory");
-        else
-            asm volatile(
-                "{\n .reg .pred p, e;\n setp.ne.b32 p, %6, 0;\n elect.sync _|e, 0xffffffff;\n"
-                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %5, p;\n"
-                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %5, 1;\n}" ::"r"(d_tmem),
-                "l"(a), "l"(b), "l"(a2), "l"(b2), "r"(idesc), "r"(accumulate)
-                : "memory");
-    } else {
-        if (COMMIT)
-            asm volatile(
-                "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
-                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-                " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%5];\n}" ::"r"(d_tmem),
-                "l"(a), "l"(b), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
-                : "memory");
-        else
-            asm volatile(
-                "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
-                " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-                "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-                : "memory");
-    }
-}
-
-// N (3 or 4) kind::f16 products (a0, b0) .. (a{N-1}, b{N-1}) into D by one elected lane, then a
-// commit to `bar`; the first accumulates when `accumulate` is nonzero, the others always.
+// N (1 to 3) kind::f16 products (a0, b0) .. into D by one elected lane, then a commit to
+// `bar`, in one instruction group with a non-blocking test of the phase `parity` of `probe_bar`
+// (returned, 1 = complete): the test's latency passes while the MMAs issue, instead of before
+// the next wait.  The first product accumulates when `accumulate` is nonzero, the others always.
 template <int N>
-__device__ __forceinline__ void mma_f16_n_w(uint32_t d_tmem, uint64_t a0, uint64_t b0, uint64_t a1, uint64_t b1,
-                                            uint64_t a2, uint64_t b2, uint64_t a3, uint64_t b3, uint32_t idesc,
-                                            uint32_t accumulate, uint64_t* bar) {
-    static_assert(N == 3 || N == 4, "3 or 4 products");
-    if (N == 3)
+__device__ __forceinline__ uint32_t mma_f16_n_probe_w(uint32_t d_tmem, uint64_t a0, uint64_t b0, uint64_t a1,
+                                                      uint64_t b1, uint64_t a2, uint64_t b2, uint32_t idesc,
+                                                      uint32_t accumulate, uint64_t* bar, uint64_t* probe_bar,
+                                                      uint32_t parity) {
+    static_assert(N >= 1 && N <= 3, "1 to 3 products");
+    uint32_t ready;
+    if (N == 1)
         asm volatile(
-            "{\n .reg .pred p, e;\n setp.ne.b32 p, %8, 0;\n elect.sync _|e, 0xffffffff;\n"
-            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %7, p;\n"
-            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %7, 1;\n"
-            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %7, 1;\n"
-            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%9];\n}" ::"r"(d_tmem),
-            "l"(a0), "l"(b0), "l"(a1), "l"(b1), "l"(a2), "l"(b2), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar))
+            "{\n .reg .pred p, e, q;\n mbarrier.test_wait.parity.shared::cta.b64 q, [%6], %7;\n"
+            " setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %3, %8, p;\n"
+            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%5];\n"
+            " selp.u32 %0, 1, 0, q;\n}"
+            : "=r"(ready)
+            : "r"(d_tmem), "l"(a0), "l"(b0), "r"(accumulate), "r"(smem_u32(bar)), "r"(smem_u32(probe_bar)),
+              "r"(parity), "r"(idesc)
+            : "memory");
+    else if (N == 2)
+        asm volatile(
+            "{\n .reg .pred p, e, q;\n mbarrier.test_wait.parity.shared::cta.b64 q, [%9], %10;\n"
+            " setp.ne.b32 p, %7, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %3, %6, p;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %5, %6, 1;\n"
+            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%8];\n"
+            " selp.u32 %0, 1, 0, q;\n}"
+            : "=r"(ready)
+            : "r"(d_tmem), "l"(a0), "l"(b0), "l"(a1), "l"(b1), "r"(idesc), "r"(accumulate), "r"(smem_u32(bar)),
+              "r"(smem_u32(probe_bar)), "r"(parity)
             : "memory");
     else
         asm volatile(
-            "{\n .reg .pred p, e;\n setp.ne.b32 p, %10, 0;\n elect.sync _|e, 0xffffffff;\n"
-            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %9, p;\n"
-            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %4, %9, 1;\n"
-            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %9, 1;\n"
-            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %9, 1;\n"
-            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%11];\n}" ::"r"(d_tmem),
-            "l"(a0), "l"(b0), "l"(a1), "l"(b1), "l"(a2), "l"(b2), "l"(a3), "l"(b3), "r"(idesc), "r"(accumulate),
-            "r"(smem_u32(bar))
+            "{\n .reg .pred p, e, q;\n mbarrier.test_wait.parity.shared::cta.b64 q, [%11], %12;\n"
+            " setp.ne.b32 p, %9, 0;\n elect.sync _|e, 0xffffffff;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %3, %8, p;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%1], %4, %5, %8, 1;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%1], %6, %7, %8, 1;\n"
+            " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%10];\n"
+            " selp.u32 %0, 1, 0, q;\n}"
+            : "=r"(ready)
+            : "r"(d_tmem), "l"(a0), "l"(b0), "l"(a1), "l"(b1), "l"(a2), "l"(b2), "r"(idesc), "r"(accumulate),
+              "r"(smem_u32(bar)), "r"(smem_u32(probe_bar)), "r"(parity)
             : "memory");
+    return ready;
 }
 
 // One TF32 MMA by one elected lane, optionally followed by a commit to `bar`.
@@ -308,6 +290,16 @@ __device__ __forceinline__ void mma1_tf32_w(uint32_t d_tmem, uint64_t a, uint64_
 
 // 32 lanes x 32 bits, 16 consecutive columns per thread: thread t of warp w reads
 // TMEM lane (32 w + t), columns [col, col + 16).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
