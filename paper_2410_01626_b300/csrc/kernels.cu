@@ -846,6 +846,38 @@ void f32_bricks(int lmin, int depth, std::vector<F32Brick>& out) {
     }
 }
 
+// ---- packed two-wide FP32 arithmetic (f32x2) ----
+__device__ __forceinline__ unsigned long long f2pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2unpack(unsigned long long v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__ bricks, int ncp,
                                                     const float* __restrict__ T, const float* __restrict__ M,
                                                     float* __restrict__ part, long part_stride, LevelOffsets lo,
@@ -868,11 +900,14 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
     // the thread's 8 boxes are the pencil (i, j) = (tb / 4, tb % 4), k = 0..7: halo entries
     // hb0 + e at delta = (-1, -1, -1)
     const int hb0 = ((tb >> 2) * hy + (tb & 3)) * hz;
-    float acc[8][8];
+    // accumulators in coefficient pairs (2 a, 2 a + 1) x 8 boxes, updated with f32x2 FMAs: half
+    // the FMA instructions of scalar code for the same FMA-pipe work; every element is still one
+    // FP32 FMA per term, in the same order
+    unsigned long long acc2[4][8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) acc[a][e] = 0.f;
+        for (int e = 0; e < 8; ++e) acc2[a][e] = 0ull;
     const int nkc = ncp / kF32KC;
     const int pi = blockIdx.y;
     {
@@ -943,20 +978,19 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
                     for (int k = 0; k < kF32KC; ++k) {
                         const float4 a0 = *reinterpret_cast<const float4*>(&ts[cur][k][8 * tc]);
                         const float4 a1 = *reinterpret_cast<const float4*>(&ts[cur][k][8 * tc + 4]);
+                        const unsigned long long A0 = f2pack(a0.x, a0.y), A1 = f2pack(a0.z, a0.w),
+                                                 A2 = f2pack(a1.x, a1.y), A3 = f2pack(a1.z, a1.w);
                         float bv[8];
                         const float* hrow = &hs[k][hb0 + so];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) bv[e] = hrow[e];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
-                            acc[0][e] = fmaf(a0.x, bv[e], acc[0][e]);
-                            acc[1][e] = fmaf(a0.y, bv[e], acc[1][e]);
-                            acc[2][e] = fmaf(a0.z, bv[e], acc[2][e]);
-                            acc[3][e] = fmaf(a0.w, bv[e], acc[3][e]);
-                            acc[4][e] = fmaf(a1.x, bv[e], acc[4][e]);
-                            acc[5][e] = fmaf(a1.y, bv[e], acc[5][e]);
-                            acc[6][e] = fmaf(a1.z, bv[e], acc[6][e]);
-                            acc[7][e] = fmaf(a1.w, bv[e], acc[7][e]);
+                            const unsigned long long B = f2pack(bv[e], bv[e]);
+                            acc2[0][e] = f2fma(A0, B, acc2[0][e]);
+                            acc2[1][e] = f2fma(A1, B, acc2[1][e]);
+                            acc2[2][e] = f2fma(A2, B, acc2[2][e]);
+                            acc2[3][e] = f2fma(A3, B, acc2[3][e]);
                         }
                     }
                 }
@@ -976,8 +1010,10 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
         if (ti >= n || tj >= n || tk >= n) continue;  // padding of a coarse level's brick
         const uint32_t box = morton3(2 * ti + cx, 2 * tj + cy, 2 * tk + cz);
         float4* dst = reinterpret_cast<float4*>(Ll + (long)box * ncp + 8 * tc);
-        dst[0] = make_float4(acc[0][e], acc[1][e], acc[2][e], acc[3][e]);
-        dst[1] = make_float4(acc[4][e], acc[5][e], acc[6][e], acc[7][e]);
+        const float2 c0 = f2unpack(acc2[0][e]), c1 = f2unpack(acc2[1][e]), c2 = f2unpack(acc2[2][e]),
+                     c3 = f2unpack(acc2[3][e]);
+        dst[0] = make_float4(c0.x, c0.y, c1.x, c1.y);
+        dst[1] = make_float4(c2.x, c2.y, c3.x, c3.y);
     }
 }
 
@@ -1297,38 +1333,6 @@ __global__ void __launch_bounds__(128) k_hi(HiParams p) {
 template <int P>
 static void launch_hi(const HiParams& hp, cudaStream_t st) {
     k_hi<P><<<(hp.K + 3) / 4, 128, 0, st>>>(hp);
-}
-
-// ---- packed two-wide FP32 arithmetic (f32x2) ----
-__device__ __forceinline__ unsigned long long f2pack(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 f2unpack(unsigned long long v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return make_float2(a, b);
-}
-__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
 }
 
 // Near field, one warp per target leaf.

@@ -86,6 +86,22 @@ def periodic_uniform(seed=0, n=2000, L=3.0, n_sites=8, site_size=4, p=8, depth=3
     return _finish(f"periodic_uniform_n{n}", x, qA, groups, rng, L, True, p, depth)
 
 
+def periodic_dense_cluster(seed=0, n_bg=6000, n_cluster=3000, radius=0.3, center=(1.1, 1.3, 2.2), L=4.0,
+                           n_sites=8, site_size=4, p=10, depth=3):
+    """A periodic cube of +-1 charges, uniform, plus a dense ball of +-1 charges (about 30 times
+    the background density at the defaults): the leaves around the ball hold hundreds of atoms."""
+    rng = np.random.default_rng(seed)
+    xb = rng.uniform(0.0, L, (n_bg, 3))
+    d = rng.normal(size=(n_cluster, 3))
+    d *= (radius * rng.uniform(0.0, 1.0, (n_cluster, 1)) ** (1.0 / 3.0)) / np.linalg.norm(d, axis=1, keepdims=True)
+    x = np.concatenate([xb, np.asarray(center) + d]).astype(np.float32)
+    n = n_bg + n_cluster
+    qA = rng.permutation(np.concatenate([np.ones(n // 2), -np.ones(n - n // 2)]))
+    chosen = rng.choice(n, n_sites * site_size, replace=False)
+    groups = [chosen[site_size * k: site_size * (k + 1)] for k in range(n_sites)]
+    return _finish(f"periodic_dense_cluster_n{n}", x, qA, groups, rng, L, True, p, depth)
+
+
 def _random_rotations(rng, n):
     q = rng.normal(size=(n, 4))
     q /= np.linalg.norm(q, axis=1, keepdims=True)
