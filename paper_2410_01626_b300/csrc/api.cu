@@ -311,6 +311,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         return FMM_ERR_ARG;
     }
     upload_constants(p);
+    near_configure(&h);
 
     const int nc = h.nc, ncp = h.ncp;
     fmm_status st = FMM_OK;

@@ -160,6 +160,7 @@ struct Handle {
 
 // kernels.cu
 void upload_constants(int p);
+void near_configure(Handle* h);  // the near field's shared-memory limit and grid (per handle)
 int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, float* phi,
                 cudaStream_t st);
 int leafcnt_words(int nleaf);  // the binning's counters: one per leaf, one per scan tile

@@ -23,6 +23,7 @@
 
 #include "fmm_internal.h"
 #include "sgemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace fmmcph {
 
@@ -1086,6 +1087,9 @@ struct NearParams {
     float* phi_out;
     float* phis;
     float2* epart;  // per-block sum of q phi as a compensated (hi, lo) pair; totalled in FP64 by k_final
+    int* status;          // device status word (FMM_DEV_TIMEOUT when a near-field staging wait expires)
+    long long wlim;       // bound of the near field's staging waits (clock cycles)
+    int leaves_per_warp;  // target leaves of each near-field warp
 };
 
 // Outputs per atom, one thread per atom in leaf order: the far field (L2P of the leaf's local
@@ -1335,139 +1339,240 @@ static void launch_hi(const HiParams& hp, cudaStream_t st) {
     k_hi<P><<<(hp.K + 3) / 4, 128, 0, st>>>(hp);
 }
 
-// Near field, one warp per target leaf.
-// (1) Lanes 0..26 resolve the 27 neighbour leaves at once (periodic image shift, start,
-//     count); the target's own leaf is listed first, its count rounded up to even.  A warp
-//     scan gives each neighbour's offset in a per-warp source list.
-// (2) When the list fits (kNearCap atoms, the common case), all lanes copy it into shared
-//     memory in one pass as packed pairs (x0 x1 y0 y1 | z0 z1 q0 q1), so that every global
-//     load is in flight together; otherwise the sources are streamed neighbour by neighbour.
-// (3) Every lane holds two targets.  The warp is split into G source slices of TPG lanes
-//     (lane = target lane + slice * TPG; TPG need not be a power of two), over as many passes
-//     as the leaf needs; (passes, TPG) is chosen per leaf to minimise padded slots x source
-//     iterations.  Each iteration loads one source pair and applies it to both targets with
-//     f32x2 arithmetic; only the own leaf's pairs need the r > 0 test (self, coincident
-//     atoms), since equal positions always share a leaf.  Slice sums are combined by a
-//     fixed-order shuffle tree; k_far_out adds the far field and writes the outputs.
-constexpr int kNearCap = 640;
-constexpr int kNT = 2;  // target atoms per lane in the near field's pair loop (4 measured slower)
+// Near field (P2P).  Each warp takes leaves_per_warp target leaves (the block's warps on
+// neighbouring leaves) and stages each leaf's 27-leaf neighbourhood in shared memory with bulk
+// copies.  With NB = 2 staging buffers the next leaf lands while the warp sums the current one;
+// with NB = 1 (the default, measured faster at 500,000 atoms: 0.152 against 0.21-0.24 ms) the
+// warp waits for its copies and the other resident warps, five per SM sub-partition in 44 KB
+// blocks and 93 registers, keep the FMA pipe busy meanwhile.  One leaf per warp (also measured
+// best) keeps blocks short, so the higher-priority multipole chain takes SMs as they retire.
+// (1) Neighbour table: lanes 0..26 resolve the 27 neighbour leaves (periodic image shift,
+//     start, count); the target's own leaf is segment 0, its count rounded up to even.  A warp
+//     scan gives each segment's offset in the buffer, and lane o copies segment o with one
+//     cp.async.bulk (a leaf's atoms are contiguous in leaf order), completing on the buffer's
+//     mbarrier.
+// (2) After the (bounded) wait: the image shift added to the wrapped segments, zero-charge pads
+//     far away in the odd slots, then the atoms repacked in place into pairs
+//     (x0 x1 y0 y1 | z0 z1 q0 q1) for the f32x2 arithmetic.
+// (3) Work mapping: tp target pairs (two targets per lane) x np source pairs.  Each target pair
+//     gets k source slices (source pairs j, j + k, j + 2k, ...); slice g = j tp + t runs on lane
+//     g mod 32 in phase g / 32.  (phases, k) is chosen per leaf to minimise phases x slice
+//     length, and every lane of a phase runs the same trip count, so lanes never diverge in the
+//     pair loop.  Only the own leaf's pairs need the r > 0 test (self, coincident atoms), since
+//     equal positions always share a leaf.  After each phase the slice sums go to shared
+//     memory, and the owner lane of each target pair adds them in slice order: a fixed order,
+//     so results are bitwise reproducible for every block shape.
+// Leaves whose neighbourhood does not fit a buffer (kNearCap atoms) stream their sources from
+// global memory instead, one target per lane.  k_far_out adds the far field and writes the
+// outputs.
+constexpr int kNearCap = 592;                   // staged atoms per buffer (neighbourhood + 2 pads)
+constexpr long long kNearWait = 4000000000LL;  // default bound of a staging wait (clock cycles, about 2 s)
 __device__ __forceinline__ float rsqrt_approx(float x) {  // MUFU reciprocal square root
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// Near-field potential and gradient of the target atom at sorted slot s; k_far_out adds the far
-// field and writes the outputs.
+
+template <int NB>
+struct NearWarpSmem {
+    float4 buf[NB][kNearCap];  // staging buffers: AoS (x, y, z, q) as copied, then packed pairs
+    float4 part[32][2];        // slice sums of one phase: (pot, gx, gy, gz) of the lane's two targets
+    uint64_t bar[NB];          // one mbarrier per buffer
+    int off[NB][28];           // segment offsets (atoms) in the buffer, off[27] = total slots
+    int s0[NB][27];            // first sorted atom of each segment
+    float sh[NB][27][3];       // image shift of each segment
+    int info[NB][4];           // leaf, own count, total slots, mask of wrapped segments
+};
+
 __device__ __forceinline__ void near_output(float4* __restrict__ near, int s, float pot, float gx, float gy,
                                             float gz) {
     near[s] = make_float4(pot, gx, gy, gz);
 }
 
-// W warps (target leaves) per block: 2 or 4 (the near-field block shape the autotuner picks; the
-// static shared memory of 4 warps is 43.5 KB, under the 48 KB a static allocation may use).
-template <int W>
-__global__ void __launch_bounds__(32 * W) k_p2p(NearParams a, float4* __restrict__ near) {
-    __shared__ float4 src_sm[W][kNearCap];  // packed pairs: [2j] = (x x y y), [2j+1] = (z z q q)
-    __shared__ int nb_off[W][28];
-    __shared__ int nb_s0[W][27];
-    __shared__ int nb_sc[W][27];
-    __shared__ float nb_sh[W][27][3];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int leaf = blockIdx.x * W + w;
-    if (leaf < a.nleaf) {
+// Sums of one source pair (A = (x0 x1 y0 y1), B = (z0 z1 q0 q1)) at two targets: the potential
+// q/r and the gradient of q/r at the target, q (s - x) / r^3.
+template <bool kCheck>
+__device__ __forceinline__ void near_step(const float4 A, const float4 B, const unsigned long long (&mx)[2],
+                                          const unsigned long long (&my)[2], const unsigned long long (&mz)[2],
+                                          unsigned long long (&P)[2], unsigned long long (&X)[2],
+                                          unsigned long long (&Y)[2], unsigned long long (&Z)[2]) {
+    const unsigned long long sx = f2pack(A.x, A.y), sy = f2pack(A.z, A.w), sz = f2pack(B.x, B.y),
+                             sq = f2pack(B.z, B.w);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const unsigned long long dx = f2sub(sx, mx[r]), dy = f2sub(sy, my[r]), dz = f2sub(sz, mz[r]);
+        const float2 r2 = f2unpack(f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx))));
+        float r0 = rsqrt_approx(r2.x), r1 = rsqrt_approx(r2.y);
+        if (kCheck) {  // the self pair and coincident atoms
+            r0 = (r2.x > 0.f) ? r0 : 0.f;
+            r1 = (r2.y > 0.f) ? r1 : 0.f;
+        }
+        const unsigned long long ri = f2pack(r0, r1);
+        const unsigned long long qri = f2mul(sq, ri);
+        P[r] = f2add(P[r], qri);
+        const unsigned long long qri3 = f2mul(qri, f2mul(ri, ri));
+        X[r] = f2fma(qri3, dx, X[r]);
+        Y[r] = f2fma(qri3, dy, Y[r]);
+        Z[r] = f2fma(qri3, dz, Z[r]);
+    }
+}
+
+// (phases, slices per target pair, slice length) for tpg target pairs and np source pairs
+__device__ __forceinline__ void near_map(int tpg, int np, int& P, int& k, int& n) {
+    int best = 1 << 30;
+    P = 1, k = 1, n = np;
+    for (int pc = 1; pc <= 4; ++pc) {
+        const int kc = max(1, min((32 * pc) / tpg, np));
+        const int nc = (np + kc - 1) / kc;
+        const int cost = pc * (nc + 3);  // + the per-phase work (targets, slice sums), in steps
+        if (cost < best) {
+            best = cost;
+            P = pc;
+            k = kc;
+            n = nc;
+        }
+    }
+}
+
+// (1) of k_p2p, first half: lane o < 27 loads the start and count of neighbour segment o of
+// `leaf` (segment 0 = the own leaf, neighbour offset 13).  The loads are issued a leaf ahead of
+// their use, so that their latency hides behind the pair loop.
+struct NearTab {
+    int s0, sc;
+};
+__device__ __forceinline__ int near_segment(const NearParams& a, int lane, int leaf, int& sx, int& sy, int& sz) {
+    const int nb = 1 << a.depth;
+    const int o = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);
+    sx = (int)compact3(leaf) + o / 9 - 1;
+    sy = (int)compact3(leaf >> 1) + (o / 3) % 3 - 1;
+    sz = (int)compact3(leaf >> 2) + o % 3 - 1;
+    if (a.periodic) return 1;
+    return sx >= 0 && sx < nb && sy >= 0 && sy < nb && sz >= 0 && sz < nb;
+}
+__device__ __forceinline__ NearTab near_table(const NearParams& a, int lane, int leaf) {
+    NearTab t{0, 0};
+    if (lane < 27 && leaf < a.nleaf) {
         const int nb = 1 << a.depth;
-        const int ix = (int)compact3(leaf), iy = (int)compact3(leaf >> 1), iz = (int)compact3(leaf >> 2);
-        const float h = a.h;
-        const int st = a.start[leaf], cnt = a.count[leaf];
-        // (1) neighbour table: lane 0 = own leaf (offset 13), lanes 1..26 = the others
-        int my_s0 = 0, my_sc = 0;
-        float shx = 0.f, shy = 0.f, shz = 0.f;
-        if (lane < 27) {
-            const int o = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);
-            int sx = ix + o / 9 - 1, sy = iy + (o / 3) % 3 - 1, sz = iz + o % 3 - 1;
-            bool ok = true;
-            if (a.periodic) {
-                const int wx = (sx + nb) & (nb - 1), wy = (sy + nb) & (nb - 1), wz = (sz + nb) & (nb - 1);
-                shx = (float)(sx - wx) * h;
-                shy = (float)(sy - wy) * h;
-                shz = (float)(sz - wz) * h;
-                sx = wx;
-                sy = wy;
-                sz = wz;
-            } else {
-                ok = sx >= 0 && sx < nb && sy >= 0 && sy < nb && sz >= 0 && sz < nb;
-            }
-            if (ok) {
-                const uint32_t src = morton3(sx, sy, sz);
-                my_s0 = (int)a.start[src];
-                my_sc = (int)a.count[src];
-            }
+        int sx, sy, sz;
+        if (near_segment(a, lane, leaf, sx, sy, sz)) {
+            const uint32_t src = morton3(sx & (nb - 1), sy & (nb - 1), sz & (nb - 1));
+            t.s0 = (int)a.start[src];
+            t.sc = (int)a.count[src];
         }
-        const int slot = (lane == 0) ? ((my_sc + 1) & ~1) : my_sc;  // own leaf padded to even
-        int incl = slot;
+    }
+    return t;
+}
+
+// (1) of k_p2p, second half: the segment offsets of `leaf` in buffer b of the warp's staging
+// area (warp scan), its metadata, and the bulk copies of its segments.
+template <int NB>
+__device__ __forceinline__ void near_issue(const NearParams& a, NearWarpSmem<NB>& S, int lane, int leaf, int b,
+                                           NearTab tab) {
+    const int my_s0 = tab.s0, my_sc = tab.sc;
+    float shx = 0.f, shy = 0.f, shz = 0.f;
+    if (lane < 27 && a.periodic) {  // image shift of the segment
+        const int nb = 1 << a.depth;
+        int sx, sy, sz;
+        near_segment(a, lane, leaf, sx, sy, sz);
+        shx = (float)(sx - (sx & (nb - 1))) * a.h;
+        shy = (float)(sy - (sy & (nb - 1))) * a.h;
+        shz = (float)(sz - (sz & (nb - 1))) * a.h;
+    }
+    const int slot = (lane == 0) ? ((my_sc + 1) & ~1) : my_sc;  // own leaf padded to even
+    int incl = slot;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int cnt = __shfl_sync(0xffffffffu, my_sc, 0);
+    const unsigned wrap =
+        __ballot_sync(0xffffffffu, lane < 27 && my_sc > 0 && (shx != 0.f || shy != 0.f || shz != 0.f));
+    if (lane < 27) {
+        S.off[b][lane + 1] = incl;
+        S.s0[b][lane] = my_s0;
+        S.sh[b][lane][0] = shx;
+        S.sh[b][lane][1] = shy;
+        S.sh[b][lane][2] = shz;
+    }
+    if (lane == 0) {
+        S.off[b][0] = 0;
+        S.info[b][0] = leaf;
+        S.info[b][1] = cnt;
+        S.info[b][2] = total;
+        S.info[b][3] = (int)wrap;
+    }
+    const bool staged = ((total + 1) & ~1) <= kNearCap;
+    // this lane's generic accesses to the buffer (the previous leaf's) before the async copies
+    tc::fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive_expect_tx(&S.bar[b], staged ? 16u * (uint32_t)(total - (cnt & 1)) : 0u);
+    __syncwarp();
+    if (staged && lane < 27 && my_sc > 0)
+        tc::bulk_g2s(&S.buf[b][incl - slot], a.pos + my_s0, 16u * (uint32_t)my_sc, &S.bar[b]);
+}
+
+// W warps per block: 2 or 4 (the near-field block shape the autotuner picks).  NB staging
+// buffers per warp: with 2, a warp's next leaf lands while it sums the current one; with 1, the
+// warp waits for its copies, and the other resident warps (more of them, in less shared memory
+// and fewer registers) fill the pipe meanwhile.
+template <int W, int NB>
+__global__ void __launch_bounds__(32 * W, NB == 2 ? 1 : 20 / W) k_p2p(NearParams a, float4* __restrict__ near) {
+    extern __shared__ __align__(128) unsigned char near_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    NearWarpSmem<NB>& S = reinterpret_cast<NearWarpSmem<NB>*>(near_smem)[w];
+    if (lane == 0) {
+        for (int b = 0; b < NB; ++b) tc::mbar_init(&S.bar[b], 1);
+        tc::fence_mbar_init();
+    }
+    __syncwarp();
+    // this warp's leaves: first + i W, i < leaves_per_warp (the block's warps on neighbouring leaves)
+    const int first = blockIdx.x * W * a.leaves_per_warp + w;
+    const int last = min(a.nleaf, first + W * a.leaves_per_warp);
+    int it = 0;
+    int leaf = first;
+    NearTab tab_next = near_table(a, lane, NB == 2 ? leaf + W : leaf);
+    if (NB == 2 && leaf < last) near_issue(a, S, lane, leaf, 0, near_table(a, lane, leaf));
+    for (; leaf < last; leaf += W, ++it) {
+        const int b = NB == 2 ? (it & 1) : 0;
+        const uint32_t parity = (uint32_t)((NB == 2 ? it >> 1 : it) & 1);
+        const bool more = NB == 2 && leaf + W < last;
+        if (NB == 1) {  // this leaf's copies, then the next leaf's table (its loads in flight meanwhile)
+            const NearTab tab = tab_next;
+            tab_next = near_table(a, lane, leaf + W < last ? leaf + W : a.nleaf);
+            near_issue(a, S, lane, leaf, 0, tab);
+        } else if (more) {
+            const NearTab tab = tab_next;
+            tab_next = near_table(a, lane, leaf + 2 * W < last ? leaf + 2 * W : a.nleaf);
+            near_issue(a, S, lane, leaf + W, b ^ 1, tab);
         }
-        int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int own_pairs = __shfl_sync(0xffffffffu, slot, 0) >> 1;
-        if (lane < 27) {
-            nb_off[w][lane + 1] = incl;
-            nb_s0[w][lane] = my_s0;
-            nb_sc[w][lane] = my_sc;
-            nb_sh[w][lane][0] = shx;
-            nb_sh[w][lane][1] = shy;
-            nb_sh[w][lane][2] = shz;
+        if (!tc::mbar_wait_all(&S.bar[b], parity, a.wlim)) {
+            if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
+            // nothing may still be copying into this block's shared memory when it exits
+            tc::mbar_wait_all(&S.bar[b], parity, kNearWait);
+            if (more) tc::mbar_wait_all(&S.bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kNearWait);
+            return;
         }
-        if (lane == 0) nb_off[w][0] = 0;
-        __syncwarp();
+        const int cnt = S.info[b][1], total = S.info[b][2];
+        const int st = S.s0[b][0];
         const int npairs = (total + 1) >> 1;
-        const bool staged = 2 * npairs <= kNearCap;
-        if (staged) {  // (2) one pass over every source atom of the 27 neighbours
-            for (int j0 = 0; j0 < 2 * npairs; j0 += 32) {  // uniform trip count: shuffles below
-                const int j = j0 + lane;
-                int o = 0;  // largest neighbour slot with nb_off[o] <= j
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1)
-                    if (o + step < 27 && nb_off[w][o + step] <= j) o += step;
-                const int k = j - nb_off[w][o];
-                // padding (own leaf odd, list odd): a zero charge far away contributes nothing
-                float4 sp = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
-                if (j < total && k < nb_sc[w][o]) {
-                    sp = a.pos[nb_s0[w][o] + k];
-                    sp.x += nb_sh[w][o][0];
-                    sp.y += nb_sh[w][o][1];
-                    sp.z += nb_sh[w][o][2];
-                }
-                // lane pair (2i, 2i+1) holds one source pair; each lane writes one float4 of it
-                const float4 nb4 = make_float4(__shfl_xor_sync(0xffffffffu, sp.x, 1), __shfl_xor_sync(0xffffffffu, sp.y, 1),
-                                               __shfl_xor_sync(0xffffffffu, sp.z, 1), __shfl_xor_sync(0xffffffffu, sp.w, 1));
-                const bool even = (lane & 1) == 0;
-                const float4 lo = even ? sp : nb4, hi = even ? nb4 : sp;  // sources 2i and 2i+1
-                if (j < 2 * npairs) {
-                    float4* dst = src_sm[w] + 2 * (j >> 1);
-                    if (even) dst[0] = make_float4(lo.x, hi.x, lo.y, hi.y);
-                    else dst[1] = make_float4(lo.z, hi.z, lo.w, hi.w);
-                }
-            }
-            __syncwarp();
-        }
-        if (!staged) {  // streamed sources (rare): one target per lane, 32 targets per pass
+        float4* buf = S.buf[b];
+        if (2 * npairs > kNearCap) {  // streamed sources (rare): one target per lane, 32 targets per pass
+            float4* stage = buf;      // nothing was copied into this buffer for this leaf
             for (int tb = 0; tb < cnt; tb += 32) {
                 const int ti = tb + lane;
                 const bool valid = ti < cnt;
                 const float4 me = valid ? a.pos[st + ti] : make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
                 float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-                float4* stage = src_sm[w];
                 for (int o = 0; o < 27; ++o) {
-                    const int s0 = nb_s0[w][o], sc = nb_sc[w][o];
+                    const int s0 = S.s0[b][o], sc = S.off[b][o + 1] - S.off[b][o] - (o == 0 ? (cnt & 1) : 0);
                     for (int sb = 0; sb < sc; sb += 32) {
                         float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
-                        sp.x += nb_sh[w][o][0];
-                        sp.y += nb_sh[w][o][1];
-                        sp.z += nb_sh[w][o][2];
+                        sp.x += S.sh[b][o][0];
+                        sp.y += S.sh[b][o][1];
+                        sp.z += S.sh[b][o][2];
                         __syncwarp();
                         stage[lane] = sp;
                         __syncwarp();
@@ -1489,97 +1594,135 @@ __global__ void __launch_bounds__(32 * W) k_p2p(NearParams a, float4* __restrict
                 if (valid) near_output(near, st + ti, pot, gx, gy, gz);
             }
         } else if (cnt > 0) {
-            // (3) mapping: passes x TPG lanes (kNT targets each) x G slices
-            int TPG = 32, G = 1, passes = (cnt + 32 * kNT - 1) / (32 * kNT), best = 1 << 30;
-            const int p0 = passes;
-            for (int ps = p0; ps < p0 + 4; ++ps) {
-                const int tpg = (cnt + kNT * ps - 1) / (kNT * ps);
-                const int g = 32 / tpg;
-                const int cost = ps * ((npairs + g - 1) / g + 4 * g + 16);
-                if (cost < best) {
-                    best = cost;
-                    TPG = tpg;
-                    G = g;
-                    passes = ps;
+            // (2) image shifts of the wrapped segments, pads, packed pairs
+            for (unsigned wm = (unsigned)S.info[b][3]; wm; wm &= wm - 1) {
+                const int o = __ffs(wm) - 1;
+                const int o0 = S.off[b][o], no = S.off[b][o + 1] - o0;
+                const float ax = S.sh[b][o][0], ay = S.sh[b][o][1], az = S.sh[b][o][2];
+                for (int j = lane; j < no; j += 32) {
+                    float4 v = buf[o0 + j];
+                    v.x += ax;
+                    v.y += ay;
+                    v.z += az;
+                    buf[o0 + j] = v;
                 }
             }
-            const int tl = lane % TPG, slice = lane / TPG;
-            const bool active = slice < G;
-            const float4* sp4 = src_sm[w];
-            for (int ps = 0; ps < passes; ++ps) {
-                int ti[kNT];
-                bool tv[kNT];
-                unsigned long long mx[kNT], my[kNT], mz[kNT], P[kNT], X[kNT], Y[kNT], Z[kNT];
+            // a zero charge far away contributes nothing (own leaf odd, list odd)
+            if (lane == 0 && (cnt & 1)) buf[cnt] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+            if (lane == 1 && (total & 1)) buf[total] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+            __syncwarp();
+            for (int j = lane; j < npairs; j += 32) {
+                const float4 A = buf[2 * j], B = buf[2 * j + 1];
+                buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
+                buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
+            }
+            __syncwarp();
+            // (3) phases of target-pair slices
+            const int tp = (cnt + 1) >> 1;
+            const int own_pairs = S.off[b][1] >> 1;
+            for (int tg = 0; tg < tp; tg += 32) {  // groups of up to 32 target pairs
+                const int tpg = min(32, tp - tg);
+                int P, k, n;
+                near_map(tpg, npairs, P, k, n);
+                const int nslices = tpg * k;
+                const int nchk = min(n - 1, (own_pairs + k - 1) / k);  // i < ceil(own / k): pairs j + i k may be own
+                float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+                for (int ph = 0; ph < P; ++ph) {
+                    const int g = ph * 32 + lane;
+                    const bool act = g < nslices;
+                    // slice-major: the lanes of a quarter warp mostly share a slice, so their source
+                    // loads are broadcasts
+                    const int t = act ? g % tpg : 0, j = act ? g / tpg : 0;
+                    const bool full = act && j + (n - 1) * k < npairs;  // this slice has n source pairs
+                    const float4 TA = buf[2 * (tg + t)], TB = buf[2 * (tg + t) + 1];
+                    unsigned long long mx[2], my[2], mz[2], Pv[2], Xv[2], Yv[2], Zv[2];
+                    mx[0] = f2pack(TA.x, TA.x);
+                    mx[1] = f2pack(TA.y, TA.y);
+                    my[0] = f2pack(TA.z, TA.z);
+                    my[1] = f2pack(TA.w, TA.w);
+                    mz[0] = f2pack(TB.x, TB.x);
+                    mz[1] = f2pack(TB.y, TB.y);
 #pragma unroll
-                for (int r = 0; r < kNT; ++r) {
-                    ti[r] = ps * kNT * TPG + r * TPG + tl;
-                    tv[r] = active && ti[r] < cnt;
-                    const float4 me = tv[r] ? a.pos[st + ti[r]] : make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
-                    mx[r] = f2pack(me.x, me.x);
-                    my[r] = f2pack(me.y, me.y);
-                    mz[r] = f2pack(me.z, me.z);
-                    P[r] = X[r] = Y[r] = Z[r] = 0ull;
-                }
-                // sources minus target: the gradient of q/r at the target is q (s - x) / r^3
-                auto apply = [&](const unsigned long long sx, const unsigned long long sy, const unsigned long long sz,
-                                 const unsigned long long sq, const int r, const bool check) {
-                    const unsigned long long dx = f2sub(sx, mx[r]), dy = f2sub(sy, my[r]), dz = f2sub(sz, mz[r]);
-                    const float2 r2 = f2unpack(f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx))));
-                    float r0 = rsqrt_approx(r2.x), r1 = rsqrt_approx(r2.y);
-                    if (check) {
-                        r0 = (r2.x > 0.f) ? r0 : 0.f;
-                        r1 = (r2.y > 0.f) ? r1 : 0.f;
+                    for (int r = 0; r < 2; ++r) Pv[r] = Xv[r] = Yv[r] = Zv[r] = 0ull;
+                    const float4* sp = buf + 2 * j;
+                    const int stride = 2 * k;
+                    int i = 0;
+                    for (; i < nchk; ++i, sp += stride) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
+                    if (i < n - 1) {  // steps i .. n - 2 exist for every lane: sources loaded a step ahead
+                        float4 pa = sp[0], pb = sp[1];
+#pragma unroll 2
+                        for (; i + 1 < n - 1; ++i) {
+                            sp += stride;
+                            const float4 na = sp[0], nb = sp[1];
+                            near_step<false>(pa, pb, mx, my, mz, Pv, Xv, Yv, Zv);
+                            pa = na;
+                            pb = nb;
+                        }
+                        near_step<false>(pa, pb, mx, my, mz, Pv, Xv, Yv, Zv);
+                        ++i;
+                        sp += stride;
                     }
-                    const unsigned long long ri = f2pack(r0, r1);
-                    const unsigned long long qri = f2mul(sq, ri);
-                    P[r] = f2add(P[r], qri);
-                    const unsigned long long qri3 = f2mul(qri, f2mul(ri, ri));
-                    X[r] = f2fma(qri3, dx, X[r]);
-                    Y[r] = f2fma(qri3, dy, Y[r]);
-                    Z[r] = f2fma(qri3, dz, Z[r]);
-                };
-                auto step = [&](int t, const bool check) {
-                    const float4 A = sp4[2 * t], B = sp4[2 * t + 1];
-                    const unsigned long long sx = f2pack(A.x, A.y), sy = f2pack(A.z, A.w), sz = f2pack(B.x, B.y),
-                                             sq = f2pack(B.z, B.w);
-#pragma unroll
-                    for (int r = 0; r < kNT; ++r) apply(sx, sy, sz, sq, r, check);
-                };
-                if (active) {
-                    int t = slice;
-                    for (; t < own_pairs; t += G) step(t, true);
-                    for (; t + G < npairs; t += 2 * G) {
-                        step(t, false);
-                        step(t + G, false);
+                    if (full) {  // the last source pair of the slices that have n
+                        if ((n - 1) * k < own_pairs) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
+                        else near_step<false>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
                     }
-                    for (; t < npairs; t += G) step(t, false);
-                }
-                float v[4 * kNT];
-#pragma unroll
-                for (int r = 0; r < kNT; ++r) {
-                    const float2 pv = f2unpack(P[r]), xv = f2unpack(X[r]), yv = f2unpack(Y[r]), zv = f2unpack(Z[r]);
-                    v[4 * r] = pv.x + pv.y;
-                    v[4 * r + 1] = xv.x + xv.y;
-                    v[4 * r + 2] = yv.x + yv.y;
-                    v[4 * r + 3] = zv.x + zv.y;
-                }
-                // slice sums: fixed-order tree over the slices (slice 0 ends with the total)
-                for (int off = 1; off < G; off <<= 1) {
-                    const bool take = (slice % (2 * off)) == 0 && slice + off < G;
-#pragma unroll
-                    for (int e = 0; e < 4 * kNT; ++e) {
-                        const float o = __shfl_down_sync(0xffffffffu, v[e], off * TPG);
-                        if (take) v[e] += o;
+                    if (act) {
+                        const float2 p0 = f2unpack(Pv[0]), x0 = f2unpack(Xv[0]), y0 = f2unpack(Yv[0]),
+                                     z0 = f2unpack(Zv[0]);
+                        const float2 p1 = f2unpack(Pv[1]), x1 = f2unpack(Xv[1]), y1 = f2unpack(Yv[1]),
+                                     z1 = f2unpack(Zv[1]);
+                        S.part[lane][0] = make_float4(p0.x + p0.y, x0.x + x0.y, y0.x + y0.y, z0.x + z0.y);
+                        S.part[lane][1] = make_float4(p1.x + p1.y, x1.x + x1.y, y1.x + y1.y, z1.x + z1.y);
                     }
+                    __syncwarp();
+                    if (lane < tpg) {  // owner of target pair tg + lane: its slices j lane + j tpg of this phase, in order
+                        const int j0 = max(0, (ph * 32 - lane + tpg - 1) / tpg);
+                        const int j1 = min(k, (ph * 32 + 32 - lane + tpg - 1) / tpg);
+                        for (int jj = j0; jj < j1; ++jj) {
+                            const int gg = jj * tpg + lane - ph * 32;
+                            const float4 u = S.part[gg][0], v = S.part[gg][1];
+                            acc0.x += u.x;
+                            acc0.y += u.y;
+                            acc0.z += u.z;
+                            acc0.w += u.w;
+                            acc1.x += v.x;
+                            acc1.y += v.y;
+                            acc1.z += v.z;
+                            acc1.w += v.w;
+                        }
+                    }
+                    __syncwarp();
                 }
-                if (slice == 0) {
-#pragma unroll
-                    for (int r = 0; r < kNT; ++r)
-                        if (tv[r]) near_output(near, st + ti[r], v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
+                if (lane < tpg) {
+                    const int t0 = 2 * (tg + lane);
+                    near_output(near, st + t0, acc0.x, acc0.y, acc0.z, acc0.w);
+                    if (t0 + 1 < cnt) near_output(near, st + t0 + 1, acc1.x, acc1.y, acc1.z, acc1.w);
                 }
             }
         }
+        __syncwarp();
     }
+}
+
+// Grid of the near field: each warp takes leaves_per_warp leaves, so that blocks stay short
+// and the higher-priority multipole chain gets SMs as they retire.
+constexpr int kNearLeavesPerWarp = 1;
+constexpr int kNearBufs = 1;
+template <int W>
+static void launch_p2p(NearParams a, float4* near, cudaStream_t st) {
+    a.leaves_per_warp = kNearLeavesPerWarp;
+    const int blocks = (a.nleaf + W * kNearLeavesPerWarp - 1) / (W * kNearLeavesPerWarp);
+    k_p2p<W, kNearBufs><<<blocks, 32 * W, (size_t)W * sizeof(NearWarpSmem<kNearBufs>), st>>>(a, near);
+}
+
+// Per handle, with its device current: the near field's dynamic shared-memory limit (both
+// block shapes).
+void near_configure(Handle* h) {
+    (void)h;
+    cudaFuncSetAttribute(k_p2p<2, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * sizeof(NearWarpSmem<kNearBufs>)));
+    cudaFuncSetAttribute(k_p2p<4, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(4 * sizeof(NearWarpSmem<kNearBufs>)));
 }
 
 // E = 1/2 k sum of the per-block partials of q phi, totalled in FP64: each of the
@@ -1825,6 +1968,8 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.phi_out = phi;
     a.phis = h->phis;
     a.epart = h->epart;
+    a.status = h->status;
+    a.wlim = h->wait_limit > 0 ? h->wait_limit : kNearWait;
     const int e1 = mark(h, st);
     span(h, 0, e0, e1);
     // fork: the chain P2M .. L2L on h->chain (highest priority), P2P here.  Serialised
@@ -1835,8 +1980,8 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lc = coarse_top(h);  // top coarse level of the side branch, -1 without one
     cudaEventRecord(h->fork_ev, st);
     cudaStreamWaitEvent(cs, h->fork_ev, 0);
-    if (h->p2p_warps == 2) k_p2p<2><<<(nleaf + 1) / 2, 64, 0, st>>>(a, h->near);
-    else k_p2p<4><<<(nleaf + 3) / 4, 128, 0, st>>>(a, h->near);
+    if (h->p2p_warps == 2) launch_p2p<2>(a, h->near, st);
+    else launch_p2p<4>(a, h->near, st);
     const int e1n = mark(h, st);
     span(h, 8, e1, e1n);
     const int e1c = serial ? e1n : e1;  // start of the chain's first stage
