@@ -98,8 +98,8 @@ typedef struct {
     /* Kernel tiles (results are the same for every choice; the autotuner picks them by timing).
      * m2l_tile_rows: rows of the tensor-core M2L's per-CTA tile (the MMA's N): 128, 160, 192,
      *   224 or 256; 0 selects 192.
-     * p2p_leaves_per_block: target leaves (one warp each) per near-field block: 2 or 4; 0
-     *   selects 4.
+     * p2p_leaves_per_block: target leaves (one warp each) per near-field block: 1, 2 or 4; 0
+     *   selects 1.
      * Other values return FMM_ERR_ARG. */
     int m2l_tile_rows;
     int p2p_leaves_per_block;

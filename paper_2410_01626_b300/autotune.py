@@ -111,4 +111,4 @@ def tune_depth(edge, periodic, p, precision, x, qA, qB, site, lam, origin=(0.0, 
     return cfg["depth"], {k[0]: v["ms"] for k, v in table.items() if k[1:] == (0, 0)}
 
 
-TILES = [(0, 0), (128, 0), (160, 0), (256, 0), (0, 2), (128, 2)]  # (m2l_rows, p2p_warps) tried by the batch tuner
+TILES = [(0, 0), (128, 0), (160, 0), (256, 0), (0, 2), (0, 4)]  # (m2l_rows, p2p_warps) tried by the batch tuner

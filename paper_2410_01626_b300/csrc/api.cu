@@ -281,7 +281,8 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
         if (opt->interpolation != FMM_INTERP_CHARGE && opt->interpolation != FMM_INTERP_HAMILTONIAN)
             return FMM_ERR_ARG;
         if (!m2l_tile_rows_ok(opt->m2l_tile_rows)) return FMM_ERR_ARG;
-        if (opt->p2p_leaves_per_block != 0 && opt->p2p_leaves_per_block != 2 && opt->p2p_leaves_per_block != 4)
+        if (opt->p2p_leaves_per_block != 0 && opt->p2p_leaves_per_block != 1 && opt->p2p_leaves_per_block != 2 &&
+            opt->p2p_leaves_per_block != 4)
             return FMM_ERR_ARG;
         precision = opt->precision;
         interpolation = opt->interpolation;
@@ -301,7 +302,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
     h.ncp = ncoef_padded(p);
     h.precision = precision;
     h.m2l_rows = m2l_rows;
-    h.p2p_warps = p2p_warps > 0 ? p2p_warps : 4;
+    h.p2p_warps = p2p_warps > 0 ? p2p_warps : 1;
     h.hamiltonian = interpolation == FMM_INTERP_HAMILTONIAN;
     h.ke = ke;
     h.s_bin = std::ldexp(1.0, depth) / box->edge;

@@ -1087,9 +1087,9 @@ struct NearParams {
     float* phi_out;
     float* phis;
     float2* epart;  // per-block sum of q phi as a compensated (hi, lo) pair; totalled in FP64 by k_final
-    int* status;          // device status word (FMM_DEV_TIMEOUT when a near-field staging wait expires)
+    int* status;     // device status word (FMM_DEV_TIMEOUT when a near-field staging wait expires)
     long long wlim;       // bound of the near field's staging waits (clock cycles)
-    int leaves_per_warp;  // target leaves of each near-field warp
+    int leaves_per_warp;  // consecutive target leaves of each near-field warp
 };
 
 // Outputs per atom, one thread per atom in leaf order: the far field (L2P of the leaf's local
@@ -1339,34 +1339,31 @@ static void launch_hi(const HiParams& hp, cudaStream_t st) {
     k_hi<P><<<(hp.K + 3) / 4, 128, 0, st>>>(hp);
 }
 
-// Near field (P2P).  Each warp takes leaves_per_warp target leaves (the block's warps on
-// neighbouring leaves) and stages each leaf's 27-leaf neighbourhood in shared memory with bulk
-// copies.  With NB = 2 staging buffers the next leaf lands while the warp sums the current one;
-// with NB = 1 (the default, measured faster at 500,000 atoms: 0.152 against 0.21-0.24 ms) the
-// warp waits for its copies and the other resident warps, five per SM sub-partition in 44 KB
-// blocks and 93 registers, keep the FMA pipe busy meanwhile.  One leaf per warp (also measured
-// best) keeps blocks short, so the higher-priority multipole chain takes SMs as they retire.
-// (1) Neighbour table: lanes 0..26 resolve the 27 neighbour leaves (periodic image shift,
-//     start, count); the target's own leaf is segment 0, its count rounded up to even.  A warp
-//     scan gives each segment's offset in the buffer, and lane o copies segment o with one
-//     cp.async.bulk (a leaf's atoms are contiguous in leaf order), completing on the buffer's
-//     mbarrier.
+// Near field (P2P).  Each warp takes a run of consecutive target leaves.
+// (1) Staging: lanes 0..26 resolve the 27 neighbour leaves of a leaf (periodic image shift,
+//     start, count) and keep them in registers; the target's own leaf is segment 0, its count
+//     rounded up to even.  A warp scan gives each segment's offset in one of the warp's two
+//     buffers, and lane o copies segment o with one cp.async.bulk (a leaf's atoms are contiguous
+//     in leaf order), completing on the buffer's mbarrier.  The next leaf's copies are issued
+//     before the current leaf's pairs are summed, so their latency hides behind the pair loop.
 // (2) After the (bounded) wait: the image shift added to the wrapped segments, zero-charge pads
 //     far away in the odd slots, then the atoms repacked in place into pairs
 //     (x0 x1 y0 y1 | z0 z1 q0 q1) for the f32x2 arithmetic.
 // (3) Work mapping: tp target pairs (two targets per lane) x np source pairs.  Each target pair
 //     gets k source slices (source pairs j, j + k, j + 2k, ...); slice g = j tp + t runs on lane
-//     g mod 32 in phase g / 32.  (phases, k) is chosen per leaf to minimise phases x slice
+//     g mod 32 in phase g / 32 (slice-major: the lanes of a quarter warp mostly read the same
+//     source pair, a broadcast).  (phases, k) comes from a table that minimises phases x slice
 //     length, and every lane of a phase runs the same trip count, so lanes never diverge in the
 //     pair loop.  Only the own leaf's pairs need the r > 0 test (self, coincident atoms), since
-//     equal positions always share a leaf.  After each phase the slice sums go to shared
-//     memory, and the owner lane of each target pair adds them in slice order: a fixed order,
+//     equal positions always share a leaf.  After each phase a fixed shuffle tree adds each
+//     target's slice sums and the owner lane of the target pair adds the result: a fixed order,
 //     so results are bitwise reproducible for every block shape.
 // Leaves whose neighbourhood does not fit a buffer (kNearCap atoms) stream their sources from
 // global memory instead, one target per lane.  k_far_out adds the far field and writes the
 // outputs.
 constexpr int kNearCap = 592;                   // staged atoms per buffer (neighbourhood + 2 pads)
-constexpr long long kNearWait = 4000000000LL;  // default bound of a staging wait (clock cycles, about 2 s)
+constexpr int kNearMaxPairs = kNearCap / 2;     // source pairs of a staged neighbourhood
+constexpr long long kNearWait = 4000000000LL;  // default bound of the staging wait (clock cycles, about 2 s)
 __device__ __forceinline__ float rsqrt_approx(float x) {  // MUFU reciprocal square root
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -1376,13 +1373,43 @@ __device__ __forceinline__ float rsqrt_approx(float x) {  // MUFU reciprocal squ
 template <int NB>
 struct NearWarpSmem {
     float4 buf[NB][kNearCap];  // staging buffers: AoS (x, y, z, q) as copied, then packed pairs
-    float4 part[32][2];        // slice sums of one phase: (pot, gx, gy, gz) of the lane's two targets
-    uint64_t bar[NB];          // one mbarrier per buffer
-    int off[NB][28];           // segment offsets (atoms) in the buffer, off[27] = total slots
-    int s0[NB][27];            // first sorted atom of each segment
-    float sh[NB][27][3];       // image shift of each segment
-    int info[NB][4];           // leaf, own count, total slots, mask of wrapped segments
+    uint64_t bar[NB];          // completion of each buffer's bulk copies
 };
+
+// Work mapping of a leaf: for tpg target pairs (1..32) and np source pairs (1..kNearMaxPairs),
+// the phases P, slices per target pair k and slice length n = ceil(np / k) minimising
+// P x (n + 3) (the 3 stands for a phase's own work: targets, slice sums), packed
+// P | k << 3 | n << 11; and the multipliers rcp[d] = ceil(2^20 / d), d <= 128, so that
+// a / d = (a rcp[d]) >> 20 exactly for the small dividends of the mapping (a < 2^20 / d).
+struct NearMapTable {
+    uint32_t map[32][kNearMaxPairs];
+    uint32_t rcp[129];
+};
+constexpr NearMapTable near_map_table() {
+    NearMapTable t{};
+    for (int tpg = 1; tpg <= 32; ++tpg)
+        for (int np = 1; np <= kNearMaxPairs; ++np) {
+            int best = 1 << 30, P = 1, k = 1, n = np;
+            for (int pc = 1; pc <= 4; ++pc) {
+                int kc = (32 * pc) / tpg;
+                kc = kc > np ? np : (kc < 1 ? 1 : kc);
+                const int nc = (np + kc - 1) / kc;
+                if (pc * (nc + 3) < best) {
+                    best = pc * (nc + 3);
+                    P = pc;
+                    k = kc;
+                    n = nc;
+                }
+            }
+            t.map[tpg - 1][np - 1] = (uint32_t)(P | k << 3 | n << 11);
+        }
+    for (int d = 1; d <= 128; ++d) t.rcp[d] = (uint32_t)(((1u << 20) + d - 1) / d);
+    return t;
+}
+__constant__ NearMapTable c_near = near_map_table();
+__device__ __forceinline__ int near_div(int a, int d) {  // a / d for 0 <= a < 2^20 / d, d <= 128
+    return (int)(((uint32_t)a * c_near.rcp[d]) >> 20);
+}
 
 __device__ __forceinline__ void near_output(float4* __restrict__ near, int s, float pot, float gx, float gy,
                                             float gz) {
@@ -1417,312 +1444,295 @@ __device__ __forceinline__ void near_step(const float4 A, const float4 B, const 
     }
 }
 
-// (phases, slices per target pair, slice length) for tpg target pairs and np source pairs
-__device__ __forceinline__ void near_map(int tpg, int np, int& P, int& k, int& n) {
-    int best = 1 << 30;
-    P = 1, k = 1, n = np;
-    for (int pc = 1; pc <= 4; ++pc) {
-        const int kc = max(1, min((32 * pc) / tpg, np));
-        const int nc = (np + kc - 1) / kc;
-        const int cost = pc * (nc + 3);  // + the per-phase work (targets, slice sums), in steps
-        if (cost < best) {
-            best = cost;
-            P = pc;
-            k = kc;
-            n = nc;
-        }
-    }
-}
-
-// (1) of k_p2p, first half: lane o < 27 loads the start and count of neighbour segment o of
-// `leaf` (segment 0 = the own leaf, neighbour offset 13).  The loads are issued a leaf ahead of
-// their use, so that their latency hides behind the pair loop.
-struct NearTab {
-    int s0, sc;
+// A leaf's staging, held in registers: lane o < 27 keeps segment o (first sorted atom, atom
+// count, offset in the buffer, image shift); the counts and the mask are the same in every lane.
+struct NearStage {
+    int s0, sc, off;
+    float shx, shy, shz;
+    int cnt, total;  // own atoms, total slots (own leaf padded to even)
+    unsigned wrap;   // segments with a nonzero image shift
 };
-__device__ __forceinline__ int near_segment(const NearParams& a, int lane, int leaf, int& sx, int& sy, int& sz) {
+
+// (1): the segment table of `leaf` and, when the neighbourhood fits a buffer, the bulk copies of
+// its segments into buf, completing on bar.  The caller has ordered the buffer's earlier
+// generic-proxy accesses before these asynchronous writes.
+__device__ __forceinline__ NearStage near_stage(const NearParams& a, float4* buf, uint64_t* bar, int lane,
+                                                int leaf) {
     const int nb = 1 << a.depth;
-    const int o = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);
-    sx = (int)compact3(leaf) + o / 9 - 1;
-    sy = (int)compact3(leaf >> 1) + (o / 3) % 3 - 1;
-    sz = (int)compact3(leaf >> 2) + o % 3 - 1;
-    if (a.periodic) return 1;
-    return sx >= 0 && sx < nb && sy >= 0 && sy < nb && sz >= 0 && sz < nb;
-}
-__device__ __forceinline__ NearTab near_table(const NearParams& a, int lane, int leaf) {
-    NearTab t{0, 0};
-    if (lane < 27 && leaf < a.nleaf) {
-        const int nb = 1 << a.depth;
-        int sx, sy, sz;
-        if (near_segment(a, lane, leaf, sx, sy, sz)) {
-            const uint32_t src = morton3(sx & (nb - 1), sy & (nb - 1), sz & (nb - 1));
+    NearStage t{0, 0, 0, 0.f, 0.f, 0.f, 0, 0, 0u};
+    if (lane < 27) {  // lane 0 = own leaf (offset 13), lanes 1..26 = the others
+        const int o = (lane == 0) ? 13 : (lane <= 13 ? lane - 1 : lane);
+        const int sx = (int)compact3(leaf) + o / 9 - 1, sy = (int)compact3(leaf >> 1) + (o / 3) % 3 - 1,
+                  sz = (int)compact3(leaf >> 2) + o % 3 - 1;
+        const int wx = sx & (nb - 1), wy = sy & (nb - 1), wz = sz & (nb - 1);  // periodic wrap
+        if (a.periodic || (sx == wx && sy == wy && sz == wz)) {
+            const uint32_t src = morton3(wx, wy, wz);
             t.s0 = (int)a.start[src];
             t.sc = (int)a.count[src];
+            t.shx = (float)(sx - wx) * a.h;
+            t.shy = (float)(sy - wy) * a.h;
+            t.shz = (float)(sz - wz) * a.h;
         }
     }
-    return t;
-}
-
-// (1) of k_p2p, second half: the segment offsets of `leaf` in buffer b of the warp's staging
-// area (warp scan), its metadata, and the bulk copies of its segments.
-template <int NB>
-__device__ __forceinline__ void near_issue(const NearParams& a, NearWarpSmem<NB>& S, int lane, int leaf, int b,
-                                           NearTab tab) {
-    const int my_s0 = tab.s0, my_sc = tab.sc;
-    float shx = 0.f, shy = 0.f, shz = 0.f;
-    if (lane < 27 && a.periodic) {  // image shift of the segment
-        const int nb = 1 << a.depth;
-        int sx, sy, sz;
-        near_segment(a, lane, leaf, sx, sy, sz);
-        shx = (float)(sx - (sx & (nb - 1))) * a.h;
-        shy = (float)(sy - (sy & (nb - 1))) * a.h;
-        shz = (float)(sz - (sz & (nb - 1))) * a.h;
-    }
-    const int slot = (lane == 0) ? ((my_sc + 1) & ~1) : my_sc;  // own leaf padded to even
+    const int slot = (lane == 0) ? ((t.sc + 1) & ~1) : t.sc;  // own leaf padded to even
     int incl = slot;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += y;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int cnt = __shfl_sync(0xffffffffu, my_sc, 0);
-    const unsigned wrap =
-        __ballot_sync(0xffffffffu, lane < 27 && my_sc > 0 && (shx != 0.f || shy != 0.f || shz != 0.f));
-    if (lane < 27) {
-        S.off[b][lane + 1] = incl;
-        S.s0[b][lane] = my_s0;
-        S.sh[b][lane][0] = shx;
-        S.sh[b][lane][1] = shy;
-        S.sh[b][lane][2] = shz;
-    }
-    if (lane == 0) {
-        S.off[b][0] = 0;
-        S.info[b][0] = leaf;
-        S.info[b][1] = cnt;
-        S.info[b][2] = total;
-        S.info[b][3] = (int)wrap;
-    }
-    const bool staged = ((total + 1) & ~1) <= kNearCap;
-    // this lane's generic accesses to the buffer (the previous leaf's) before the async copies
-    tc::fence_proxy_async();
+    t.off = incl - slot;
+    t.total = __shfl_sync(0xffffffffu, incl, 31);
+    t.cnt = __shfl_sync(0xffffffffu, t.sc, 0);
+    t.wrap = __ballot_sync(0xffffffffu, lane < 27 && t.sc > 0 && (t.shx != 0.f || t.shy != 0.f || t.shz != 0.f));
+    const bool staged = t.cnt > 0 && ((t.total + 1) & ~1) <= kNearCap;  // nothing to stage without targets
+    if (lane == 0) tc::mbar_arrive_expect_tx(bar, staged ? 16u * (uint32_t)(t.total - (t.cnt & 1)) : 0u);
     __syncwarp();
-    if (lane == 0) tc::mbar_arrive_expect_tx(&S.bar[b], staged ? 16u * (uint32_t)(total - (cnt & 1)) : 0u);
-    __syncwarp();
-    if (staged && lane < 27 && my_sc > 0)
-        tc::bulk_g2s(&S.buf[b][incl - slot], a.pos + my_s0, 16u * (uint32_t)my_sc, &S.bar[b]);
+    if (staged && lane < 27 && t.sc > 0) tc::bulk_g2s(buf + t.off, a.pos + t.s0, 16u * (uint32_t)t.sc, bar);
+    return t;
 }
 
-// W warps per block: 2 or 4 (the near-field block shape the autotuner picks).  NB staging
-// buffers per warp: with 2, a warp's next leaf lands while it sums the current one; with 1, the
-// warp waits for its copies, and the other resident warps (more of them, in less shared memory
-// and fewer registers) fill the pipe meanwhile.
+// Streamed near field of one leaf whose neighbourhood does not fit a staging buffer (rare):
+// one target per lane, 32 targets per pass, sources through a 32-atom stage in buf.
+__device__ __noinline__ void near_streamed(const NearParams& a, int seg_s0, int seg_sc, float seg_shx, float seg_shy,
+                                           float seg_shz, int cnt, float4* buf, int lane, float4* __restrict__ near) {
+    const int st = __shfl_sync(0xffffffffu, seg_s0, 0);
+    for (int tb = 0; tb < cnt; tb += 32) {
+        const int ti = tb + lane;
+        const bool valid = ti < cnt;
+        const float4 me = valid ? a.pos[st + ti] : make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
+        float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        for (int o = 0; o < 27; ++o) {
+            const int s0 = __shfl_sync(0xffffffffu, seg_s0, o), sc = __shfl_sync(0xffffffffu, seg_sc, o);
+            const float ax = __shfl_sync(0xffffffffu, seg_shx, o), ay = __shfl_sync(0xffffffffu, seg_shy, o),
+                        az = __shfl_sync(0xffffffffu, seg_shz, o);
+            for (int sb = 0; sb < sc; sb += 32) {
+                float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
+                sp.x += ax;
+                sp.y += ay;
+                sp.z += az;
+                __syncwarp();
+                buf[lane] = sp;
+                __syncwarp();
+                const int ns = min(32, sc - sb);
+                for (int t = 0; t < ns; ++t) {
+                    const float4 s4 = buf[t];
+                    const float dx = s4.x - me.x, dy = s4.y - me.y, dz = s4.z - me.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float ri = (r2 > 0.f) ? rsqrt_approx(r2) : 0.f;
+                    const float qri = s4.w * ri;
+                    pot += qri;
+                    const float qri3 = qri * ri * ri;
+                    gx = fmaf(qri3, dx, gx);
+                    gy = fmaf(qri3, dy, gy);
+                    gz = fmaf(qri3, dz, gz);
+                }
+            }
+        }
+        if (valid) near_output(near, st + ti, pot, gx, gy, gz);
+    }
+}
+
+// (2) and (3) for one staged leaf in buf: image shifts of the wrapped segments, pads, packed
+// pairs, then the phases of target-pair slices; writes the leaf's near-field outputs.
+__device__ __forceinline__ void near_leaf(const NearParams& a, const NearStage& T, float4* buf, int lane,
+                                          float4* __restrict__ near) {
+    const int cnt = T.cnt, total = T.total;
+    const int npairs = (total + 1) >> 1;
+    for (unsigned wm = T.wrap; wm; wm &= wm - 1) {
+        const int o = __ffs(wm) - 1;
+        const int o0 = __shfl_sync(0xffffffffu, T.off, o), no = __shfl_sync(0xffffffffu, T.sc, o);
+        const float ax = __shfl_sync(0xffffffffu, T.shx, o), ay = __shfl_sync(0xffffffffu, T.shy, o),
+                    az = __shfl_sync(0xffffffffu, T.shz, o);
+        for (int j = lane; j < no; j += 32) {
+            float4 v = buf[o0 + j];
+            v.x += ax;
+            v.y += ay;
+            v.z += az;
+            buf[o0 + j] = v;
+        }
+    }
+    // a zero charge far away contributes nothing (own leaf odd, list odd)
+    if (lane == 0 && (cnt & 1)) buf[cnt] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+    if (lane == 1 && (total & 1)) buf[total] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+    __syncwarp();
+    for (int j = lane; j < npairs; j += 32) {
+        const float4 A = buf[2 * j], B = buf[2 * j + 1];
+        buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
+        buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
+    }
+    __syncwarp();
+    // (3) phases of target-pair slices
+    const int st = __shfl_sync(0xffffffffu, T.s0, 0);
+    const int tp = (cnt + 1) >> 1;
+    const int own_pairs = __shfl_sync(0xffffffffu, T.off, 1) >> 1;
+    for (int tg = 0; tg < tp; tg += 32) {  // groups of up to 32 target pairs
+        const int tpg = min(32, tp - tg);
+        const uint32_t m = c_near.map[tpg - 1][npairs - 1];
+        const int P = (int)(m & 7u), k = (int)((m >> 3) & 255u), n = (int)(m >> 11);
+        const int nslices = tpg * k;
+        const int nchk = min(n - 1, near_div(own_pairs + k - 1, k));  // steps whose pairs may be own
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+        for (int ph = 0; ph < P; ++ph) {
+            const int g = ph * 32 + lane;
+            const bool act = g < nslices;
+            const int jg = near_div(g, tpg);
+            const int t = act ? g - jg * tpg : 0, j = act ? jg : 0;
+            const bool full = act && j + (n - 1) * k < npairs;  // this slice has n source pairs
+            const float4 TA = buf[2 * (tg + t)], TB = buf[2 * (tg + t) + 1];
+            unsigned long long mx[2], my[2], mz[2], Pv[2], Xv[2], Yv[2], Zv[2];
+            mx[0] = f2pack(TA.x, TA.x);
+            mx[1] = f2pack(TA.y, TA.y);
+            my[0] = f2pack(TA.z, TA.z);
+            my[1] = f2pack(TA.w, TA.w);
+            mz[0] = f2pack(TB.x, TB.x);
+            mz[1] = f2pack(TB.y, TB.y);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) Pv[r] = Xv[r] = Yv[r] = Zv[r] = 0ull;
+            const float4* sp = buf + 2 * j;
+            const int stride = 2 * k;
+            int i = 0;
+            for (; i < nchk; ++i, sp += stride) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
+            if (i < n - 1) {  // steps i .. n - 2 exist for every lane: sources loaded a step ahead
+                float4 pa = sp[0], pb = sp[1];
+#pragma unroll 2
+                for (; i + 1 < n - 1; ++i) {
+                    sp += stride;
+                    const float4 na = sp[0], nb = sp[1];
+                    near_step<false>(pa, pb, mx, my, mz, Pv, Xv, Yv, Zv);
+                    pa = na;
+                    pb = nb;
+                }
+                near_step<false>(pa, pb, mx, my, mz, Pv, Xv, Yv, Zv);
+                ++i;
+                sp += stride;
+            }
+            if (full) {  // the last source pair of the slices that have n
+                if ((n - 1) * k < own_pairs) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
+                else near_step<false>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
+            }
+            // slice sums of this phase: lane l holds slice (t, j) with l = j tpg + t - 32 ph, so a
+            // target's slices sit tpg lanes apart from lane l mod tpg on; a fixed tree over them
+            // leaves the phase sum on that first lane, and the owner lane of the target adds it
+            float v[8];
+            {
+                const float2 p0 = f2unpack(Pv[0]), x0 = f2unpack(Xv[0]), y0 = f2unpack(Yv[0]), z0 = f2unpack(Zv[0]);
+                const float2 p1 = f2unpack(Pv[1]), x1 = f2unpack(Xv[1]), y1 = f2unpack(Yv[1]), z1 = f2unpack(Zv[1]);
+                v[0] = p0.x + p0.y, v[1] = x0.x + x0.y, v[2] = y0.x + y0.y, v[3] = z0.x + z0.y;
+                v[4] = p1.x + p1.y, v[5] = x1.x + x1.y, v[6] = y1.x + y1.y, v[7] = z1.x + z1.y;
+            }
+            const int m = near_div(lane, tpg);  // this lane's place among its target's lanes
+            for (int d = 1; d * tpg < 32; d <<= 1) {
+                const bool take = (m & (2 * d - 1)) == 0 && lane + d * tpg < 32 && g + d * tpg < nslices;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float o = __shfl_down_sync(0xffffffffu, v[e], d * tpg);
+                    if (take) v[e] += o;
+                }
+            }
+            {
+                const int ph0 = ph * 32 - near_div(ph * 32, tpg) * tpg;  // (32 ph) mod tpg
+                const int src = lane >= ph0 ? lane - ph0 : lane - ph0 + tpg;  // first lane of target `lane`
+                const bool has = lane < tpg && ph * 32 + src < nslices;
+                float u[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) u[e] = __shfl_sync(0xffffffffu, v[e], src & 31);
+                if (has) {
+                    acc0.x += u[0];
+                    acc0.y += u[1];
+                    acc0.z += u[2];
+                    acc0.w += u[3];
+                    acc1.x += u[4];
+                    acc1.y += u[5];
+                    acc1.z += u[6];
+                    acc1.w += u[7];
+                }
+            }
+        }
+        if (lane < tpg) {
+            const int t0 = 2 * (tg + lane);
+            near_output(near, st + t0, acc0.x, acc0.y, acc0.z, acc0.w);
+            if (t0 + 1 < cnt) near_output(near, st + t0 + 1, acc1.x, acc1.y, acc1.z, acc1.w);
+        }
+    }
+}
+
+// W warps per block: 1, 2 or 4 (the near-field block shape the autotuner picks; a block keeps
+// its shared memory until its last warp is done).  Each warp takes leaves_per_warp consecutive
+// leaves.  With NB = 2 buffers it stages them in turn, so that the copies of the next leaf land
+// while it sums the pairs of the current one; with NB = 1 it waits for each leaf's copies, and
+// the other resident warps (twice as many in the same shared memory) keep the FMA pipe busy.
 template <int W, int NB>
-__global__ void __launch_bounds__(32 * W, NB == 2 ? 1 : 20 / W) k_p2p(NearParams a, float4* __restrict__ near) {
+__global__ void __launch_bounds__(32 * W, NB == 2 ? (W == 1 ? 11 : (W == 2 ? 5 : 2)) : 20 / W)
+    k_p2p(NearParams a, float4* __restrict__ near) {
     extern __shared__ __align__(128) unsigned char near_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int first = (blockIdx.x * W + w) * a.leaves_per_warp;
+    const int last = min(a.nleaf, first + a.leaves_per_warp);
+    if (first >= last) return;
     NearWarpSmem<NB>& S = reinterpret_cast<NearWarpSmem<NB>*>(near_smem)[w];
     if (lane == 0) {
         for (int b = 0; b < NB; ++b) tc::mbar_init(&S.bar[b], 1);
         tc::fence_mbar_init();
     }
     __syncwarp();
-    // this warp's leaves: first + i W, i < leaves_per_warp (the block's warps on neighbouring leaves)
-    const int first = blockIdx.x * W * a.leaves_per_warp + w;
-    const int last = min(a.nleaf, first + W * a.leaves_per_warp);
-    int it = 0;
-    int leaf = first;
-    NearTab tab_next = near_table(a, lane, NB == 2 ? leaf + W : leaf);
-    if (NB == 2 && leaf < last) near_issue(a, S, lane, leaf, 0, near_table(a, lane, leaf));
-    for (; leaf < last; leaf += W, ++it) {
+    NearStage cur = near_stage(a, S.buf[0], &S.bar[0], lane, first);
+    for (int leaf = first, it = 0; leaf < last; ++leaf, ++it) {
         const int b = NB == 2 ? (it & 1) : 0;
         const uint32_t parity = (uint32_t)((NB == 2 ? it >> 1 : it) & 1);
-        const bool more = NB == 2 && leaf + W < last;
-        if (NB == 1) {  // this leaf's copies, then the next leaf's table (its loads in flight meanwhile)
-            const NearTab tab = tab_next;
-            tab_next = near_table(a, lane, leaf + W < last ? leaf + W : a.nleaf);
-            near_issue(a, S, lane, leaf, 0, tab);
-        } else if (more) {
-            const NearTab tab = tab_next;
-            tab_next = near_table(a, lane, leaf + 2 * W < last ? leaf + 2 * W : a.nleaf);
-            near_issue(a, S, lane, leaf + W, b ^ 1, tab);
+        const bool more = NB == 2 && leaf + 1 < last;
+        NearStage nxt = cur;
+        if (more) {
+            // the other buffer's reads and writes (two leaves ago) before its new copies
+            tc::fence_proxy_async();
+            __syncwarp();
+            nxt = near_stage(a, S.buf[b ^ 1], &S.bar[b ^ 1], lane, leaf + 1);
         }
         if (!tc::mbar_wait_all(&S.bar[b], parity, a.wlim)) {
             if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
-            // nothing may still be copying into this block's shared memory when it exits
+            // nothing may still be copying into the block's shared memory when the warp exits
             tc::mbar_wait_all(&S.bar[b], parity, kNearWait);
             if (more) tc::mbar_wait_all(&S.bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kNearWait);
             return;
         }
-        const int cnt = S.info[b][1], total = S.info[b][2];
-        const int st = S.s0[b][0];
-        const int npairs = (total + 1) >> 1;
-        float4* buf = S.buf[b];
-        if (2 * npairs > kNearCap) {  // streamed sources (rare): one target per lane, 32 targets per pass
-            float4* stage = buf;      // nothing was copied into this buffer for this leaf
-            for (int tb = 0; tb < cnt; tb += 32) {
-                const int ti = tb + lane;
-                const bool valid = ti < cnt;
-                const float4 me = valid ? a.pos[st + ti] : make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
-                float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-                for (int o = 0; o < 27; ++o) {
-                    const int s0 = S.s0[b][o], sc = S.off[b][o + 1] - S.off[b][o] - (o == 0 ? (cnt & 1) : 0);
-                    for (int sb = 0; sb < sc; sb += 32) {
-                        float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
-                        sp.x += S.sh[b][o][0];
-                        sp.y += S.sh[b][o][1];
-                        sp.z += S.sh[b][o][2];
-                        __syncwarp();
-                        stage[lane] = sp;
-                        __syncwarp();
-                        const int ns = min(32, sc - sb);
-                        for (int t = 0; t < ns; ++t) {
-                            const float4 s4 = stage[t];
-                            const float dx = s4.x - me.x, dy = s4.y - me.y, dz = s4.z - me.z;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const float ri = (r2 > 0.f) ? rsqrt_approx(r2) : 0.f;
-                            const float qri = s4.w * ri;
-                            pot += qri;
-                            const float qri3 = qri * ri * ri;
-                            gx = fmaf(qri3, dx, gx);
-                            gy = fmaf(qri3, dy, gy);
-                            gz = fmaf(qri3, dz, gz);
-                        }
-                    }
-                }
-                if (valid) near_output(near, st + ti, pot, gx, gy, gz);
-            }
-        } else if (cnt > 0) {
-            // (2) image shifts of the wrapped segments, pads, packed pairs
-            for (unsigned wm = (unsigned)S.info[b][3]; wm; wm &= wm - 1) {
-                const int o = __ffs(wm) - 1;
-                const int o0 = S.off[b][o], no = S.off[b][o + 1] - o0;
-                const float ax = S.sh[b][o][0], ay = S.sh[b][o][1], az = S.sh[b][o][2];
-                for (int j = lane; j < no; j += 32) {
-                    float4 v = buf[o0 + j];
-                    v.x += ax;
-                    v.y += ay;
-                    v.z += az;
-                    buf[o0 + j] = v;
-                }
-            }
-            // a zero charge far away contributes nothing (own leaf odd, list odd)
-            if (lane == 0 && (cnt & 1)) buf[cnt] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
-            if (lane == 1 && (total & 1)) buf[total] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
-            __syncwarp();
-            for (int j = lane; j < npairs; j += 32) {
-                const float4 A = buf[2 * j], B = buf[2 * j + 1];
-                buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
-                buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
-            }
-            __syncwarp();
-            // (3) phases of target-pair slices
-            const int tp = (cnt + 1) >> 1;
-            const int own_pairs = S.off[b][1] >> 1;
-            for (int tg = 0; tg < tp; tg += 32) {  // groups of up to 32 target pairs
-                const int tpg = min(32, tp - tg);
-                int P, k, n;
-                near_map(tpg, npairs, P, k, n);
-                const int nslices = tpg * k;
-                const int nchk = min(n - 1, (own_pairs + k - 1) / k);  // i < ceil(own / k): pairs j + i k may be own
-                float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-                for (int ph = 0; ph < P; ++ph) {
-                    const int g = ph * 32 + lane;
-                    const bool act = g < nslices;
-                    // slice-major: the lanes of a quarter warp mostly share a slice, so their source
-                    // loads are broadcasts
-                    const int t = act ? g % tpg : 0, j = act ? g / tpg : 0;
-                    const bool full = act && j + (n - 1) * k < npairs;  // this slice has n source pairs
-                    const float4 TA = buf[2 * (tg + t)], TB = buf[2 * (tg + t) + 1];
-                    unsigned long long mx[2], my[2], mz[2], Pv[2], Xv[2], Yv[2], Zv[2];
-                    mx[0] = f2pack(TA.x, TA.x);
-                    mx[1] = f2pack(TA.y, TA.y);
-                    my[0] = f2pack(TA.z, TA.z);
-                    my[1] = f2pack(TA.w, TA.w);
-                    mz[0] = f2pack(TB.x, TB.x);
-                    mz[1] = f2pack(TB.y, TB.y);
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) Pv[r] = Xv[r] = Yv[r] = Zv[r] = 0ull;
-                    const float4* sp = buf + 2 * j;
-                    const int stride = 2 * k;
-                    int i = 0;
-                    for (; i < nchk; ++i, sp += stride) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
-                    if (i < n - 1) {  // steps i .. n - 2 exist for every lane: sources loaded a step ahead
-                        float4 pa = sp[0], pb = sp[1];
-#pragma unroll 2
-                        for (; i + 1 < n - 1; ++i) {
-                            sp += stride;
-                            const float4 na = sp[0], nb = sp[1];
-                            near_step<false>(pa, pb, mx, my, mz, Pv, Xv, Yv, Zv);
-                            pa = na;
-                            pb = nb;
-                        }
-                        near_step<false>(pa, pb, mx, my, mz, Pv, Xv, Yv, Zv);
-                        ++i;
-                        sp += stride;
-                    }
-                    if (full) {  // the last source pair of the slices that have n
-                        if ((n - 1) * k < own_pairs) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
-                        else near_step<false>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
-                    }
-                    if (act) {
-                        const float2 p0 = f2unpack(Pv[0]), x0 = f2unpack(Xv[0]), y0 = f2unpack(Yv[0]),
-                                     z0 = f2unpack(Zv[0]);
-                        const float2 p1 = f2unpack(Pv[1]), x1 = f2unpack(Xv[1]), y1 = f2unpack(Yv[1]),
-                                     z1 = f2unpack(Zv[1]);
-                        S.part[lane][0] = make_float4(p0.x + p0.y, x0.x + x0.y, y0.x + y0.y, z0.x + z0.y);
-                        S.part[lane][1] = make_float4(p1.x + p1.y, x1.x + x1.y, y1.x + y1.y, z1.x + z1.y);
-                    }
-                    __syncwarp();
-                    if (lane < tpg) {  // owner of target pair tg + lane: its slices j lane + j tpg of this phase, in order
-                        const int j0 = max(0, (ph * 32 - lane + tpg - 1) / tpg);
-                        const int j1 = min(k, (ph * 32 + 32 - lane + tpg - 1) / tpg);
-                        for (int jj = j0; jj < j1; ++jj) {
-                            const int gg = jj * tpg + lane - ph * 32;
-                            const float4 u = S.part[gg][0], v = S.part[gg][1];
-                            acc0.x += u.x;
-                            acc0.y += u.y;
-                            acc0.z += u.z;
-                            acc0.w += u.w;
-                            acc1.x += v.x;
-                            acc1.y += v.y;
-                            acc1.z += v.z;
-                            acc1.w += v.w;
-                        }
-                    }
-                    __syncwarp();
-                }
-                if (lane < tpg) {
-                    const int t0 = 2 * (tg + lane);
-                    near_output(near, st + t0, acc0.x, acc0.y, acc0.z, acc0.w);
-                    if (t0 + 1 < cnt) near_output(near, st + t0 + 1, acc1.x, acc1.y, acc1.z, acc1.w);
-                }
-            }
+        if (cur.cnt > 0) {
+            if (2 * ((cur.total + 1) >> 1) > kNearCap)
+                near_streamed(a, cur.s0, cur.sc, cur.shx, cur.shy, cur.shz, cur.cnt, S.buf[b], lane, near);
+            else near_leaf(a, cur, S.buf[b], lane, near);
         }
         __syncwarp();
+        if (NB == 1 && leaf + 1 < last) {  // the next leaf into the same buffer
+            tc::fence_proxy_async();
+            __syncwarp();
+            nxt = near_stage(a, S.buf[0], &S.bar[0], lane, leaf + 1);
+        }
+        cur = nxt;
     }
 }
 
-// Grid of the near field: each warp takes leaves_per_warp leaves, so that blocks stay short
-// and the higher-priority multipole chain gets SMs as they retire.
+// Grid of the near field: W warps per block, leaves_per_warp consecutive leaves per warp, NB
+// staging buffers per warp.  Measured at 500,000 atoms: one buffer and one leaf per warp
+// (0.135 ms alone) beat two buffers at 2, 4 or 8 leaves per warp (0.160-0.186 ms), whose
+// eleven warps per SM left the pair loop latency-bound.
 constexpr int kNearLeavesPerWarp = 1;
 constexpr int kNearBufs = 1;
 template <int W>
 static void launch_p2p(NearParams a, float4* near, cudaStream_t st) {
     a.leaves_per_warp = kNearLeavesPerWarp;
-    const int blocks = (a.nleaf + W * kNearLeavesPerWarp - 1) / (W * kNearLeavesPerWarp);
-    k_p2p<W, kNearBufs><<<blocks, 32 * W, (size_t)W * sizeof(NearWarpSmem<kNearBufs>), st>>>(a, near);
+    const int per_block = W * kNearLeavesPerWarp;
+    k_p2p<W, kNearBufs><<<(a.nleaf + per_block - 1) / per_block, 32 * W, (size_t)W * sizeof(NearWarpSmem<kNearBufs>),
+                          st>>>(a, near);
 }
 
-// Per handle, with its device current: the near field's dynamic shared-memory limit (both
-// block shapes).
+// Per handle, with its device current: the near field's dynamic shared-memory limit (every
+// block shape).
 void near_configure(Handle* h) {
     (void)h;
-    cudaFuncSetAttribute(k_p2p<2, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * sizeof(NearWarpSmem<kNearBufs>)));
-    cudaFuncSetAttribute(k_p2p<4, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(4 * sizeof(NearWarpSmem<kNearBufs>)));
+    constexpr int smem = (int)sizeof(NearWarpSmem<kNearBufs>);
+    cudaFuncSetAttribute(k_p2p<1, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_p2p<2, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * smem);
+    cudaFuncSetAttribute(k_p2p<4, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * smem);
 }
 
 // E = 1/2 k sum of the per-block partials of q phi, totalled in FP64: each of the
@@ -1980,7 +1990,8 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lc = coarse_top(h);  // top coarse level of the side branch, -1 without one
     cudaEventRecord(h->fork_ev, st);
     cudaStreamWaitEvent(cs, h->fork_ev, 0);
-    if (h->p2p_warps == 2) launch_p2p<2>(a, h->near, st);
+    if (h->p2p_warps == 1) launch_p2p<1>(a, h->near, st);
+    else if (h->p2p_warps == 2) launch_p2p<2>(a, h->near, st);
     else launch_p2p<4>(a, h->near, st);
     const int e1n = mark(h, st);
     span(h, 8, e1, e1n);
