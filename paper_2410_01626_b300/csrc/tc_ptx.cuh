@@ -71,29 +71,6 @@ __device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity
     return true;
 }
 
-// Bounded wait for a phase that is expected to take microseconds (copies from L2): each try
-// lets the thread sleep until the phase completes or about hint_ns pass, so that a waiting warp
-// takes no issue slots from the warps of its SM sub-partition that are computing.
-__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_sleep_all(uint64_t* bar, uint32_t parity, long long limit,
-                                                    uint32_t hint_ns) {
-    bool done = mbar_try_wait_hint(bar, parity, hint_ns);
-    if (!done) {
-        const long long t0 = clock64();
-        while (!(done = mbar_try_wait_hint(bar, parity, hint_ns)))
-            if (clock64() - t0 > limit) break;
-    }
-    return __all_sync(0xffffffffu, done);
-}
-
 // Bounded waits that also give up when another role of the CTA has set the shared abort flag
 // (read only while the barrier is not yet complete, so the fast path is unchanged).  They
 // return true only when the phase has completed.
