@@ -353,15 +353,27 @@ def run_native(args):
             e1.record(stream)
             torch.cuda.synchronize()
             tms.append(e0.elapsed_time(e1))
+        m2l_alone = None
+        if prec == "fp32":  # the CUDA-core M2L alone (every level), for its roofline
+            g.set_profiling(True, serial=True)
+            runs = []
+            for _ in range(3):
+                flush.zero_()
+                g.eval_into(t["x"], Eg, Fg, dVg)
+                runs.append(g.stage_times()["m2l"])
+            g.set_profiling(False)
+            m2l_alone = statistics.median(runs)
         g.close()
-        return ws * 1000.0 / (sum(tms) / len(tms)), (Eg, Fg, dVg)
+        return ws * 1000.0 / (sum(tms) / len(tms)), (Eg, Fg, dVg), m2l_alone
 
     modes = {precision: {"evals_per_s": value, "out": (E, F, dV)}}
     for prec in ("fp32", "tf32", "3xtf32", "3xbf16", "fp16"):
         if prec not in modes:
             try:
-                v, o = time_mode(prec, min(args.steps, 10))
+                v, o, m2l_alone = time_mode(prec, min(args.steps, 10))
                 modes[prec] = {"evals_per_s": v, "out": o}
+                if m2l_alone:
+                    modes[prec]["m2l_alone_ms"] = m2l_alone
             except Exception as exc:  # mode not offered for this p / depth
                 modes[prec] = {"error": str(exc)}
     # sites with two lambda coordinates over four charge forms (Sec. 2.1 Eq. 2): half the sites
@@ -392,7 +404,7 @@ def run_native(args):
     # the Hamiltonian-interpolation form (intra-site correction, Sec. 2.1 Eq. 1) in the default precision
     hname = precision + "+hamiltonian"
     try:
-        v, o = time_mode(precision, min(args.steps, 10), interpolation="hamiltonian")
+        v, o, _ = time_mode(precision, min(args.steps, 10), interpolation="hamiltonian")
         modes[hname] = {"evals_per_s": v, "out": o, "hamiltonian": True}
     except Exception as exc:
         modes[hname] = {"error": str(exc)}
@@ -541,6 +553,14 @@ def run_native(args):
                 "F_rms": float(np.sqrt(((Fs - r["F"]) ** 2).sum() / (r["F"] ** 2).sum())),
                 "dVdl": float(np.linalg.norm(dVm.double().cpu().numpy() - r["dVdl"]) / np.linalg.norm(r["dVdl"])),
                 "atoms_compared": int(len(idx))}
+    m32 = modes.get("fp32", {})
+    if m32.get("m2l_alone_ms"):  # the FP32 CUDA-core M2L (every level), alone, against the FP32 pipe
+        f32_flop = sum(8 ** l for l in range(1, s["depth"] + 1)) * 189 * 2 * nc * nc
+        f32_ach = f32_flop / (m32["m2l_alone_ms"] * 1e-3) / 1e12
+        m32["roofline_m2l"] = {"bound": "alu", "achieved": f32_ach, "peak": p2p_peak, "unit": "TFLOP/s",
+                               "frac": f32_ach / p2p_peak, "flop_per_launch": f32_flop,
+                               "peak_source": roof_p2p["peak_source"],
+                               "kernel": "FP32 CUDA-core M2L (k_m2l_f32 + k_sum8), every level, alone"}
     for prec, m in modes.items():
         if ("out" in m and prec != "fp32" and not m.get("hamiltonian") and "system" not in m
                 and "out" in modes.get("fp32", {})):

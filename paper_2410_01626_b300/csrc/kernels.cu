@@ -831,7 +831,16 @@ __global__ void k_m2l_fp32(const M2LTile* __restrict__ tiles, int nc, int ncp, c
 // writes its partial local expansions to part[pi]; k_sum8 adds the eight partials in a fixed
 // order into L.
 constexpr int kF32KC = 16;
-constexpr int kF32Halo = 6 * 6 * 10;
+// The source halo of a 4 x 4 x 8 brick (6 x 6 x 10 boxes) in shared memory, three times: copy s
+// holds the boxes z + s at z, so that a thread's pencil of 8 boxes at any z shift is two aligned
+// 16-byte loads.  A pencil row is 12 floats (16-byte aligned), a plane 80 floats (the 8 pencils
+// of a warp then fall in 8 distinct 4-bank groups).
+constexpr int kF32Row = 12, kF32Plane = 80;
+constexpr int kF32Halo = 6 * kF32Plane;
+struct F32Smem {
+    float hs[3][kF32KC][kF32Halo];
+    __align__(16) float ts[2][kF32KC][128];
+};
 
 void f32_bricks(int lmin, int depth, std::vector<F32Brick>& out) {
     out.clear();
@@ -883,8 +892,9 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
                                                     const float* __restrict__ T, const float* __restrict__ M,
                                                     float* __restrict__ part, long part_stride, LevelOffsets lo,
                                                     int periodic) {
-    __shared__ float hs[kF32KC][kF32Halo];
-    __shared__ __align__(16) float ts[2][kF32KC][128];
+    extern __shared__ __align__(16) unsigned char f32_smem[];
+    F32Smem& sm = *reinterpret_cast<F32Smem*>(f32_smem);
+    auto& ts = sm.ts;
     const F32Brick br = bricks[blockIdx.x];
     const int n = 1 << (br.level - 1);
     const int cx = br.cls & 1, cy = (br.cls >> 1) & 1, cz = (br.cls >> 2) & 1;
@@ -898,9 +908,9 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
     const int w = tid >> 5, lane = tid & 31;
     const int tc = 4 * (w & 3) + (lane & 3), tb = 8 * (w >> 2) + (lane >> 2);
     const bool cact = 8 * tc < ncp;
-    // the thread's 8 boxes are the pencil (i, j) = (tb / 4, tb % 4), k = 0..7: halo entries
-    // hb0 + e at delta = (-1, -1, -1)
-    const int hb0 = ((tb >> 2) * hy + (tb & 3)) * hz;
+    // the thread's 8 boxes are the pencil (i, j) = (tb / 4, tb % 4), k = 0..7: halo row of plane
+    // i + dx + 1, row j + dy + 1, entries dz + 1 .. dz + 8 (copy dz + 1 from its start)
+    const int hb0 = (tb >> 2) * kF32Plane + (tb & 3) * kF32Row;
     // accumulators in coefficient pairs (2 a, 2 a + 1) x 8 boxes, updated with f32x2 FMAs: half
     // the FMA instructions of scalar code for the same FMA-pipe work; every element is still one
     // FP32 FMA per term, in the same order
@@ -930,7 +940,10 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
                 }
                 float v = 0.f;
                 if (ok) v = Ml[(long)morton3(2 * si + px, 2 * sj + py, 2 * sk + pz) * ncp + kc * kF32KC + kk];
-                hs[kk][hbx] = v;
+                const int q = hi * kF32Plane + hj * kF32Row + hk;
+#pragma unroll
+                for (int c3 = 0; c3 < 3; ++c3)
+                    if (hk >= c3) sm.hs[c3][kk][q - c3] = v;
             }
             // the valid shifts of (c, pi): a bit per delta; operator chunks double-buffered --
             // the next shift's chunk is read into registers while the current one is used
@@ -973,18 +986,18 @@ __global__ void __launch_bounds__(256, 2) k_m2l_f32(const F32Brick* __restrict__
                 m &= m - 1;
                 if (dn >= 0) fetch(dn);
                 const int dx = d / 9 - 1, dy = (d / 3) % 3 - 1, dz = d % 3 - 1;
-                const int so = ((dx + 1) * hy + (dy + 1)) * hz + (dz + 1);
+                const int so = (dx + 1) * kF32Plane + (dy + 1) * kF32Row;
+                const float* hcopy = &sm.hs[dz + 1][0][0];
                 if (cact) {
-#pragma unroll 4
+#pragma unroll 8
                     for (int k = 0; k < kF32KC; ++k) {
                         const float4 a0 = *reinterpret_cast<const float4*>(&ts[cur][k][8 * tc]);
                         const float4 a1 = *reinterpret_cast<const float4*>(&ts[cur][k][8 * tc + 4]);
                         const unsigned long long A0 = f2pack(a0.x, a0.y), A1 = f2pack(a0.z, a0.w),
                                                  A2 = f2pack(a1.x, a1.y), A3 = f2pack(a1.z, a1.w);
-                        float bv[8];
-                        const float* hrow = &hs[k][hb0 + so];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) bv[e] = hrow[e];
+                        const float4* hrow = reinterpret_cast<const float4*>(hcopy + k * kF32Halo + hb0 + so);
+                        const float4 b0 = hrow[0], b1 = hrow[1];
+                        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             const unsigned long long B = f2pack(bv[e], bv[e]);
@@ -1725,10 +1738,11 @@ static void launch_p2p(NearParams a, float4* near, cudaStream_t st) {
                           st>>>(a, near);
 }
 
-// Per handle, with its device current: the near field's dynamic shared-memory limit (every
-// block shape).
+// Per handle, with its device current: the dynamic shared-memory limits of the near field
+// (every block shape) and of the FP32 M2L.
 void near_configure(Handle* h) {
     (void)h;
+    cudaFuncSetAttribute(k_m2l_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F32Smem));
     constexpr int smem = (int)sizeof(NearWarpSmem<kNearBufs>);
     cudaFuncSetAttribute(k_p2p<1, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_p2p<2, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * smem);
@@ -2074,8 +2088,8 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
                     // partials of every level lmin .. d (the part of the level arrays from lmin on)
                     const long a0 = h->lvl_off[lmin] * h->ncp, n = (h->lvl_off[d + 1] - h->lvl_off[lmin]) * h->ncp;
                     const long stride = h->nbox_total * h->ncp;
-                    k_m2l_f32<<<dim3(h->nbricks, 8), 256, 0, cs>>>(h->bricks, h->ncp, h->T, h->M, h->m2l_part, stride,
-                                                                   lo, h->periodic);
+                    k_m2l_f32<<<dim3(h->nbricks, 8), 256, sizeof(F32Smem), cs>>>(h->bricks, h->ncp, h->T, h->M,
+                                                                                h->m2l_part, stride, lo, h->periodic);
                     k_sum8<<<std::min<long>((n / 4 + 255) / 256, 148L * 16), 256, 0, cs>>>(
                         n / 4, reinterpret_cast<const float4*>(h->m2l_part + a0), stride / 4,
                         reinterpret_cast<float4*>(h->L + a0));
