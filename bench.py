@@ -7,7 +7,7 @@ M2L, L2L, L2P + P2P, reductions) of the solvated 500,000-atom periodic system
 with 200 titratable sites; p = 10, depth 5), from unsorted positions in HBM
 to E, F (input order) and dV/dlambda.  Synthetic, seeded inputs.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32|3xtf32|3xbf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32|3xtf32|3xbf16|fp16]
   python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
 
 Under torchrun (N > 1) every rank evaluates its own replica of the system
@@ -672,7 +672,7 @@ def run_loop(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = "3xbf16" if args.precision == "auto" else args.precision
+    prec = "fp16" if args.precision == "auto" else args.precision
     s = synth.solvated_500k()
     t = {k: torch.from_numpy(np.ascontiguousarray(s[k])).to(dev) for k in ("x", "qA", "qB", "site", "lam")}
     f = FMM(s["L"], True, s["p"], s["depth"], precision=prec)
