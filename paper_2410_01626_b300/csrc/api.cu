@@ -80,6 +80,8 @@ void free_atoms(Handle& h) {
     dfree(h.dq);
     dfree(h.phis);
     dfree(h.near);
+    dfree(h.near_items);
+    h.near_items_cap = 0;
     dfree(h.qC);
     dfree(h.qD);
     dfree(h.dqt);
@@ -467,12 +469,17 @@ static fmm_status set_charges_impl(fmm_handle* H, int n, int K, int nforms, cons
         if ((e = dalloc(&h.qA, n)) || (e = dalloc(&h.qB, n)) || (e = dalloc(&h.site, n)) || (e = dalloc(&h.key, n)) ||
             (e = dalloc(&h.kA, n)) || (e = dalloc(&h.kB, n)) || (e = dalloc(&h.vA, n)) || (e = dalloc(&h.vB, n)) ||
             (e = dalloc(&h.inv, n)) || (e = dalloc(&h.pos, n)) || (e = dalloc(&h.dq, n)) ||
-            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.near, n)) ||
+            (e = dalloc(&h.phis, n)) || (e = dalloc(&h.near, n)) || (e = dalloc(&h.near_items, n / 32 + 2)) ||
             (nforms == 4 && ((e = dalloc(&h.qC, n)) || (e = dalloc(&h.qD, n)) || (e = dalloc(&h.dqt, n))))) {
             free_atoms(h);
             return e;
         }
         h.cap = n;
+        h.near_items_cap = n / 32 + 1;
+        if ((e = cuda_ok(cudaMemset(h.near_items, 0, sizeof(int2))))) {
+            free_atoms(h);
+            return e;
+        }
     }
     {  // one q phi partial per 128 atoms (k_far_out blocks)
         const int nparts = (n + 127) / 128;

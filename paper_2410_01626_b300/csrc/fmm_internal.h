@@ -94,6 +94,10 @@ struct Handle {
     float* dq = nullptr;
     float* phis = nullptr;   // sorted-order potential (without k_e)
     float4* near = nullptr;  // sorted-order near-field potential and gradient (k_p2p -> k_far_out)
+    // the near field's work items (leaf, tile) of leaves above 64 atoms: count in [0].x, then the
+    // items (listed by the binning)
+    int2* near_items = nullptr;
+    int near_items_cap = 0;
     float2* epart = nullptr;  // per-block (hi, lo) partial sums of q phi
     int epart_cap = 0;
     float* leafmom = nullptr;   // [nleaf][kLeafMomStride] periodic: leaf moments for the Q, D, T sums

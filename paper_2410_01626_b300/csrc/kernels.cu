@@ -168,8 +168,9 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(int n, const float*
                                                              uint32_t* __restrict__ key, uint32_t* __restrict__ slot,
                                                              uint32_t* __restrict__ leafcnt, int ntiles,
                                                              uint32_t* __restrict__ tilecnt,
-                                                             int* __restrict__ status) {
+                                                             int* __restrict__ status, int2* __restrict__ items) {
     __shared__ uint32_t hist[kMaxScanTiles];
+    if (items && blockIdx.x == 0 && threadIdx.x == 0) items[0].x = 0;  // the near field's item list (k_bin_order_gather)
     for (int t = threadIdx.x; t < ntiles; t += kCountThreads) hist[t] = 0u;
     __syncthreads();
     const int i = blockIdx.x * kCountThreads + threadIdx.x;
@@ -320,18 +321,32 @@ __device__ __forceinline__ void gather_atom(int i, int s, const float* __restric
     inv[i] = (uint32_t)s;
 }
 
+// The near field takes leaves with more than kNearTile atoms in tiles of kNearTile targets, listed
+// by the binning (k_bin_order_gather) as items (leaf, tile) after a count in items[0].x.
+constexpr int kNearTile = 64;
+
 __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint32_t* __restrict__ start,
                                                           const uint32_t* __restrict__ count,
                                                           const uint32_t* __restrict__ placed,
                                                           uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
                                                           const float* __restrict__ x, BoxGeom g, ChargeForms cf,
                                                           float4* __restrict__ pos, uint32_t* __restrict__ inv,
-                                                          int* __restrict__ status) {
+                                                          int* __restrict__ status, int2* __restrict__ items,
+                                                          int items_cap) {
     // a warp takes leaves l0 and l0 + 1
     const int l0 = 2 * (blockIdx.x * 4 + (threadIdx.x >> 5)), lane = threadIdx.x & 31;
     if (l0 >= nleaf) return;
     const bool two = l0 + 1 < nleaf;
     const int c0 = (int)count[l0], c1 = two ? (int)count[l0 + 1] : 0;
+    if (lane == 0 && items) {  // the near field's work items of leaves above kNearTile atoms
+        for (int q = 0; q < (two ? 2 : 1); ++q) {
+            const int c = q ? c1 : c0;
+            if (c <= kNearTile) continue;
+            const int nt = (c + kNearTile - 1) / kNearTile;
+            const int base = atomicAdd(&items[0].x, nt);
+            for (int t = 0; t < nt && base + t < items_cap; ++t) items[1 + base + t] = make_int2(l0 + q, t);
+        }
+    }
     if (c0 <= 16 && c1 <= 16) {  // one leaf per half-warp, one atom per lane
         const int half = lane >> 4, sub = lane & 15, c = half ? c1 : c0;
         const int leaf = l0 + half;
@@ -1103,6 +1118,8 @@ struct NearParams {
     int* status;     // device status word (FMM_DEV_TIMEOUT when a near-field staging wait expires)
     long long wlim;       // bound of the near field's staging waits (clock cycles)
     int leaves_per_warp;  // consecutive target leaves of each near-field warp
+    const int2* items;    // work items (leaf, tile) of the leaves above kNearTile atoms, count in items[0].x
+    int items_cap;
 };
 
 // Outputs per atom, one thread per atom in leaf order: the far field (L2P of the leaf's local
@@ -1371,9 +1388,10 @@ static void launch_hi(const HiParams& hp, cudaStream_t st) {
 //     equal positions always share a leaf.  After each phase a fixed shuffle tree adds each
 //     target's slice sums and the owner lane of the target pair adds the result: a fixed order,
 //     so results are bitwise reproducible for every block shape.
-// Leaves whose neighbourhood does not fit a buffer (kNearCap atoms) stream their sources from
-// global memory instead, one target per lane.  k_far_out adds the far field and writes the
-// outputs.
+// Leaves whose neighbourhood does not fit a buffer (kNearCap atoms) stage it in rounds of
+// neighbour segments, the own leaf kept at the start of the buffer (near_rounds); only leaves whose
+// own atoms or single neighbours are too many even for that stream their sources from global
+// memory, one target per lane.  k_far_out adds the far field and writes the outputs.
 constexpr int kNearCap = 592;                   // staged atoms per buffer (neighbourhood + 2 pads)
 constexpr int kNearMaxPairs = kNearCap / 2;     // source pairs of a staged neighbourhood
 constexpr long long kNearWait = 4000000000LL;  // default bound of the staging wait (clock cycles, about 2 s)
@@ -1466,11 +1484,9 @@ struct NearStage {
     unsigned wrap;   // segments with a nonzero image shift
 };
 
-// (1): the segment table of `leaf` and, when the neighbourhood fits a buffer, the bulk copies of
-// its segments into buf, completing on bar.  The caller has ordered the buffer's earlier
-// generic-proxy accesses before these asynchronous writes.
-__device__ __forceinline__ NearStage near_stage(const NearParams& a, float4* buf, uint64_t* bar, int lane,
-                                                int leaf) {
+// (1), the segment table of `leaf`: lane o < 27 gets neighbour segment o (segment 0 = the own
+// leaf), its offset in a buffer that holds all of them (the own leaf padded to even).
+__device__ __forceinline__ NearStage near_segments(const NearParams& a, int lane, int leaf) {
     const int nb = 1 << a.depth;
     NearStage t{0, 0, 0, 0.f, 0.f, 0.f, 0, 0, 0u};
     if (lane < 27) {  // lane 0 = own leaf (offset 13), lanes 1..26 = the others
@@ -1498,7 +1514,17 @@ __device__ __forceinline__ NearStage near_stage(const NearParams& a, float4* buf
     t.total = __shfl_sync(0xffffffffu, incl, 31);
     t.cnt = __shfl_sync(0xffffffffu, t.sc, 0);
     t.wrap = __ballot_sync(0xffffffffu, lane < 27 && t.sc > 0 && (t.shx != 0.f || t.shy != 0.f || t.shz != 0.f));
-    const bool staged = t.cnt > 0 && ((t.total + 1) & ~1) <= kNearCap;  // nothing to stage without targets
+    return t;
+}
+
+// (1): the segment table of `leaf` and, when the neighbourhood fits a buffer, the bulk copies of
+// its segments into buf, completing on bar.  The caller has ordered the buffer's earlier
+// generic-proxy accesses before these asynchronous writes.
+__device__ __forceinline__ NearStage near_stage(const NearParams& a, float4* buf, uint64_t* bar, int lane,
+                                                int leaf) {
+    const NearStage t = near_segments(a, lane, leaf);
+    // nothing to stage without targets, or for a leaf that k_p2p_big takes
+    const bool staged = t.cnt > 0 && t.cnt <= kNearTile && ((t.total + 1) & ~1) <= kNearCap;
     if (lane == 0) tc::mbar_arrive_expect_tx(bar, staged ? 16u * (uint32_t)(t.total - (t.cnt & 1)) : 0u);
     __syncwarp();
     if (staged && lane < 27 && t.sc > 0) tc::bulk_g2s(buf + t.off, a.pos + t.s0, 16u * (uint32_t)t.sc, bar);
@@ -1547,52 +1573,26 @@ __device__ __noinline__ void near_streamed(const NearParams& a, int seg_s0, int 
     }
 }
 
-// (2) and (3) for one staged leaf in buf: image shifts of the wrapped segments, pads, packed
-// pairs, then the phases of target-pair slices; writes the leaf's near-field outputs.
-__device__ __forceinline__ void near_leaf(const NearParams& a, const NearStage& T, float4* buf, int lane,
-                                          float4* __restrict__ near) {
-    const int cnt = T.cnt, total = T.total;
-    const int npairs = (total + 1) >> 1;
-    for (unsigned wm = T.wrap; wm; wm &= wm - 1) {
-        const int o = __ffs(wm) - 1;
-        const int o0 = __shfl_sync(0xffffffffu, T.off, o), no = __shfl_sync(0xffffffffu, T.sc, o);
-        const float ax = __shfl_sync(0xffffffffu, T.shx, o), ay = __shfl_sync(0xffffffffu, T.shy, o),
-                    az = __shfl_sync(0xffffffffu, T.shz, o);
-        for (int j = lane; j < no; j += 32) {
-            float4 v = buf[o0 + j];
-            v.x += ax;
-            v.y += ay;
-            v.z += az;
-            buf[o0 + j] = v;
-        }
-    }
-    // a zero charge far away contributes nothing (own leaf odd, list odd)
-    if (lane == 0 && (cnt & 1)) buf[cnt] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
-    if (lane == 1 && (total & 1)) buf[total] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
-    __syncwarp();
-    for (int j = lane; j < npairs; j += 32) {
-        const float4 A = buf[2 * j], B = buf[2 * j + 1];
-        buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
-        buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
-    }
-    __syncwarp();
-    // (3) phases of target-pair slices
-    const int st = __shfl_sync(0xffffffffu, T.s0, 0);
+// (3) for a staged source list: the phases of target-pair slices over the source pairs
+// [sb, sb + np) of buf, of which the first nck may be own pairs (the r > 0 test); the targets
+// are the own leaf's pairs at the start of buf.  Writes the outputs of the leaf's cnt target
+// atoms (sorted slots st ..), or adds to them (add: a later round of the same leaf).
+__device__ __forceinline__ void near_phases(const float4* buf, int lane, int cnt, int st, int sb, int np, int nck,
+                                            bool add, float4* __restrict__ near) {
     const int tp = (cnt + 1) >> 1;
-    const int own_pairs = __shfl_sync(0xffffffffu, T.off, 1) >> 1;
     for (int tg = 0; tg < tp; tg += 32) {  // groups of up to 32 target pairs
         const int tpg = min(32, tp - tg);
-        const uint32_t m = c_near.map[tpg - 1][npairs - 1];
+        const uint32_t m = c_near.map[tpg - 1][np - 1];
         const int P = (int)(m & 7u), k = (int)((m >> 3) & 255u), n = (int)(m >> 11);
         const int nslices = tpg * k;
-        const int nchk = min(n - 1, near_div(own_pairs + k - 1, k));  // steps whose pairs may be own
+        const int nchk = min(n - 1, near_div(nck + k - 1, k));  // steps whose pairs may be own
         float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
         for (int ph = 0; ph < P; ++ph) {
             const int g = ph * 32 + lane;
             const bool act = g < nslices;
             const int jg = near_div(g, tpg);
             const int t = act ? g - jg * tpg : 0, j = act ? jg : 0;
-            const bool full = act && j + (n - 1) * k < npairs;  // this slice has n source pairs
+            const bool full = act && j + (n - 1) * k < np;  // this slice has n source pairs
             const float4 TA = buf[2 * (tg + t)], TB = buf[2 * (tg + t) + 1];
             unsigned long long mx[2], my[2], mz[2], Pv[2], Xv[2], Yv[2], Zv[2];
             mx[0] = f2pack(TA.x, TA.x);
@@ -1603,7 +1603,7 @@ __device__ __forceinline__ void near_leaf(const NearParams& a, const NearStage& 
             mz[1] = f2pack(TB.y, TB.y);
 #pragma unroll
             for (int r = 0; r < 2; ++r) Pv[r] = Xv[r] = Yv[r] = Zv[r] = 0ull;
-            const float4* sp = buf + 2 * j;
+            const float4* sp = buf + 2 * (sb + j);
             const int stride = 2 * k;
             int i = 0;
             for (; i < nchk; ++i, sp += stride) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
@@ -1622,7 +1622,7 @@ __device__ __forceinline__ void near_leaf(const NearParams& a, const NearStage& 
                 sp += stride;
             }
             if (full) {  // the last source pair of the slices that have n
-                if ((n - 1) * k < own_pairs) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
+                if ((n - 1) * k < nck) near_step<true>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
                 else near_step<false>(sp[0], sp[1], mx, my, mz, Pv, Xv, Yv, Zv);
             }
             // slice sums of this phase: lane l holds slice (t, j) with l = j tpg + t - 32 ph, so a
@@ -1665,11 +1665,226 @@ __device__ __forceinline__ void near_leaf(const NearParams& a, const NearStage& 
         }
         if (lane < tpg) {
             const int t0 = 2 * (tg + lane);
+            if (add) {  // a later round of the same leaf: add to the earlier rounds' sums
+                const float4 u = near[st + t0];
+                acc0 = make_float4(u.x + acc0.x, u.y + acc0.y, u.z + acc0.z, u.w + acc0.w);
+                if (t0 + 1 < cnt) {
+                    const float4 v = near[st + t0 + 1];
+                    acc1 = make_float4(v.x + acc1.x, v.y + acc1.y, v.z + acc1.z, v.w + acc1.w);
+                }
+            }
             near_output(near, st + t0, acc0.x, acc0.y, acc0.z, acc0.w);
             if (t0 + 1 < cnt) near_output(near, st + t0 + 1, acc1.x, acc1.y, acc1.z, acc1.w);
         }
     }
 }
+
+
+// (2) and (3) for one staged leaf in buf: image shifts of the wrapped segments, pads, packed
+// pairs, then the phases of target-pair slices; writes the leaf's near-field outputs.
+__device__ __forceinline__ void near_leaf(const NearParams& a, const NearStage& T, float4* buf, int lane,
+                                          float4* __restrict__ near) {
+    const int cnt = T.cnt, total = T.total;
+    const int npairs = (total + 1) >> 1;
+    for (unsigned wm = T.wrap; wm; wm &= wm - 1) {
+        const int o = __ffs(wm) - 1;
+        const int o0 = __shfl_sync(0xffffffffu, T.off, o), no = __shfl_sync(0xffffffffu, T.sc, o);
+        const float ax = __shfl_sync(0xffffffffu, T.shx, o), ay = __shfl_sync(0xffffffffu, T.shy, o),
+                    az = __shfl_sync(0xffffffffu, T.shz, o);
+        for (int j = lane; j < no; j += 32) {
+            float4 v = buf[o0 + j];
+            v.x += ax;
+            v.y += ay;
+            v.z += az;
+            buf[o0 + j] = v;
+        }
+    }
+    // a zero charge far away contributes nothing (own leaf odd, list odd)
+    if (lane == 0 && (cnt & 1)) buf[cnt] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+    if (lane == 1 && (total & 1)) buf[total] = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);
+    __syncwarp();
+    for (int j = lane; j < npairs; j += 32) {
+        const float4 A = buf[2 * j], B = buf[2 * j + 1];
+        buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
+        buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
+    }
+    __syncwarp();
+    near_phases(buf, lane, cnt, __shfl_sync(0xffffffffu, T.s0, 0), 0, npairs, __shfl_sync(0xffffffffu, T.off, 1) >> 1,
+                false, near);
+}
+
+// A leaf whose neighbourhood does not fit the staging buffer in one piece: its own leaf stays at
+// the start of the buffer (targets, and in the first round also sources), and the other 26
+// segments are staged in rounds of consecutive segments that fit the rest of the buffer.  Each
+// round runs the same phases over its source pairs; later rounds add to the outputs the earlier
+// ones wrote, in round order.  Requires the own leaf to fit half the buffer and every other
+// segment the remainder (near_rounds_fit).  ph counts the completed phases of bar; returns false
+// when a wait expired (FMM_DEV_TIMEOUT is set and nothing is left copying).
+__device__ __forceinline__ bool near_rounds_fit(const NearStage& T, int lane) {
+    const int own_slot = (T.cnt + 1) & ~1;
+    const int room = kNearCap - own_slot - 2;
+    return own_slot <= kNearCap / 2 && __all_sync(0xffffffffu, lane == 0 || lane >= 27 || T.sc <= room);
+}
+
+__device__ __forceinline__ bool near_rounds(const NearParams& a, const NearStage& T, float4* buf, uint64_t* bar,
+                                            uint32_t& ph, int lane, float4* __restrict__ near) {
+    const int cnt = T.cnt;
+    const int own_slot = (cnt + 1) & ~1, own_pairs = own_slot >> 1;
+    const int room = kNearCap - own_slot - 2;  // source atoms of one round (its pad included)
+    const int st = __shfl_sync(0xffffffffu, T.s0, 0);
+    // exclusive prefix of the other segments' atom counts (lanes 1..26)
+    const int mine = (lane >= 1 && lane < 27) ? T.sc : 0;
+    int incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int excl = incl - mine;
+    const float4 pad = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);  // a zero charge far away
+    int a0 = 1;
+    for (int r = 0; r == 0 || a0 < 27; ++r) {
+        // the round: segments a0 .. b0 - 1, as many as fit
+        const int base = __shfl_sync(0xffffffffu, excl, a0);  // a0 <= 26
+        const unsigned fit = __ballot_sync(0xffffffffu, lane >= a0 && lane < 27 && incl - base <= room);
+        const int b0 = a0 + __popc(fit);
+        const int ra = (b0 > a0) ? __shfl_sync(0xffffffffu, incl, b0 - 1) - base : 0;
+        if (r > 0 && ra == 0) {  // only empty segments are left
+            a0 = b0;
+            continue;
+        }
+        // this round's copies overwrite what the warp read and wrote in the buffer before
+        tc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_expect_tx(bar, 16u * (uint32_t)(ra + (r == 0 ? cnt : 0)));
+        __syncwarp();
+        if (r == 0 && lane == 0) tc::bulk_g2s(buf, a.pos + T.s0, 16u * (uint32_t)cnt, bar);
+        if (lane >= a0 && lane < b0 && T.sc > 0)
+            tc::bulk_g2s(buf + own_slot + (excl - base), a.pos + T.s0, 16u * (uint32_t)T.sc, bar);
+        if (!tc::mbar_wait_all(bar, ph & 1u, a.wlim)) {
+            if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
+            tc::mbar_wait_all(bar, ph & 1u, kNearWait);  // nothing may still be copying when the warp exits
+            return false;
+        }
+        ++ph;
+        // image shifts of this round's wrapped segments, pads, packed pairs
+        const unsigned rmask = (b0 >= 32 ? 0xffffffffu : ((1u << b0) - 1u)) & ~((1u << a0) - 1u);
+        for (unsigned wm = T.wrap & rmask; wm; wm &= wm - 1) {
+            const int o = __ffs(wm) - 1;
+            const int o0 = own_slot + __shfl_sync(0xffffffffu, excl, o) - base, no = __shfl_sync(0xffffffffu, T.sc, o);
+            const float ax = __shfl_sync(0xffffffffu, T.shx, o), ay = __shfl_sync(0xffffffffu, T.shy, o),
+                        az = __shfl_sync(0xffffffffu, T.shz, o);
+            for (int j = lane; j < no; j += 32) {
+                float4 v = buf[o0 + j];
+                v.x += ax;
+                v.y += ay;
+                v.z += az;
+                buf[o0 + j] = v;
+            }
+        }
+        if (r == 0 && lane == 0 && (cnt & 1)) buf[cnt] = pad;
+        if (lane == 1 && (ra & 1)) buf[own_slot + ra] = pad;
+        __syncwarp();
+        const int np_r = (ra + 1) >> 1;
+        for (int j = (r == 0 ? 0 : own_pairs) + lane; j < own_pairs + np_r; j += 32) {
+            const float4 A = buf[2 * j], B = buf[2 * j + 1];
+            buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
+            buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
+        }
+        __syncwarp();
+        if (r == 0) near_phases(buf, lane, cnt, st, 0, own_pairs + np_r, own_pairs, false, near);
+        else near_phases(buf, lane, cnt, st, own_pairs, np_r, 0, true, near);
+        __syncwarp();
+        a0 = b0;
+    }
+    return true;
+}
+
+// Near field of the leaves with more than kNearTile atoms (the items the binning listed), one
+// warp per item (leaf, tile): the
+// tile's targets (up to kNearTile own atoms) at the start of the buffer, and the neighbourhood --
+// the own leaf first, then the other 26 segments -- staged in rounds of the remaining room, a
+// segment split across rounds where it does not fit.  Every round runs the phases of the staged
+// near field over its source pairs (the own leaf's pairs with the r > 0 test); later rounds add
+// to the outputs the earlier ones wrote, in round order.  The warps first .. first + k stride
+// take the items in turn (the grid does not know their number).  buf and bar: the warp's staging
+// buffer and its initialised mbarrier, ph phases of which have completed.
+__device__ __noinline__ void near_big(const NearParams& a, float4* buf, uint64_t* bar, uint32_t ph, int lane, int first,
+                                      int stride, float4* __restrict__ near) {
+    const int2* __restrict__ items = a.items;
+    if (!items || first >= a.items_cap) return;  // no list (a handle without atoms) or nothing for this warp
+    const int nitems = min(items[0].x, a.items_cap);
+    if (first >= nitems) return;
+    const float4 pad = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);  // a zero charge far away
+    for (int item = first; item < nitems; item += stride) {
+        const int2 it = items[1 + item];
+        const NearStage T = near_segments(a, lane, it.x);
+        const int cnt = T.cnt, t0 = it.y * kNearTile;
+        const int tcnt = min(kNearTile, cnt - t0);
+        if (tcnt <= 0) continue;  // (a stale item: cannot happen after a binning of this call)
+        const int tslot = (tcnt + 1) & ~1, tpairs = tslot >> 1;
+        const int room = kNearCap - tslot - 2;  // source atoms of one round (its pad included)
+        const int st = __shfl_sync(0xffffffffu, T.s0, 0) + t0;
+        const int own = cnt;  // the own leaf is the first stretch of the source list
+        // the sources as one list: segment o at [excl, excl + sc)
+        const int mine = lane < 27 ? T.sc : 0;
+        int incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int excl = incl - mine, total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int r0 = 0, r = 0; r0 < total; r0 += room, ++r) {
+            const int r1 = min(r0 + room, total), ra = r1 - r0;
+            // this lane's piece of its segment in the round
+            const int lo = max(excl, r0), hi = min(excl + mine, r1);
+            const bool has = lane < 27 && hi > lo;
+            tc::fence_proxy_async();  // the warp's earlier reads and writes of the buffer first
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_expect_tx(bar, 16u * (uint32_t)(ra + (r == 0 ? tcnt : 0)));
+            __syncwarp();
+            if (r == 0 && lane == 0) tc::bulk_g2s(buf, a.pos + st, 16u * (uint32_t)tcnt, bar);
+            if (has) tc::bulk_g2s(buf + tslot + (lo - r0), a.pos + T.s0 + (lo - excl), 16u * (uint32_t)(hi - lo), bar);
+            if (!tc::mbar_wait_all(bar, ph & 1u, a.wlim)) {
+                if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
+                tc::mbar_wait_all(bar, ph & 1u, kNearWait);  // nothing may still be copying when the warp exits
+                return;
+            }
+            ++ph;
+            // image shifts of the wrapped pieces, pads, packed pairs
+            const unsigned wm0 = T.wrap & __ballot_sync(0xffffffffu, has);
+            for (unsigned wm = wm0; wm; wm &= wm - 1) {
+                const int o = __ffs(wm) - 1;
+                const int plo = __shfl_sync(0xffffffffu, lo, o), phi = __shfl_sync(0xffffffffu, hi, o);
+                const float ax = __shfl_sync(0xffffffffu, T.shx, o), ay = __shfl_sync(0xffffffffu, T.shy, o),
+                            az = __shfl_sync(0xffffffffu, T.shz, o);
+                for (int j = plo + lane; j < phi; j += 32) {
+                    float4 v = buf[tslot + (j - r0)];
+                    v.x += ax;
+                    v.y += ay;
+                    v.z += az;
+                    buf[tslot + (j - r0)] = v;
+                }
+            }
+            if (r == 0 && lane == 0 && (tcnt & 1)) buf[tcnt] = pad;
+            if (lane == 1 && (ra & 1)) buf[tslot + ra] = pad;
+            __syncwarp();
+            const int np_r = (ra + 1) >> 1;
+            for (int j = (r == 0 ? 0 : tpairs) + lane; j < tpairs + np_r; j += 32) {
+                const float4 A = buf[2 * j], B = buf[2 * j + 1];
+                buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
+                buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
+            }
+            __syncwarp();
+            // source pairs of this round that may hold own atoms: those before the own leaf's end
+            const int own_r = max(0, min(own, r1) - r0);
+            near_phases(buf, lane, tcnt, st, tpairs, np_r, (own_r + 1) >> 1, r > 0, near);
+            __syncwarp();
+        }
+    }
+}
+
 
 // W warps per block: 1, 2 or 4 (the near-field block shape the autotuner picks; a block keeps
 // its shared memory until its last warp is done).  Each warp takes leaves_per_warp consecutive
@@ -1681,19 +1896,29 @@ __global__ void __launch_bounds__(32 * W, NB == 2 ? (W == 1 ? 11 : (W == 2 ? 5 :
     k_p2p(NearParams a, float4* __restrict__ near) {
     extern __shared__ __align__(128) unsigned char near_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int first = (blockIdx.x * W + w) * a.leaves_per_warp;
-    const int last = min(a.nleaf, first + a.leaves_per_warp);
-    if (first >= last) return;
     NearWarpSmem<NB>& S = reinterpret_cast<NearWarpSmem<NB>*>(near_smem)[w];
+    const int leaf_blocks = (a.nleaf + W * a.leaves_per_warp - 1) / (W * a.leaves_per_warp);
+    // the big leaves' items: every warp of the grid takes them in turn after its own leaves (the
+    // grid has at least kNearBigWarps warps, the blocks after the leaves' only for them)
+    const int gw = blockIdx.x * W + w, gstride = gridDim.x * W;
     if (lane == 0) {
         for (int b = 0; b < NB; ++b) tc::mbar_init(&S.bar[b], 1);
         tc::fence_mbar_init();
     }
     __syncwarp();
-    NearStage cur = near_stage(a, S.buf[0], &S.bar[0], lane, first);
+    if ((int)blockIdx.x >= leaf_blocks) {  // (with two buffers only these warps take items)
+        const int skip = NB == 1 ? 0 : leaf_blocks * W;
+        near_big(a, S.buf[0], &S.bar[0], 0u, lane, gw - skip, gstride - skip, near);
+        return;
+    }
+    const int first = gw * a.leaves_per_warp;
+    const int last = min(a.nleaf, first + a.leaves_per_warp);
+    NearStage cur{};
+    if (first < last) cur = near_stage(a, S.buf[0], &S.bar[0], lane, first);
+    uint32_t ph0 = 0;  // completed phases of bar[0] (one buffer: a leaf staged in rounds takes several)
     for (int leaf = first, it = 0; leaf < last; ++leaf, ++it) {
         const int b = NB == 2 ? (it & 1) : 0;
-        const uint32_t parity = (uint32_t)((NB == 2 ? it >> 1 : it) & 1);
+        const uint32_t parity = NB == 2 ? (uint32_t)((it >> 1) & 1) : (ph0 & 1u);
         const bool more = NB == 2 && leaf + 1 < last;
         NearStage nxt = cur;
         if (more) {
@@ -1709,10 +1934,15 @@ __global__ void __launch_bounds__(32 * W, NB == 2 ? (W == 1 ? 11 : (W == 2 ? 5 :
             if (more) tc::mbar_wait_all(&S.bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kNearWait);
             return;
         }
-        if (cur.cnt > 0) {
-            if (2 * ((cur.total + 1) >> 1) > kNearCap)
+        if (NB == 1) ++ph0;
+        if (cur.cnt > 0 && cur.cnt <= kNearTile) {  // larger leaves: k_p2p_big
+            if (2 * ((cur.total + 1) >> 1) <= kNearCap) {
+                near_leaf(a, cur, S.buf[b], lane, near);
+            } else if (NB == 1 && near_rounds_fit(cur, lane)) {
+                if (!near_rounds(a, cur, S.buf[0], &S.bar[0], ph0, lane, near)) return;
+            } else {
                 near_streamed(a, cur.s0, cur.sc, cur.shx, cur.shy, cur.shz, cur.cnt, S.buf[b], lane, near);
-            else near_leaf(a, cur, S.buf[b], lane, near);
+            }
         }
         __syncwarp();
         if (NB == 1 && leaf + 1 < last) {  // the next leaf into the same buffer
@@ -1722,20 +1952,27 @@ __global__ void __launch_bounds__(32 * W, NB == 2 ? (W == 1 ? 11 : (W == 2 ? 5 :
         }
         cur = nxt;
     }
+    if (NB == 1) near_big(a, S.buf[0], &S.bar[0], ph0, lane, gw, gstride, near);
 }
 
 // Grid of the near field: W warps per block, leaves_per_warp consecutive leaves per warp, NB
-// staging buffers per warp.  Measured at 500,000 atoms: one buffer and one leaf per warp
+// staging buffers per warp; then up to kNearBigWarps warps for the items of the big leaves (they
+// return at once when there are none).  Measured at 500,000 atoms: one buffer and one leaf per warp
 // (0.135 ms alone) beat two buffers at 2, 4 or 8 leaves per warp (0.160-0.186 ms), whose
 // eleven warps per SM left the pair loop latency-bound.
 constexpr int kNearLeavesPerWarp = 1;
+constexpr int kNearBigWarps = 148 * 8;  // warps for the big leaves' items (they loop over them)
 constexpr int kNearBufs = 1;
 template <int W>
 static void launch_p2p(NearParams a, float4* near, cudaStream_t st) {
     a.leaves_per_warp = kNearLeavesPerWarp;
     const int per_block = W * kNearLeavesPerWarp;
-    k_p2p<W, kNearBufs><<<(a.nleaf + per_block - 1) / per_block, 32 * W, (size_t)W * sizeof(NearWarpSmem<kNearBufs>),
-                          st>>>(a, near);
+    const int leaf_blocks = (a.nleaf + per_block - 1) / per_block;
+    // one buffer: the leaves' warps take the big items too, extra blocks only up to kNearBigWarps
+    const int item_warps = std::min(a.items_cap, kNearBigWarps) - (kNearBufs == 1 ? leaf_blocks * W : 0);
+    const int big_blocks = item_warps > 0 ? (item_warps + W - 1) / W : 0;
+    k_p2p<W, kNearBufs><<<leaf_blocks + big_blocks, 32 * W,
+                          (size_t)W * sizeof(NearWarpSmem<kNearBufs>), st>>>(a, near);
 }
 
 // Per handle, with its device current: the dynamic shared-memory limits of the near field
@@ -1962,7 +2199,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     uint32_t* tilecnt = h->leafcnt + nleaf;  // [ntiles] atoms per tile of kScanTile leaves
     if (n > 0)
         k_bin_count<<<(n + kCountThreads - 1) / kCountThreads, kCountThreads, 0, st>>>(
-            n, x, g, h->key, h->vA, h->leafcnt, ntiles, tilecnt, h->status);
+            n, x, g, h->key, h->vA, h->leafcnt, ntiles, tilecnt, h->status, h->near_items);
     k_bin_scan<<<ntiles, kScanThreads, 0, st>>>(nleaf, h->leafcnt, tilecnt, h->start, h->count);
     h->perm = h->kA;
     h->sorted_key = h->kB;
@@ -1970,7 +2207,8 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         k_bin_place<<<(n + 255) / 256, 256, 0, st>>>(n, h->key, h->vA, h->start, h->vB, ntiles, tilecnt);
         ChargeForms cf{{h->qA, h->qB, h->qC, h->qD}, h->nforms, h->site, h->K, lam, h->dq, h->dqt};
         k_bin_order_gather<<<((nleaf + 1) / 2 + 3) / 4, 128, 0, st>>>(nleaf, h->start, h->count, h->vB, h->perm,
-                                                            h->sorted_key, x, g, cf, h->pos, h->inv, h->status);
+                                                            h->sorted_key, x, g, cf, h->pos, h->inv, h->status,
+                                                            h->near_items, h->near_items_cap);
     }
     // --- near field on the caller's stream, concurrent with the multipole chain ---
     NearParams a{};
@@ -1994,6 +2232,8 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.epart = h->epart;
     a.status = h->status;
     a.wlim = h->wait_limit > 0 ? h->wait_limit : kNearWait;
+    a.items = h->near_items;
+    a.items_cap = h->near_items_cap;
     const int e1 = mark(h, st);
     span(h, 0, e0, e1);
     // fork: the chain P2M .. L2L on h->chain (highest priority), P2P here.  Serialised
