@@ -1369,13 +1369,14 @@ static void launch_hi(const HiParams& hp, cudaStream_t st) {
     k_hi<P><<<(hp.K + 3) / 4, 128, 0, st>>>(hp);
 }
 
-// Near field (P2P).  Each warp takes a run of consecutive target leaves.
+// Near field (P2P).  Each warp takes a run of consecutive target leaves (one by default).
 // (1) Staging: lanes 0..26 resolve the 27 neighbour leaves of a leaf (periodic image shift,
 //     start, count) and keep them in registers; the target's own leaf is segment 0, its count
-//     rounded up to even.  A warp scan gives each segment's offset in one of the warp's two
-//     buffers, and lane o copies segment o with one cp.async.bulk (a leaf's atoms are contiguous
-//     in leaf order), completing on the buffer's mbarrier.  The next leaf's copies are issued
-//     before the current leaf's pairs are summed, so their latency hides behind the pair loop.
+//     rounded up to even.  A warp scan gives each segment's offset in the warp's buffer, and lane
+//     o copies segment o with one cp.async.bulk (a leaf's atoms are contiguous in leaf order),
+//     completing on the buffer's mbarrier.  While a warp waits, the other resident warps (five
+//     per SM sub-partition) keep the FMA pipe busy; with two buffers per warp (NB = 2) the next
+//     leaf's copies would be issued before the current leaf's pairs are summed instead.
 // (2) After the (bounded) wait: the image shift added to the wrapped segments, zero-charge pads
 //     far away in the odd slots, then the atoms repacked in place into pairs
 //     (x0 x1 y0 y1 | z0 z1 q0 q1) for the f32x2 arithmetic.
@@ -1389,9 +1390,10 @@ static void launch_hi(const HiParams& hp, cudaStream_t st) {
 //     target's slice sums and the owner lane of the target pair adds the result: a fixed order,
 //     so results are bitwise reproducible for every block shape.
 // Leaves whose neighbourhood does not fit a buffer (kNearCap atoms) stage it in rounds of
-// neighbour segments, the own leaf kept at the start of the buffer (near_rounds); only leaves whose
-// own atoms or single neighbours are too many even for that stream their sources from global
-// memory, one target per lane.  k_far_out adds the far field and writes the outputs.
+// neighbour segments, the own leaf kept at the start of the buffer (near_rounds).  Leaves above
+// kNearTile atoms are split into work items of kNearTile targets (near_big, items listed by the
+// binning); only a small leaf with a neighbour too large for a round streams its sources from
+// global memory, one target per lane.  k_far_out adds the far field and writes the outputs.
 constexpr int kNearCap = 592;                   // staged atoms per buffer (neighbourhood + 2 pads)
 constexpr int kNearMaxPairs = kNearCap / 2;     // source pairs of a staged neighbourhood
 constexpr long long kNearWait = 4000000000LL;  // default bound of the staging wait (clock cycles, about 2 s)
