@@ -1375,8 +1375,7 @@ static void launch_hi(const HiParams& hp, cudaStream_t st) {
 //     rounded up to even.  A warp scan gives each segment's offset in the warp's buffer, and lane
 //     o copies segment o with one cp.async.bulk (a leaf's atoms are contiguous in leaf order),
 //     completing on the buffer's mbarrier.  While a warp waits, the other resident warps (five
-//     per SM sub-partition) keep the FMA pipe busy; with two buffers per warp (NB = 2) the next
-//     leaf's copies would be issued before the current leaf's pairs are summed instead.
+//     per SM sub-partition) keep the FMA pipe busy.
 // (2) After the (bounded) wait: the image shift added to the wrapped segments, zero-charge pads
 //     far away in the odd slots, then the atoms repacked in place into pairs
 //     (x0 x1 y0 y1 | z0 z1 q0 q1) for the f32x2 arithmetic.
@@ -1389,11 +1388,9 @@ static void launch_hi(const HiParams& hp, cudaStream_t st) {
 //     equal positions always share a leaf.  After each phase a fixed shuffle tree adds each
 //     target's slice sums and the owner lane of the target pair adds the result: a fixed order,
 //     so results are bitwise reproducible for every block shape.
-// Leaves whose neighbourhood does not fit a buffer (kNearCap atoms) stage it in rounds of
-// neighbour segments, the own leaf kept at the start of the buffer (near_rounds).  Leaves above
-// kNearTile atoms are split into work items of kNearTile targets (near_big, items listed by the
-// binning); only a small leaf with a neighbour too large for a round streams its sources from
-// global memory, one target per lane.  k_far_out adds the far field and writes the outputs.
+// A leaf whose neighbourhood does not fit the buffer (kNearCap atoms) stages it in rounds, and
+// leaves above kNearTile atoms are split into work items of kNearTile targets listed by the
+// binning (near_item, near_big).  k_far_out adds the far field and writes the outputs.
 constexpr int kNearCap = 592;                   // staged atoms per buffer (neighbourhood + 2 pads)
 constexpr int kNearMaxPairs = kNearCap / 2;     // source pairs of a staged neighbourhood
 constexpr long long kNearWait = 4000000000LL;  // default bound of the staging wait (clock cycles, about 2 s)
@@ -1403,10 +1400,9 @@ __device__ __forceinline__ float rsqrt_approx(float x) {  // MUFU reciprocal squ
     return y;
 }
 
-template <int NB>
 struct NearWarpSmem {
-    float4 buf[NB][kNearCap];  // staging buffers: AoS (x, y, z, q) as copied, then packed pairs
-    uint64_t bar[NB];          // completion of each buffer's bulk copies
+    float4 buf[kNearCap];  // the staging buffer: AoS (x, y, z, q) as copied, then packed pairs
+    uint64_t bar;          // completion of its bulk copies
 };
 
 // Work mapping of a leaf: for tpg target pairs (1..32) and np source pairs (1..kNearMaxPairs),
@@ -1531,48 +1527,6 @@ __device__ __forceinline__ NearStage near_stage(const NearParams& a, float4* buf
     __syncwarp();
     if (staged && lane < 27 && t.sc > 0) tc::bulk_g2s(buf + t.off, a.pos + t.s0, 16u * (uint32_t)t.sc, bar);
     return t;
-}
-
-// Streamed near field of one leaf whose neighbourhood does not fit a staging buffer (rare):
-// one target per lane, 32 targets per pass, sources through a 32-atom stage in buf.
-__device__ __noinline__ void near_streamed(const NearParams& a, int seg_s0, int seg_sc, float seg_shx, float seg_shy,
-                                           float seg_shz, int cnt, float4* buf, int lane, float4* __restrict__ near) {
-    const int st = __shfl_sync(0xffffffffu, seg_s0, 0);
-    for (int tb = 0; tb < cnt; tb += 32) {
-        const int ti = tb + lane;
-        const bool valid = ti < cnt;
-        const float4 me = valid ? a.pos[st + ti] : make_float4(-1.0e6f, -1.0e6f, -1.0e6f, 0.f);
-        float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-        for (int o = 0; o < 27; ++o) {
-            const int s0 = __shfl_sync(0xffffffffu, seg_s0, o), sc = __shfl_sync(0xffffffffu, seg_sc, o);
-            const float ax = __shfl_sync(0xffffffffu, seg_shx, o), ay = __shfl_sync(0xffffffffu, seg_shy, o),
-                        az = __shfl_sync(0xffffffffu, seg_shz, o);
-            for (int sb = 0; sb < sc; sb += 32) {
-                float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (sb + lane < sc) sp = a.pos[s0 + sb + lane];
-                sp.x += ax;
-                sp.y += ay;
-                sp.z += az;
-                __syncwarp();
-                buf[lane] = sp;
-                __syncwarp();
-                const int ns = min(32, sc - sb);
-                for (int t = 0; t < ns; ++t) {
-                    const float4 s4 = buf[t];
-                    const float dx = s4.x - me.x, dy = s4.y - me.y, dz = s4.z - me.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float ri = (r2 > 0.f) ? rsqrt_approx(r2) : 0.f;
-                    const float qri = s4.w * ri;
-                    pot += qri;
-                    const float qri3 = qri * ri * ri;
-                    gx = fmaf(qri3, dx, gx);
-                    gy = fmaf(qri3, dy, gy);
-                    gz = fmaf(qri3, dz, gz);
-                }
-            }
-        }
-        if (valid) near_output(near, st + ti, pot, gx, gy, gz);
-    }
 }
 
 // (3) for a staged source list: the phases of target-pair slices over the source pairs
@@ -1715,266 +1669,160 @@ __device__ __forceinline__ void near_leaf(const NearParams& a, const NearStage& 
                 false, near);
 }
 
-// A leaf whose neighbourhood does not fit the staging buffer in one piece: its own leaf stays at
-// the start of the buffer (targets, and in the first round also sources), and the other 26
-// segments are staged in rounds of consecutive segments that fit the rest of the buffer.  Each
-// round runs the same phases over its source pairs; later rounds add to the outputs the earlier
-// ones wrote, in round order.  Requires the own leaf to fit half the buffer and every other
-// segment the remainder (near_rounds_fit).  ph counts the completed phases of bar; returns false
-// when a wait expired (FMM_DEV_TIMEOUT is set and nothing is left copying).
-__device__ __forceinline__ bool near_rounds_fit(const NearStage& T, int lane) {
-    const int own_slot = (T.cnt + 1) & ~1;
-    const int room = kNearCap - own_slot - 2;
-    return own_slot <= kNearCap / 2 && __all_sync(0xffffffffu, lane == 0 || lane >= 27 || T.sc <= room);
-}
-
-__device__ __forceinline__ bool near_rounds(const NearParams& a, const NearStage& T, float4* buf, uint64_t* bar,
-                                            uint32_t& ph, int lane, float4* __restrict__ near) {
+// One work item of the near field: the targets t0 .. t0 + kNearTile - 1 of `leaf` (at most
+// kNearTile) at the start of the buffer, and the neighbourhood -- the own leaf first, then the
+// other 26 segments, as one list -- staged in rounds of the remaining room, a segment split
+// across rounds where it does not fit.  Every round runs the phases of the staged near field over
+// its source pairs (the own leaf's pairs with the r > 0 test); later rounds add to the outputs
+// the earlier ones wrote, in round order.  It serves the leaves above kNearTile atoms (one item
+// per tile, listed by the binning) and the smaller leaves whose neighbourhood does not fit the
+// buffer in one piece (one item).  buf and bar: the warp's staging buffer and its initialised
+// mbarrier, ph the count of its completed phases; returns false when a wait expired
+// (FMM_DEV_TIMEOUT is set and nothing is left copying).
+__device__ __noinline__ bool near_item(const NearParams& a, float4* buf, uint64_t* bar, uint32_t& ph, int lane,
+                                       int leaf, int t0, float4* __restrict__ near) {
+    const float4 pad = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);  // a zero charge far away
+    const NearStage T = near_segments(a, lane, leaf);
     const int cnt = T.cnt;
-    const int own_slot = (cnt + 1) & ~1, own_pairs = own_slot >> 1;
-    const int room = kNearCap - own_slot - 2;  // source atoms of one round (its pad included)
-    const int st = __shfl_sync(0xffffffffu, T.s0, 0);
-    // exclusive prefix of the other segments' atom counts (lanes 1..26)
-    const int mine = (lane >= 1 && lane < 27) ? T.sc : 0;
+    const int tcnt = min(kNearTile, cnt - t0);
+    if (tcnt <= 0) return true;  // (a stale item: cannot happen after a binning of this call)
+    const int tslot = (tcnt + 1) & ~1, tpairs = tslot >> 1;
+    const int room = kNearCap - tslot - 2;  // source atoms of one round (its pad included)
+    const int st = __shfl_sync(0xffffffffu, T.s0, 0) + t0;
+    const int own = cnt;  // the own leaf is the first stretch of the source list
+    // the sources as one list: segment o at [excl, excl + sc)
+    const int mine = lane < 27 ? T.sc : 0;
     int incl = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += y;
     }
-    const int excl = incl - mine;
-    const float4 pad = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);  // a zero charge far away
-    int a0 = 1;
-    for (int r = 0; r == 0 || a0 < 27; ++r) {
-        // the round: segments a0 .. b0 - 1, as many as fit
-        const int base = __shfl_sync(0xffffffffu, excl, a0);  // a0 <= 26
-        const unsigned fit = __ballot_sync(0xffffffffu, lane >= a0 && lane < 27 && incl - base <= room);
-        const int b0 = a0 + __popc(fit);
-        const int ra = (b0 > a0) ? __shfl_sync(0xffffffffu, incl, b0 - 1) - base : 0;
-        if (r > 0 && ra == 0) {  // only empty segments are left
-            a0 = b0;
-            continue;
-        }
-        // this round's copies overwrite what the warp read and wrote in the buffer before
-        tc::fence_proxy_async();
+    const int excl = incl - mine, total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int r0 = 0, r = 0; r0 < total; r0 += room, ++r) {
+        const int r1 = min(r0 + room, total), ra = r1 - r0;
+        // this lane's piece of its segment in the round
+        const int lo = max(excl, r0), hi = min(excl + mine, r1);
+        const bool has = lane < 27 && hi > lo;
+        tc::fence_proxy_async();  // the warp's earlier reads and writes of the buffer first
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive_expect_tx(bar, 16u * (uint32_t)(ra + (r == 0 ? cnt : 0)));
+        if (lane == 0) tc::mbar_arrive_expect_tx(bar, 16u * (uint32_t)(ra + (r == 0 ? tcnt : 0)));
         __syncwarp();
-        if (r == 0 && lane == 0) tc::bulk_g2s(buf, a.pos + T.s0, 16u * (uint32_t)cnt, bar);
-        if (lane >= a0 && lane < b0 && T.sc > 0)
-            tc::bulk_g2s(buf + own_slot + (excl - base), a.pos + T.s0, 16u * (uint32_t)T.sc, bar);
+        if (r == 0 && lane == 0) tc::bulk_g2s(buf, a.pos + st, 16u * (uint32_t)tcnt, bar);
+        if (has) tc::bulk_g2s(buf + tslot + (lo - r0), a.pos + T.s0 + (lo - excl), 16u * (uint32_t)(hi - lo), bar);
         if (!tc::mbar_wait_all(bar, ph & 1u, a.wlim)) {
             if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
             tc::mbar_wait_all(bar, ph & 1u, kNearWait);  // nothing may still be copying when the warp exits
             return false;
         }
         ++ph;
-        // image shifts of this round's wrapped segments, pads, packed pairs
-        const unsigned rmask = (b0 >= 32 ? 0xffffffffu : ((1u << b0) - 1u)) & ~((1u << a0) - 1u);
-        for (unsigned wm = T.wrap & rmask; wm; wm &= wm - 1) {
+        // image shifts of the wrapped pieces, pads, packed pairs
+        const unsigned wm0 = T.wrap & __ballot_sync(0xffffffffu, has);
+        for (unsigned wm = wm0; wm; wm &= wm - 1) {
             const int o = __ffs(wm) - 1;
-            const int o0 = own_slot + __shfl_sync(0xffffffffu, excl, o) - base, no = __shfl_sync(0xffffffffu, T.sc, o);
+            const int plo = __shfl_sync(0xffffffffu, lo, o), phi = __shfl_sync(0xffffffffu, hi, o);
             const float ax = __shfl_sync(0xffffffffu, T.shx, o), ay = __shfl_sync(0xffffffffu, T.shy, o),
                         az = __shfl_sync(0xffffffffu, T.shz, o);
-            for (int j = lane; j < no; j += 32) {
-                float4 v = buf[o0 + j];
+            for (int j = plo + lane; j < phi; j += 32) {
+                float4 v = buf[tslot + (j - r0)];
                 v.x += ax;
                 v.y += ay;
                 v.z += az;
-                buf[o0 + j] = v;
+                buf[tslot + (j - r0)] = v;
             }
         }
-        if (r == 0 && lane == 0 && (cnt & 1)) buf[cnt] = pad;
-        if (lane == 1 && (ra & 1)) buf[own_slot + ra] = pad;
+        if (r == 0 && lane == 0 && (tcnt & 1)) buf[tcnt] = pad;
+        if (lane == 1 && (ra & 1)) buf[tslot + ra] = pad;
         __syncwarp();
         const int np_r = (ra + 1) >> 1;
-        for (int j = (r == 0 ? 0 : own_pairs) + lane; j < own_pairs + np_r; j += 32) {
+        for (int j = (r == 0 ? 0 : tpairs) + lane; j < tpairs + np_r; j += 32) {
             const float4 A = buf[2 * j], B = buf[2 * j + 1];
             buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
             buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
         }
         __syncwarp();
-        if (r == 0) near_phases(buf, lane, cnt, st, 0, own_pairs + np_r, own_pairs, false, near);
-        else near_phases(buf, lane, cnt, st, own_pairs, np_r, 0, true, near);
+        // source pairs of this round that may hold own atoms: those before the own leaf's end
+        const int own_r = max(0, min(own, r1) - r0);
+        near_phases(buf, lane, tcnt, st, tpairs, np_r, (own_r + 1) >> 1, r > 0, near);
         __syncwarp();
-        a0 = b0;
     }
     return true;
 }
 
-// Near field of the leaves with more than kNearTile atoms (the items the binning listed), one
-// warp per item (leaf, tile): the
-// tile's targets (up to kNearTile own atoms) at the start of the buffer, and the neighbourhood --
-// the own leaf first, then the other 26 segments -- staged in rounds of the remaining room, a
-// segment split across rounds where it does not fit.  Every round runs the phases of the staged
-// near field over its source pairs (the own leaf's pairs with the r > 0 test); later rounds add
-// to the outputs the earlier ones wrote, in round order.  The warps first .. first + k stride
-// take the items in turn (the grid does not know their number).  buf and bar: the warp's staging
-// buffer and its initialised mbarrier, ph phases of which have completed.
-__device__ __noinline__ void near_big(const NearParams& a, float4* buf, uint64_t* bar, uint32_t ph, int lane, int first,
-                                      int stride, float4* __restrict__ near) {
+// The items of the leaves above kNearTile atoms (listed by the binning): warps first, first +
+// stride, ... take them in turn (the grid does not know their number).
+__device__ __forceinline__ void near_big(const NearParams& a, float4* buf, uint64_t* bar, uint32_t ph, int lane,
+                                         int first, int stride, float4* __restrict__ near) {
     const int2* __restrict__ items = a.items;
     if (!items || first >= a.items_cap) return;  // no list (a handle without atoms) or nothing for this warp
     const int nitems = min(items[0].x, a.items_cap);
-    if (first >= nitems) return;
-    const float4 pad = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f);  // a zero charge far away
     for (int item = first; item < nitems; item += stride) {
         const int2 it = items[1 + item];
-        const NearStage T = near_segments(a, lane, it.x);
-        const int cnt = T.cnt, t0 = it.y * kNearTile;
-        const int tcnt = min(kNearTile, cnt - t0);
-        if (tcnt <= 0) continue;  // (a stale item: cannot happen after a binning of this call)
-        const int tslot = (tcnt + 1) & ~1, tpairs = tslot >> 1;
-        const int room = kNearCap - tslot - 2;  // source atoms of one round (its pad included)
-        const int st = __shfl_sync(0xffffffffu, T.s0, 0) + t0;
-        const int own = cnt;  // the own leaf is the first stretch of the source list
-        // the sources as one list: segment o at [excl, excl + sc)
-        const int mine = lane < 27 ? T.sc : 0;
-        int incl = mine;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        const int excl = incl - mine, total = __shfl_sync(0xffffffffu, incl, 31);
-        for (int r0 = 0, r = 0; r0 < total; r0 += room, ++r) {
-            const int r1 = min(r0 + room, total), ra = r1 - r0;
-            // this lane's piece of its segment in the round
-            const int lo = max(excl, r0), hi = min(excl + mine, r1);
-            const bool has = lane < 27 && hi > lo;
-            tc::fence_proxy_async();  // the warp's earlier reads and writes of the buffer first
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive_expect_tx(bar, 16u * (uint32_t)(ra + (r == 0 ? tcnt : 0)));
-            __syncwarp();
-            if (r == 0 && lane == 0) tc::bulk_g2s(buf, a.pos + st, 16u * (uint32_t)tcnt, bar);
-            if (has) tc::bulk_g2s(buf + tslot + (lo - r0), a.pos + T.s0 + (lo - excl), 16u * (uint32_t)(hi - lo), bar);
-            if (!tc::mbar_wait_all(bar, ph & 1u, a.wlim)) {
-                if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
-                tc::mbar_wait_all(bar, ph & 1u, kNearWait);  // nothing may still be copying when the warp exits
-                return;
-            }
-            ++ph;
-            // image shifts of the wrapped pieces, pads, packed pairs
-            const unsigned wm0 = T.wrap & __ballot_sync(0xffffffffu, has);
-            for (unsigned wm = wm0; wm; wm &= wm - 1) {
-                const int o = __ffs(wm) - 1;
-                const int plo = __shfl_sync(0xffffffffu, lo, o), phi = __shfl_sync(0xffffffffu, hi, o);
-                const float ax = __shfl_sync(0xffffffffu, T.shx, o), ay = __shfl_sync(0xffffffffu, T.shy, o),
-                            az = __shfl_sync(0xffffffffu, T.shz, o);
-                for (int j = plo + lane; j < phi; j += 32) {
-                    float4 v = buf[tslot + (j - r0)];
-                    v.x += ax;
-                    v.y += ay;
-                    v.z += az;
-                    buf[tslot + (j - r0)] = v;
-                }
-            }
-            if (r == 0 && lane == 0 && (tcnt & 1)) buf[tcnt] = pad;
-            if (lane == 1 && (ra & 1)) buf[tslot + ra] = pad;
-            __syncwarp();
-            const int np_r = (ra + 1) >> 1;
-            for (int j = (r == 0 ? 0 : tpairs) + lane; j < tpairs + np_r; j += 32) {
-                const float4 A = buf[2 * j], B = buf[2 * j + 1];
-                buf[2 * j] = make_float4(A.x, B.x, A.y, B.y);
-                buf[2 * j + 1] = make_float4(A.z, B.z, A.w, B.w);
-            }
-            __syncwarp();
-            // source pairs of this round that may hold own atoms: those before the own leaf's end
-            const int own_r = max(0, min(own, r1) - r0);
-            near_phases(buf, lane, tcnt, st, tpairs, np_r, (own_r + 1) >> 1, r > 0, near);
-            __syncwarp();
-        }
+        if (!near_item(a, buf, bar, ph, lane, it.x, it.y * kNearTile, near)) return;
     }
 }
-
 
 // W warps per block: 1, 2 or 4 (the near-field block shape the autotuner picks; a block keeps
 // its shared memory until its last warp is done).  Each warp takes leaves_per_warp consecutive
-// leaves.  With NB = 2 buffers it stages them in turn, so that the copies of the next leaf land
-// while it sums the pairs of the current one; with NB = 1 it waits for each leaf's copies, and
-// the other resident warps (twice as many in the same shared memory) keep the FMA pipe busy.
-template <int W, int NB>
-__global__ void __launch_bounds__(32 * W, NB == 2 ? (W == 1 ? 11 : (W == 2 ? 5 : 2)) : 20 / W)
-    k_p2p(NearParams a, float4* __restrict__ near) {
+// leaves, waits for each leaf's copies while the other resident warps keep the FMA pipe busy,
+// then takes its turn at the big leaves' items; the blocks after the leaves' (when the leaves'
+// warps are fewer than kNearBigWarps) take only items.
+template <int W>
+__global__ void __launch_bounds__(32 * W, 20 / W) k_p2p(NearParams a, float4* __restrict__ near) {
     extern __shared__ __align__(128) unsigned char near_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    NearWarpSmem<NB>& S = reinterpret_cast<NearWarpSmem<NB>*>(near_smem)[w];
+    NearWarpSmem& S = reinterpret_cast<NearWarpSmem*>(near_smem)[w];
     const int leaf_blocks = (a.nleaf + W * a.leaves_per_warp - 1) / (W * a.leaves_per_warp);
-    // the big leaves' items: every warp of the grid takes them in turn after its own leaves (the
-    // grid has at least kNearBigWarps warps, the blocks after the leaves' only for them)
     const int gw = blockIdx.x * W + w, gstride = gridDim.x * W;
     if (lane == 0) {
-        for (int b = 0; b < NB; ++b) tc::mbar_init(&S.bar[b], 1);
+        tc::mbar_init(&S.bar, 1);
         tc::fence_mbar_init();
     }
     __syncwarp();
-    if ((int)blockIdx.x >= leaf_blocks) {  // (with two buffers only these warps take items)
-        const int skip = NB == 1 ? 0 : leaf_blocks * W;
-        near_big(a, S.buf[0], &S.bar[0], 0u, lane, gw - skip, gstride - skip, near);
-        return;
-    }
-    const int first = gw * a.leaves_per_warp;
-    const int last = min(a.nleaf, first + a.leaves_per_warp);
-    NearStage cur{};
-    if (first < last) cur = near_stage(a, S.buf[0], &S.bar[0], lane, first);
-    uint32_t ph0 = 0;  // completed phases of bar[0] (one buffer: a leaf staged in rounds takes several)
-    for (int leaf = first, it = 0; leaf < last; ++leaf, ++it) {
-        const int b = NB == 2 ? (it & 1) : 0;
-        const uint32_t parity = NB == 2 ? (uint32_t)((it >> 1) & 1) : (ph0 & 1u);
-        const bool more = NB == 2 && leaf + 1 < last;
-        NearStage nxt = cur;
-        if (more) {
-            // the other buffer's reads and writes (two leaves ago) before its new copies
-            tc::fence_proxy_async();
-            __syncwarp();
-            nxt = near_stage(a, S.buf[b ^ 1], &S.bar[b ^ 1], lane, leaf + 1);
-        }
-        if (!tc::mbar_wait_all(&S.bar[b], parity, a.wlim)) {
-            if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
-            // nothing may still be copying into the block's shared memory when the warp exits
-            tc::mbar_wait_all(&S.bar[b], parity, kNearWait);
-            if (more) tc::mbar_wait_all(&S.bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kNearWait);
-            return;
-        }
-        if (NB == 1) ++ph0;
-        if (cur.cnt > 0 && cur.cnt <= kNearTile) {  // larger leaves: k_p2p_big
-            if (2 * ((cur.total + 1) >> 1) <= kNearCap) {
-                near_leaf(a, cur, S.buf[b], lane, near);
-            } else if (NB == 1 && near_rounds_fit(cur, lane)) {
-                if (!near_rounds(a, cur, S.buf[0], &S.bar[0], ph0, lane, near)) return;
-            } else {
-                near_streamed(a, cur.s0, cur.sc, cur.shx, cur.shy, cur.shz, cur.cnt, S.buf[b], lane, near);
+    uint32_t ph = 0;  // completed phases of the warp's mbarrier
+    if ((int)blockIdx.x < leaf_blocks) {
+        const int first = gw * a.leaves_per_warp;
+        const int last = min(a.nleaf, first + a.leaves_per_warp);
+        for (int leaf = first; leaf < last; ++leaf) {
+            if (leaf > first) {  // this leaf's copies overwrite what the warp read and wrote before
+                tc::fence_proxy_async();
+                __syncwarp();
             }
-        }
-        __syncwarp();
-        if (NB == 1 && leaf + 1 < last) {  // the next leaf into the same buffer
-            tc::fence_proxy_async();
+            const NearStage cur = near_stage(a, S.buf, &S.bar, lane, leaf);
+            if (!tc::mbar_wait_all(&S.bar, ph & 1u, a.wlim)) {
+                if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
+                tc::mbar_wait_all(&S.bar, ph & 1u, kNearWait);  // nothing may still be copying when the warp exits
+                return;
+            }
+            ++ph;
+            if (cur.cnt > 0 && cur.cnt <= kNearTile) {  // larger leaves: their items
+                if (2 * ((cur.total + 1) >> 1) <= kNearCap) {
+                    near_leaf(a, cur, S.buf, lane, near);
+                } else if (!near_item(a, S.buf, &S.bar, ph, lane, leaf, 0, near)) {  // in rounds
+                    return;
+                }
+            }
             __syncwarp();
-            nxt = near_stage(a, S.buf[0], &S.bar[0], lane, leaf + 1);
         }
-        cur = nxt;
     }
-    if (NB == 1) near_big(a, S.buf[0], &S.bar[0], ph0, lane, gw, gstride, near);
+    near_big(a, S.buf, &S.bar, ph, lane, gw, gstride, near);
 }
 
-// Grid of the near field: W warps per block, leaves_per_warp consecutive leaves per warp, NB
-// staging buffers per warp; then up to kNearBigWarps warps for the items of the big leaves (they
-// return at once when there are none).  Measured at 500,000 atoms: one buffer and one leaf per warp
-// (0.135 ms alone) beat two buffers at 2, 4 or 8 leaves per warp (0.160-0.186 ms), whose
-// eleven warps per SM left the pair loop latency-bound.
+// Grid of the near field: W warps per block, leaves_per_warp consecutive leaves per warp, and at
+// least kNearBigWarps warps in all for the items of the big leaves (the extra ones return at once
+// when there are none).  Measured at 500,000 atoms: one leaf per warp and one warp per block
+// (0.135 ms alone) beat two staging buffers per warp at 2, 4 or 8 leaves per warp (0.160-0.186
+// ms: eleven warps per SM left the pair loop latency-bound) and four warps per block (0.143 ms).
 constexpr int kNearLeavesPerWarp = 1;
-constexpr int kNearBigWarps = 148 * 8;  // warps for the big leaves' items (they loop over them)
-constexpr int kNearBufs = 1;
+constexpr int kNearBigWarps = 148 * 8;
 template <int W>
 static void launch_p2p(NearParams a, float4* near, cudaStream_t st) {
     a.leaves_per_warp = kNearLeavesPerWarp;
     const int per_block = W * kNearLeavesPerWarp;
     const int leaf_blocks = (a.nleaf + per_block - 1) / per_block;
-    // one buffer: the leaves' warps take the big items too, extra blocks only up to kNearBigWarps
-    const int item_warps = std::min(a.items_cap, kNearBigWarps) - (kNearBufs == 1 ? leaf_blocks * W : 0);
+    const int item_warps = std::min(a.items_cap, kNearBigWarps) - leaf_blocks * W;
     const int big_blocks = item_warps > 0 ? (item_warps + W - 1) / W : 0;
-    k_p2p<W, kNearBufs><<<leaf_blocks + big_blocks, 32 * W,
-                          (size_t)W * sizeof(NearWarpSmem<kNearBufs>), st>>>(a, near);
+    k_p2p<W><<<leaf_blocks + big_blocks, 32 * W, (size_t)W * sizeof(NearWarpSmem), st>>>(a, near);
 }
 
 // Per handle, with its device current: the dynamic shared-memory limits of the near field
@@ -1982,10 +1830,10 @@ static void launch_p2p(NearParams a, float4* near, cudaStream_t st) {
 void near_configure(Handle* h) {
     (void)h;
     cudaFuncSetAttribute(k_m2l_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F32Smem));
-    constexpr int smem = (int)sizeof(NearWarpSmem<kNearBufs>);
-    cudaFuncSetAttribute(k_p2p<1, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_p2p<2, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * smem);
-    cudaFuncSetAttribute(k_p2p<4, kNearBufs>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * smem);
+    constexpr int smem = (int)sizeof(NearWarpSmem);
+    cudaFuncSetAttribute(k_p2p<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_p2p<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * smem);
+    cudaFuncSetAttribute(k_p2p<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * smem);
 }
 
 // E = 1/2 k sum of the per-block partials of q phi, totalled in FP64: each of the

@@ -1,11 +1,12 @@
-"""The near field's two source paths: staged and streamed.
+"""The near field's source paths.
 
 One warp per target leaf copies its 27 neighbour leaves' atoms into shared memory when they fit
-(640 atoms, the common case) and otherwise streams them neighbour by neighbour, one target per
-lane.  A dense ball in a periodic background makes the leaves around the ball take the streamed
-path and the others the staged one (the host counts the neighbourhoods to show that both run);
-an open box at depth 1 puts every atom in every leaf's neighbourhood.  Each case is checked
-against the FP64 oracle: the direct sum where the far field is absent, the Ewald sum otherwise.
+(592 atoms, the common case).  A larger neighbourhood is staged in rounds (a neighbour leaf split
+across rounds where it does not fit), and a leaf above 64 atoms is split into work items of 64
+targets that stage the whole neighbourhood the same way.  A dense ball in a periodic background exercises every path (the host counts
+the leaves to show that each runs); an open box at depth 1 puts every atom in every leaf's
+neighbourhood.  Each case is checked against the FP64 oracle: the direct sum where the far field
+is absent, the Ewald sum otherwise.
 """
 import numpy as np
 import pytest
@@ -14,7 +15,8 @@ import synth
 from fmm_check import errors, oracle_ref, run_gpu
 
 pytestmark = pytest.mark.gpu
-STAGE_CAP = 640  # atoms one warp stages
+STAGE_CAP = 592  # atoms one warp stages
+TILE = 64        # targets of one work item of a large leaf
 
 
 def neighbourhood_sizes(s, depth):
@@ -39,12 +41,35 @@ def neighbourhood_sizes(s, depth):
     return (tot + (grid & 1)).ravel()
 
 
+def leaf_paths(s, depth):
+    """Which near-field path each non-empty leaf takes: 'staged' (one piece), 'rounds' (a leaf of
+    at most TILE atoms whose neighbourhood is staged in rounds) or 'items' (a leaf above TILE
+    atoms, split into work items)."""
+    nb = 1 << depth
+    cell = np.floor((s["x"].astype(np.float64) - np.asarray(s["origin"])) / (s["L"] / nb)).astype(np.int64)
+    cell = cell % nb if s["periodic"] else np.clip(cell, 0, nb - 1)
+    grid = np.zeros((nb, nb, nb), np.int64).ravel()
+    np.add.at(grid, np.ravel_multi_index((cell[:, 0], cell[:, 1], cell[:, 2]), (nb, nb, nb)), 1)
+    total = neighbourhood_sizes(s, depth)
+    paths = []
+    for own, tot in zip(grid, total):
+        if own == 0:
+            continue
+        if own > TILE:
+            paths.append("items")
+        else:
+            paths.append("staged" if tot + (tot & 1) <= STAGE_CAP else "rounds")
+    return paths
+
+
 @pytest.mark.parametrize("n", [500, 3000])
 def test_open_depth1_equals_direct_sum(n):
     """Depth 1 in an open box: every leaf's neighbourhood is the whole system, so the near field
-    is everything.  500 atoms are staged, 3000 streamed."""
+    is everything.  At 500 atoms the leaves of at most 64 atoms are staged in one piece and the
+    others are work items in one round; 3000 make every leaf a set of work items in rounds."""
     s = synth.open_uniform(seed=40 + n, n=n, L=3.0, n_sites=4, p=2, depth=1)
-    assert (neighbourhood_sizes(s, 1).max() > STAGE_CAP) == (n > STAGE_CAP)
+    paths = set(leaf_paths(s, 1))
+    assert paths == ({"staged", "items"} if n < STAGE_CAP else {"items"}), paths
     ref = oracle_ref(s)
     g = run_gpu(s, depth=1)
     e = errors(g, ref)
@@ -54,12 +79,13 @@ def test_open_depth1_equals_direct_sum(n):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_periodic_dense_ball_staged_and_streamed(precision):
-    """A dense ball in a periodic background at depth 3: the leaves around the ball stream their
-    sources, the others stage them; E, F and dV/dlambda against the Ewald oracle at p = 10."""
+def test_periodic_dense_ball_every_path(precision):
+    """A dense ball in a periodic background at depth 3: the ball's leaves are large (work items),
+    their neighbours stage in rounds, the others stage in one piece; E, F and dV/dlambda
+    against the Ewald oracle at p = 10."""
     s = synth.periodic_dense_cluster(seed=41)
-    sizes = neighbourhood_sizes(s, 3)
-    assert (sizes > STAGE_CAP).any() and (sizes <= STAGE_CAP).any(), sizes
+    paths = leaf_paths(s, 3)
+    assert {"staged", "rounds", "items"} <= set(paths), sorted(set(paths))
     ref = oracle_ref(s)
     g = run_gpu(s, precision=precision)
     e = errors(g, ref)
