@@ -58,6 +58,10 @@ typedef enum {
 #define FMM_DEV_DOMAIN 1   /* atom outside [origin, origin + edge] of an open box */
 #define FMM_DEV_SITE 2     /* site index >= K (atom treated as not in a site)    */
 #define FMM_DEV_TIMEOUT 4  /* bounded wait expired                               */
+#define FMM_DEV_BOUNDS 8   /* an index check failed (bounds-checked build only)   */
+
+/* fmm_build_flags bits */
+#define FMM_BUILD_BOUNDS_CHECK 1 /* built with -DFMM_BOUNDS_CHECK (libfmmcph_checked.so) */
 
 typedef enum {
     FMM_FP32 = 0,        /* every stage in FP32 on CUDA cores (root/lattice FP64) */
@@ -251,8 +255,19 @@ fmm_status fmm_get_binning(fmm_handle* h, uint32_t* key, uint32_t* perm, uint32_
                            uint32_t* count, void* stream);
 
 /* Read and clear the device status word (FMM_DEV_* bits).  Synchronises
- * `stream` first. */
+ * `stream` first.  In the bounds-checked build it also reads and clears the
+ * library's index-check words: after a failed check it sets FMM_DEV_BOUNDS
+ * and fmm_last_error names the source file and line of the first failure
+ * (the words are per library, not per handle). */
 fmm_status fmm_status_word(fmm_handle* h, int* device_status, void* stream);
+
+/* How this library was built: FMM_BUILD_* bits.  The bounds-checked build
+ * (-DFMM_BOUNDS_CHECK) checks the data-dependent indices of its kernels
+ * (leaf keys, sorted slots, permutation entries, leaf ranges, site atoms,
+ * staged-buffer offsets, packed-box and operator indices) against their
+ * extents; a failed check skips the access it guards and is reported
+ * through fmm_status_word.  No GPU needed. */
+int fmm_build_flags(void);
 
 /* Per-stage device times of the last fmm_eval when profiling is enabled
  * (CUDA events; profiling mode launches kernel by kernel).  ms[0..n):
@@ -285,13 +300,27 @@ fmm_status fmm_set_profiling(fmm_handle* h, int enable);
 
 /* Bounded device waits.  The tensor-core M2L kernel runs as a pipeline of warps (bulk-copy
  * producer, MMA issuer, accumulator drains) that wait on one another through shared-memory
- * barriers; every such wait gives up after a limit of `cycles` GPU clock cycles (<= 0 selects
- * the default, about 2 s).  A CTA whose wait expires stops issuing work, lets its other warps
- * stop, waits (with the default limit) for the copies and MMAs it already issued, frees its
- * tensor memory and returns; the evaluation then sets FMM_DEV_TIMEOUT in the status word (its
- * results are not valid) and the handle stays usable.  A small limit is a test of that path;
- * no evaluation should need more than the default.  Discards the handle's evaluation graph. */
+ * barriers; the tensor-core M2M and L2L wait for their operator copies and MMAs, and every
+ * near-field warp for the copies of its staged atoms.  Each such wait gives up after a limit
+ * of `cycles` GPU clock cycles (<= 0 selects the default, about 2 s).  A CTA (or near-field
+ * warp) whose wait expires stops issuing work, waits (with the default limit) for the copies
+ * and MMAs it already issued, frees its tensor memory and returns; the evaluation then sets
+ * FMM_DEV_TIMEOUT in the status word (its results are not valid) and the handle stays usable.
+ * A small limit is a test of that path; no evaluation should need more than the default.
+ * Discards the handle's evaluation graph. */
 fmm_status fmm_set_wait_limit(fmm_handle* h, long long cycles);
+
+/* Test hook for the bounded waits of kernels whose waits do not otherwise run out: in the
+ * kernels named by `mask` the bulk copies are announced on their barriers but never issued,
+ * so their waits expire after the handle's wait limit (fmm_set_wait_limit; set a short one)
+ * and the evaluation sets FMM_DEV_TIMEOUT.  FMM_LOSE_TRANSLATE: the operator copies of the
+ * tensor-core M2M and L2L (the mixed-precision forms; FMM_FP32 translates on CUDA cores);
+ * FMM_LOSE_NEAR: the near field's staging copies of leaves that fit
+ * the staging buffer.  0 restores normal evaluation.  Discards the handle's evaluation graph.
+ * FMM_ERR_ARG for a null handle or other bits. */
+#define FMM_LOSE_TRANSLATE 1
+#define FMM_LOSE_NEAR 2
+fmm_status fmm_inject_copy_loss(fmm_handle* h, int mask);
 
 /* Allocation-failure injection, for tests of the out-of-memory paths: with n >= 1 the n-th
  * device allocation the library makes from now on (in any handle or thread) fails as if the

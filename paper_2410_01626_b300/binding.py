@@ -23,7 +23,7 @@ PRECISIONS = {"fp32": FMM_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF
               "fp16": FMM_MIXED_FP16}
 # lambda dependence within a site (Sec. 2.1, Eq. 1): interpolated charges, or interpolated Hamiltonian
 INTERPOLATIONS = {"charge": 0, "hamiltonian": 1}
-DEV_DOMAIN, DEV_SITE, DEV_TIMEOUT = 1, 2, 4
+DEV_DOMAIN, DEV_SITE, DEV_TIMEOUT, DEV_BOUNDS = 1, 2, 4, 8
 KE_DEFAULT = 138.935458
 # stage intervals of one evaluation (fmm_stage_times): the chain binning .. final, the near field
 # ("p2p", concurrent with p2m .. m2m), and the coarse levels' M2L and L2L, which run on a side
@@ -74,13 +74,21 @@ EXPORTS = {
     "fmm_destroy": (None, [P]),
     "fmm_error_string": (ctypes.c_char_p, [I]),
     "fmm_last_error": (ctypes.c_char_p, []),
+    "fmm_build_flags": (I, []),
+    "fmm_inject_copy_loss": (I, [P, I]),
 }
 
 _lib = None
 
 
+def _checked() -> bool:
+    return os.environ.get("FMMCPH_BOUNDS_CHECK", "") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the bounds-checked build when the environment variable
+    FMMCPH_BOUNDS_CHECK is set (to anything but 0) before the first load, else the normal one."""
+    return _build.LIB_CHECKED if _checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -88,9 +96,9 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = library_path()
     if build_if_missing and not os.path.exists(path):
-        _build.build()
+        _build.build(checked=_checked())
     lib = ctypes.CDLL(path)
     for name, (res, args) in EXPORTS.items():
         fn = getattr(lib, name)
@@ -288,8 +296,14 @@ class FMM:
         return s.value
 
     def set_wait_limit(self, cycles=0):
-        """Limit (GPU clock cycles) of the tensor-core M2L's pipeline waits; 0 = the default."""
+        """Limit (GPU clock cycles) of the kernels' bounded waits (tensor-core M2L, M2M and L2L,
+        near-field staging); 0 = the default (about 2 s)."""
         _check(self._lib.fmm_set_wait_limit(self._h, int(cycles)), "fmm_set_wait_limit")
+
+    def inject_copy_loss(self, mask=0):
+        """Test hook: the bulk copies of the kernels in `mask` (1 = M2M/L2L operator copies,
+        2 = near-field staging) are announced but never issued, so their waits run out."""
+        _check(self._lib.fmm_inject_copy_loss(self._h, int(mask)), "fmm_inject_copy_loss")
 
     def set_profiling(self, on=True, serial=False):
         """Per-stage event timing (stage_times); with ``serial`` every stage runs alone."""

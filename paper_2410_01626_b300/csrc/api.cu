@@ -602,6 +602,7 @@ static fmm_status eval_dispatch(Handle& h, const float* x, double* E, float* F, 
         for (auto& g : h.g_slot)
             if (g.exec && g.gen == h.gen && same(g.key)) {
                 g.used = ++h.g_tick;
+                TraceRange trace("fmm:eval (graph)");
                 return cuda_ok(cudaGraphLaunch(g.exec, st));
             }
         bool seen = false;
@@ -788,12 +789,36 @@ fmm_status fmm_status_word(fmm_handle* H, int* device_status, void* stream) {
     fmm_status e;
     if ((e = cuda_ok(cudaStreamSynchronize(st)))) return e;
     if ((e = cuda_ok(cudaMemcpy(device_status, h.status, sizeof(int), cudaMemcpyDeviceToHost)))) return e;
+    // the bounds-checked build's index-check words (always 0 otherwise)
+    const int bc[3] = {bc_take_kernels(), bc_take_m2l(), bc_take_translate()};
+    const char* files[3] = {"kernels.cu", "m2l_tc.cu", "translate_tc.cu"};
+    for (int i = 0; i < 3; ++i)
+        if (bc[i]) {
+            if (!(*device_status & FMM_DEV_BOUNDS))
+                snprintf(g_last_error, sizeof(g_last_error), "index check failed at %s:%d", files[i], bc[i]);
+            *device_status |= FMM_DEV_BOUNDS;
+        }
     return cuda_ok(cudaMemset(h.status, 0, sizeof(int)));
+}
+
+int fmm_build_flags(void) {
+#ifdef FMM_BOUNDS_CHECK
+    return FMM_BUILD_BOUNDS_CHECK;
+#else
+    return 0;
+#endif
 }
 
 fmm_status fmm_inject_alloc_failure(int n) {
     if (n < 0) return FMM_ERR_ARG;
     g_fail_alloc_in.store(n);
+    return FMM_OK;
+}
+
+fmm_status fmm_inject_copy_loss(fmm_handle* H, int mask) {
+    if (!H || (mask & ~(FMM_LOSE_TRANSLATE | FMM_LOSE_NEAR))) return FMM_ERR_ARG;
+    H->h.copy_loss = mask;
+    ++H->h.gen;  // a kernel argument: the captured evaluation graph no longer applies
     return FMM_OK;
 }
 

@@ -1,6 +1,8 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -11,6 +13,22 @@ namespace fmmcph {
 // Every device allocation of the library goes through here, so that a test can make one fail
 // (fmm_inject_alloc_failure) and check the FMM_ERR_OOM paths.
 cudaError_t device_alloc(void** p, size_t bytes);
+
+// NVTX range "fmm:<stage>" around the host-side launches of one stage of an evaluation, so that
+// a profiler attributes the kernels to stages (ncu --nvtx --nvtx-include "fmm:near/").  Without
+// an attached tool the calls do nothing.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+
+// The bounds-checked build's per-file words (bounds.cuh): the source line of the first failed
+// index check since the last call, 0 for none (always 0 in the normal build).
+int bc_take_kernels();
+int bc_take_m2l();
+int bc_take_translate();
 
 constexpr int kMaxP = FMM_MAX_P;
 constexpr int kMaxDepth = 7;
@@ -112,9 +130,13 @@ struct Handle {
     int* status = nullptr;
     float* work = nullptr;  // split-K partial products (8 x the largest M2M output level)
     bool charges_set = false;
-    // limit (clock cycles) of the pipeline waits of the tensor-core M2L; 0 = the default
-    // (about 2 s), a small value lets a test make the waits expire (fmm_set_wait_limit)
+    // limit (clock cycles) of the pipeline waits of the tensor-core M2L, M2M and L2L and of the
+    // near field's staging waits; 0 = the default (about 2 s), a small value lets a test make
+    // the waits expire (fmm_set_wait_limit)
     long long wait_limit = 0;
+    // test hook (fmm_inject_copy_loss): FMM_LOSE_* bits of the kernels whose bulk copies are
+    // announced on their barriers but not issued, so that their bounded waits run out
+    int copy_loss = 0;
     // kernel tiles (fmm_options): the tensor-core M2L's rows per CTA (0 = 192) and the near
     // field's leaves (warps) per block (2, 4 or 8)
     int m2l_rows = 0;
@@ -178,7 +200,8 @@ TranslateOp translate_pack(const std::vector<float>& W, int Mtot, int K);  // W 
 void translate_free(TranslateOp& op);
 void translate_configure();
 void translate_tc(const TranslateOp& op, const float* X, int ldx, int N, float* C, int ldc, bool accumulate,
-                  int* status, cudaStream_t st, int ksplit = 1, float* work = nullptr);
+                  int* status, cudaStream_t st, int ksplit = 1, float* work = nullptr, long long wait_limit = 0,
+                  bool lose_copies = false);
 // m2l_tc.cu
 bool m2l_tc_supported(const Handle* h);
 bool m2l_tile_rows_ok(int rows);  // 0 (the default) or a width the kernel is instantiated for

@@ -21,11 +21,14 @@
 #include <cstdio>
 #include <mutex>
 
+#include "bounds.cuh"
 #include "fmm_internal.h"
 #include "sgemm.cuh"
 #include "tc_ptx.cuh"
 
 namespace fmmcph {
+
+FMM_BC_TAKE(bc_take_kernels)
 
 // ---- constant tables of the normalised regular-harmonic recurrences ----
 __constant__ float c_dg[kMaxP + 2];                   // sqrt((2m-1)/(2m))
@@ -178,8 +181,10 @@ __global__ void __launch_bounds__(kCountThreads) k_bin_count(int n, const float*
         bool bad = false;
         const uint32_t k = leaf_key(x, i, g, bad);
         key[i] = k;
-        slot[i] = atomicAdd(leafcnt + k, 1u);
-        if (ntiles > 1) atomicAdd(hist + k / kScanTile, 1u);
+        if (FMM_IN(k, 1u << (3 * g.depth))) {
+            slot[i] = atomicAdd(leafcnt + k, 1u);
+            if (ntiles > 1) atomicAdd(hist + k / kScanTile, 1u);
+        }
         if (bad) atomicOr(status, FMM_DEV_DOMAIN);
     }
     if (ntiles > 1) {
@@ -263,7 +268,8 @@ __global__ void k_bin_place(int n, const uint32_t* __restrict__ key, const uint3
     if (blockIdx.x == 0)  // every k_bin_scan block has read them
         for (int t = threadIdx.x; t < ntiles; t += blockDim.x) tilecnt[t] = 0u;
     if (i >= n) return;
-    placed[start[key[i]] + slot[i]] = (uint32_t)i;
+    const uint32_t d = start[key[i]] + slot[i];
+    if (FMM_IN(d, n)) placed[d] = (uint32_t)i;
 }
 
 // The charge forms of the atoms and the site coordinates (Sec. 2.1, Eq. 1 and Eq. 2).
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
                                                           const float* __restrict__ x, BoxGeom g, ChargeForms cf,
                                                           float4* __restrict__ pos, uint32_t* __restrict__ inv,
                                                           int* __restrict__ status, int2* __restrict__ items,
-                                                          int items_cap) {
+                                                          int items_cap, int n) {
     // a warp takes leaves l0 and l0 + 1
     const int l0 = 2 * (blockIdx.x * 4 + (threadIdx.x >> 5)), lane = threadIdx.x & 31;
     if (l0 >= nleaf) return;
@@ -351,10 +357,10 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
         const int half = lane >> 4, sub = lane & 15, c = half ? c1 : c0;
         const int leaf = l0 + half;
         const int st = c > 0 ? (int)start[leaf] : 0;
-        const uint32_t v = sub < c ? placed[st + sub] : 0xFFFFFFFFu;
+        const uint32_t v = sub < c && FMM_IN(st + sub, n) ? placed[st + sub] : 0xFFFFFFFFu;
         int r = 0;  // rank = number of smaller indices in the leaf (padding is never smaller)
         for (int k = 0; k < 16; ++k) r += __shfl_sync(0xffffffffu, v, k, 16) < v ? 1 : 0;
-        if (sub < c) {
+        if (sub < c && FMM_IN(v, n) && FMM_IN(st + r, n)) {
             perm[st + r] = v;
             skey[st + r] = (uint32_t)leaf;
             gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
@@ -363,11 +369,12 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
     }
     for (int leaf = l0; leaf < l0 + (two ? 2 : 1); ++leaf) {
         const int st = (int)start[leaf], c = leaf == l0 ? c0 : c1;
+        if (!FMM_OK(st >= 0 && st + c <= n)) continue;  // (st and c are the warp's own: no divergence)
         if (c <= 32) {  // the whole leaf in one register per lane
             const uint32_t v = lane < c ? placed[st + lane] : 0xFFFFFFFFu;
             int r = 0;
             for (int k = 0; k < c; ++k) r += __shfl_sync(0xffffffffu, v, k) < v ? 1 : 0;
-            if (lane < c) {
+            if (lane < c && FMM_IN(v, n)) {
                 perm[st + r] = v;
                 skey[st + r] = (uint32_t)leaf;
                 gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
@@ -380,6 +387,7 @@ __global__ void __launch_bounds__(128) k_bin_order_gather(int nleaf, const uint3
             const uint32_t v = placed[st + e];
             int r = 0;
             for (int k = 0; k < c; ++k) r += placed[st + k] < v ? 1 : 0;
+            if (!FMM_IN(v, n)) continue;
             perm[st + r] = v;
             skey[st + r] = (uint32_t)leaf;
             gather_atom((int)v, st + r, x, g, cf, pos, inv, status);
@@ -661,14 +669,16 @@ __device__ __forceinline__ void p2m_leaf_cols(const float4* __restrict__ pos, in
 template <int P>
 __global__ void __launch_bounds__(128) k_p2m(int nleaf, float h, const uint32_t* __restrict__ start,
                                              const uint32_t* __restrict__ count, const float4* __restrict__ pos,
-                                             float* __restrict__ M, int ncp, float* __restrict__ leafmom) {
+                                             float* __restrict__ M, int ncp, float* __restrict__ leafmom, int n) {
     using Cfg = P2mCfg<P>;
     constexpr int NC = Cfg::NC, MS = Cfg::MS;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int leaf = blockIdx.x * kP2mLeaves + (w & 1) * 16 + (lane >> 1);
     const int par = lane & 1;
     const bool valid = leaf < nleaf;
-    const int st = valid ? (int)start[leaf] : 0, cnt = valid ? (int)count[leaf] : 0;
+    const int st = valid ? (int)start[leaf] : 0;
+    int cnt = valid ? (int)count[leaf] : 0;
+    if (!FMM_OK(st >= 0 && st + cnt <= n)) cnt = 0;  // (the lanes still run the shuffles together)
     const uint32_t lf = valid ? (uint32_t)leaf : 0u;
     const float cx = (compact3(lf) + 0.5f) * h, cy = (compact3(lf >> 1) + 0.5f) * h,
                 cz = (compact3(lf >> 2) + 0.5f) * h;
@@ -1103,7 +1113,7 @@ __device__ __forceinline__ void l2p_eval(const float* __restrict__ Lb, float x, 
 }
 
 struct NearParams {
-    int nleaf, depth, periodic, use_far, ncp;
+    int n, nleaf, depth, periodic, use_far, ncp;
     float h, Lbox, ke;
     const uint32_t* start;
     const uint32_t* count;
@@ -1120,6 +1130,7 @@ struct NearParams {
     int leaves_per_warp;  // consecutive target leaves of each near-field warp
     const int2* items;    // work items (leaf, tile) of the leaves above kNearTile atoms, count in items[0].x
     int items_cap;
+    int lose_copies;      // test hook (fmm_inject_copy_loss): staging copies announced, not issued
 };
 
 // Outputs per atom, one thread per atom in leaf order: the far field (L2P of the leaf's local
@@ -1143,12 +1154,13 @@ __global__ void __launch_bounds__(kOutThreads) k_far_out(int n, int use_far, Nea
     float2 e = make_float2(0.f, 0.f);
     if (s < n) {
         const uint32_t leaf = skey[s];
+        const bool leaf_ok = FMM_IN(leaf, a.nleaf);
         const float h = a.h;
         const float cx = (compact3(leaf) + 0.5f) * h, cy = (compact3(leaf >> 1) + 0.5f) * h,
                     cz = (compact3(leaf >> 2) + 0.5f) * h;
         const float4 me = a.pos[s];
         float pot = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-        if (use_far) {
+        if (use_far && leaf_ok) {
             const float ih = 1.0f / h;
             l2p_eval<P>(a.Lleaf + (long)leaf * a.ncp, (me.x - cx) * ih, (me.y - cy) * ih, (me.z - cz) * ih, pot, gx,
                         gy, gz);
@@ -1173,12 +1185,12 @@ __global__ void __launch_bounds__(kOutThreads) k_far_out(int n, int use_far, Nea
         gz += nr.w;
         const int i = (int)a.perm[s];
         const float q = me.w;
-        if (a.F) {
+        if (a.F && FMM_IN(i, n)) {
             a.F[3L * i] = -a.ke * q * gx;
             a.F[3L * i + 1] = -a.ke * q * gy;
             a.F[3L * i + 2] = -a.ke * q * gz;
         }
-        if (a.phi_out) a.phi_out[i] = a.ke * pot;
+        if (a.phi_out && FMM_IN(i, n)) a.phi_out[i] = a.ke * pot;
         a.phis[s] = pot;
         const float qp = q * pot;
         e = make_float2(qp, fmaf(q, pot, -qp));
@@ -1208,7 +1220,7 @@ __global__ void __launch_bounds__(kOutThreads) k_far_out(int n, int use_far, Nea
 // local expansion of a unit charge at the root centre (the lattice operator's first column)
 // at u = r / L.
 struct HiParams {
-    int K, periodic, nforms;
+    int n, K, periodic, nforms;
     float L, ke, c2;
     const float* coef;  // h, normalised root local expansion (periodic)
     const int* site_ptr;
@@ -1298,6 +1310,7 @@ __global__ void __launch_bounds__(128) k_hi(HiParams p) {
     double e = 0.0, ep = 0.0, et = 0.0;
     for (int a = lane; a < na; a += 32) {
         const int ia = p.site_atoms[a0 + a];
+        if (!FMM_IN(ia, p.n) || !FMM_IN(p.inv[ia], p.n)) continue;  // (no shuffle inside this loop)
         const float4 pa = p.pos[p.inv[ia]];
         float da[4];
         hi_dev(p, ia, w, da);
@@ -1314,6 +1327,7 @@ __global__ void __launch_bounds__(128) k_hi(HiParams p) {
         for (int b = 0; b < na; ++b) {
             if (b == a) continue;
             const int ib = p.site_atoms[a0 + b];
+            if (!FMM_IN(ib, p.n) || !FMM_IN(p.inv[ib], p.n)) continue;
             const float4 pb = p.pos[p.inv[ib]];
             float db[4];
             hi_dev(p, ib, w, db);
@@ -1496,6 +1510,7 @@ __device__ __forceinline__ NearStage near_segments(const NearParams& a, int lane
             const uint32_t src = morton3(wx, wy, wz);
             t.s0 = (int)a.start[src];
             t.sc = (int)a.count[src];
+            if (!FMM_OK(t.s0 >= 0 && t.s0 + t.sc <= a.n)) t.sc = 0;  // an empty segment instead
             t.shx = (float)(sx - wx) * a.h;
             t.shy = (float)(sy - wy) * a.h;
             t.shz = (float)(sz - wz) * a.h;
@@ -1525,7 +1540,8 @@ __device__ __forceinline__ NearStage near_stage(const NearParams& a, float4* buf
     const bool staged = t.cnt > 0 && t.cnt <= kNearTile && ((t.total + 1) & ~1) <= kNearCap;
     if (lane == 0) tc::mbar_arrive_expect_tx(bar, staged ? 16u * (uint32_t)(t.total - (t.cnt & 1)) : 0u);
     __syncwarp();
-    if (staged && lane < 27 && t.sc > 0) tc::bulk_g2s(buf + t.off, a.pos + t.s0, 16u * (uint32_t)t.sc, bar);
+    if (staged && lane < 27 && t.sc > 0 && !a.lose_copies && FMM_OK(t.off + t.sc <= kNearCap))
+        tc::bulk_g2s(buf + t.off, a.pos + t.s0, 16u * (uint32_t)t.sc, bar);
     return t;
 }
 
@@ -1709,7 +1725,8 @@ __device__ __noinline__ bool near_item(const NearParams& a, float4* buf, uint64_
         if (lane == 0) tc::mbar_arrive_expect_tx(bar, 16u * (uint32_t)(ra + (r == 0 ? tcnt : 0)));
         __syncwarp();
         if (r == 0 && lane == 0) tc::bulk_g2s(buf, a.pos + st, 16u * (uint32_t)tcnt, bar);
-        if (has) tc::bulk_g2s(buf + tslot + (lo - r0), a.pos + T.s0 + (lo - excl), 16u * (uint32_t)(hi - lo), bar);
+        if (has && FMM_OK(tslot + (hi - r0) <= kNearCap))  // (a skipped copy ends in the bounded wait)
+            tc::bulk_g2s(buf + tslot + (lo - r0), a.pos + T.s0 + (lo - excl), 16u * (uint32_t)(hi - lo), bar);
         if (!tc::mbar_wait_all(bar, ph & 1u, a.wlim)) {
             if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
             tc::mbar_wait_all(bar, ph & 1u, kNearWait);  // nothing may still be copying when the warp exits
@@ -1758,6 +1775,7 @@ __device__ __forceinline__ void near_big(const NearParams& a, float4* buf, uint6
     const int nitems = min(items[0].x, a.items_cap);
     for (int item = first; item < nitems; item += stride) {
         const int2 it = items[1 + item];
+        if (!FMM_IN(it.x, a.nleaf)) continue;  // (the warp's lanes read the same item)
         if (!near_item(a, buf, bar, ph, lane, it.x, it.y * kNearTile, near)) return;
     }
 }
@@ -1791,7 +1809,8 @@ __global__ void __launch_bounds__(32 * W, 20 / W) k_p2p(NearParams a, float4* __
             const NearStage cur = near_stage(a, S.buf, &S.bar, lane, leaf);
             if (!tc::mbar_wait_all(&S.bar, ph & 1u, a.wlim)) {
                 if (lane == 0) atomicOr(a.status, FMM_DEV_TIMEOUT);
-                tc::mbar_wait_all(&S.bar, ph & 1u, kNearWait);  // nothing may still be copying when the warp exits
+                // nothing may still be copying when the warp exits (with lost copies nothing is)
+                if (!a.lose_copies) tc::mbar_wait_all(&S.bar, ph & 1u, kNearWait);
                 return;
             }
             ++ph;
@@ -1842,7 +1861,7 @@ void near_configure(Handle* h) {
 // site's atoms of dq phi (FP64), one warp per site in a fixed order.
 constexpr int kFinalBlocks = 32;
 static_assert(8 + 5 * kQdtBlocks + 4 + kFinalBlocks + 1 <= kRootDoubles, "root scratch layout");
-__global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restrict__ epart, double ke,
+__global__ void __launch_bounds__(256) k_final(int n, int nparts, const float2* __restrict__ epart, double ke,
                                                double* __restrict__ E, int K, int ncoord,
                                                const int* __restrict__ site_ptr,
                                                const int* __restrict__ site_atoms, const uint32_t* __restrict__ inv,
@@ -1885,6 +1904,7 @@ __global__ void __launch_bounds__(256) k_final(int nparts, const float2* __restr
         for (int k = (blockIdx.x * 256 + threadIdx.x) >> 5; k < K; k += kFinalBlocks * 8) {
             double v = 0.0, vt = 0.0;  // dE/dlambda(_p), dE/dlambda_t
             for (int a = site_ptr[k] + lane; a < site_ptr[k + 1]; a += 32) {
+                if (!FMM_IN(site_atoms[a], n) || !FMM_IN(inv[site_atoms[a]], n)) continue;  // (no shuffle in the loop)
                 const uint32_t si = inv[site_atoms[a]];
                 v += (double)dq[si] * (double)phis[si];
                 if (ncoord == 2) vt += (double)dqt[si] * (double)phis[si];
@@ -1944,7 +1964,7 @@ template <int P>
 static void launch_p2m(int nleaf, float h, const Handle* hd, float* Mleaf, float* mom,
                        cudaStream_t st) {
     k_p2m<P><<<(nleaf + kP2mLeaves - 1) / kP2mLeaves, 128, 0, st>>>(nleaf, h, hd->start, hd->count, hd->pos,
-                                                                     Mleaf, hd->ncp, mom);
+                                                                     Mleaf, hd->ncp, mom, hd->n);
 }
 template <int P>
 static void launch_far_out(int n, int use_far, const NearParams& a, const uint32_t* skey, const float4* near,
@@ -1999,7 +2019,8 @@ static void l2l_level(Handle* h, int l, cudaStream_t st) {
     const int np = 1 << (3 * (l - 1));
     if (h->l2l_tc.dev)  // coarse levels split over K (one chunk per block), summed in a fixed order
         translate_tc(h->l2l_tc, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, np, h->L + h->lvl_off[l] * h->ncp,
-                     8 * h->ncp, true, h->status, st, split_slices(h->depth, l, 8), h->work);
+                     8 * h->ncp, true, h->status, st, split_slices(h->depth, l, 8), h->work, h->wait_limit,
+                     (h->copy_loss & FMM_LOSE_TRANSLATE) != 0);
     else
         sgemm(np, 8 * h->ncp, h->ncp, h->L + h->lvl_off[l - 1] * h->ncp, h->ncp, h->B2, 8 * h->ncp,
               h->L + h->lvl_off[l] * h->ncp, 8 * h->ncp, true, st);
@@ -2043,8 +2064,10 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const float* lam = h->lam_bound ? h->lam_bound : h->lam;
     h->ev_used = 0;
     for (auto& se : h->stage_ev) se[0] = se[1] = -1;
+    TraceRange trace_eval("fmm:eval");
     const int e0 = mark(h, st);
     // --- binning: counting sort by leaf (see k_bin_count .. k_bin_order_gather) ---
+    nvtxRangePushA("fmm:binning");
     const int ntiles = scan_tiles(nleaf);
     uint32_t* tilecnt = h->leafcnt + nleaf;  // [ntiles] atoms per tile of kScanTile leaves
     if (n > 0)
@@ -2058,10 +2081,12 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         ChargeForms cf{{h->qA, h->qB, h->qC, h->qD}, h->nforms, h->site, h->K, lam, h->dq, h->dqt};
         k_bin_order_gather<<<((nleaf + 1) / 2 + 3) / 4, 128, 0, st>>>(nleaf, h->start, h->count, h->vB, h->perm,
                                                             h->sorted_key, x, g, cf, h->pos, h->inv, h->status,
-                                                            h->near_items, h->near_items_cap);
+                                                            h->near_items, h->near_items_cap, n);
     }
+    nvtxRangePop();
     // --- near field on the caller's stream, concurrent with the multipole chain ---
     NearParams a{};
+    a.n = n;
     a.nleaf = nleaf;
     a.depth = d;
     a.periodic = h->periodic;
@@ -2084,6 +2109,7 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     a.wlim = h->wait_limit > 0 ? h->wait_limit : kNearWait;
     a.items = h->near_items;
     a.items_cap = h->near_items_cap;
+    a.lose_copies = (h->copy_loss & FMM_LOSE_NEAR) != 0;
     const int e1 = mark(h, st);
     span(h, 0, e0, e1);
     // fork: the chain P2M .. L2L on h->chain (highest priority), P2P here.  Serialised
@@ -2094,35 +2120,43 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
     const int lc = coarse_top(h);  // top coarse level of the side branch, -1 without one
     cudaEventRecord(h->fork_ev, st);
     cudaStreamWaitEvent(cs, h->fork_ev, 0);
+    nvtxRangePushA("fmm:near");
     if (h->p2p_warps == 1) launch_p2p<1>(a, h->near, st);
     else if (h->p2p_warps == 2) launch_p2p<2>(a, h->near, st);
     else launch_p2p<4>(a, h->near, st);
+    nvtxRangePop();
     const int e1n = mark(h, st);
     span(h, 8, e1, e1n);
     const int e1c = serial ? e1n : e1;  // start of the chain's first stage
     // --- P2M ---
     float* Mleaf = h->M + h->lvl_off[d] * h->ncp;
     float* Lleaf = h->L + h->lvl_off[d] * h->ncp;
+    nvtxRangePushA("fmm:P2M");
     FMM_DISPATCH_P(h->p, launch_p2m, nleaf, hleaf, h, Mleaf, h->periodic ? h->leafmom : nullptr, cs);
+    nvtxRangePop();
     const int e2 = mark(h, cs);
     span(h, 1, e1c, e2);
     // --- M2M (FP32) for parent levels d-1 .. lmin: one GEMM per level,
     //     [parents x 8 ncp] (the 8 children are contiguous) x [8 ncp x ncp] ---
     const int lmin = h->periodic ? 1 : 2;
+    nvtxRangePushA("fmm:M2M");
     for (int l = d - 1; l >= lmin; --l) {
         const int np = 1 << (3 * l);
         if (h->m2m_tc.dev)  // split K by child octant; coarse levels into up to 32 slices (their latency)
             translate_tc(h->m2m_tc, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, np, h->M + h->lvl_off[l] * h->ncp,
-                         h->ncp, false, h->status, cs, split_slices(d, l, 32), h->work);
+                         h->ncp, false, h->status, cs, split_slices(d, l, 32), h->work, h->wait_limit,
+                         (h->copy_loss & FMM_LOSE_TRANSLATE) != 0);
         else
             sgemm(np, h->ncp, 8 * h->ncp, h->M + h->lvl_off[l + 1] * h->ncp, 8 * h->ncp, h->A, h->ncp,
                   h->M + h->lvl_off[l] * h->ncp, h->ncp, false, cs, 8, h->work);  // split K by child octant
     }
+    nvtxRangePop();
     const int e3 = mark(h, cs);
     span(h, 2, e2, e3);
     // --- periodic root (FP64): root multipole, lattice operator, Q/D/T for the background term ---
     auto root = [&](cudaStream_t rs) {
         if (!h->periodic) return;
+        TraceRange trace("fmm:root");
         const int nrowblk = (h->nc + 3) / 4;
         const float* M1 = (d >= 1) ? h->M + h->lvl_off[1] * h->ncp : nullptr;
         k_qdt<<<kQdtBlocks, 256, 0, rs>>>(nleaf, h->box.edge / nb, 0.5 * h->box.edge, h->leafmom, h->root + h->nc + 8);
@@ -2144,30 +2178,39 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         cudaStream_t ss = serial ? st : h->side;
         cudaEventRecord(h->m2m_ev, cs);
         cudaStreamWaitEvent(ss, h->m2m_ev, 0);
+        nvtxRangePushA("fmm:M2L coarse");
         launch_m2l_tc(h, ss, lmin, lc, kM2lPack);
         launch_m2l_tc(h, cs, lc + 1, d, kM2lPack);
         const int s0 = mark(h, ss);
         launch_m2l_tc(h, ss, lmin, lc, kM2lMma);
+        nvtxRangePop();
         const int s1 = mark(h, ss);
         span(h, 9, s0, s1);
         root(ss);
         const int s2 = mark(h, ss);
         if (h->periodic) span(h, 3, s1, s2);
+        nvtxRangePushA("fmm:L2L coarse");
         for (int l = lfirst; l <= lc; ++l) l2l_level(h, l, ss);
+        nvtxRangePop();
         span(h, 10, s2, mark(h, ss));
         cudaEventRecord(h->side_ev, ss);
         // chain: the finest levels' M2L, then the L2L into them from the side branch's levels
         const int e4 = mark(h, cs);
+        nvtxRangePushA("fmm:M2L");
         launch_m2l_tc(h, cs, lc + 1, d, kM2lMma);
+        nvtxRangePop();
         const int e5 = mark(h, cs);
         span(h, 4, e4, e5);
         cudaStreamWaitEvent(cs, h->side_ev, 0);
+        nvtxRangePushA("fmm:L2L");
         for (int l = std::max(lfirst, lc + 1); l <= d; ++l) l2l_level(h, l, cs);
+        nvtxRangePop();
         span(h, 5, e5, mark(h, cs));
     } else {
         root(cs);
         const int e4 = mark(h, cs);
         if (h->periodic) span(h, 3, e3, e4);
+        nvtxRangePushA("fmm:M2L");
         if (d >= lmin && h->ntiles > 0) {
             if (h->precision != FMM_FP32 && m2l_tc_supported(h)) {
                 launch_m2l_tc(h, cs, lmin, d);
@@ -2188,19 +2231,24 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
                         h->tiles, h->nc, h->ncp, h->T, h->M, h->L, lo, h->periodic);
             }
         }
+        nvtxRangePop();
         const int e5 = mark(h, cs);
         span(h, 4, e4, e5);
+        nvtxRangePushA("fmm:L2L");
         for (int l = lfirst; l <= d; ++l) l2l_level(h, l, cs);
+        nvtxRangePop();
         span(h, 5, e5, mark(h, cs));
     }
     const int e6 = h->stage_ev[5][1];
     // join, then the far field and the outputs per atom
     cudaEventRecord(h->join_ev, cs);
     cudaStreamWaitEvent(st, h->join_ev, 0);
+    nvtxRangePushA("fmm:far+outputs");
     if (n > 0) FMM_DISPATCH_P(h->p, launch_far_out, n, a.use_far, a, h->sorted_key, h->near, st);
     const bool hi = h->hamiltonian && h->K > 0;
     if (hi) {
         HiParams hp{};
+        hp.n = n;
         hp.K = h->K;
         hp.periodic = h->periodic;
         hp.nforms = h->nforms;
@@ -2222,11 +2270,12 @@ int launch_eval(Handle* h, const float* x, double* E, float* F, float* dVdl, flo
         hp.g_h = h->hi_g;
         FMM_DISPATCH_P(h->p, launch_hi, hp, st);
     }
+    nvtxRangePop();
     const int e7 = mark(h, st);
     span(h, 6, e6, e7);
     const int nparts = (n + kOutThreads - 1) / kOutThreads;  // one q phi partial per output block
     double* fin = h->root + h->nc + 8 + 5 * kQdtBlocks + 4;  // [kFinalBlocks] block totals, then the ticket
-    k_final<<<kFinalBlocks, 256, 0, st>>>(nparts, h->epart, h->ke, E, h->K, h->ncoord, h->site_ptr, h->site_atoms,
+    k_final<<<kFinalBlocks, 256, 0, st>>>(n, nparts, h->epart, h->ke, E, h->K, h->ncoord, h->site_ptr, h->site_atoms,
                                           h->inv, h->dq, h->dqt, h->phis, dVdl, fin,
                                           reinterpret_cast<unsigned int*>(fin + kFinalBlocks), hi ? h->hi_site : nullptr);
     span(h, 7, e7, mark(h, st));

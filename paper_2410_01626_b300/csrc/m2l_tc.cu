@@ -33,10 +33,13 @@
 #include <cstring>
 #include <vector>
 
+#include "bounds.cuh"
 #include "fmm_internal.h"
 #include "tc_ptx.cuh"
 
 namespace fmmcph {
+
+FMM_BC_TAKE(bc_take_m2l)
 
 namespace {
 
@@ -160,6 +163,10 @@ __global__ void k_m2l_pack(PackLevels pl, int NKG, int ncp, int periodic, const 
     }
     if (ok) {
         const uint32_t box = ((spread3_tc(i) | (spread3_tc(j) << 1) | (spread3_tc(k) << 2)) << 3) | (uint32_t)cls;
+        ok = FMM_IN(box, 8L * n * n * n);
+    }
+    if (ok) {
+        const uint32_t box = ((spread3_tc(i) | (spread3_tc(j) << 1) | (spread3_tc(k) << 2)) << 3) | (uint32_t)cls;
         if (BF16) {
             const float4 x0 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + 8 * g);
             const float4 x1 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + 8 * g + 4);
@@ -218,8 +225,8 @@ __global__ void k_m2l_pack_f16mix(PackLevels pl, int NKG, int ncp, int periodic,
         ok = ok && i >= 0 && i < n && j >= 0 && j < n && k >= 0 && k < n;
     }
     uint4 out = make_uint4(0u, 0u, 0u, 0u);
-    if (ok) {
-        const uint32_t box = ((spread3_tc(i) | (spread3_tc(j) << 1) | (spread3_tc(k) << 2)) << 3) | (uint32_t)cls;
+    const uint32_t box = ((spread3_tc(i) | (spread3_tc(j) << 1) | (spread3_tc(k) << 2)) << 3) | (uint32_t)cls;
+    if (ok && FMM_IN(box, 8L * n * n * n)) {
         const float4 x0 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + base);
         const float4 x1 = *reinterpret_cast<const float4*>(Mlev + (long)box * ncp + base + 4);
         float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
@@ -349,8 +356,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int rlq = min(nr + 2 * hal, R - rsq);
                 const long e = (((long)pi * NKG + ch * kTcKG + kg) * R + rsq) * 4;
                 uint8_t* dq = dst + (size_t)kg * kg_stride + (size_t)q * slab_rows * 16;
-                tc::bulk_g2s(dq, Mlev + e, (uint32_t)rlq * 16u, slab_full + buf);
-                if (SPLIT) tc::bulk_g2s(dq + part_bytes, Mlev_lo + e, (uint32_t)rlq * 16u, slab_full + buf);
+                // (a skipped copy ends in the bounded wait of the MMA issuer)
+                if (FMM_OK(rsq >= 0 && rlq > 0 && rlq <= slab_rows && rsq + rlq <= R)) {
+                    tc::bulk_g2s(dq, Mlev + e, (uint32_t)rlq * 16u, slab_full + buf);
+                    if (SPLIT) tc::bulk_g2s(dq + part_bytes, Mlev_lo + e, (uint32_t)rlq * 16u, slab_full + buf);
+                }
             }
             ++slabs_issued;
         };
@@ -408,7 +418,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (mine) {
                     const int op = sel[i0 + lane];
                     tc::mbar_arrive_expect_tx(t_full + stage, kTcTBytes);
-                    tc::bulk_g2s(tring + (size_t)stage * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
+                    if (FMM_IN(op, kNumOps))
+                        tc::bulk_g2s(tring + (size_t)stage * kTcTBytes, Ttc + ((long)op * NKC + ch) * (kTcTBytes / 4),
                                  kTcTBytes, t_full + stage);  // hi (+ lo) operator chunk
                 }
                 t_issued += nr;
@@ -626,6 +637,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (r < R && ip >= 1 && ip <= n && jp >= 1 && jp <= n && kp >= 1 && kp <= n)
                     off = (int)(((spread3_tc(ip - 1) | (spread3_tc(jp - 1) << 1) | (spread3_tc(kp - 1) << 2)) << 3) |
                                 (uint32_t)c) * ncp;
+                if (off >= 0 && !FMM_IN(off / ncp, 8L * n * n * n)) off = -1;
                 tab[e] = off;
             }
             __syncwarp();

@@ -21,10 +21,13 @@
 #include <cstring>
 #include <vector>
 
+#include "bounds.cuh"
 #include "fmm_internal.h"
 #include "tc_ptx.cuh"
 
 namespace fmmcph {
+
+FMM_BC_TAKE(bc_take_translate)
 
 namespace {
 
@@ -35,16 +38,21 @@ constexpr int kGChunk = 16;               // K coefficients per stage
 constexpr int kGCells = kGChunk / 4;      // 16-byte cells (4 TF32) per row and stage
 constexpr uint32_t kGPart = kGRows * kGChunk * 4;  // one hi or lo part of a stage operand: 8 KB
 constexpr uint32_t kGStage = 2 * kGPart;           // hi + lo: 16 KB
-constexpr long long kGWaitLimit = 4000000000LL;    // clock cycles (about 2 s)
+constexpr long long kGWaitLimit = 4000000000LL;    // clock cycles (about 2 s): the default
+                                                   // pipeline limit, and always that of the
+                                                   // drains after an abort
 constexpr size_t kGSmem = 2 * (size_t)kGStage * 2 + 1024;  // two stages of W and X, barriers
 
 
 // grid: (N tiles, M tiles, K slices).  Slice z covers chunks [z kps, (z + 1) kps) and writes
-// C + z cstride; accumulate adds to C instead of overwriting it.
+// C + z cstride; accumulate adds to C instead of overwriting it.  wlim bounds the pipeline's
+// waits (clock cycles); when one expires the CTA stops issuing, waits for what it issued, sets
+// FMM_DEV_TIMEOUT and writes nothing.  lose_copies (a test hook, fmm_inject_copy_loss): the W
+// copies are announced on their barrier but not issued.
 __global__ void __launch_bounds__(kGThreads, 1)
     k_translate_tc(const uint8_t* __restrict__ Wp, int Mtot, int nkc, int K, const float* __restrict__ X, int ldx,
                    int N, float* __restrict__ C, int ldc, int accumulate, int kps, long cstride,
-                   int* __restrict__ status) {
+                   int* __restrict__ status, long long wlim, int lose_copies) {
     extern __shared__ __align__(1024) uint8_t gsm[];
     uint8_t* wst = gsm;                       // [2 stages][hi, lo][cell][128 rows][16 B]
     uint8_t* xst = gsm + 2 * (size_t)kGStage;
@@ -95,9 +103,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
     int w_issued = 0, w_taken = 0;  // W chunks copied / consumed (thread 0)
     auto issue_w = [&](int i) {  // W chunk kc0 + i into stage i & 1 (thread 0)
         const int s = i & 1;
-        ++w_issued;
         tc::mbar_arrive_expect_tx(w_full + s, kGStage);
-        tc::bulk_g2s(wst + (size_t)s * kGStage, Wp + ((size_t)mt * nkc + kc0 + i) * kGStage, kGStage, w_full + s);
+        if (lose_copies) return;  // test hook: announced, never issued, so the wait runs out
+        ++w_issued;
+        if (FMM_IN((long)mt * nkc + kc0 + i, (long)((Mtot + kGRows - 1) / kGRows) * nkc))  // (else the bounded wait)
+            tc::bulk_g2s(wst + (size_t)s * kGStage, Wp + ((size_t)mt * nkc + kc0 + i) * kGStage, kGStage, w_full + s);
     };
     float4 xv[kHalfCells], xn[kHalfCells];
     if (nch > 0) {
@@ -108,7 +118,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const int s = i & 1;
         // stage s is free once the MMAs of chunk i - 2 have completed; every thread waits, and
         // the abort decision is taken by all threads together after the barrier
-        if (i >= 2 && !tc::mbar_wait(mma_done + s, ((i >> 1) - 1) & 1, kGWaitLimit)) *abort_flag = 1;
+        if (i >= 2 && !tc::mbar_wait(mma_done + s, ((i >> 1) - 1) & 1, wlim)) *abort_flag = 1;
         __syncthreads();
         if (*abort_flag) break;
         if (i + 1 < nch) load_x(kc0 + i + 1, xn);  // next chunk's rows, in flight during this one
@@ -129,7 +139,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         tc::fence_proxy_async();  // the generic-proxy stores above, for the tensor core
         __syncthreads();
         if (t == 0) {
-            if (!tc::mbar_wait(w_full + s, (i >> 1) & 1, kGWaitLimit)) {
+            if (!tc::mbar_wait(w_full + s, (i >> 1) & 1, wlim)) {
                 *abort_flag = 1;
             } else {
                 ++w_taken;
@@ -146,7 +156,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 tc::mma_commit(mma_done + s);
                 // the next W chunk goes to the other stage once the MMAs of chunk i - 1 are done
                 if (i + 1 < nch) {
-                    if (i >= 1 && !tc::mbar_wait(mma_done + (s ^ 1), ((i - 1) >> 1) & 1, kGWaitLimit))
+                    if (i >= 1 && !tc::mbar_wait(mma_done + (s ^ 1), ((i - 1) >> 1) & 1, wlim))
                         *abort_flag = 1;
                     else
                         issue_w(i + 1);
@@ -269,10 +279,12 @@ void translate_configure() {
 
 // C[p * ldc + m] (=|+=) sum_k W[m][k] X[p * ldx + k] for boxes p < N.  With ksplit > 1 and
 // `work` (>= ksplit * N * ldc floats, ldc == Mtot) the K chunks are split over ksplit CTAs
-// and the partial products summed in a fixed order.
+// and the partial products summed in a fixed order.  wait_limit: the bound of the pipeline's
+// waits in clock cycles, 0 for the default (about 2 s); lose_copies: the test hook above.
 void translate_tc(const TranslateOp& op, const float* X, int ldx, int N, float* C, int ldc, bool accumulate,
-                  int* status, cudaStream_t st, int ksplit, float* work) {
+                  int* status, cudaStream_t st, int ksplit, float* work, long long wait_limit, bool lose_copies) {
     if (N <= 0) return;
+    const long long wlim = wait_limit > 0 ? wait_limit : kGWaitLimit;
     ksplit = std::max(1, std::min(ksplit, op.nkc));
     const bool split = ksplit > 1 && work && ldc == op.Mtot;
     const int kps = (op.nkc + (split ? ksplit : 1) - 1) / (split ? ksplit : 1);
@@ -281,12 +293,13 @@ void translate_tc(const TranslateOp& op, const float* X, int ldx, int N, float* 
     if (split) {
         const long cst = (long)N * ldc;
         k_translate_tc<<<grid, kGThreads, kGSmem, st>>>(op.dev, op.Mtot, op.nkc, op.K, X, ldx, N, work, ldc, 0, kps,
-                                                        cst, status);
+                                                        cst, status, wlim, lose_copies ? 1 : 0);
         const long tot = (long)N * ldc;
         k_translate_sum<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(N, ldc, nz, work, cst, C, accumulate ? 1 : 0);
     } else {
         k_translate_tc<<<grid, kGThreads, kGSmem, st>>>(op.dev, op.Mtot, op.nkc, op.K, X, ldx, N, C, ldc,
-                                                        accumulate ? 1 : 0, kps, 0, status);
+                                                        accumulate ? 1 : 0, kps, 0, status, wlim,
+                                                        lose_copies ? 1 : 0);
     }
 }
 

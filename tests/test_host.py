@@ -27,6 +27,22 @@ def test_library_exports_every_declared_symbol():
     for name in declared:
         assert hasattr(lib, name), name
     assert declared == set(binding.EXPORTS), declared ^ set(binding.EXPORTS)
+    assert lib.fmm_build_flags() == 0
+
+
+def test_bounds_checked_build_exports_every_declared_symbol():
+    """The -DFMM_BOUNDS_CHECK variant (loaded by the tests with FMMCPH_BOUNDS_CHECK=1) has the
+    same C ABI and says how it was built; no GPU call is made."""
+    import ctypes
+    path = binding._build.LIB_CHECKED
+    if not os.path.exists(path):
+        binding._build.build(checked=True)
+    hdr = open(os.path.join(ROOT, "include", "fmmcph.h")).read()
+    lib = ctypes.CDLL(path)
+    for name in set(re.findall(r"\b(fmm_[a-z_0-9]+)\s*\(", hdr)):
+        assert hasattr(lib, name), name
+    lib.fmm_build_flags.restype = ctypes.c_int
+    assert lib.fmm_build_flags() == 1
 
 
 def _p2m(xs, qs, c, h, p):
