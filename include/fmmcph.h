@@ -172,6 +172,10 @@ fmm_status fmm_bind_lambda(fmm_handle* h, const float* lambda);
  *               input order (may be NULL)
  * Stream-ordered; all outputs are complete when the stream reaches the end
  * of the call.  Returns FMM_ERR_STATE before fmm_set_charges.
+ * Evaluations of one handle on different streams are ordered by the handle:
+ * an evaluation on a stream other than the previous evaluation's waits for
+ * the end of that evaluation's kernels (not for later work on its stream),
+ * except inside a capture by the caller.
  * When the same five pointers come again within the handle's last two eager
  * evaluations, the evaluation is captured into a CUDA graph owned by the
  * handle (on a private stream), and later calls with those pointers replay
@@ -185,6 +189,15 @@ fmm_status fmm_bind_lambda(fmm_handle* h, const float* lambda);
  * so join the caller's capture). */
 fmm_status fmm_eval(fmm_handle* h, const float* x, double* E, float* F, float* dVdlambda,
                     float* phi, void* stream);
+
+/* Makes `stream` wait for the end of the kernels of the handle's last
+ * evaluation (fmm_eval, fmm_eval_host, fmm_eval_host_async), not for the
+ * result copies that fmm_eval_host(_async) enqueues after them: work the
+ * caller enqueues on `stream` afterwards runs after that evaluation, beside
+ * its copies.  Nothing to do when no evaluation has been enqueued, or the
+ * last one was on `stream` or inside a capture.  FMM_ERR_ARG for a null
+ * handle. */
+fmm_status fmm_stream_wait_eval(fmm_handle* h, void* stream);
 
 /* The same evaluation with HOST buffers: copies x_host to the device, runs
  * fmm_eval (on the handle's own device staging buffers, so from the second
@@ -202,8 +215,10 @@ fmm_status fmm_eval_host(fmm_handle* h, const float* x_host, double* E_host, flo
  * after it); until then the caller must keep the buffers and leave x_host unchanged.
  * Consecutive calls use two device staging sets in turn: a call's position copy runs on the
  * handle's own copy stream as soon as its set's previous use has finished, so with
- * page-locked buffers it overlaps the previous call's evaluation.  When `stream` is being
- * captured the copy runs on `stream` itself. */
+ * page-locked buffers it overlaps the previous call's evaluation.  Calls that alternate two
+ * streams also overlap a call's result copies with the next call's evaluation (the handle
+ * orders the evaluations, see fmm_eval); give each call in flight its own output buffers.
+ * When `stream` is being captured the copy runs on `stream` itself. */
 fmm_status fmm_eval_host_async(fmm_handle* h, const float* x_host, double* E_host, float* F_host,
                                float* dVdlambda_host, void* stream);
 

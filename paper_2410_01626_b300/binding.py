@@ -76,6 +76,7 @@ EXPORTS = {
     "fmm_last_error": (ctypes.c_char_p, []),
     "fmm_build_flags": (I, []),
     "fmm_inject_copy_loss": (I, [P, I]),
+    "fmm_stream_wait_eval": (I, [P, P]),
 }
 
 _lib = None
@@ -242,6 +243,11 @@ class FMM:
             return a.ctypes.data_as(ctypes.c_void_p)
         _check(self._lib.fmm_eval_host(self._h, hp(x_host), hp(E_host), hp(F_host), hp(dV_host), _stream()),
                "fmm_eval_host")
+
+    def stream_wait_eval(self):
+        """Make the current stream wait for the end of the last evaluation's kernels (not for
+        the result copies of eval_host(_async) that follow them)."""
+        _check(self._lib.fmm_stream_wait_eval(self._h, _stream()), "fmm_stream_wait_eval")
 
     def eval_host_async(self, x_host, E_host, F_host, dV_host):
         """As eval_host without waiting: the results are in the host buffers once the current

@@ -132,6 +132,9 @@ void free_all(Handle& h) {
     h.ev_valid = false;
     if (h.fork_ev) cudaEventDestroy(h.fork_ev);
     if (h.join_ev) cudaEventDestroy(h.join_ev);
+    if (h.eval_ev) cudaEventDestroy(h.eval_ev);
+    h.eval_ev = nullptr;
+    h.eval_ev_valid = false;
     for (cudaEvent_t* e : {&h.m2m_ev, &h.side_ev}) {
         if (*e) cudaEventDestroy(*e);
         *e = nullptr;
@@ -431,6 +434,7 @@ fmm_status fmm_create(const fmm_box* box, int periodic, int p, int depth, const 
             cudaEventCreateWithFlags(&h.hfree_ev[0], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.hfree_ev[1], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h.eval_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.join_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.m2m_ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&h.side_ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -585,13 +589,36 @@ fmm_status fmm_bind_lambda(fmm_handle* H, const float* lambda) {
 // evaluations (so two buffer sets used in turn both get graphs); otherwise, while profiling, or
 // while `st` is itself being captured by the caller, the kernels are launched one by one.  Both
 // paths run the same kernels.
+static fmm_status eval_launch(Handle& h, const float* x, double* E, float* F, float* dVdl, float* phi,
+                              cudaStream_t st, bool capturing);
+
+// An evaluation on a stream other than the last one's waits for the end of the last one's
+// kernels (the handle's buffers are shared), but not for what that stream does after it, e.g.
+// the copies of fmm_eval_host_async: a caller that alternates two streams overlaps one call's
+// result copies with the next call's evaluation.  Inside the caller's own capture no cross-
+// stream order is kept (the caller's graph orders its nodes).
 static fmm_status eval_dispatch(Handle& h, const float* x, double* E, float* F, float* dVdl, float* phi,
                                 cudaStream_t st) {
     cudaGetLastError();
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const bool graphs = !h.profiling && !h.g_off && h.gcap && cudaStreamIsCapturing(st, &cs) == cudaSuccess &&
-                        cs == cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     cudaGetLastError();
+    if (!capturing && h.eval_ev_valid && h.eval_last != st) {
+        fmm_status e = cuda_ok(cudaStreamWaitEvent(st, h.eval_ev, 0));
+        if (e) return e;
+    }
+    fmm_status e = eval_launch(h, x, E, F, dVdl, phi, st, capturing);
+    if (e == FMM_OK && !capturing) {
+        if ((e = cuda_ok(cudaEventRecord(h.eval_ev, st)))) return e;
+        h.eval_last = st;
+        h.eval_ev_valid = true;
+    }
+    return e;
+}
+
+static fmm_status eval_launch(Handle& h, const float* x, double* E, float* F, float* dVdl, float* phi,
+                              cudaStream_t st, bool capturing) {
+    const bool graphs = !h.profiling && !h.g_off && h.gcap && !capturing;
     if (graphs) {
         const void* key[5] = {x, E, F, dVdl, phi};
         auto same = [&](const void* const* k) {
@@ -642,6 +669,13 @@ static fmm_status eval_dispatch(Handle& h, const float* x, double* E, float* F, 
     }
     launch_eval(&h, x, E, F, dVdl, phi, st);
     return cuda_ok(cudaGetLastError());
+}
+
+fmm_status fmm_stream_wait_eval(fmm_handle* H, void* stream) {
+    if (!H) return FMM_ERR_ARG;
+    Handle& h = H->h;
+    if (!h.eval_ev_valid || h.eval_last == S(stream)) return FMM_OK;
+    return cuda_ok(cudaStreamWaitEvent(S(stream), h.eval_ev, 0));
 }
 
 fmm_status fmm_eval(fmm_handle* H, const float* x, double* E, float* F, float* dVdl, float* phi, void* stream) {

@@ -170,6 +170,11 @@ struct Handle {
     unsigned long long gen = 0, g_tick = 0;
     bool g_off = false;  // a capture failed once: evaluations stay eager launches
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // the end of the last evaluation's kernels and its stream: an evaluation on another stream
+    // waits for it (the handle's buffers are shared), not for what that stream does afterwards
+    cudaEvent_t eval_ev = nullptr;
+    cudaStream_t eval_last = nullptr;
+    bool eval_ev_valid = false;
     // host staging for fmm_eval_host(_async): two device sets used in turn, so that the copy
     // of one call's positions (on h2d) overlaps the previous call's evaluation
     float* hx_dev[2] = {nullptr, nullptr};

@@ -308,6 +308,54 @@ def test_eval_host_async_calls_in_flight_match_device():
     f.close()
 
 
+def test_evaluations_on_two_streams_in_turn_match_device():
+    """fmm_eval_host_async and fmm_eval calls alternating between two streams, several in
+    flight, with different positions each: the handle orders its evaluations across the
+    streams (each waits for the previous evaluation's kernels, not for its result copies), so
+    every call's results equal a one-at-a-time device evaluation bit for bit -- eager, captured
+    and replayed.  fmm_stream_wait_eval orders a caller's own work (here an L2-sized write
+    that the next evaluation must not overlap) after the previous evaluation."""
+    s = synth.periodic_uniform(seed=6, n=3000, L=3.0, p=8, depth=3)
+    f, d = make_solver(s, precision="fp16")
+    rng = np.random.default_rng(4)
+    xs = [np.ascontiguousarray((s["x"] + rng.uniform(-0.01, 0.01, s["x"].shape)).astype(np.float32))
+          for _ in range(6)]
+    refs = []
+    for x in xs:
+        E, F, dV, _ = f.eval(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        refs.append((E.item(), F.cpu(), dV.cpu()))
+    n, K = len(s["x"]), len(s["lam"])
+    bufs = [(torch.from_numpy(x).pin_memory(), torch.empty(1, dtype=torch.float64).pin_memory(),
+             torch.empty(n, 3).pin_memory(), torch.empty(K).pin_memory()) for x in xs]
+    dev = [(torch.from_numpy(x).cuda(), torch.empty(1, dtype=torch.float64, device="cuda"),
+            torch.empty(n, 3, device="cuda"), torch.empty(K, device="cuda")) for x in xs]
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    scratch = torch.empty(64 << 20, device="cuda")
+    torch.cuda.synchronize()
+    for rnd in range(3):  # eager, then capture of both staging sets' graphs, then replays
+        for i, (xh, Eh, Fh, dVh) in enumerate(bufs):
+            with torch.cuda.stream(streams[i & 1]):
+                f.stream_wait_eval()
+                scratch.zero_()
+                f.eval_host_async(xh, Eh, Fh, dVh)
+        torch.cuda.synchronize()
+        for (xh, Eh, Fh, dVh), (E, F, dV) in zip(bufs, refs):
+            assert Eh.item() == E
+            assert torch.equal(Fh, F) and torch.equal(dVh, dV)
+            Eh.zero_(); Fh.zero_(); dVh.zero_()
+        for i, (x, E, F, dV) in enumerate(dev):  # device buffers, the same alternation
+            with torch.cuda.stream(streams[i & 1]):
+                f.eval_into(x, E, F, dV)
+        torch.cuda.synchronize()
+        for (x, E, F, dV), (Er, Fr, dVr) in zip(dev, refs):
+            assert E.item() == Er
+            assert torch.equal(F.cpu(), Fr) and torch.equal(dV.cpu(), dVr)
+            F.zero_()
+    assert f.status_word() == 0
+    f.close()
+
+
 def test_open_domain_error_is_reported():
     s = synth.small_open()
     s["x"][5] = [4.5, 1.0, 1.0]
