@@ -134,6 +134,13 @@ def m2l_traffic(precision):
     return NCU_M2L_TRAFFIC.get(precision) if sha == NCU_M2L_TRAFFIC["sha1"] else None
 
 
+def step_stats(step_ms):
+    """Median, 10th and 90th percentile (nearest rank) of this rank's per-step device times."""
+    v = sorted(step_ms)
+    pick = lambda q: v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+    return {"median": statistics.median(v), "p10": pick(0.10), "p90": pick(0.90), "n": len(v)}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -618,7 +625,8 @@ def run_native(args):
                            "parallelism": f"replicas x{ws}"},
                 "stages_ms": stages, "stages_alone_ms": stages_alone, "roofline": roof, "roofline_p2p": roof_p2p,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "wall_s_timed": wall1 - wall0}
+                "clocks": clocks, "wall_s_timed": wall1 - wall0,
+                "step_ms_stats": step_stats(step_ms)}
         line["modes"] = modes
         print(json.dumps(line), flush=True)
     if pg:
