@@ -117,6 +117,9 @@ typedef struct fmm_handle fmm_handle;
  *   p:        maximum expansion degree, 1 <= p <= FMM_MAX_P
  *   depth:    octree depth, 8^depth leaves; 0 <= depth <= 7
  *   opt:      may be NULL (FP32, default k_e)
+ * The mixed precisions (tensor-core M2L) need p <= 10 and depth <= 5; other
+ * combinations return FMM_ERR_ARG rather than fall back to another precision
+ * (FMM_FP32 takes every p and depth).
  * Builds the translation operators on the host in FP64 (the periodic lattice
  * operator by projecting the Ewald remainder onto solid harmonics) and
  * uploads them.  Synchronous.  Returns FMM_ERR_ARG, FMM_ERR_OOM or
