@@ -111,4 +111,8 @@ def tune_depth(edge, periodic, p, precision, x, qA, qB, site, lam, origin=(0.0, 
     return cfg["depth"], {k[0]: v["ms"] for k, v in table.items() if k[1:] == (0, 0)}
 
 
-TILES = [(0, 0), (128, 0), (160, 0), (256, 0), (0, 2), (0, 4)]  # (m2l_rows, p2p_warps) tried by the batch tuner
+# (m2l_rows, p2p_warps) tried by the batch tuner.  Only one-warp near-field blocks: each replica is
+# timed alone, where 2- or 4-warp blocks can look as fast, but beside other work (the multipole
+# chain, other replicas) they take about twice as long as one-warp blocks (measured at 500k
+# atoms: 0.39-0.43 against 0.20 ms in the step), and a batch is such concurrent work.
+TILES = [(0, 0), (128, 0), (160, 0), (256, 0)]

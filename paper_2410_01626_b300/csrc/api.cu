@@ -1008,6 +1008,7 @@ fmm_status fmm_batch_eval(fmm_batch* b, const float* const* x, double* const* E,
         if (e != FMM_OK) return e;
         b->key = key;
     }
+    TraceRange trace("fmm:batch");  // the kernels of one batched evaluation, for a profiler
     const cudaError_t le = cudaGraphLaunch(b->exec, st);
     if (le != cudaSuccess) return cuda_fail("fmm_batch_eval: graph launch", le);
     return FMM_OK;
