@@ -641,8 +641,10 @@ __device__ __forceinline__ void for_cols(F&& f) {  // the coefficient slots of c
 template <int P, int M0, int M1, bool MOM>
 __device__ __forceinline__ void p2m_leaf_cols(const float4* __restrict__ pos, int st, int cnt, int par, float cx,
                                               float cy, float cz, float ih, float* acc, float* mom) {
+    float4 nxt = par < cnt ? pos[st + par] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = par; k < cnt; k += 2) {
-        const float4 p4 = pos[st + k];
+        const float4 p4 = nxt;
+        if (k + 2 < cnt) nxt = pos[st + k + 2];  // the lane's next atom, in flight during this one
         const float q = p4.w, dx = p4.x - cx, dy = p4.y - cy, dz = p4.z - cz;
         regular_harmonics_cols<P, M0, M1>(dx * ih, dy * ih, dz * ih, [&](int n, int m, float re, float im) {
             if (m == 0) {
@@ -667,7 +669,7 @@ __device__ __forceinline__ void p2m_leaf_cols(const float4* __restrict__ pos, in
     for_cols<P, M0, M1>([&](int i) { acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 1); });
 }
 template <int P>
-__global__ void __launch_bounds__(128) k_p2m(int nleaf, float h, const uint32_t* __restrict__ start,
+__global__ void __launch_bounds__(128, P <= 10 ? 5 : 3) k_p2m(int nleaf, float h, const uint32_t* __restrict__ start,
                                              const uint32_t* __restrict__ count, const float4* __restrict__ pos,
                                              float* __restrict__ M, int ncp, float* __restrict__ leafmom, int n) {
     using Cfg = P2mCfg<P>;
