@@ -5,7 +5,7 @@
 //   binning   k_bin_count -> k_bin_scan -> k_bin_place -> k_bin_order_gather (counting sort by leaf)
 //             (Morton keys of the leaf cells, stable on (key, index); the gather also forms
 //             q_i = qA_i + lambda_s (qB_i - qA_i), Sec. 2.1 Eq. 1 with charge-only forms)
-//   P2M       k_p2m<P>        32 leaves per block, two column sets x two atom parities per leaf, sums in registers
+//   P2M       k_p2m<P>        16 leaves per block, two column sets x four atom slices per leaf, sums in registers
 //   M2M       k_translate_tc  per level, one product over the 8 contiguous children (translate_tc.cu;
 //                             FP32 SGEMM in the FP32 mode)
 //   root      k_qdt, k_root, k_lattice (periodic) FP64 root multipole, lattice operator, Q/D/T
@@ -623,7 +623,8 @@ struct P2mCfg {
     static constexpr int MS = P >= 1 ? split() : 1;
 };
 
-constexpr int kP2mLeaves = 32;
+constexpr int kP2mSlices = 4;   // lanes per leaf and column set, each taking every 4th atom
+constexpr int kP2mLeaves = 64 / kP2mSlices;  // leaves per block of 4 warps (2 column sets)
 template <int P, int M0, int M1, class F>
 __device__ __forceinline__ void for_cols(F&& f) {  // the coefficient slots of columns M0 .. M1
 #pragma unroll
@@ -642,9 +643,9 @@ template <int P, int M0, int M1, bool MOM>
 __device__ __forceinline__ void p2m_leaf_cols(const float4* __restrict__ pos, int st, int cnt, int par, float cx,
                                               float cy, float cz, float ih, float* acc, float* mom) {
     float4 nxt = par < cnt ? pos[st + par] : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = par; k < cnt; k += 2) {
+    for (int k = par; k < cnt; k += kP2mSlices) {
         const float4 p4 = nxt;
-        if (k + 2 < cnt) nxt = pos[st + k + 2];  // the lane's next atom, in flight during this one
+        if (k + kP2mSlices < cnt) nxt = pos[st + k + kP2mSlices];  // the lane's next atom, in flight during this one
         const float q = p4.w, dx = p4.x - cx, dy = p4.y - cy, dz = p4.z - cz;
         regular_harmonics_cols<P, M0, M1>(dx * ih, dy * ih, dz * ih, [&](int n, int m, float re, float im) {
             if (m == 0) {
@@ -665,8 +666,11 @@ __device__ __forceinline__ void p2m_leaf_cols(const float4* __restrict__ pos, in
         }
     }
 #pragma unroll
-    for (int i = 0; i < (MOM ? kMom : 0); ++i) mom[i] += __shfl_xor_sync(0xffffffffu, mom[i], 1);
-    for_cols<P, M0, M1>([&](int i) { acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 1); });
+    for (int d = 1; d < kP2mSlices; d <<= 1) {  // the leaf's slices, added in a fixed tree
+#pragma unroll
+        for (int i = 0; i < (MOM ? kMom : 0); ++i) mom[i] += __shfl_xor_sync(0xffffffffu, mom[i], d);
+        for_cols<P, M0, M1>([&](int i) { acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], d); });
+    }
 }
 template <int P>
 __global__ void __launch_bounds__(128, P <= 10 ? 5 : 3) k_p2m(int nleaf, float h, const uint32_t* __restrict__ start,
@@ -675,8 +679,8 @@ __global__ void __launch_bounds__(128, P <= 10 ? 5 : 3) k_p2m(int nleaf, float h
     using Cfg = P2mCfg<P>;
     constexpr int NC = Cfg::NC, MS = Cfg::MS;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int leaf = blockIdx.x * kP2mLeaves + (w & 1) * 16 + (lane >> 1);
-    const int par = lane & 1;
+    const int leaf = blockIdx.x * kP2mLeaves + (w & 1) * (32 / kP2mSlices) + lane / kP2mSlices;
+    const int par = lane % kP2mSlices;
     const bool valid = leaf < nleaf;
     const int st = valid ? (int)start[leaf] : 0;
     int cnt = valid ? (int)count[leaf] : 0;
@@ -692,8 +696,8 @@ __global__ void __launch_bounds__(128, P <= 10 ? 5 : 3) k_p2m(int nleaf, float h
 #pragma unroll
     for (int i = 0; i < kMom; ++i) mom[i] = 0.f;
     float* out = M + (long)lf * ncp;
-    auto put = [&](int i) {  // the two lanes of a leaf write alternate slots
-        if (valid && (i & 1) == par) out[i] = acc[i];
+    auto put = [&](int i) {  // the lanes of a leaf write the slots in turn
+        if (valid && i % kP2mSlices == par) out[i] = acc[i];
     };
     if (w < 2) {
         p2m_leaf_cols<P, 0, MS - 1, false>(pos, st, cnt, par, cx, cy, cz, ih, acc, mom);
@@ -702,7 +706,7 @@ __global__ void __launch_bounds__(128, P <= 10 ? 5 : 3) k_p2m(int nleaf, float h
         p2m_leaf_cols<P, MS, P, true>(pos, st, cnt, par, cx, cy, cz, ih, acc, mom);
         for_cols<P, MS, P>(put);
         if (valid) {
-            for (int v = NC + par; v < ncp; v += 2) out[v] = 0.f;
+            for (int v = NC + par; v < ncp; v += kP2mSlices) out[v] = 0.f;
             if (leafmom && par == 0)
 #pragma unroll
                 for (int k = 0; k < kMom; ++k) leafmom[(long)lf * kMomStride + k] = mom[k];
